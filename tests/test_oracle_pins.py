@@ -1,0 +1,299 @@
+"""Pins of the FP64 CPU oracle against things other than itself.
+
+Each check would fail for a plausible slip in the oracle (dropped term, wrong
+sign or index, transposed operand):
+
+* eigensolver      vs LAPACK (numpy.linalg.eigh) and HU = U eps residuals;
+* bands / phonons  vs the closed forms of a nearest-neighbour model;
+* Fourier sums     round trip through a coarse grid (exact for any data), both
+                   the direct double sum and the first (Rp) step of the
+                   two-step order, with Wigner-Seitz weights for even grids;
+* two-step order   vs the direct double sum, rotated with LAPACK eigenvectors
+                   (also a gauge-invariance check: different eigensolvers);
+* linewidth        vs the closed-form one-band model (no Fourier sum and no
+                   eigensolve on the checking side);
+* symmetries       time reversal with real inputs, acoustic sum rule,
+                   non-negativity;
+* occupations      closed forms, limits, n(-w) = -1 - n(w), unit-norm delta;
+* adjoint          central finite differences of the forward oracle.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._util import degenerate_sums, ws_vectors
+
+KB = 8.617333262e-5
+
+
+def test_eigh_matches_lapack(oracle_lib):
+    rng = np.random.default_rng(1)
+    for n in (1, 2, 3, 4, 5, 6, 8, 9, 12, 18):
+        A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        A = A + A.conj().T
+        w, V, _ = oracle_lib.eigh(A)
+        assert np.allclose(w, np.linalg.eigvalsh(A), atol=1e-12 * n)
+        assert np.abs(A @ V - V * w).max() < 1e-12 * n
+        assert np.abs(V.conj().T @ V - np.eye(n)).max() < 1e-13 * n
+        assert np.all(np.diff(w) >= 0)
+
+
+def test_eigh_degenerate_and_nonhermitian_input(oracle_lib):
+    rng = np.random.default_rng(2)
+    n = 6
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    d = np.array([-1.0, -1.0, 0.5, 0.5, 0.5, 2.0])
+    A = Q @ np.diag(d) @ Q.conj().T
+    w, V, _ = oracle_lib.eigh(A)
+    assert np.allclose(w, d, atol=1e-13)
+    assert np.abs(A @ V - V * w).max() < 1e-12
+    # Only the Hermitian part enters.
+    B = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    w2, _, _ = oracle_lib.eigh(B)
+    assert np.allclose(w2, np.linalg.eigvalsh(0.5 * (B + B.conj().T)), atol=1e-12)
+
+
+def _tb():
+    return W.tight_binding_model(eps0=0.2, t=0.5, K=0.01, g0=0.05, mass=1.3)
+
+
+def test_tight_binding_bands_and_phonons(oracle_lib):
+    m = _tb()
+    rng = np.random.default_rng(3)
+    k = rng.random((20, 3))
+    eps, _ = oracle_lib.bands(m, k)
+    ref = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * k).sum(axis=1)
+    assert np.allclose(eps[:, 0], ref, atol=1e-13)
+    w, ev = oracle_lib.phonons(m, k)
+    wref = np.sort(2 * np.sqrt(0.01 / 1.3) * np.abs(np.sin(np.pi * k)), axis=1)
+    assert np.allclose(w, wref, atol=1e-12)
+
+
+def test_tight_binding_vertex_closed_form(oracle_lib):
+    m = _tb()
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        k, q = rng.random(3), rng.random(3)
+        g = oracle_lib.g_wannier_direct(m, k, q)
+        assert np.allclose(g[:, 0, 0], 0.05 * np.sin(2 * np.pi * q), atol=1e-14)
+        gReq = oracle_lib.g_Re_q(m, q)
+        i0 = [i for i, R in enumerate(m.Re) if not R.any()][0]
+        assert np.allclose(gReq[i0, :, 0, 0], 0.05 * np.sin(2 * np.pi * q), atol=1e-14)
+        assert np.abs(np.delete(gReq, i0, axis=0)).max() == 0.0
+
+
+def _bose(w, T):
+    if T == 0 or w / (KB * T) > 700:
+        return 0.0
+    return 1.0 / (math.exp(w / (KB * T)) - 1.0)
+
+
+def _fermi(e, EF, T):
+    if T == 0:
+        return 1.0 if e < EF else (0.0 if e > EF else 0.5)
+    x = (e - EF) / (KB * T)
+    return 0.0 if x > 700 else 1.0 / (math.exp(x) + 1.0)
+
+
+def _gauss(x, s):
+    return math.exp(-(x / s) ** 2) / (s * math.sqrt(math.pi))
+
+
+def _tb_linewidth_closed_form(k, q, T, EF, sigma, eps0=0.2, t=0.5, K=0.01, g0=0.05, M=1.3, wmin=1e-5):
+    out = np.zeros(len(k))
+    for ik, kk in enumerate(k):
+        ek = eps0 - 2 * t * np.cos(2 * np.pi * kk).sum()
+        s = 0.0
+        for qq in q:
+            ekq = eps0 - 2 * t * np.cos(2 * np.pi * (kk + qq)).sum()
+            f = _fermi(ekq, EF, T)
+            for a in range(3):
+                w = 2 * math.sqrt(K / M) * abs(math.sin(math.pi * qq[a]))
+                if w < wmin:
+                    continue
+                g2 = g0**2 * math.sin(2 * math.pi * qq[a]) ** 2 / (2 * M * w)
+                n = _bose(w, T)
+                s += g2 * ((n + f) * _gauss(ek - ekq + w, sigma) + (n + 1 - f) * _gauss(ek - ekq - w, sigma))
+        out[ik] = math.pi * s / len(q)
+    return out
+
+
+@pytest.mark.parametrize("T,EF,sigma", [(300.0, 0.1, 0.05), (10.0, -0.3, 0.02), (0.0, 0.0, 0.08)])
+def test_linewidth_closed_form_one_band(oracle_lib, T, EF, sigma):
+    m = _tb()
+    k = W.uniform_grid(3) + 0.05
+    q = W.uniform_grid(6)
+    got = oracle_lib.linewidth(m, k, q, None, T, EF, sigma)[:, 0]
+    ref = _tb_linewidth_closed_form(k, q, T, EF, sigma)
+    assert np.all(ref > 0)
+    assert np.allclose(got, ref, rtol=1e-11, atol=1e-14 * ref.max())
+
+
+def _inverse_dft(vals, pts, R):
+    """X(R) = (1/Npts) sum_p e^{-2 pi i p.R} vals[p]   (vals [Npts, ...])."""
+    ph = np.exp(-2j * np.pi * (pts @ R.T))  # [Npts, nR]
+    return np.tensordot(ph, vals, axes=(0, 0)) / len(pts)
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_round_trip_through_coarse_grid(oracle_lib, N):
+    """Wannierize random coarse-grid data, interpolate back at the same points: exact."""
+    rng = np.random.default_rng(10 + N)
+    R, wR = ws_vectors(N)
+    nw, nat = 2, 1
+    kc = W.uniform_grid(N)
+    Hc = rng.standard_normal((len(kc), nw, nw)) + 1j * rng.standard_normal((len(kc), nw, nw))
+    Hc = Hc + Hc.conj().transpose(0, 2, 1)
+    HR = _inverse_dft(Hc, kc, R)
+    gc = rng.standard_normal((len(kc), len(kc), 3, nw, nw)) + 1j * rng.standard_normal((len(kc), len(kc), 3, nw, nw))
+    tmp = _inverse_dft(gc, kc, R)  # over k -> [nR, nq, ...]
+    gR = _inverse_dft(np.moveaxis(tmp, 1, 0), kc, R)  # over q -> [nRp, nRe, ...]
+    gR = np.moveaxis(gR, 0, 1).copy()  # [nRe, nRp, ...]
+    m = W.WannierModel("sc", nw, nat, np.ones(1), R, wR, HR, R, wR, np.zeros((len(R), 3, 3), complex), R, wR, gR)
+    eps, _ = oracle_lib.bands(m, kc)
+    assert np.allclose(eps, np.linalg.eigvalsh(Hc), atol=1e-12)
+    for ik, iq in [(0, 0), (1, len(kc) - 1), (len(kc) // 2, 3)]:
+        got = oracle_lib.g_wannier_direct(m, kc[ik], kc[iq])
+        assert np.allclose(got, gc[ik, iq], atol=1e-12)
+        # first step of the two-step order: g(Re,q) = inverse DFT over k of g_c(., q)
+        got_req = oracle_lib.g_Re_q(m, kc[iq]) * wR[:, None, None, None]
+        assert np.allclose(got_req, _inverse_dft(gc[:, iq], kc, R) * wR[:, None, None, None], atol=1e-12)
+
+
+def _small_model(seed, nw=3, nat=2, real=False):
+    rng = np.random.default_rng(seed)
+    return W.make_model("diamond", nw, nat, [1.0, 1.2], 20, 20, rng, real=real)
+
+
+def test_two_step_order_matches_direct_sum_and_lapack_rotation(oracle_lib):
+    m = _small_model(20)
+    rng = np.random.default_rng(21)
+    k = rng.random((3, 3))
+    q = rng.random((4, 3))
+    eps_k, eps_kq, omega, g = oracle_lib.interp(m, k, q)
+    nw, nm = m.nw, 3 * m.nat
+    for ik in range(len(k)):
+        for iq in range(len(q)):
+            gw = oracle_lib.g_wannier_direct(m, k[ik], q[iq])
+            # LAPACK eigenvectors (a different gauge from the oracle's Jacobi)
+            Hk = sum(np.exp(2j * np.pi * k[ik] @ R) * H for R, H in zip(m.Re, m.H))
+            Hkq = sum(np.exp(2j * np.pi * (k[ik] + q[iq]) @ R) * H for R, H in zip(m.Re, m.H))
+            D = sum(np.exp(2j * np.pi * q[iq] @ R) * P for R, P in zip(m.Rph, m.Phi))
+            msq = np.repeat(np.sqrt(m.mass), 3)
+            D = D / np.outer(msq, msq)
+            ek, Uk = np.linalg.eigh(Hk)
+            ekq, Ukq = np.linalg.eigh(Hkq)
+            w2, e = np.linalg.eigh(D)
+            w = np.sqrt(np.abs(w2)) * np.sign(w2)
+            assert np.allclose(ek, eps_k[ik], atol=1e-12)
+            assert np.allclose(ekq, eps_kq[ik, iq], atol=1e-12)
+            assert np.allclose(w, omega[iq], atol=1e-12)
+            keep = w >= 1e-5
+            mrep = np.repeat(m.mass, 3)
+            E = np.where(keep[None, :], e / np.sqrt(2 * np.outer(mrep, np.where(keep, w, 1.0))), 0)
+            gB = np.einsum("im,aij,jn->amn", Ukq.conj(), gw, Uk)
+            ref = np.einsum("amn,av->vmn", gB, E)
+            a = degenerate_sums(np.abs(g[ik, iq]) ** 2, ekq, ek, w, 1e-8)
+            b = degenerate_sums(np.abs(ref) ** 2, ekq, ek, w, 1e-8)
+            assert np.allclose(a, b, rtol=1e-10, atol=1e-14 * b.max())
+
+
+def test_time_reversal_with_real_inputs(oracle_lib):
+    m = _small_model(30, nw=2, nat=2, real=True)
+    rng = np.random.default_rng(31)
+    k = rng.random((4, 3))
+    q = W.uniform_grid(3)  # closed under q -> -q (mod 1)
+    e1, _ = oracle_lib.bands(m, k)
+    e2, _ = oracle_lib.bands(m, -k)
+    assert np.allclose(e1, e2, atol=1e-12)
+    w1, _ = oracle_lib.phonons(m, k)
+    w2, _ = oracle_lib.phonons(m, -k)
+    assert np.allclose(w1, w2, atol=1e-12)
+    s1 = oracle_lib.linewidth(m, k, q, None, 300.0, 0.0, 0.1)
+    s2 = oracle_lib.linewidth(m, -k, q, None, 300.0, 0.0, 0.1)
+    assert np.allclose(s1, s2, rtol=1e-10, atol=1e-14)
+    a = oracle_lib.interp(m, k[:2], q[:5])
+    b = oracle_lib.interp(m, -k[:2], -q[:5])
+    for ik in range(2):
+        for iq in range(5):
+            sa = degenerate_sums(np.abs(a[3][ik, iq]) ** 2, a[1][ik, iq], a[0][ik], a[2][iq], 1e-8)
+            sb = degenerate_sums(np.abs(b[3][ik, iq]) ** 2, b[1][ik, iq], b[0][ik], b[2][iq], 1e-8)
+            assert np.allclose(sa, sb, rtol=1e-9, atol=1e-14)
+
+
+def test_acoustic_sum_rule_and_stability(oracle_lib):
+    m = _small_model(40)
+    w, _ = oracle_lib.phonons(m, np.zeros((1, 3)))
+    assert np.abs(w[0, :3]).max() < 1e-6
+    assert w[0, 3:].min() > 1e-4
+    wq, _ = oracle_lib.phonons(m, np.random.default_rng(41).random((50, 3)))
+    assert wq.min() > 0 and wq.max() <= 0.1 + 1e-12
+
+
+def test_linewidth_non_negative_and_weighting(oracle_lib):
+    m = _small_model(50, nw=2, nat=1)
+    rng = np.random.default_rng(51)
+    k = rng.random((3, 3))
+    q = rng.random((10, 3))
+    s = oracle_lib.linewidth(m, k, q, None, 100.0, 0.0, 0.05)
+    assert np.all(s >= 0)
+    # explicit weights: the BZ sum is linear in w_q
+    wq = rng.random(10)
+    s1 = oracle_lib.linewidth(m, k, q, wq, 100.0, 0.0, 0.05)
+    parts = [oracle_lib.linewidth(m, k, q[i:i + 1], wq[i:i + 1], 100.0, 0.0, 0.05) for i in range(10)]
+    assert np.allclose(s1, sum(parts), rtol=1e-12)
+
+
+def test_occupations_and_delta(oracle_lib):
+    for w, T in [(0.01, 300.0), (0.2, 50.0), (1e-4, 10.0)]:
+        assert math.isclose(oracle_lib.bose(w, T), 1 / math.expm1(w / (KB * T)), rel_tol=1e-14)
+        assert math.isclose(oracle_lib.bose(-w, T), -1 - oracle_lib.bose(w, T), rel_tol=1e-12)
+    assert oracle_lib.bose(0.05, 0.0) == 0.0
+    assert oracle_lib.bose(5.0, 1.0) == 0.0  # overflow-safe limit
+    for e, EF, T in [(0.1, 0.0, 300.0), (-0.02, 0.01, 77.0), (0.5, 0.0, 300.0)]:
+        assert math.isclose(oracle_lib.fermi(e, EF, T), 1 / (math.exp((e - EF) / (KB * T)) + 1), rel_tol=1e-13)
+        assert math.isclose(oracle_lib.fermi(e, EF, T) + oracle_lib.fermi(2 * EF - e, EF, T), 1.0, rel_tol=1e-14)
+    assert oracle_lib.fermi(-0.1, 0.0, 0.0) == 1.0 and oracle_lib.fermi(0.1, 0.0, 0.0) == 0.0
+    assert oracle_lib.fermi(0.0, 0.0, 0.0) == 0.5
+    s = 0.02
+    x = np.linspace(-12 * s, 12 * s, 20001)
+    vals = np.array([oracle_lib.gauss(v, s) for v in x])
+    assert abs(np.trapezoid(vals, x) - 1.0) < 1e-10
+    assert math.isclose(oracle_lib.gauss(0.0, s), 1 / (s * math.sqrt(math.pi)), rel_tol=1e-15)
+    assert math.isclose(oracle_lib.gauss(s, s), math.exp(-1) / (s * math.sqrt(math.pi)), rel_tol=1e-15)
+
+
+def test_adjoint_matches_finite_differences(oracle_lib):
+    rng = np.random.default_rng(60)
+    m = W.make_model("sc", 2, 1, [1.0], None, None, rng, box=1, omega_max=0.2)
+    k = rng.random((3, 3))
+    q = rng.random((6, 3))
+    T, EF, sig = 300.0, 0.2, 0.2
+    cot = rng.random((3, 2))
+    dg, dT, dEF = oracle_lib.linewidth_grad(m, k, q, None, T, EF, sig, cot=cot)
+
+    def L(model, T=T, EF=EF):
+        return float((oracle_lib.linewidth(model, k, q, None, T, EF, sig) * cot).sum())
+
+    h = 1e-6
+    L0 = L(m)
+    assert L0 > 0
+    idxs = [tuple(int(rng.integers(s)) for s in m.g.shape) for _ in range(6)]
+    for idx in idxs:
+        for part, unit in (("re", 1.0), ("im", 1j)):
+            gp = m.g.copy()
+            gm = m.g.copy()
+            gp[idx] += h * unit
+            gm[idx] -= h * unit
+            mp = W.WannierModel(**{**m.__dict__, "g": gp})
+            mm = W.WannierModel(**{**m.__dict__, "g": gm})
+            fd = (L(mp) - L(mm)) / (2 * h)
+            an = dg[idx].real if part == "re" else dg[idx].imag
+            assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * np.abs(dg).max()), (idx, part, fd, an)
+    fdT = (L(m, T=T + 1e-3) - L(m, T=T - 1e-3)) / 2e-3
+    assert abs(fdT - dT) <= 1e-6 * abs(dT)
+    fdE = (L(m, EF=EF + 1e-6) - L(m, EF=EF - 1e-6)) / 2e-6
+    assert abs(fdE - dEF) <= 1e-6 * abs(dEF)
