@@ -1,0 +1,315 @@
+"""Benchmark: k.q pairs/s of the electron linewidth (Eq. linewidthel) on one GB300.
+
+Workload: fcc lattice, nw=4 Wannier functions, 1 atom (3 modes), 135 Re and 135
+Rp vectors (whole shells), 1000 k-points inside a 0.2 eV window of E_F, a
+uniform 40^3 q grid (64,000 q), sigma = 20 meV, T = 300 K: 6.4e7 (k,q) pairs
+per step.  A step is one epw_linewidth call: phases, phonons, k-side bands and
+vertex, the per-pair interpolation/rotation/reduction and the final sum.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp32|fp64]
+  python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample
+
+Under torchrun each rank runs its own copy of the workload at one temperature
+of the T sweep (300, 100, 50, 10 K): weak scaling, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "fcc_nw4"
+METRIC = "k·q pairs/s for ImΣ_nk on 1 GB300 (and % roofline) at stated error vs FP64 oracle"
+T_SWEEP = [300.0, 100.0, 50.0, 10.0]
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def algorithmic_flops_per_pair(m):
+    """Contractions S5+S7 per (k,q) pair (complex MAC = 8 flops).
+
+    H(k+q): 8 nRe nw^2; g(k,q) U_k: 8 nRp 3nat nw^2; U_k+q^+ rotation: 8 3nat nw^3;
+    mode projection: 8 (3nat)^2 nw^2.  Eigensolve sweeps and the delta/occupation
+    terms are not counted (iterative / transcendental, not a fixed flop count).
+    """
+    nw, nm = m.nw, 3 * m.nat
+    tensor = 8 * nw * nw * (len(m.Re) + nm * len(m.Rp))
+    simt = 8 * nm * nw**3 + 8 * nm * nm * nw * nw
+    return tensor, simt
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm_, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm_)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def cpu_baseline(wl_name, nk_s, nq_s):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+    import workloads as W
+    wl = W.make_workload(wl_name, nq_sub=nq_s)
+    k = wl.k[:nk_s]
+    t0 = time.perf_counter()
+    oracle.linewidth(wl.model, k, wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
+    dt = time.perf_counter() - t0
+    pairs = len(k) * len(wl.q)
+    return {"value": pairs / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(k)} k x {len(wl.q)} q (seeded subsample of the 40^3 grid), {pairs} pairs, {dt:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    oracle.build()
+    nq_s = 512
+    wl = W.make_workload(WORKLOAD, nq_sub=nq_s)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.linewidth(wl.model, wl.k, wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    pairs = len(wl.k) * len(wl.q)
+    ms = 1e3 * float(np.mean(times))
+    val = pairs / (ms / 1e3)
+    sample = f"{len(wl.k)} k x {nq_s} q per step (seeded subsample of the 40^3 grid), {pairs} pairs"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "fcc nw=4 nat=1, 135 Re/Rp, 1000 k (0.2 eV window) x 40^3 q, sigma=20 meV, T=300 K",
+                   "sample_per_step": sample},
+        "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16x3", "fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU form (0: skip)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1604_03525_gb300 as epw
+    import workloads as W
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = W.make_workload(WORKLOAD, T=T_SWEEP[rank % len(T_SWEEP)])
+    m = epw.Model(wl.model)
+    dev = torch.device("cuda", local)
+    k = torch.tensor(wl.k, device=dev)
+    q = torch.tensor(wl.q, device=dev)
+    wq = torch.tensor(wl.wq, device=dev)
+    out = torch.empty((len(wl.k), wl.model.nw), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    pairs = len(wl.k) * len(wl.q)
+
+    precs = {"bf16x3": epw.BF16X3, "fp32": epw.FP32, "fp64": epw.FP64}
+    if args.precision == "auto":
+        name = "bf16x3"
+        try:
+            m.linewidth(k[:8], q[:256], wq[:256], T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.BF16X3)
+        except epw.EPWError:
+            name = "fp32"
+    else:
+        name = args.precision
+    prec = precs[name]
+    kw = dict(T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=prec, out=out)
+
+    def timed_steps(nsteps, nwarm, precision):
+        kw2 = dict(kw, precision=precision)
+        for _ in range(nwarm):
+            m.linewidth(k, q, wq, **kw2)
+        stream = torch.cuda.current_stream()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        barrier()
+        m.timing(True)
+        l0 = epw.launch_count()
+        for e0, e1 in evs:
+            flush.zero_()  # evict L2 between timed steps (outside the timed events)
+            e0.record(stream)
+            m.linewidth(k, q, wq, **kw2)
+            e1.record(stream)
+        barrier()
+        launches = epw.launch_count() - l0
+        kms, kn = m.timing_read()
+        m.timing(False)
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        return step_ms, kms / max(kn, 1), kn, launches
+
+    with ClockSampler(local) as clk:
+        step_ms, kern_ms, kern_n, launches = timed_steps(args.steps, args.warmup, prec)
+    t_local = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([t_local], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    ms_per_step = t_max / args.steps
+    value = world * pairs / (ms_per_step / 1e3)
+
+    # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        kh = torch.tensor(wl.k).pin_memory()
+        qh = torch.tensor(wl.q).pin_memory()
+        wh = torch.tensor(wl.wq).pin_memory()
+        oh = torch.empty((len(wl.k), wl.model.nw), dtype=torch.float64).pin_memory()
+        m.linewidth(kh, qh, wh, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=prec, out=oh)
+        barrier()
+        t0 = time.perf_counter()
+        ne = max(1, min(args.steps, 5))
+        for _ in range(ne):
+            m.linewidth(kh, qh, wh, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=prec, out=oh)
+        barrier()
+        dt = (time.perf_counter() - t0) / ne
+        e2e = {"value": world * pairs / dt, "unit": "pairs/s",
+               "h2d_bytes_per_step": int(kh.nbytes + qh.nbytes + wh.nbytes), "d2h_bytes_per_step": int(oh.nbytes)}
+
+    fp64 = None
+    if args.fp64_steps > 0 and prec != epw.FP64:
+        s64, k64, _, _ = timed_steps(args.fp64_steps, 1, epw.FP64)
+        fp64 = {"value": pairs / (np.mean(s64) / 1e3), "unit": "pairs/s", "ms_per_step": float(np.mean(s64)),
+                "kernel_ms": k64}
+
+    peaks, peak_src = measured_peaks()
+    tflops, sflops = algorithmic_flops_per_pair(wl.model)
+    if prec == epw.BF16X3:
+        achieved = tflops * pairs / (kern_ms / 1e3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "work": f"{tflops} algorithmic contraction flops/pair x {pairs} pairs"}
+    else:
+        # plain CUDA-core arithmetic: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz, FP64 1.25 TFLOP/s nominal
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12 if prec == epw.FP32 else 1.25
+        achieved = (tflops + sflops) * pairs / (kern_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "derived from unit counts and max clock" if prec == epw.FP32
+                else "nominal FP64 rate", "work": f"{tflops + sflops} algorithmic flops/pair x {pairs} pairs"}
+    roof["kernel_ms"] = kern_ms
+    roof["kernel_launches"] = kern_n
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(WORKLOAD, 1000, 2560)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"bf16x3": "bf16x3+f32+f64", "fp32": "f32+f64", "fp64": "f64"}[name],
+            "data": "synthetic",
+            "config": {"workload": "fcc nw=4 nat=1, 135 Re/Rp, 1000 k (0.2 eV window) x 40^3 q, sigma=20 meV, "
+                                   f"T={T_SWEEP[0]:.0f} K (rank r: T_sweep[r])", "pairs_per_step_per_gpu": pairs,
+                       "precision": name, "l2": "flushed between timed steps (256 MB write)"},
+            "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof,
+            "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu_form": fp64,
+        }
+        print(json.dumps(line))
+    m.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

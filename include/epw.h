@@ -1,0 +1,195 @@
+/*
+ * epw.h -- C ABI of the GB300 (sm_103a) electron-linewidth library.
+ *
+ * The library evaluates the hot path of EPW's method (Ponce, Margine, Verdi,
+ * Giustino, Comput. Phys. Commun. 209, 116 (2016)):
+ *
+ *   Wannier interpolation of the electronic Hamiltonian H(Re), the force
+ *   constants Phi(R) and the electron-phonon vertex g(Re,Rp) onto lists of
+ *   k and q points (the "standard Wannier electron-phonon interpolation",
+ *   step (iii) of Sec. "Electron-phonon coupling in polar materials"), the
+ *   rotation of g into the Bloch / phonon-mode basis with the U matrices of
+ *   the interpolated Hamiltonian (overlap equation of the same section), and
+ *   the electron linewidth of Eq. (linewidthel):
+ *
+ *     Im Sigma_nk = pi sum_{m,nu} sum_q w_q |g_mn,nu(k,q)|^2
+ *        { [n_qnu + f_mk+q] delta(e_nk - e_mk+q + w_qnu)
+ *        + [n_qnu + 1 - f_mk+q] delta(e_nk - e_mk+q - w_qnu) }
+ *
+ *   evaluated on shell (w = e_nk - e_F, Sec. "Examples": Sigma''(e_nk)), with
+ *   Bose-Einstein n and Fermi-Dirac f (definitions after Eq. phselfenergy) and
+ *   a Gaussian delta(x) = exp(-(x/sigma)^2) / (sigma sqrt(pi)).  1/tau = 2 Im
+ *   Sigma (Eq. scatteringRate) is left to the caller.
+ *
+ * Conventions
+ *   - k, q and R are in crystal coordinates; R are integer triples.  Phases
+ *     are e^{+2 pi i x.R}; the argument x.R is reduced modulo 1 in FP64.
+ *       H(k)     = sum_Re wRe e^{2pi i k.Re} H(Re)
+ *       D(q)     = sum_R  wR  e^{2pi i q.R} Phi(R) / sqrt(M_kappa M_kappa')
+ *       g(k,q)   = sum_Re sum_Rp wRe wRp e^{2pi i (k.Re + q.Rp)} g(Re,Rp)
+ *       g_mn,nu  = sum_{kappa alpha} [U_k+q^+ g_{kappa alpha}(k,q) U_k]_mn
+ *                    e_{kappa alpha,nu}(q) / sqrt(2 M_kappa w_qnu)
+ *     with H(k) U_k = U_k diag(e_k) (eigenvalues ascending) and
+ *     D(q) e_nu = w_nu^2 e_nu, w_nu = sign(w^2) sqrt|w^2|.  Modes with
+ *     w_qnu < omega_min are left out of every sum.
+ *   - Energies in eV, temperatures in K, k_B = 8.617333262e-5 eV/K.
+ *   - Complex arrays are interleaved (re, im) doubles, row-major, C order.
+ *
+ * Pointers
+ *   - epw_wannier_desc arrays are HOST pointers; the model copies them.
+ *   - k, q, wq and every output may be host or device pointers; the library
+ *     tells them apart with cudaPointerGetAttributes.  With device pointers a
+ *     call is asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream); with any host pointer the call stages through device memory and
+ *     returns after the results are copied back.
+ *   - Outputs are caller-owned.  The model owns its device buffers and a
+ *     workspace that grows on demand (epw_reserve pre-sizes it).
+ *
+ * Errors
+ *   Every entry point returns an epw_status; on failure outputs are undefined,
+ *   nothing is freed and epw_last_error() returns a message (per thread).
+ *   Device-side failures (an eigensolver that did not converge within its sweep
+ *   cap) raise a flag that epw_sync() reports; calls with host outputs check it
+ *   before returning.  No exception crosses the ABI.
+ */
+#ifndef EPW_H
+#define EPW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EPW_ABI_VERSION 1
+#define EPW_MAX_NW 18    /* largest number of Wannier functions */
+#define EPW_MAX_MODES 18 /* largest 3*nat */
+
+typedef enum {
+  EPW_OK = 0,
+  EPW_ERR_INVALID_ARG = 1,
+  EPW_ERR_CUDA = 2,
+  EPW_ERR_OOM = 3,
+  EPW_ERR_NOT_CONVERGED = 4,
+  EPW_ERR_TIMEOUT = 5,
+  EPW_ERR_UNSUPPORTED = 6
+} epw_status;
+
+/* Arithmetic of the interpolation contractions and the per-pair eigensolves.
+ *   EPW_FP64   : everything in FP64 (CUDA cores).
+ *   EPW_FP32   : contractions, eigensolves and rotations in FP32 (CUDA cores);
+ *                phases, phonons, k-side eigensolves and the reduction in FP64.
+ *   EPW_BF16X3 : contractions on the tensor cores (tcgen05) with operands split
+ *                into two bfloat16 terms (x = hi + lo; hi*hi + hi*lo + lo*hi,
+ *                FP32 accumulation); per-pair eigensolves and rotations in
+ *                FP32; phases, phonons, k-side work and the reduction in FP64. */
+typedef enum { EPW_FP64 = 0, EPW_FP32 = 1, EPW_BF16X3 = 2 } epw_precision;
+
+typedef struct epw_model epw_model; /* opaque */
+
+/* Real-space inputs (HOST pointers).  Weights may be NULL (all ones).
+ *   mass [nat]
+ *   Re  [nRe][3]  int32,  wRe  [nRe],  H   [nRe][nw][nw] complex
+ *   Rph [nRph][3] int32,  wRph [nRph], Phi [nRph][3nat][3nat] complex,
+ *        row/column index kappa*3 + alpha
+ *   Rp  [nRp][3]  int32,  wRp  [nRp],  g   [nRe][nRp][3nat][nw][nw] complex
+ *        (g_{kappa alpha}(Re,Rp)_{mn}); complex128 unless g_is_c64 != 0, in
+ *        which case g holds interleaved float pairs. */
+typedef struct {
+  int nw, nat;
+  const double *mass;
+  int nRe;
+  const int32_t *Re;
+  const double *wRe;
+  const double *H;
+  int nRph;
+  const int32_t *Rph;
+  const double *wRph;
+  const double *Phi;
+  int nRp;
+  const int32_t *Rp;
+  const double *wRp;
+  const void *g;
+  int g_is_c64;
+} epw_wannier_desc;
+
+typedef struct {
+  double T_K;          /* temperature (K), >= 0 */
+  double EF_eV;        /* Fermi level (eV) */
+  double sigma_eV;     /* Gaussian width (eV), > 0 */
+  double omega_min_eV; /* modes below this frequency are left out (eV), >= 0 */
+  int precision;       /* epw_precision */
+  int reserved;        /* must be 0 */
+} epw_params;
+
+/* Copy a Wannier model onto the current CUDA device.  Returns EPW_ERR_INVALID_ARG
+ * for sizes outside 1 <= nw <= EPW_MAX_NW, 1 <= 3*nat <= EPW_MAX_MODES, empty R
+ * sets, or a non-positive mass; EPW_ERR_OOM when device memory runs out. */
+epw_status epw_load_wannier(const epw_wannier_desc *desc, epw_model **out);
+
+/* Release a model and its device memory (NULL is a no-op).  Not stream-ordered:
+ * the caller makes sure no work that uses the model is still running. */
+void epw_free_model(epw_model *model);
+
+/* Pre-size the workspace for calls with up to nk k-points and nq q-points at
+ * the given precision (so that later calls do not allocate, e.g. inside a CUDA
+ * graph capture). */
+epw_status epw_reserve(epw_model *model, int nk, int nq, int precision);
+
+/* Interpolated quantities on the product k x q (the unreduced path):
+ *   eps_k  [nk][nw]          band energies at k (FP64)
+ *   eps_kq [nk][nq][nw]      band energies at k+q
+ *   omega  [nq][3nat]        phonon frequencies
+ *   g      [nk][nq][3nat][nw][nw] complex  g_mn,nu(k,q) (index order nu, m, n);
+ *                            zero for modes below omega_min.
+ * Any output may be NULL (not written).  Per-element g depends on the
+ * eigenvector gauge inside degenerate subspaces; sums over degenerate blocks
+ * do not.  nk, nq >= 0 (zero is a no-op). */
+epw_status epw_interp_g(const epw_model *model, int nk, const double *k, int nq, const double *q,
+                        int precision, double omega_min_eV, double *eps_k, double *eps_kq,
+                        double *omega, double *g, void *stream);
+
+/* Electron linewidth Im Sigma_nk [nk][nw] (eV) on the k list, summed over the
+ * q list with weights wq (NULL: 1/nq each).  Sums of the positive terms are
+ * deterministic (fixed order, compensated in FP64). */
+epw_status epw_linewidth(const epw_model *model, int nk, const double *k, int nq, const double *q,
+                         const double *wq, const epw_params *params, double *imsigma, void *stream);
+
+/* Adjoint of L = sum_{k,n} grad_imsigma[k][n] * Im Sigma_nk:
+ *   dg  [nRe][nRp][3nat][nw][nw] complex: dL/dRe g + i dL/dIm g  (may be NULL)
+ *   dT, dEF: dL/dT and dL/dE_F (host or device double, may be NULL).
+ * g(k,q) is recomputed, not stored.  Requires T_K > 0. */
+epw_status epw_linewidth_backward(const epw_model *model, int nk, const double *k, int nq,
+                                  const double *q, const double *wq, const epw_params *params,
+                                  const double *grad_imsigma, double *dg, double *dT, double *dEF,
+                                  void *stream);
+
+/* Wait for the model's work on `stream` and report device-side failures
+ * (EPW_ERR_NOT_CONVERGED) raised since the previous epw_sync; clears them. */
+epw_status epw_sync(const epw_model *model, void *stream);
+
+/* Model sizes: nw, nat, nRe, nRp, nRph (any pointer may be NULL). */
+epw_status epw_model_info(const epw_model *model, int *nw, int *nat, int *nRe, int *nRp, int *nRph);
+
+/* Number of kernel launches the library has issued in this process. */
+uint64_t epw_launch_count(void);
+
+/* Measurement hook.  While enabled, each launch of the dominant (per-pair)
+ * kernel is bracketed by CUDA events recorded on its launch stream (at most
+ * 4096 launches are kept).  epw_timing_read synchronizes those events and
+ * returns the summed device time (ms) and the number of launches, then
+ * clears them. */
+epw_status epw_timing_enable(epw_model *model, int enable);
+epw_status epw_timing_read(epw_model *model, double *total_ms, int *launches);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *epw_last_error(void);
+
+/* EPW_ABI_VERSION of the loaded library. */
+int epw_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPW_H */

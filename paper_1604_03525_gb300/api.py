@@ -1,0 +1,193 @@
+"""Python face of the linewidth library: same operations as the C ABI.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA).  With CUDA
+tensors the call runs asynchronously on the current torch stream and returns
+CUDA tensors; with host arrays it stages through device memory and returns
+numpy arrays.  Every step of the path runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+FP64, FP32, BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
+
+
+class EPWError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int):
+    if status != _lib.EPW_OK:
+        msg = _lib.load().epw_last_error().decode(errors="replace")
+        raise EPWError(status, msg)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class _Arg:
+    """Pointer to a contiguous array (kept alive while the call runs)."""
+
+    def __init__(self, x, dtype):
+        self.keep = None
+        self.device = False
+        if x is None:
+            self.ptr = None
+            return
+        if _is_torch(x):
+            import torch
+            tdt = {np.float64: torch.float64, np.int32: torch.int32, np.complex128: torch.complex128}[dtype]
+            t = x.detach()
+            if t.dtype != tdt:
+                t = t.to(tdt)
+            t = t.contiguous()
+            self.keep = t
+            self.device = t.is_cuda
+            self.ptr = t.data_ptr()
+        else:
+            a = np.ascontiguousarray(x, dtype=dtype)
+            self.keep = a
+            self.ptr = a.ctypes.data
+
+
+def _stream_of(*args):
+    if any(a.device for a in args):
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+class Model:
+    """A Wannier model resident on the current CUDA device (epw_load_wannier).
+
+    ``wm`` is any object with the attributes nw, nat, mass, Re, wRe, H, Rph,
+    wRph, Phi, Rp, wRp, g (see the layouts in include/epw.h).
+    """
+
+    def __init__(self, wm, g_is_c64: bool = False):
+        lib = _lib.load()
+        self.nw, self.nat = int(wm.nw), int(wm.nat)
+        self.nm = 3 * self.nat
+        c = np.ascontiguousarray
+        gdt = np.complex64 if g_is_c64 else np.complex128
+        self._keep = [
+            c(wm.mass, np.float64), c(wm.Re, np.int32), c(wm.wRe, np.float64), c(wm.H, np.complex128),
+            c(wm.Rph, np.int32), c(wm.wRph, np.float64), c(wm.Phi, np.complex128),
+            c(wm.Rp, np.int32), c(wm.wRp, np.float64), c(wm.g, gdt),
+        ]
+        k = self._keep
+        self.nRe, self.nRph, self.nRp = len(k[1]), len(k[4]), len(k[7])
+        self.g_shape = (self.nRe, self.nRp, self.nm, self.nw, self.nw)
+        d = _lib.WannierDesc(self.nw, self.nat, k[0].ctypes.data,
+                             self.nRe, k[1].ctypes.data, k[2].ctypes.data, k[3].ctypes.data,
+                             self.nRph, k[4].ctypes.data, k[5].ctypes.data, k[6].ctypes.data,
+                             self.nRp, k[7].ctypes.data, k[8].ctypes.data, k[9].ctypes.data, int(g_is_c64))
+        h = ctypes.c_void_p()
+        _check(lib.epw_load_wannier(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().epw_free_model(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reserve(self, nk: int, nq: int, precision: int = FP64):
+        _check(_lib.load().epw_reserve(self._h, int(nk), int(nq), int(precision)))
+
+    def sync(self, stream=None):
+        _check(_lib.load().epw_sync(self._h, ctypes.c_void_p(stream or 0)))
+
+    def timing(self, enable: bool):
+        """Bracket each dominant-kernel launch with CUDA events (measurement hook)."""
+        _check(_lib.load().epw_timing_enable(self._h, int(enable)))
+
+    def timing_read(self):
+        """(summed device ms, launches) of the dominant kernel since the last read."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int(0)
+        _check(_lib.load().epw_timing_read(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    # ------------------------------------------------------------- linewidth
+    def linewidth(self, k, q, wq=None, *, T: float, EF: float, sigma: float, omega_min: float = 1e-5,
+                  precision: int = FP64, out=None):
+        """Im Sigma_nk [nk, nw] (eV), Eq. (linewidthel) on shell."""
+        lib = _lib.load()
+        ka, qa, wa = _Arg(k, np.float64), _Arg(q, np.float64), _Arg(wq, np.float64)
+        nk = int(np.prod(ka.keep.shape)) // 3
+        nq = int(np.prod(qa.keep.shape)) // 3
+        if out is None:
+            if ka.device:
+                import torch
+                out = torch.empty((nk, self.nw), dtype=torch.float64, device=ka.keep.device)
+            else:
+                out = np.zeros((nk, self.nw))
+        oa = _Arg(out, np.float64)
+        if oa.keep is not out and not _is_torch(out):
+            raise ValueError("out must be a contiguous float64 array")
+        pr = _lib.Params(float(T), float(EF), float(sigma), float(omega_min), int(precision), 0)
+        _check(lib.epw_linewidth(self._h, nk, ka.ptr, nq, qa.ptr, wa.ptr, ctypes.byref(pr), oa.ptr,
+                                 _stream_of(ka, qa, wa, oa)))
+        return out
+
+    # ---------------------------------------------------------------- interp
+    def interp(self, k, q, precision: int = FP64, omega_min: float = 1e-5, want_g: bool = True):
+        """(eps_k [nk,nw], eps_kq [nk,nq,nw], omega [nq,3nat], g [nk,nq,3nat,nw,nw]) as numpy arrays."""
+        lib = _lib.load()
+        ka, qa = _Arg(k, np.float64), _Arg(q, np.float64)
+        nk = int(np.prod(ka.keep.shape)) // 3
+        nq = int(np.prod(qa.keep.shape)) // 3
+        eps_k = np.zeros((nk, self.nw))
+        eps_kq = np.zeros((nk, nq, self.nw))
+        omega = np.zeros((nq, self.nm))
+        g = np.zeros((nk, nq, self.nm, self.nw, self.nw), dtype=np.complex128) if want_g else None
+        _check(lib.epw_interp_g(self._h, nk, ka.ptr, nq, qa.ptr, int(precision), float(omega_min),
+                                eps_k.ctypes.data, eps_kq.ctypes.data, omega.ctypes.data,
+                                None if g is None else g.ctypes.data, _stream_of(ka, qa)))
+        return eps_k, eps_kq, omega, g
+
+    # -------------------------------------------------------------- backward
+    def linewidth_backward(self, k, q, grad, wq=None, *, T: float, EF: float, sigma: float,
+                           omega_min: float = 1e-5, precision: int = FP64, want_dg: bool = True):
+        """Adjoint of sum(grad * Im Sigma): (dg like g, dL/dT, dL/dE_F)."""
+        lib = _lib.load()
+        ka, qa, wa, ca = _Arg(k, np.float64), _Arg(q, np.float64), _Arg(wq, np.float64), _Arg(grad, np.float64)
+        nk = int(np.prod(ka.keep.shape)) // 3
+        nq = int(np.prod(qa.keep.shape)) // 3
+        dT = ctypes.c_double(0.0)
+        dE = ctypes.c_double(0.0)
+        if ka.device:
+            import torch
+            dg = torch.zeros(self.g_shape, dtype=torch.complex128, device=ka.keep.device) if want_dg else None
+            dptr = dg.data_ptr() if want_dg else None
+        else:
+            dg = np.zeros(self.g_shape, dtype=np.complex128) if want_dg else None
+            dptr = dg.ctypes.data if want_dg else None
+        pr = _lib.Params(float(T), float(EF), float(sigma), float(omega_min), int(precision), 0)
+        st = _stream_of(ka, qa, wa, ca)
+        _check(lib.epw_linewidth_backward(self._h, nk, ka.ptr, nq, qa.ptr, wa.ptr, ctypes.byref(pr), ca.ptr,
+                                          dptr, ctypes.byref(dT), ctypes.byref(dE), st))
+        return dg, dT.value, dE.value
+
+
+def launch_count() -> int:
+    return int(_lib.load().epw_launch_count())

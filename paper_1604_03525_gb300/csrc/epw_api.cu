@@ -1,0 +1,705 @@
+// C ABI of the linewidth library: model ownership, workspace, argument
+// checking and orchestration of the kernels (declared in include/epw.h).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "epw_internal.cuh"
+#include "epw_tc.cuh"
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+static std::atomic<uint64_t> g_launches{0};
+
+void epw_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static epw_status fail(epw_status s, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CK(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? EPW_ERR_OOM : EPW_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                                      \
+    }                                                                                               \
+  } while (0)
+
+#define CKS(expr)                      \
+  do {                                 \
+    epw_status s_ = (expr);            \
+    if (s_ != EPW_OK) return s_;       \
+  } while (0)
+
+static bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------------ model
+static bool same_set(int n1, const int32_t *a, int n2, const int32_t *b) {
+  return n1 == n2 && std::memcmp(a, b, sizeof(int32_t) * 3 * (size_t)n1) == 0;
+}
+
+template <typename T>
+static epw_status upload(T **dst, const T *src, size_t n) {
+  *dst = nullptr;
+  if (n == 0) return EPW_OK;
+  CK(cudaMalloc((void **)dst, n * sizeof(T)));
+  CK(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return EPW_OK;
+}
+
+static void free_model_arrays(epw_model *m) {
+  void *ptrs[] = {m->Re, m->Rp, m->Rph, m->wRe, m->wRp, m->Hw, m->Phiw, m->gw, m->mass, m->dstatus, m->ws};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (m->ev) {
+    for (int i = 0; i < 2 * EPW_MAX_TIMED; i++)
+      if (m->ev[i]) cudaEventDestroy(m->ev[i]);
+    free(m->ev);
+    m->ev = nullptr;
+  }
+  tc_free(m);
+}
+
+extern "C" epw_status epw_load_wannier(const epw_wannier_desc *d, epw_model **out) {
+  g_err[0] = 0;
+  if (!d || !out) return fail(EPW_ERR_INVALID_ARG, "null descriptor or output");
+  *out = nullptr;
+  const int nw = d->nw, nat = d->nat, nm = 3 * nat;
+  if (nw < 1 || nw > EPW_MAX_NW) return fail(EPW_ERR_INVALID_ARG, "nw=%d outside [1,%d]", nw, EPW_MAX_NW);
+  if (nat < 1 || nm > EPW_MAX_MODES) return fail(EPW_ERR_INVALID_ARG, "3*nat=%d outside [3,%d]", nm, EPW_MAX_MODES);
+  if (d->nRe < 1 || d->nRp < 1 || d->nRph < 1) return fail(EPW_ERR_INVALID_ARG, "empty R set");
+  if (!d->mass || !d->Re || !d->H || !d->Rph || !d->Phi || !d->Rp || !d->g)
+    return fail(EPW_ERR_INVALID_ARG, "null array in descriptor");
+  for (int a = 0; a < nat; a++)
+    if (!(d->mass[a] > 0.0)) return fail(EPW_ERR_INVALID_ARG, "mass[%d] must be > 0", a);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+
+  const size_t nw2 = (size_t)nw * nw, nm2 = (size_t)nm * nm;
+  std::vector<cx<double>> Hw((size_t)d->nRe * nw2), Phiw((size_t)d->nRph * nm2);
+  for (int r = 0; r < d->nRe; r++) {
+    double w = d->wRe ? d->wRe[r] : 1.0;
+    for (size_t e = 0; e < nw2; e++)
+      Hw[r * nw2 + e] = mkc(w * d->H[2 * (r * nw2 + e)], w * d->H[2 * (r * nw2 + e) + 1]);
+  }
+  for (int r = 0; r < d->nRph; r++) {
+    double w = d->wRph ? d->wRph[r] : 1.0;
+    for (int a = 0; a < nm; a++)
+      for (int b = 0; b < nm; b++) {
+        size_t e = r * nm2 + a * nm + b;
+        double s = w / std::sqrt(d->mass[a / 3] * d->mass[b / 3]);
+        Phiw[e] = mkc(s * d->Phi[2 * e], s * d->Phi[2 * e + 1]);
+      }
+  }
+  const size_t per = nm * nw2;
+  std::vector<cx<double>> gw((size_t)d->nRe * d->nRp * per);
+  std::vector<double> wRe(d->nRe, 1.0), wRp(d->nRp, 1.0);
+  if (d->wRe) std::memcpy(wRe.data(), d->wRe, sizeof(double) * d->nRe);
+  if (d->wRp) std::memcpy(wRp.data(), d->wRp, sizeof(double) * d->nRp);
+  for (int a = 0; a < d->nRe; a++)
+    for (int b = 0; b < d->nRp; b++) {
+      double s = wRe[a] * wRp[b];
+      size_t o = ((size_t)a * d->nRp + b) * per;
+      for (size_t e = 0; e < per; e++) {
+        double re, im;
+        if (d->g_is_c64) {
+          re = ((const float *)d->g)[2 * (o + e)];
+          im = ((const float *)d->g)[2 * (o + e) + 1];
+        } else {
+          re = ((const double *)d->g)[2 * (o + e)];
+          im = ((const double *)d->g)[2 * (o + e) + 1];
+        }
+        gw[o + e] = mkc(s * re, s * im);
+      }
+    }
+
+  epw_model *m = (epw_model *)calloc(1, sizeof(epw_model));
+  if (!m) return fail(EPW_ERR_OOM, "host allocation failed");
+  m->device = dev;
+  m->nw = nw;
+  m->nat = nat;
+  m->nm = nm;
+  m->nRe = d->nRe;
+  m->nRp = d->nRp;
+  m->nRph = d->nRph;
+  m->same_ep = same_set(d->nRe, d->Re, d->nRp, d->Rp);
+  m->same_eph = same_set(d->nRe, d->Re, d->nRph, d->Rph);
+  epw_status s = EPW_OK;
+  if ((s = upload(&m->Re, (const int *)d->Re, 3 * (size_t)d->nRe)) != EPW_OK ||
+      (s = upload(&m->Rp, (const int *)d->Rp, 3 * (size_t)d->nRp)) != EPW_OK ||
+      (s = upload(&m->Rph, (const int *)d->Rph, 3 * (size_t)d->nRph)) != EPW_OK ||
+      (s = upload(&m->wRe, wRe.data(), wRe.size())) != EPW_OK || (s = upload(&m->wRp, wRp.data(), wRp.size())) != EPW_OK ||
+      (s = upload(&m->Hw, Hw.data(), Hw.size())) != EPW_OK || (s = upload(&m->Phiw, Phiw.data(), Phiw.size())) != EPW_OK ||
+      (s = upload(&m->gw, gw.data(), gw.size())) != EPW_OK ||
+      (s = upload(&m->mass, d->mass, (size_t)nat)) != EPW_OK) {
+    free_model_arrays(m);
+    free(m);
+    return s;
+  }
+  cudaError_t e = cudaMalloc((void **)&m->dstatus, 16);
+  if (e == cudaSuccess) e = cudaMemset(m->dstatus, 0, 16);
+  if (e != cudaSuccess) {
+    free_model_arrays(m);
+    free(m);
+    return fail(EPW_ERR_CUDA, "status word: %s", cudaGetErrorString(e));
+  }
+  *out = m;
+  return EPW_OK;
+}
+
+extern "C" void epw_free_model(epw_model *m) {
+  if (!m) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  free_model_arrays(m);
+  free(m);
+  cudaSetDevice(cur);
+}
+
+extern "C" epw_status epw_model_info(const epw_model *m, int *nw, int *nat, int *nRe, int *nRp, int *nRph) {
+  if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
+  if (nw) *nw = m->nw;
+  if (nat) *nat = m->nat;
+  if (nRe) *nRe = m->nRe;
+  if (nRp) *nRp = m->nRp;
+  if (nRph) *nRph = m->nRph;
+  return EPW_OK;
+}
+
+extern "C" uint64_t epw_launch_count(void) { return g_launches.load(); }
+
+// ------------------------------------------------------ measurement hook
+void epw_timing_begin(epw_model *m, cudaStream_t st) {
+  if (!m->timing || !m->ev || m->nev >= EPW_MAX_TIMED) return;
+  cudaEventRecord(m->ev[2 * m->nev], st);
+}
+void epw_timing_end(epw_model *m, cudaStream_t st) {
+  if (!m->timing || !m->ev || m->nev >= EPW_MAX_TIMED) return;
+  cudaEventRecord(m->ev[2 * m->nev + 1], st);
+  m->nev++;
+}
+
+extern "C" epw_status epw_timing_enable(epw_model *m, int enable) {
+  if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
+  if (enable && !m->ev) {
+    m->ev = (cudaEvent_t *)calloc(2 * EPW_MAX_TIMED, sizeof(cudaEvent_t));
+    if (!m->ev) return fail(EPW_ERR_OOM, "host allocation failed");
+    for (int i = 0; i < 2 * EPW_MAX_TIMED; i++) CK(cudaEventCreate(&m->ev[i]));
+  }
+  m->timing = enable ? 1 : 0;
+  m->nev = 0;
+  return EPW_OK;
+}
+
+extern "C" epw_status epw_timing_read(epw_model *m, double *total_ms, int *launches) {
+  if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
+  double tot = 0.0;
+  for (int i = 0; i < m->nev; i++) {
+    float ms = 0.0f;
+    CK(cudaEventSynchronize(m->ev[2 * i + 1]));
+    CK(cudaEventElapsedTime(&ms, m->ev[2 * i], m->ev[2 * i + 1]));
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = m->nev;
+  m->nev = 0;
+  return EPW_OK;
+}
+extern "C" const char *epw_last_error(void) { return g_err; }
+extern "C" int epw_abi_version(void) { return EPW_ABI_VERSION; }
+
+// -------------------------------------------------------------- workspace
+static epw_status ensure_ws(epw_model *m, size_t bytes) {
+  if (bytes <= m->ws_bytes) return EPW_OK;
+  CK(cudaDeviceSynchronize());
+  if (m->ws) cudaFree(m->ws);
+  m->ws = nullptr;
+  m->ws_bytes = 0;
+  size_t b = bytes + bytes / 8 + (1 << 20);
+  CK(cudaMalloc(&m->ws, b));
+  m->ws_bytes = b;
+  return EPW_OK;
+}
+
+// Per-call device state of the preparation steps shared by every entry point.
+struct Prep {
+  double *kd, *qd, *wqd;
+  cx<double> *PkRM, *PkT;  // k phases [nk][nRe], [nRe][nk]
+  cx<double> *Hk;          // [nk][nw][nw]
+  double *epsk;            // [nk][nw]
+  cx<double> *Uk;          // [nk][nw][nw]
+  void *PqTe, *PqTp;       // [nR][nq] in working precision
+  cx<double> *PqTph;       // [nRph][nq] FP64 (phonons)
+  cx<double> *D;           // [nq][nm][nm]
+  double *w2;              // [nq][nm]
+  cx<double> *ev;          // [nq][nm][nm]
+  double *omegaT;          // [nm][nq]
+  void *ET;                // [nm*nm][nq] working precision
+  void *G1, *Bg, *BH;      // working precision
+  cx<float> *Pk32, *gw32;  // FP32 copies for the k-side contraction
+};
+
+static size_t rsize(int prec) { return prec == EPW_FP64 ? sizeof(cx<double>) : sizeof(cx<float>); }
+
+// Lay out (or, with a null base, measure) the preparation buffers.
+static void plan_prep(Arena &A, const epw_model *m, int nk, int nq, int prec, bool stage_k, bool stage_q,
+                      bool stage_wq, bool need_B, Prep &p) {
+  const size_t sR = rsize(prec);
+  const size_t nw2 = (size_t)m->nw * m->nw, nm2 = (size_t)m->nm * m->nm;
+  p.kd = stage_k ? A.take<double>(3 * (size_t)nk) : nullptr;
+  p.qd = stage_q ? A.take<double>(3 * (size_t)nq) : nullptr;
+  p.wqd = stage_wq ? A.take<double>((size_t)nq) : nullptr;
+  p.PkRM = A.take<cx<double>>((size_t)nk * m->nRe);
+  p.PkT = A.take<cx<double>>((size_t)nk * m->nRe);
+  p.Hk = A.take<cx<double>>((size_t)nk * nw2);
+  p.epsk = A.take<double>((size_t)nk * m->nw);
+  p.Uk = A.take<cx<double>>((size_t)nk * nw2);
+  p.PqTe = A.take<char>(sR * m->nRe * (size_t)nq);
+  p.PqTp = m->same_ep ? p.PqTe : A.take<char>(sR * m->nRp * (size_t)nq);
+  p.PqTph = (m->same_eph && prec == EPW_FP64) ? (cx<double> *)p.PqTe : A.take<cx<double>>((size_t)m->nRph * nq);
+  p.D = A.take<cx<double>>((size_t)nq * nm2);
+  p.w2 = A.take<double>((size_t)nq * m->nm);
+  p.ev = A.take<cx<double>>((size_t)nq * nm2);
+  p.omegaT = A.take<double>((size_t)nq * m->nm);
+  p.ET = A.take<char>(sR * nm2 * (size_t)nq);
+  if (need_B) {
+    size_t nbg = (size_t)nk * m->nRp * m->nm * nw2;
+    p.G1 = A.take<char>(sR * nbg);
+    p.Bg = A.take<char>(sR * nbg);
+    p.BH = A.take<char>(sR * (size_t)nk * m->nRe * nw2);
+    if (prec != EPW_FP64) {
+      p.Pk32 = A.take<cx<float>>((size_t)nk * m->nRe);
+      p.gw32 = A.take<cx<float>>((size_t)m->nRe * m->nRp * m->nm * nw2);
+    } else {
+      p.Pk32 = nullptr;
+      p.gw32 = nullptr;
+    }
+  } else {
+    p.G1 = p.Bg = p.BH = nullptr;
+    p.Pk32 = p.gw32 = nullptr;
+  }
+}
+
+// Phases, k-side bands, phonons and the k-side vertex (Bg, BH).
+static epw_status run_prep(const epw_model *m, int nk, const double *k, int nq, const double *q, int prec,
+                           double omega_min, bool need_B, Prep &p, double *omega_out, cudaStream_t st) {
+  const int nw = m->nw, nm = m->nm;
+  const size_t nw2 = (size_t)nw * nw;
+  // k side (FP64): phases, H(k), eigensolve
+  launch_phases(nk, k, m->nRe, m->Re, p.PkRM, p.PkT, nullptr, st);
+  launch_fourier_d(nk, m->nRe, p.PkT, m->Hw, (int)nw2, p.Hk, st);
+  launch_eigh_d(nk, nw, p.Hk, p.epsk, p.Uk, m->dstatus, st);
+  // q side: phases in working precision (+ FP64 for phonons)
+  if (prec == EPW_FP64) {
+    launch_phases(nq, q, m->nRe, m->Re, nullptr, (cx<double> *)p.PqTe, nullptr, st);
+    if (!m->same_ep) launch_phases(nq, q, m->nRp, m->Rp, nullptr, (cx<double> *)p.PqTp, nullptr, st);
+    if (!m->same_eph) launch_phases(nq, q, m->nRph, m->Rph, nullptr, p.PqTph, nullptr, st);
+  } else {
+    launch_phases(nq, q, m->nRe, m->Re, nullptr, m->same_eph ? p.PqTph : nullptr, (cx<float> *)p.PqTe, st);
+    if (!m->same_ep) launch_phases(nq, q, m->nRp, m->Rp, nullptr, nullptr, (cx<float> *)p.PqTp, st);
+    if (!m->same_eph) launch_phases(nq, q, m->nRph, m->Rph, nullptr, p.PqTph, nullptr, st);
+  }
+  // phonons (FP64)
+  launch_fourier_d(nq, m->nRph, p.PqTph, m->Phiw, nm * nm, p.D, st);
+  launch_eigh_d(nq, nm, p.D, p.w2, p.ev, m->dstatus, st);
+  launch_phonon_post(nq, nm, p.w2, p.ev, m->mass, omega_min, p.omegaT,
+                     prec == EPW_FP64 ? (cx<double> *)p.ET : nullptr, prec == EPW_FP64 ? nullptr : (cx<float> *)p.ET,
+                     omega_out, st);
+  if (need_B && nk > 0) {
+    const int ncol = m->nRp * nm * (int)nw2;
+    if (prec == EPW_FP64) {
+      launch_cgemm<double>(nk, ncol, m->nRe, p.PkRM, m->nRe, false, false, m->gw, ncol, (cx<double> *)p.G1, ncol,
+                           false, st);
+      launch_build_B<double>(m, nk, p.PkRM, (const cx<double> *)p.G1, p.Uk, (cx<double> *)p.Bg, (cx<double> *)p.BH,
+                             st);
+    } else {
+      launch_cast_c64_to_c32((size_t)nk * m->nRe, p.PkRM, p.Pk32, st);
+      launch_cast_c64_to_c32((size_t)m->nRe * ncol, m->gw, p.gw32, st);
+      launch_cgemm<float>(nk, ncol, m->nRe, p.Pk32, m->nRe, false, false, p.gw32, ncol, (cx<float> *)p.G1, ncol,
+                          false, st);
+      launch_build_B<float>(m, nk, p.PkRM, (const cx<float> *)p.G1, p.Uk, (cx<float> *)p.Bg, (cx<float> *)p.BH, st);
+    }
+  }
+  CK(cudaGetLastError());
+  return EPW_OK;
+}
+
+static epw_status check_common(const epw_model *m, int nk, const double *k, int nq, const double *q) {
+  if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
+  if (nk < 0 || nq < 0) return fail(EPW_ERR_INVALID_ARG, "negative nk or nq");
+  if ((nk > 0 && !k) || (nq > 0 && !q)) return fail(EPW_ERR_INVALID_ARG, "null k or q");
+  if ((size_t)nk * (size_t)nq > (size_t)1 << 44) return fail(EPW_ERR_INVALID_ARG, "nk*nq too large");
+  int cur = -1;
+  CK(cudaGetDevice(&cur));
+  if (cur != m->device) return fail(EPW_ERR_INVALID_ARG, "model lives on device %d, current device is %d", m->device, cur);
+  return EPW_OK;
+}
+
+static epw_status check_params(const epw_params *p) {
+  if (!p) return fail(EPW_ERR_INVALID_ARG, "null params");
+  if (!(p->T_K >= 0.0) || !std::isfinite(p->T_K)) return fail(EPW_ERR_INVALID_ARG, "T_K must be finite and >= 0");
+  if (!(p->sigma_eV > 0.0) || !std::isfinite(p->sigma_eV)) return fail(EPW_ERR_INVALID_ARG, "sigma_eV must be > 0");
+  if (!(p->omega_min_eV >= 0.0)) return fail(EPW_ERR_INVALID_ARG, "omega_min_eV must be >= 0");
+  if (!std::isfinite(p->EF_eV)) return fail(EPW_ERR_INVALID_ARG, "EF_eV must be finite");
+  if (p->precision < EPW_FP64 || p->precision > EPW_BF16X3) return fail(EPW_ERR_INVALID_ARG, "unknown precision");
+  if (p->reserved != 0) return fail(EPW_ERR_INVALID_ARG, "reserved field must be 0");
+  return EPW_OK;
+}
+
+static epw_status read_status(const epw_model *m, cudaStream_t st) {
+  unsigned h[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h, m->dstatus, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemsetAsync(m->dstatus, 0, sizeof(h), st));
+  CK(cudaStreamSynchronize(st));
+  if (h[0] & EPW_DEV_NOT_CONVERGED) return fail(EPW_ERR_NOT_CONVERGED, "an eigensolve did not converge");
+  if (h[0] & EPW_DEV_TIMEOUT) return fail(EPW_ERR_TIMEOUT, "a device wait ran out of its iteration budget");
+  if (h[0] & EPW_DEV_BAD_SHAPE) return fail(EPW_ERR_UNSUPPORTED, "kernel met an unsupported shape");
+  return EPW_OK;
+}
+
+extern "C" epw_status epw_sync(const epw_model *m, void *stream) {
+  if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
+  return read_status(m, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------- linewidth
+struct LwPlan {
+  Prep p;
+  double *partial;
+  double *out_d;
+  TcBuffers tc;
+};
+
+static epw_status plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,
+                                 bool sout, LwPlan &L) {
+  const bool tc = prec == EPW_BF16X3;
+  plan_prep(A, m, nk, nq, tc ? EPW_FP32 : prec, sk, sq, swq, true, L.p);
+  if (tc) {
+    CKS(tc_plan(A, m, nk, nq, L.tc));
+    L.partial = nullptr;
+  } else {
+    int nqb = (nq + 127) / 128;
+    L.partial = A.take<double>((size_t)nk * nqb * m->nw);
+  }
+  L.out_d = sout ? A.take<double>((size_t)nk * m->nw) : nullptr;
+  return EPW_OK;
+}
+
+extern "C" epw_status epw_reserve(epw_model *m, int nk, int nq, int precision) {
+  CKS(check_common(m, nk, (const double *)1, nq, (const double *)1));
+  if (precision < EPW_FP64 || precision > EPW_BF16X3) return fail(EPW_ERR_INVALID_ARG, "unknown precision");
+  Arena A{nullptr, 0, 0};
+  LwPlan L;
+  CKS(plan_linewidth(A, m, nk, nq, precision, true, true, true, true, L));
+  return ensure_ws(m, A.off);
+}
+
+extern "C" epw_status epw_linewidth(const epw_model *mc, int nk, const double *k, int nq, const double *q,
+                                    const double *wq, const epw_params *par, double *imsigma, void *stream) {
+  g_err[0] = 0;
+  epw_model *m = const_cast<epw_model *>(mc);
+  CKS(check_common(m, nk, k, nq, q));
+  CKS(check_params(par));
+  if (nk > 0 && !imsigma) return fail(EPW_ERR_INVALID_ARG, "null imsigma");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (nk == 0) return EPW_OK;
+  const int prec = par->precision;
+  const bool sk = !is_device_ptr(k), sq = nq > 0 && !is_device_ptr(q), swq = wq && nq > 0 && !is_device_ptr(wq);
+  const bool sout = !is_device_ptr(imsigma);
+  if (nq == 0) {
+    if (sout) {
+      std::memset(imsigma, 0, sizeof(double) * (size_t)nk * m->nw);
+      return EPW_OK;
+    }
+    CK(cudaMemsetAsync(imsigma, 0, sizeof(double) * (size_t)nk * m->nw, st));
+    return EPW_OK;
+  }
+  Arena A{nullptr, 0, 0};
+  LwPlan L;
+  CKS(plan_linewidth(A, m, nk, nq, prec, sk, sq, swq, sout, L));
+  CKS(ensure_ws(m, A.off));
+  A = Arena{(char *)m->ws, m->ws_bytes, 0};
+  CKS(plan_linewidth(A, m, nk, nq, prec, sk, sq, swq, sout, L));
+  Prep &p = L.p;
+  const double *kd = k, *qd = q, *wqd = wq;
+  if (sk) {
+    CK(cudaMemcpyAsync(p.kd, k, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
+    kd = p.kd;
+  }
+  if (sq) {
+    CK(cudaMemcpyAsync(p.qd, q, sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, st));
+    qd = p.qd;
+  }
+  if (swq) {
+    CK(cudaMemcpyAsync(p.wqd, wq, sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+    wqd = p.wqd;
+  }
+  double *out = sout ? L.out_d : imsigma;
+  if (prec == EPW_BF16X3) {
+    CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
+    epw_status s = tc_linewidth(m, nk, kd, nq, qd, wqd, par, p.PkRM, p.epsk, p.Uk, p.omegaT, (const cx<float> *)p.ET,
+                                (const cx<float> *)p.Bg, (const cx<float> *)p.BH, L.tc, out, st);
+    if (s != EPW_OK) return fail(s, "tensor-core path: %s", g_err[0] ? g_err : "unsupported shape");
+  } else {
+    CKS(run_prep(m, nk, kd, nq, qd, prec, par->omega_min_eV, true, p, nullptr, st));
+    PairArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nk = nk;
+    a.nq = nq;
+    a.nw = m->nw;
+    a.nm = m->nm;
+    a.nRe = m->nRe;
+    a.nRp = m->nRp;
+    a.k0 = 0;
+    a.PqTe = p.PqTe;
+    a.PqTp = p.PqTp;
+    a.BH = p.BH;
+    a.Bg = p.Bg;
+    a.ET = p.ET;
+    a.omegaT = p.omegaT;
+    a.eps_k = p.epsk;
+    a.wq = wqd;
+    a.T = par->T_K;
+    a.EF = par->EF_eV;
+    a.sigma = par->sigma_eV;
+    a.omega_min = par->omega_min_eV;
+    a.partial = L.partial;
+    a.dstatus = m->dstatus;
+    epw_timing_begin(m, st);
+    epw_status s = prec == EPW_FP64 ? launch_pair<double>(a, 0, st) : launch_pair<float>(a, 0, st);
+    epw_timing_end(m, st);
+    if (s != EPW_OK) return fail(s, "no per-pair kernel for nw=%d, 3nat=%d in this precision", m->nw, m->nm);
+    launch_finalize(nk, (nq + 127) / 128, m->nw, L.partial, out, st);
+  }
+  CK(cudaGetLastError());
+  if (sout) {
+    CK(cudaMemcpyAsync(imsigma, out, sizeof(double) * (size_t)nk * m->nw, cudaMemcpyDeviceToHost, st));
+  }
+  if (sk || sq || swq || sout) return read_status(m, st);
+  return EPW_OK;
+}
+
+// ---------------------------------------------------------------- interp
+extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k, int nq, const double *q,
+                                   int precision, double omega_min, double *eps_k, double *eps_kq, double *omega,
+                                   double *g, void *stream) {
+  g_err[0] = 0;
+  epw_model *m = const_cast<epw_model *>(mc);
+  CKS(check_common(m, nk, k, nq, q));
+  if (precision != EPW_FP64 && precision != EPW_FP32)
+    return fail(EPW_ERR_UNSUPPORTED, "epw_interp_g supports EPW_FP64 and EPW_FP32");
+  if (!(omega_min >= 0.0)) return fail(EPW_ERR_INVALID_ARG, "omega_min must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (nk == 0 && nq == 0) return EPW_OK;
+  const bool sk = nk > 0 && !is_device_ptr(k), sq = nq > 0 && !is_device_ptr(q);
+  const size_t nw = m->nw, nm = m->nm;
+  const bool s_ek = eps_k && !is_device_ptr(eps_k), s_ekq = eps_kq && !is_device_ptr(eps_kq);
+  const bool s_om = omega && !is_device_ptr(omega), s_g = g && !is_device_ptr(g);
+  auto plan = [&](Arena &A, Prep &p, double *&ekd, double *&ekqd, double *&omd, double *&gd) {
+    plan_prep(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, precision, sk, sq, false, true, p);
+    ekd = s_ek ? A.take<double>((size_t)nk * nw) : eps_k;
+    ekqd = s_ekq ? A.take<double>((size_t)nk * nq * nw) : eps_kq;
+    omd = s_om ? A.take<double>((size_t)nq * nm) : omega;
+    gd = s_g ? (double *)A.take<cx<double>>((size_t)nk * nq * nm * nw * nw) : g;
+  };
+  Arena A{nullptr, 0, 0};
+  Prep p;
+  double *ekd, *ekqd, *omd, *gd;
+  plan(A, p, ekd, ekqd, omd, gd);
+  CKS(ensure_ws(m, A.off));
+  A = Arena{(char *)m->ws, m->ws_bytes, 0};
+  plan(A, p, ekd, ekqd, omd, gd);
+  const double *kd = k, *qd = q;
+  if (sk) {
+    CK(cudaMemcpyAsync(p.kd, k, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
+    kd = p.kd;
+  }
+  if (sq) {
+    CK(cudaMemcpyAsync(p.qd, q, sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, st));
+    qd = p.qd;
+  }
+  CKS(run_prep(m, nk, kd, nq, qd, precision, omega_min, nk > 0, p, omd, st));
+  if (ekd && nk > 0) CK(cudaMemcpyAsync(ekd, p.epsk, sizeof(double) * nk * nw, cudaMemcpyDeviceToDevice, st));
+  if (nk > 0 && nq > 0 && (ekqd || gd)) {
+    PairArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nk = nk;
+    a.nq = nq;
+    a.nw = m->nw;
+    a.nm = m->nm;
+    a.nRe = m->nRe;
+    a.nRp = m->nRp;
+    a.PqTe = p.PqTe;
+    a.PqTp = p.PqTp;
+    a.BH = p.BH;
+    a.Bg = p.Bg;
+    a.ET = p.ET;
+    a.omegaT = p.omegaT;
+    a.eps_k = p.epsk;
+    a.omega_min = omega_min;
+    a.sigma = 1.0;
+    a.eps_kq = ekqd;
+    a.gout = (cx<double> *)gd;
+    a.dstatus = m->dstatus;
+    epw_status s = precision == EPW_FP64 ? launch_pair<double>(a, 1, st) : launch_pair<float>(a, 1, st);
+    if (s != EPW_OK) return fail(s, "no per-pair kernel for nw=%d, 3nat=%d", m->nw, m->nm);
+  }
+  CK(cudaGetLastError());
+  if (s_ek) CK(cudaMemcpyAsync(eps_k, ekd, sizeof(double) * nk * nw, cudaMemcpyDeviceToHost, st));
+  if (s_ekq) CK(cudaMemcpyAsync(eps_kq, ekqd, sizeof(double) * nk * nq * nw, cudaMemcpyDeviceToHost, st));
+  if (s_om) CK(cudaMemcpyAsync(omega, omd, sizeof(double) * nq * nm, cudaMemcpyDeviceToHost, st));
+  if (s_g) CK(cudaMemcpyAsync(g, gd, sizeof(cx<double>) * nk * nq * nm * nw * nw, cudaMemcpyDeviceToHost, st));
+  if (sk || sq || s_ek || s_ekq || s_om || s_g) return read_status(m, st);
+  return EPW_OK;
+}
+
+// -------------------------------------------------------------- backward
+extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const double *k, int nq, const double *q,
+                                             const double *wq, const epw_params *par, const double *cot, double *dg,
+                                             double *dT, double *dEF, void *stream) {
+  g_err[0] = 0;
+  epw_model *m = const_cast<epw_model *>(mc);
+  CKS(check_common(m, nk, k, nq, q));
+  CKS(check_params(par));
+  if (!(par->T_K > 0.0)) return fail(EPW_ERR_INVALID_ARG, "the adjoint needs T_K > 0");
+  if (nk > 0 && !cot) return fail(EPW_ERR_INVALID_ARG, "null grad_imsigma");
+  const int prec = par->precision == EPW_BF16X3 ? EPW_FP32 : par->precision;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nw2 = (size_t)m->nw * m->nw, per = (size_t)m->nm * nw2;
+  const size_t ng = (size_t)m->nRe * m->nRp * per;
+  const bool sk = nk > 0 && !is_device_ptr(k), sq = nq > 0 && !is_device_ptr(q);
+  const bool swq = wq && nq > 0 && !is_device_ptr(wq), scot = nk > 0 && !is_device_ptr(cot);
+  const bool sdg = dg && !is_device_ptr(dg), sdT = dT && !is_device_ptr(dT), sdE = dEF && !is_device_ptr(dEF);
+  const size_t sR = rsize(prec);
+  // k chunk so that the per-chunk adjoint buffers stay near 1 GiB
+  size_t per_k = (size_t)nq * per * sR + 2 * (size_t)m->nRp * per * sR;
+  int nkc = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(nk, 1), ((size_t)1 << 30) / std::max<size_t>(per_k, 1)));
+  const int nqb = (nq + 127) / 128;
+  struct B {
+    Prep p;
+    double *cotd, *xbar, *Bbar, *G1bar, *gwbar, *pT, *pE, *sc, *dgd;
+  } b;
+  auto plan = [&](Arena &A) {
+    plan_prep(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, prec, sk, sq, swq, true, b.p);
+    b.cotd = scot ? A.take<double>((size_t)nk * m->nw) : (double *)cot;
+    b.xbar = (double *)A.take<char>(sR * (size_t)nq * nkc * per);
+    b.Bbar = (double *)A.take<char>(sR * (size_t)m->nRp * nkc * per);
+    b.G1bar = (double *)A.take<char>(sR * (size_t)m->nRp * nkc * per);
+    b.gwbar = (double *)A.take<char>(sR * ng);
+    b.pT = A.take<double>((size_t)nkc * nqb);
+    b.pE = A.take<double>((size_t)nkc * nqb);
+    b.sc = A.take<double>(2);
+    b.dgd = sdg ? A.take<double>(2 * ng) : dg;
+  };
+  Arena A{nullptr, 0, 0};
+  plan(A);
+  CKS(ensure_ws(m, A.off));
+  A = Arena{(char *)m->ws, m->ws_bytes, 0};
+  plan(A);
+  Prep &p = b.p;
+  const double *kd = k, *qd = q, *wqd = wq;
+  if (sk) {
+    CK(cudaMemcpyAsync(p.kd, k, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
+    kd = p.kd;
+  }
+  if (sq) {
+    CK(cudaMemcpyAsync(p.qd, q, sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, st));
+    qd = p.qd;
+  }
+  if (swq) {
+    CK(cudaMemcpyAsync(p.wqd, wq, sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+    wqd = p.wqd;
+  }
+  if (scot) CK(cudaMemcpyAsync(b.cotd, cot, sizeof(double) * nk * m->nw, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(b.sc, 0, 2 * sizeof(double), st));
+  CK(cudaMemsetAsync(b.gwbar, 0, sR * ng, st));
+  if (nk > 0 && nq > 0) {
+    CKS(run_prep(m, nk, kd, nq, qd, prec, par->omega_min_eV, true, p, nullptr, st));
+    for (int k0 = 0; k0 < nk; k0 += nkc) {
+      const int kc = std::min(nkc, nk - k0);
+      PairArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.nk = nk;
+      a.nq = nq;
+      a.nw = m->nw;
+      a.nm = m->nm;
+      a.nRe = m->nRe;
+      a.nRp = m->nRp;
+      a.k0 = k0;
+      a.PqTe = p.PqTe;
+      a.PqTp = p.PqTp;
+      a.BH = p.BH;
+      a.Bg = p.Bg;
+      a.ET = p.ET;
+      a.omegaT = p.omegaT;
+      a.eps_k = p.epsk;
+      a.wq = wqd;
+      a.T = par->T_K;
+      a.EF = par->EF_eV;
+      a.sigma = par->sigma_eV;
+      a.omega_min = par->omega_min_eV;
+      a.cot = b.cotd;
+      a.xbar = b.xbar;
+      a.partialT = b.pT;
+      a.partialE = b.pE;
+      a.nkc = kc;
+      a.dstatus = m->dstatus;
+      epw_status s = prec == EPW_FP64 ? launch_pair<double>(a, 2, st) : launch_pair<float>(a, 2, st);
+      if (s != EPW_OK) return fail(s, "no per-pair kernel for nw=%d, 3nat=%d", m->nw, m->nm);
+      launch_sum_scalar(kc * nqb, b.pT, 1.0, b.sc, st);
+      launch_sum_scalar(kc * nqb, b.pE, 1.0, b.sc + 1, st);
+      const int ncol = kc * (int)per;
+      const int ncol2 = m->nRp * (int)per;
+      if (prec == EPW_FP64) {
+        launch_cgemm<double>(m->nRp, ncol, nq, (const cx<double> *)p.PqTp, nq, false, true,
+                             (const cx<double> *)b.xbar, ncol, (cx<double> *)b.Bbar, ncol, false, st);
+        launch_bg_adjoint_rotate_k0<double>(kc, k0, m->nRp, m->nm, m->nw, (const cx<double> *)b.Bbar, p.Uk,
+                                            (cx<double> *)b.G1bar, st);
+        launch_cgemm<double>(m->nRe, ncol2, kc, p.PkRM + (size_t)k0 * m->nRe, m->nRe, true, true,
+                             (const cx<double> *)b.G1bar, ncol2, (cx<double> *)b.gwbar, ncol2, true, st);
+      } else {
+        launch_cgemm<float>(m->nRp, ncol, nq, (const cx<float> *)p.PqTp, nq, false, true, (const cx<float> *)b.xbar,
+                            ncol, (cx<float> *)b.Bbar, ncol, false, st);
+        launch_bg_adjoint_rotate_k0<float>(kc, k0, m->nRp, m->nm, m->nw, (const cx<float> *)b.Bbar, p.Uk,
+                                           (cx<float> *)b.G1bar, st);
+        launch_cgemm<float>(m->nRe, ncol2, kc, p.Pk32 + (size_t)k0 * m->nRe, m->nRe, true, true,
+                            (const cx<float> *)b.G1bar, ncol2, (cx<float> *)b.gwbar, ncol2, true, st);
+      }
+    }
+  }
+  if (b.dgd) {
+    if (prec == EPW_FP64)
+      launch_dg_scale<double>(m, (const cx<double> *)b.gwbar, b.dgd, false, st);
+    else
+      launch_dg_scale<float>(m, (const cx<float> *)b.gwbar, b.dgd, false, st);
+  }
+  CK(cudaGetLastError());
+  if (sdg) CK(cudaMemcpyAsync(dg, b.dgd, sizeof(double) * 2 * ng, cudaMemcpyDeviceToHost, st));
+  if (dT) CK(cudaMemcpyAsync(dT, b.sc, sizeof(double), sdT ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  if (dEF)
+    CK(cudaMemcpyAsync(dEF, b.sc + 1, sizeof(double), sdE ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  if (sk || sq || swq || scot || sdg || sdT || sdE) return read_status(m, st);
+  return EPW_OK;
+}

@@ -1,0 +1,676 @@
+// Generic SIMT kernels of the linewidth path (FP64 and FP32 forms) and the
+// shared preparation steps (phases, k-side bands, phonons, k-side vertex).
+//
+// Method: EPW (Ponce et al. 2016), Eq. (linewidthel) for the reduction and the
+// Wannier interpolation of Sec. "Electron-phonon coupling in polar materials"
+// (step iii) with the U rotations of the overlap equation there.
+#include <cuda_runtime.h>
+
+#include "epw_internal.cuh"
+
+namespace {
+
+inline int nblocks(size_t n, int bs, int cap = 152 * 32) {
+  size_t b = (n + bs - 1) / bs;
+  if (b > (size_t)cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// -------------------------------------------------------------------- phases
+// e^{2 pi i x.R}: the argument x.R is formed and reduced to [-1/2, 1/2] in
+// FP64, then sincospi gives the value.  Index idx = r*npt + i so that the
+// transposed outputs [nR][npt] are written coalesced.
+__global__ void k_phases(int npt, const double *__restrict__ x, int nR, const int *__restrict__ R,
+                         cx<double> *rowmajor, cx<double> *T64, cx<float> *T32) {
+  size_t n = (size_t)npt * nR;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % npt);
+    int r = (int)(idx / npt);
+    double a = x[3 * i] * R[3 * r] + x[3 * i + 1] * R[3 * r + 1] + x[3 * i + 2] * R[3 * r + 2];
+    a -= rint(a);
+    double s, c;
+    sincospi(2.0 * a, &s, &c);
+    if (rowmajor) rowmajor[(size_t)i * nR + r] = mkc(c, s);
+    if (T64) T64[idx] = mkc(c, s);
+    if (T32) T32[idx] = mkc((float)c, (float)s);
+  }
+}
+
+// out[i][e] = sum_r PT[r][i] X[r][e]   (PT transposed phases [nR][npt])
+__global__ void k_fourier_d(int npt, int nR, const cx<double> *__restrict__ PT, const cx<double> *__restrict__ X,
+                            int msize, cx<double> *out) {
+  size_t n = (size_t)npt * msize;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % npt);
+    int e = (int)(idx / npt);
+    cx<double> acc = mkc(0.0, 0.0);
+    for (int r = 0; r < nR; r++) cfma(acc, PT[(size_t)r * npt + i], X[(size_t)r * msize + e]);
+    out[(size_t)i * msize + e] = acc;
+  }
+}
+
+// Batched Hermitian eigensolve, one matrix per thread (FP64, converged to
+// full precision).  w ascending; V columns are eigenvectors.
+template <int N>
+__global__ void k_eigh_d(int nmat, int n, const cx<double> *__restrict__ Ain, double *w, cx<double> *V,
+                         unsigned *dstatus) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nmat) return;
+  constexpr int UR = N <= 4 ? N : 1;
+  cx<double> A[N][N], U[N][N];
+  const cx<double> *a = Ain + (size_t)t * n * n;
+#pragma unroll UR
+  for (int i = 0; i < N; i++)
+#pragma unroll UR
+    for (int j = 0; j < N; j++) A[i][j] = (i < n && j < n) ? a[i * n + j] : mkc(0.0, 0.0);
+  bool nc = false;
+  jacobi_herm<double, N>(A, U, n, jacobi_tol<double>::tol2, jacobi_tol<double>::maxsweep, nc);
+  double ww[N];
+  sort_eig<double, N>(A, U, ww, n);
+  if (nc) atomicOr(dstatus, EPW_DEV_NOT_CONVERGED);
+#pragma unroll UR
+  for (int i = 0; i < N; i++) {
+    if (i < n) w[(size_t)t * n + i] = ww[i];
+#pragma unroll UR
+    for (int j = 0; j < N; j++)
+      if (i < n && j < n) V[(size_t)t * n * n + i * n + j] = U[i][j];
+  }
+}
+
+// omega = sign(w2) sqrt|w2|;  E[ka][nu] = e_{ka,nu} / sqrt(2 M_kappa omega_nu),
+// zero when omega_nu < omega_min.  Outputs are transposed ([..][nq]).
+__global__ void k_phonon_post(int nq, int nm, const double *__restrict__ w2, const cx<double> *__restrict__ ev,
+                              const double *__restrict__ mass, double omega_min, double *omegaT, cx<double> *ET64,
+                              cx<float> *ET32, double *omega_out) {
+  size_t n = (size_t)nq * nm;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    int q = (int)(idx % nq);
+    int nu = (int)(idx / nq);
+    double x = w2[(size_t)q * nm + nu];
+    double om = x >= 0.0 ? sqrt(x) : -sqrt(-x);
+    if (omegaT) omegaT[(size_t)nu * nq + q] = om;
+    if (omega_out) omega_out[(size_t)q * nm + nu] = om;
+    bool keep = om >= omega_min && om > 0.0;
+    for (int ka = 0; ka < nm; ka++) {
+      cx<double> e = ev[(size_t)q * nm * nm + ka * nm + nu];
+      double f = keep ? 1.0 / sqrt(2.0 * mass[ka / 3] * om) : 0.0;
+      cx<double> E = mkc(e.x * f, e.y * f);
+      size_t o = ((size_t)ka * nm + nu) * nq + q;
+      if (ET64) ET64[o] = E;
+      if (ET32) ET32[o] = mkc((float)E.x, (float)E.y);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- complex GEMM
+// C[M][N] (+)= op(A)[M][K] B[K][N];  op(A) = A or A^T (A stored [K][M]), optionally conjugated.
+template <typename R>
+__global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cx<R> *__restrict__ A, int lda, bool transA,
+                                               bool conjA, const cx<R> *__restrict__ B, int ldb, cx<R> *C, int ldc,
+                                               bool acc) {
+  __shared__ cx<R> As[16][65];
+  __shared__ cx<R> Bs[16][65];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  cx<R> c[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) c[i][j] = mkc<R>(0, 0);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int t = threadIdx.x; t < 1024; t += 256) {
+      int kk, mm;
+      if (transA) {
+        mm = t % 64;
+        kk = t / 64;
+      } else {
+        kk = t % 16;
+        mm = t / 16;
+      }
+      int gm = m0 + mm, gk = k0 + kk;
+      cx<R> v = mkc<R>(0, 0);
+      if (gm < M && gk < K) v = transA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+      if (conjA) v.y = -v.y;
+      As[kk][mm] = v;
+    }
+    for (int t = threadIdx.x; t < 1024; t += 256) {
+      int nn = t % 64, kk = t / 64;
+      int gn = n0 + nn, gk = k0 + kk;
+      Bs[kk][nn] = (gn < N && gk < K) ? B[(size_t)gk * ldb + gn] : mkc<R>(0, 0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 16; kk++) {
+      cx<R> a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) cfma(c[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < M && gn < N) {
+        cx<R> *p = C + (size_t)gm * ldc + gn;
+        *p = acc ? (*p + c[i][j]) : c[i][j];
+      }
+    }
+}
+
+// Bg[k][Rp][a][j][n] = sum_i G1[k][Rp][a][j][i] U_k[i][n];  BH[k][Re][i][j] = P_k(Re) Hw(Re)_ij
+template <typename R>
+__global__ void k_build_Bg(int nk, int nRp, int nm, int nw, const cx<R> *__restrict__ G1,
+                           const cx<double> *__restrict__ Uk, cx<R> *Bg) {
+  size_t n = (size_t)nk * nRp * nm * nw * nw;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    int nn = (int)(idx % nw);
+    size_t rest = idx / nw;  // (k, Rp, a, j)
+    int k = (int)(rest / ((size_t)nRp * nm * nw));
+    const cx<R> *g = G1 + rest * nw;
+    const cx<double> *U = Uk + (size_t)k * nw * nw;
+    cx<R> acc = mkc<R>(0, 0);
+    for (int i = 0; i < nw; i++) cfma(acc, g[i], ccast<R>(U[i * nw + nn]));
+    Bg[idx] = acc;
+  }
+}
+
+template <typename R>
+__global__ void k_build_BH(int nk, int nRe, int nw, const cx<double> *__restrict__ Pk, const cx<double> *__restrict__ Hw,
+                           cx<R> *BH) {
+  size_t nw2 = (size_t)nw * nw;
+  size_t n = (size_t)nk * nRe * nw2;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    size_t e = idx % nw2;
+    size_t kr = idx / nw2;  // k*nRe + r
+    int r = (int)(kr % nRe);
+    BH[idx] = ccast<R>(Pk[kr] * Hw[(size_t)r * nw2 + e]);
+  }
+}
+
+__global__ void k_cast_c64_c32(size_t n, const cx<double> *__restrict__ in, cx<float> *out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = mkc((float)in[i].x, (float)in[i].y);
+}
+
+// ------------------------------------------------------------ per-pair kernel
+template <typename R>
+__device__ __forceinline__ R gauss_r(R x, R inv_sigma, R norm) {
+  R y = x * inv_sigma;
+  return norm * exp(-y * y);
+}
+
+template <typename R>
+__device__ __forceinline__ R occ_bose(R w, double T);
+template <>
+__device__ __forceinline__ double occ_bose<double>(double w, double T) { return bose_d(w, T); }
+template <>
+__device__ __forceinline__ float occ_bose<float>(float w, double T) {
+  return bose_f(w, T > 0.0 ? (float)(1.0 / (EPW_KB * T)) : 0.0f);
+}
+template <typename R>
+__device__ __forceinline__ R occ_fermi(R e, double EF, double T);
+template <>
+__device__ __forceinline__ double occ_fermi<double>(double e, double EF, double T) { return fermi_d(e, EF, T); }
+template <>
+__device__ __forceinline__ float occ_fermi<float>(float e, double EF, double T) {
+  return fermi_f((float)((double)e - EF), T > 0.0 ? (float)(1.0 / (EPW_KB * T)) : 0.0f);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum v over the 128-thread block in a fixed order; result valid in thread 0.
+__device__ __forceinline__ double block_sum128(double v, double *sh /*[4]*/) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) s = ((sh[0] + sh[1]) + sh[2]) + sh[3];
+  return s;
+}
+
+// One thread per (k, q) pair; a block holds 128 consecutive q of one k.
+//   H(k+q)   = sum_Re P_q(Re) BH_k(Re)                      -> Jacobi -> e_m, U
+//   X_a      = sum_Rp P_q(Rp) Bg_k(Rp, a)   (= g_a(k,q) U_k)
+//   G_nu     = sum_a E_q[a][nu] U^dagger X_a                 (= g_mn,nu)
+// mode 0: linewidth terms of Eq. (linewidthel), reduced over the block;
+// mode 1: write e_k+q and g_mn,nu;  mode 2: adjoint (see launch_pair).
+template <typename R, int MW, int MM, int MODE>
+__global__ void __launch_bounds__(128) k_pair(PairArgs a) {
+  constexpr int UW = MW <= 4 ? MW : 1;
+  constexpr int UM = MM <= 4 ? MM : 1;
+  __shared__ double sh[4];
+  const int q = blockIdx.x * 128 + threadIdx.x;
+  const int kl = blockIdx.y;
+  const int k = a.k0 + kl;
+  const bool valid = q < a.nq;
+  const int qq = valid ? q : 0;
+  const int nw = a.nw, nm = a.nm, nw2 = nw * nw, nq = a.nq;
+  const cx<R> *PqTe = (const cx<R> *)a.PqTe;
+  const cx<R> *PqTp = (const cx<R> *)a.PqTp;
+  const cx<R> *BH = (const cx<R> *)a.BH + (size_t)k * a.nRe * nw2;
+  const cx<R> *Bg = (const cx<R> *)a.Bg + (size_t)k * a.nRp * nm * nw2;
+  const cx<R> *ET = (const cx<R> *)a.ET;
+
+  cx<R> A[MW][MW];
+#pragma unroll UW
+  for (int i = 0; i < MW; i++)
+#pragma unroll UW
+    for (int j = 0; j < MW; j++) A[i][j] = mkc<R>(0, 0);
+  for (int r = 0; r < a.nRe; r++) {
+    cx<R> p = PqTe[(size_t)r * nq + qq];
+    const cx<R> *b = BH + (size_t)r * nw2;
+#pragma unroll UW
+    for (int i = 0; i < MW; i++)
+#pragma unroll UW
+      for (int j = 0; j < MW; j++)
+        if (i < nw && j < nw) cfma(A[i][j], p, b[i * nw + j]);
+  }
+  cx<R> U[MW][MW];
+  bool nc = false;
+  jacobi_herm<R, MW>(A, U, nw, jacobi_tol<R>::tol2, jacobi_tol<R>::maxsweep, nc);
+  R ekq[MW];
+  sort_eig<R, MW>(A, U, ekq, nw);
+  if (nc && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
+
+  cx<R> G[MM][MW][MW];
+#pragma unroll UM
+  for (int v = 0; v < MM; v++)
+#pragma unroll UW
+    for (int i = 0; i < MW; i++)
+#pragma unroll UW
+      for (int j = 0; j < MW; j++) G[v][i][j] = mkc<R>(0, 0);
+  for (int al = 0; al < nm; al++) {
+    cx<R> X[MW][MW];
+#pragma unroll UW
+    for (int i = 0; i < MW; i++)
+#pragma unroll UW
+      for (int j = 0; j < MW; j++) X[i][j] = mkc<R>(0, 0);
+    for (int r = 0; r < a.nRp; r++) {
+      cx<R> p = PqTp[(size_t)r * nq + qq];
+      const cx<R> *b = Bg + ((size_t)r * nm + al) * nw2;
+#pragma unroll UW
+      for (int i = 0; i < MW; i++)
+#pragma unroll UW
+        for (int j = 0; j < MW; j++)
+          if (i < nw && j < nw) cfma(X[i][j], p, b[i * nw + j]);
+    }
+    // Y = U^dagger X, then G_nu += E[al][nu] Y
+#pragma unroll UW
+    for (int m = 0; m < MW; m++) {
+      if (m >= nw) continue;
+#pragma unroll UW
+      for (int n = 0; n < MW; n++) {
+        if (n >= nw) continue;
+        cx<R> y = mkc<R>(0, 0);
+#pragma unroll UW
+        for (int i = 0; i < MW; i++)
+          if (i < nw) cfma(y, conjc(U[i][m]), X[i][n]);
+#pragma unroll UM
+        for (int v = 0; v < MM; v++)
+          if (v < nm) cfma(G[v][m][n], ET[((size_t)al * nm + v) * nq + qq], y);
+      }
+    }
+  }
+
+  const double *ek = a.eps_k + (size_t)k * nw;
+  const R inv_sigma = (R)(1.0 / a.sigma);
+  const R gnorm = (R)(1.0 / (a.sigma * 1.7724538509055160273));
+  const double wqi = valid ? (a.wq ? a.wq[q] : 1.0 / nq) : 0.0;
+
+  if (MODE == 0) {
+    R acc[MW];
+#pragma unroll UW
+    for (int n = 0; n < MW; n++) acc[n] = R(0);
+#pragma unroll UM
+    for (int v = 0; v < MM; v++) {
+      if (v >= nm) continue;
+      R w = (R)a.omegaT[(size_t)v * nq + qq];
+      if (!(w >= (R)a.omega_min) || !(w > R(0))) continue;
+      R nb = occ_bose<R>(w, a.T);
+#pragma unroll UW
+      for (int m = 0; m < MW; m++) {
+        if (m >= nw) continue;
+        R f = occ_fermi<R>(ekq[m], a.EF, a.T);
+        R cp = nb + f, cm = nb + R(1) - f;
+#pragma unroll UW
+        for (int n = 0; n < MW; n++) {
+          if (n >= nw) continue;
+          R x = (R)ek[n] - ekq[m];
+          R g2 = cabs2(G[v][m][n]);
+          acc[n] += g2 * (cp * gauss_r<R>(x + w, inv_sigma, gnorm) + cm * gauss_r<R>(x - w, inv_sigma, gnorm));
+        }
+      }
+    }
+    const int nqb = gridDim.x;
+#pragma unroll UW
+    for (int n = 0; n < MW; n++) {
+      if (n >= nw) continue;
+      double s = block_sum128((double)acc[n] * wqi, sh);
+      if (threadIdx.x == 0) a.partial[((size_t)k * nqb + blockIdx.x) * nw + n] = s;
+    }
+  } else if (MODE == 1) {
+    if (!valid) return;
+    if (a.eps_kq) {
+#pragma unroll UW
+      for (int m = 0; m < MW; m++)
+        if (m < nw) a.eps_kq[((size_t)k * nq + q) * nw + m] = (double)ekq[m];
+    }
+    if (a.gout) {
+      cx<double> *o = a.gout + ((size_t)k * nq + q) * nm * nw2;
+#pragma unroll UM
+      for (int v = 0; v < MM; v++)
+#pragma unroll UW
+        for (int m = 0; m < MW; m++)
+#pragma unroll UW
+          for (int n = 0; n < MW; n++)
+            if (v < nm && m < nw && n < nw) o[(v * nw + m) * nw + n] = ccast<double>(G[v][m][n]);
+    }
+  } else {
+    // Adjoint of L = sum_{k,n} c_nk Im Sigma_nk.
+    //   W_nu,mn = c_nk pi w_q [(n+f) d+ + (n+1-f) d-],  Gbar_nu = 2 W G_nu
+    //   Xbar_a  = U sum_nu conj(E[a][nu]) Gbar_nu   (written for the adjoint GEMMs)
+    //   dL/dT, dL/dE_F through n(T), f(T, E_F).
+    const double *cot = a.cot + (size_t)k * nw;
+    double sT = 0.0, sE = 0.0;
+    const double kT = EPW_KB * a.T;
+#pragma unroll UM
+    for (int v = 0; v < MM; v++) {
+      if (v >= nm) continue;
+      R w = (R)a.omegaT[(size_t)v * nq + qq];
+      bool keep = (w >= (R)a.omega_min) && (w > R(0));
+      R nb = keep ? occ_bose<R>(w, a.T) : R(0);
+      double dn = keep ? (double)nb * ((double)nb + 1.0) * (double)w / (kT * a.T) : 0.0;
+#pragma unroll UW
+      for (int m = 0; m < MW; m++) {
+        if (m >= nw) continue;
+        R f = occ_fermi<R>(ekq[m], a.EF, a.T);
+        double ff = (double)f * (1.0 - (double)f);
+        double dfT = ff * ((double)ekq[m] - a.EF) / (kT * a.T);
+        double dfE = ff / kT;
+#pragma unroll UW
+        for (int n = 0; n < MW; n++) {
+          if (n >= nw) continue;
+          R x = (R)ek[n] - ekq[m];
+          R dp = gauss_r<R>(x + w, inv_sigma, gnorm), dm = gauss_r<R>(x - w, inv_sigma, gnorm);
+          double c = keep ? cot[n] * EPW_PI * wqi : 0.0;
+          R W = (R)(c * ((double)(nb + f) * dp + (double)(nb + R(1) - f) * dm));
+          double g2 = (double)cabs2(G[v][m][n]);
+          sT += c * g2 * ((dn + dfT) * dp + (dn - dfT) * dm);
+          sE += c * g2 * dfE * (dp - dm);
+          G[v][m][n] = (R(2) * W) * G[v][m][n];
+        }
+      }
+    }
+    if (valid) {
+      cx<R> *xb = (cx<R> *)a.xbar + ((size_t)q * a.nkc + kl) * nm * nw2;
+      for (int al = 0; al < nm; al++) {
+        cx<R> Yb[MW][MW];
+#pragma unroll UW
+        for (int m = 0; m < MW; m++)
+#pragma unroll UW
+          for (int n = 0; n < MW; n++) {
+            cx<R> s = mkc<R>(0, 0);
+#pragma unroll UM
+            for (int v = 0; v < MM; v++)
+              if (v < nm && m < nw && n < nw) cfma(s, conjc(ET[((size_t)al * nm + v) * nq + qq]), G[v][m][n]);
+            Yb[m][n] = s;
+          }
+#pragma unroll UW
+        for (int i = 0; i < MW; i++)
+#pragma unroll UW
+          for (int n = 0; n < MW; n++) {
+            if (i >= nw || n >= nw) continue;
+            cx<R> s = mkc<R>(0, 0);
+#pragma unroll UW
+            for (int m = 0; m < MW; m++)
+              if (m < nw) cfma(s, U[i][m], Yb[m][n]);
+            xb[(size_t)al * nw2 + i * nw + n] = s;
+          }
+      }
+    }
+    const int nqb = gridDim.x;
+    double tT = block_sum128(sT, sh);
+    if (threadIdx.x == 0) a.partialT[(size_t)kl * nqb + blockIdx.x] = tT;
+    double tE = block_sum128(sE, sh);
+    if (threadIdx.x == 0) a.partialE[(size_t)kl * nqb + blockIdx.x] = tE;
+  }
+}
+
+// out[k][n] = pi * sum_qb partial[k][qb][n], compensated (Neumaier), fixed order.
+__global__ void k_finalize(int nk, int nqb, int nw, const double *__restrict__ partial, double *out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nk * nw) return;
+  int k = t / nw, n = t % nw;
+  double s = 0.0, c = 0.0;
+  for (int b = 0; b < nqb; b++) {
+    double x = partial[((size_t)k * nqb + b) * nw + n];
+    double u = s + x;
+    c += fabs(s) >= fabs(x) ? (s - u) + x : (x - u) + s;
+    s = u;
+  }
+  out[t] = EPW_PI * (s + c);
+}
+
+// out[0] (+)= scale * sum_i partial[i], one block, fixed order, compensated.
+__global__ void k_sum_scalar(int n, const double *__restrict__ partial, double scale, double *out) {
+  __shared__ double ss[256], cc[256];
+  double s = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    double x = partial[i];
+    double u = s + x;
+    c += fabs(s) >= fabs(x) ? (s - u) + x : (x - u) + s;
+    s = u;
+  }
+  ss[threadIdx.x] = s;
+  cc[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, C = 0.0;
+    for (int i = 0; i < 256; i++) {
+      double x = ss[i];
+      double u = S + x;
+      C += fabs(S) >= fabs(x) ? (S - u) + x : (x - u) + S;
+      S = u;
+      C += cc[i];
+    }
+    out[0] += scale * (S + C);
+  }
+}
+
+// G1bar[k][Rp][a][j][i] = sum_n Bbar[Rp][k][a][j][n] conj(U_k[i][n])
+template <typename R>
+__global__ void k_bg_adjoint_rotate(int nk, int k0, int nRp, int nm, int nw, const cx<R> *__restrict__ Bbar,
+                                    const cx<double> *__restrict__ Uk, cx<R> *G1bar) {
+  size_t per = (size_t)nm * nw * nw;
+  size_t n = (size_t)nk * nRp * per;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(idx % nw);
+    size_t rest = idx / nw;  // (k, Rp, a, j)
+    int aj = (int)(rest % ((size_t)nm * nw));
+    size_t kr = rest / ((size_t)nm * nw);
+    int Rp = (int)(kr % nRp);
+    int k = (int)(kr / nRp);
+    const cx<R> *b = Bbar + ((size_t)Rp * nk + k) * per + (size_t)aj * nw;
+    const cx<double> *U = Uk + (size_t)(k0 + k) * nw * nw;
+    cx<R> acc = mkc<R>(0, 0);
+    for (int nn = 0; nn < nw; nn++) cfma(acc, b[nn], conjc(ccast<R>(U[i * nw + nn])));
+    G1bar[idx] = acc;
+  }
+}
+
+// dg[Re][Rp][...] (+)= wRe wRp gwbar
+template <typename R>
+__global__ void k_dg_scale(int nRe, int nRp, size_t per, const double *__restrict__ wRe,
+                           const double *__restrict__ wRp, const cx<R> *__restrict__ gwbar, double *dg, bool acc) {
+  size_t n = (size_t)nRe * nRp * per;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    size_t rr = idx / per;
+    int a = (int)(rr / nRp), b = (int)(rr % nRp);
+    double s = wRe[a] * wRp[b];
+    double re = s * (double)gwbar[idx].x, im = s * (double)gwbar[idx].y;
+    if (acc) {
+      dg[2 * idx] += re;
+      dg[2 * idx + 1] += im;
+    } else {
+      dg[2 * idx] = re;
+      dg[2 * idx + 1] = im;
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+void launch_phases(int npt, const double *x, int nR, const int *R, cx<double> *rm, cx<double> *T64, cx<float> *T32,
+                   cudaStream_t st) {
+  size_t n = (size_t)npt * nR;
+  if (!n) return;
+  k_phases<<<nblocks(n, 256), 256, 0, st>>>(npt, x, nR, R, rm, T64, T32);
+  epw_count_launch();
+}
+
+void launch_fourier_d(int npt, int nR, const cx<double> *PT, const cx<double> *X, int msize, cx<double> *out,
+                      cudaStream_t st) {
+  size_t n = (size_t)npt * msize;
+  if (!n) return;
+  k_fourier_d<<<nblocks(n, 256), 256, 0, st>>>(npt, nR, PT, X, msize, out);
+  epw_count_launch();
+}
+
+void launch_eigh_d(int nmat, int n, cx<double> *A, double *w, cx<double> *V, unsigned *dstatus, cudaStream_t st) {
+  if (!nmat) return;
+  int b = (nmat + 63) / 64;
+  if (n <= 3)
+    k_eigh_d<3><<<b, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
+  else if (n <= 4)
+    k_eigh_d<4><<<b, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
+  else if (n <= 9)
+    k_eigh_d<9><<<b, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
+  else
+    k_eigh_d<18><<<b, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
+  epw_count_launch();
+}
+
+void launch_phonon_post(int nq, int nm, const double *w2, const cx<double> *ev, const double *mass, double omega_min,
+                        double *omegaT, cx<double> *ET64, cx<float> *ET32, double *omega_out, cudaStream_t st) {
+  size_t n = (size_t)nq * nm;
+  if (!n) return;
+  k_phonon_post<<<nblocks(n, 256), 256, 0, st>>>(nq, nm, w2, ev, mass, omega_min, omegaT, ET64, ET32, omega_out);
+  epw_count_launch();
+}
+
+template <typename R>
+void launch_cgemm(int M, int N, int K, const cx<R> *A, int lda, bool transA, bool conjA, const cx<R> *B, int ldb,
+                  cx<R> *C, int ldc, bool accumulate, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  k_cgemm<R><<<grid, 256, 0, st>>>(M, N, K, A, lda, transA, conjA, B, ldb, C, ldc, accumulate);
+  epw_count_launch();
+}
+template void launch_cgemm<double>(int, int, int, const cx<double> *, int, bool, bool, const cx<double> *, int,
+                                   cx<double> *, int, bool, cudaStream_t);
+template void launch_cgemm<float>(int, int, int, const cx<float> *, int, bool, bool, const cx<float> *, int,
+                                  cx<float> *, int, bool, cudaStream_t);
+
+template <typename R>
+void launch_build_B(const epw_model *m, int nk, const cx<double> *Pk, const cx<R> *G1, const cx<double> *Uk,
+                    cx<R> *Bg, cx<R> *BH, cudaStream_t st) {
+  size_t nbg = (size_t)nk * m->nRp * m->nm * m->nw * m->nw;
+  if (nbg && Bg) {
+    k_build_Bg<R><<<nblocks(nbg, 256), 256, 0, st>>>(nk, m->nRp, m->nm, m->nw, G1, Uk, Bg);
+    epw_count_launch();
+  }
+  size_t nbh = (size_t)nk * m->nRe * m->nw * m->nw;
+  if (nbh && BH) {
+    k_build_BH<R><<<nblocks(nbh, 256), 256, 0, st>>>(nk, m->nRe, m->nw, Pk, m->Hw, BH);
+    epw_count_launch();
+  }
+}
+template void launch_build_B<double>(const epw_model *, int, const cx<double> *, const cx<double> *,
+                                     const cx<double> *, cx<double> *, cx<double> *, cudaStream_t);
+template void launch_build_B<float>(const epw_model *, int, const cx<double> *, const cx<float> *,
+                                    const cx<double> *, cx<float> *, cx<float> *, cudaStream_t);
+
+void launch_cast_c64_to_c32(size_t n, const cx<double> *in, cx<float> *out, cudaStream_t st) {
+  if (!n) return;
+  k_cast_c64_c32<<<nblocks(n, 256), 256, 0, st>>>(n, in, out);
+  epw_count_launch();
+}
+
+template <typename R, int MW, int MM>
+static void pair_dispatch_mode(const PairArgs &a, int mode, dim3 grid, cudaStream_t st) {
+  if (mode == 0)
+    k_pair<R, MW, MM, 0><<<grid, 128, 0, st>>>(a);
+  else if (mode == 1)
+    k_pair<R, MW, MM, 1><<<grid, 128, 0, st>>>(a);
+  else
+    k_pair<R, MW, MM, 2><<<grid, 128, 0, st>>>(a);
+  epw_count_launch();
+}
+
+template <typename R>
+epw_status launch_pair(const PairArgs &a, int mode, cudaStream_t st) {
+  int nkl = (mode == 2) ? a.nkc : a.nk;
+  if (nkl <= 0 || a.nq <= 0) return EPW_OK;
+  dim3 grid((a.nq + 127) / 128, nkl);
+  if (a.nw <= 1 && a.nm <= 3)
+    pair_dispatch_mode<R, 1, 3>(a, mode, grid, st);
+  else if (a.nw <= 4 && a.nm <= 3)
+    pair_dispatch_mode<R, 4, 3>(a, mode, grid, st);
+  else if (a.nw <= 8 && a.nm <= 9)
+    pair_dispatch_mode<R, 8, 9>(a, mode, grid, st);
+  else
+    return EPW_ERR_UNSUPPORTED;
+  return EPW_OK;
+}
+template epw_status launch_pair<double>(const PairArgs &, int, cudaStream_t);
+template epw_status launch_pair<float>(const PairArgs &, int, cudaStream_t);
+
+void launch_finalize(int nk, int nqb, int nw, const double *partial, double *out, cudaStream_t st) {
+  int n = nk * nw;
+  if (!n) return;
+  k_finalize<<<(n + 127) / 128, 128, 0, st>>>(nk, nqb, nw, partial, out);
+  epw_count_launch();
+}
+
+void launch_sum_scalar(int n, const double *partial, double scale, double *out, cudaStream_t st) {
+  k_sum_scalar<<<1, 256, 0, st>>>(n, partial, scale, out);
+  epw_count_launch();
+}
+
+template <typename R>
+void launch_bg_adjoint_rotate_k0(int nk, int k0, int nRp, int nm, int nw, const cx<R> *Bbar, const cx<double> *Uk,
+                                 cx<R> *G1bar, cudaStream_t st) {
+  size_t n = (size_t)nk * nRp * nm * nw * nw;
+  if (!n) return;
+  k_bg_adjoint_rotate<R><<<nblocks(n, 256), 256, 0, st>>>(nk, k0, nRp, nm, nw, Bbar, Uk, G1bar);
+  epw_count_launch();
+}
+template void launch_bg_adjoint_rotate_k0<double>(int, int, int, int, int, const cx<double> *, const cx<double> *,
+                                                  cx<double> *, cudaStream_t);
+template void launch_bg_adjoint_rotate_k0<float>(int, int, int, int, int, const cx<float> *, const cx<double> *,
+                                                 cx<float> *, cudaStream_t);
+
+template <typename R>
+void launch_dg_scale(const epw_model *m, const cx<R> *gwbar, double *dg, bool accumulate, cudaStream_t st) {
+  size_t per = (size_t)m->nm * m->nw * m->nw;
+  size_t n = (size_t)m->nRe * m->nRp * per;
+  if (!n) return;
+  k_dg_scale<R><<<nblocks(n, 256), 256, 0, st>>>(m->nRe, m->nRp, per, m->wRe, m->wRp, gwbar, dg, accumulate);
+  epw_count_launch();
+}
+template void launch_dg_scale<double>(const epw_model *, const cx<double> *, double *, bool, cudaStream_t);
+template void launch_dg_scale<float>(const epw_model *, const cx<float> *, double *, bool, cudaStream_t);

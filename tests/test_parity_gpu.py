@@ -1,0 +1,153 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (written here, derived in the design notes):
+* EPW_FP64  path: Im Sigma within 1e-6 relative (observed ~1e-12);
+                  eps, omega within 1e-10 eV; degenerate-block |g|^2 within 1e-9.
+* EPW_FP32  path: Im Sigma within 2e-3 relative (FP32 eigensolves move each
+                  delta argument by ~1e-6 eV against sigma = 20-50 meV).
+Relative errors use a floor of 1e-6 * max|Im Sigma| for states whose linewidth
+vanishes.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._util import degenerate_sums
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(got, ref):
+    floor = 1e-6 * np.abs(ref).max()
+    return float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), floor)))
+
+
+@pytest.fixture(scope="module")
+def epw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_03525_gb300 as epw
+    return epw
+
+
+def _model(seed, lattice="diamond", nw=3, nat=2, masses=(1.0, 1.2), nR=20, real=False):
+    rng = np.random.default_rng(seed)
+    return W.make_model(lattice, nw, nat, list(masses)[:nat], nR, nR, rng, real=real)
+
+
+def test_c1_full_fp64_matches_oracle(epw, oracle_lib):
+    wl = W.make_workload("sc_nw1")
+    m = epw.Model(wl.model)
+    got = m.linewidth(wl.k, wl.q, wl.wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.FP64)
+    ref = oracle_lib.linewidth(wl.model, wl.k, wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
+    assert _rel(got, ref) < 1e-6
+
+
+def test_closed_form_one_band_on_gpu(epw):
+    from tests.test_oracle_pins import _tb, _tb_linewidth_closed_form
+    m = epw.Model(_tb())
+    k = W.uniform_grid(3) + 0.05
+    q = W.uniform_grid(6)
+    for prec, tol in ((epw.FP64, 1e-9), (epw.FP32, 2e-3)):
+        got = m.linewidth(k, q, T=300.0, EF=0.1, sigma=0.05, precision=prec)[:, 0]
+        ref = _tb_linewidth_closed_form(k, q, 300.0, 0.1, 0.05)
+        assert _rel(got, ref) < tol, prec
+
+
+@pytest.mark.parametrize("lattice,nw,nat", [("fcc", 4, 1), ("diamond", 3, 2), ("hex", 5, 3), ("fcc", 2, 1),
+                                            ("diamond", 8, 2)])
+def test_random_models_fp64_and_fp32(epw, oracle_lib, lattice, nw, nat):
+    wm = _model(100 + nw * 10 + nat, lattice, nw, nat, (1.0, 1.2, 1.1))
+    rng = np.random.default_rng(7)
+    k = rng.random((5, 3))
+    q = rng.random((300, 3))  # 3 blocks of 128 and a ragged tail
+    wq = rng.random(300) / 300
+    m = epw.Model(wm)
+    ref = oracle_lib.linewidth(wm, k, q, wq, 300.0, 0.1, 0.05)
+    got64 = m.linewidth(k, q, wq, T=300.0, EF=0.1, sigma=0.05, precision=epw.FP64)
+    assert _rel(got64, ref) < 1e-6
+    got32 = m.linewidth(k, q, wq, T=300.0, EF=0.1, sigma=0.05, precision=epw.FP32)
+    assert _rel(got32, ref) < 2e-3
+
+
+def test_device_pointers_and_stream(epw, oracle_lib):
+    import torch
+    wl = W.make_workload("sc_nw1")
+    m = epw.Model(wl.model)
+    kd = torch.tensor(wl.k, device="cuda")
+    qd = torch.tensor(wl.q, device="cuda")
+    wd = torch.tensor(wl.wq, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        out = m.linewidth(kd, qd, wd, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.FP64)
+    s.synchronize()
+    assert out.is_cuda
+    ref = oracle_lib.linewidth(wl.model, wl.k, wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
+    assert _rel(out.cpu().numpy(), ref) < 1e-6
+    m.sync()
+
+
+def test_interp_matches_oracle(epw, oracle_lib):
+    wm = _model(200, "hex", 4, 2, (1.0, 1.3))
+    rng = np.random.default_rng(8)
+    k = rng.random((3, 3))
+    q = np.concatenate([np.zeros((1, 3)), rng.random((140, 3))])  # includes Gamma (dropped modes)
+    m = epw.Model(wm)
+    ek, ekq, om, g = m.interp(k, q, precision=epw.FP64)
+    rk, rkq, rom, rg = oracle_lib.interp(wm, k, q)
+    assert np.abs(ek - rk).max() < 1e-10
+    assert np.abs(ekq - rkq).max() < 1e-10
+    assert np.abs(om - rom).max() < 1e-10
+    assert np.abs(g[:, 0, :3]).max() == 0.0  # acoustic modes at Gamma are left out
+    for ik in range(len(k)):
+        for iq in range(len(q)):
+            a = degenerate_sums(np.abs(g[ik, iq]) ** 2, rkq[ik, iq], rk[ik], rom[iq], 1e-7)
+            b = degenerate_sums(np.abs(rg[ik, iq]) ** 2, rkq[ik, iq], rk[ik], rom[iq], 1e-7)
+            assert np.allclose(a, b, rtol=1e-9, atol=1e-12 * b.max())
+
+
+def test_backward_matches_oracle_gradient(epw, oracle_lib):
+    rng = np.random.default_rng(9)
+    wm = W.make_model("sc", 2, 1, [1.0], None, None, rng, box=1, omega_max=0.2)
+    k = rng.random((4, 3))
+    q = rng.random((200, 3))
+    cot = rng.random((4, 2))
+    m = epw.Model(wm)
+    dg, dT, dE = m.linewidth_backward(k, q, cot, T=300.0, EF=0.2, sigma=0.2, precision=epw.FP64)
+    rdg, rdT, rdE = oracle_lib.linewidth_grad(wm, k, q, None, 300.0, 0.2, 0.2, cot=cot)
+    assert np.abs(dg - rdg).max() <= 1e-9 * np.abs(rdg).max()
+    assert abs(dT - rdT) <= 1e-9 * abs(rdT)
+    assert abs(dE - rdE) <= 1e-9 * abs(rdE)
+
+
+def test_edge_cases(epw, oracle_lib):
+    wl = W.make_workload("sc_nw1")
+    m = epw.Model(wl.model)
+    out = m.linewidth(wl.k[:3], wl.q[:0], T=300.0, EF=0.0, sigma=0.05)
+    assert out.shape == (3, 1) and np.all(out == 0)
+    out = m.linewidth(wl.k[:0], wl.q, T=300.0, EF=0.0, sigma=0.05)
+    assert out.shape == (0, 1)
+    # one q point, T = 0
+    got = m.linewidth(wl.k[:7], wl.q[5:6], T=0.0, EF=0.0, sigma=0.05)
+    ref = oracle_lib.linewidth(wl.model, wl.k[:7], wl.q[5:6], None, 0.0, 0.0, 0.05)
+    assert np.allclose(got, ref, rtol=1e-9, atol=1e-15)
+    with pytest.raises(epw.EPWError):
+        m.linewidth(wl.k, wl.q, T=300.0, EF=0.0, sigma=0.0)
+    with pytest.raises(epw.EPWError):
+        m.linewidth(wl.k, wl.q, T=-1.0, EF=0.0, sigma=0.05)
+    with pytest.raises(epw.EPWError):
+        m.linewidth(wl.k, wl.q, T=300.0, EF=0.0, sigma=0.05, precision=7)
+    with pytest.raises(epw.EPWError):
+        m.linewidth_backward(wl.k[:2], wl.q[:3], np.ones((2, 1)), T=0.0, EF=0.0, sigma=0.05)
+
+
+def test_fcc_workload_full_size_sampled_k(epw, oracle_lib):
+    """fcc nw=4 workload at its full size (1000 k x 40^3 q), FP64, checked on sampled k."""
+    wl = W.make_workload("fcc_nw4")
+    m = epw.Model(wl.model)
+    got = m.linewidth(wl.k, wl.q, wl.wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.FP64)
+    idx = np.array([0, 377, 999])
+    ref = oracle_lib.linewidth(wl.model, wl.k[idx], wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
+    assert _rel(got[idx], ref) < 1e-6
+    assert np.all(got >= 0)
