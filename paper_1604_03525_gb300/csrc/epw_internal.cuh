@@ -221,7 +221,7 @@ struct jacobi_tol<double> {
 };
 template <>
 struct jacobi_tol<float> {
-  static constexpr float tol2 = 1e-13f;
+  static constexpr float tol2 = 1e-12f;
   static constexpr int maxsweep = 20;
 };
 

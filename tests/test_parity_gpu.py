@@ -98,7 +98,11 @@ def test_interp_matches_oracle(epw, oracle_lib):
     rk, rkq, rom, rg = oracle_lib.interp(wm, k, q)
     assert np.abs(ek - rk).max() < 1e-10
     assert np.abs(ekq - rkq).max() < 1e-10
-    assert np.abs(om - rom).max() < 1e-10
+    # omega = sign(w2) sqrt|w2| is ill-conditioned at w2 -> 0 (acoustic modes at
+    # Gamma), so frequencies are compared through w2 there.
+    assert np.abs(om * np.abs(om) - rom * np.abs(rom)).max() < 1e-14
+    big = np.abs(rom) > 1e-4
+    assert np.abs(om - rom)[big].max() < 1e-10
     assert np.abs(g[:, 0, :3]).max() == 0.0  # acoustic modes at Gamma are left out
     for ik in range(len(k)):
         for iq in range(len(q)):
@@ -150,4 +154,52 @@ def test_fcc_workload_full_size_sampled_k(epw, oracle_lib):
     idx = np.array([0, 377, 999])
     ref = oracle_lib.linewidth(wl.model, wl.k[idx], wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
     assert _rel(got[idx], ref) < 1e-6
+    assert np.all(got >= 0)
+
+
+# ---------------------------------------------------------------- tensor cores
+BF16X3_TOL = 1e-4  # relative, per (n,k), floor 1e-6 * max
+
+
+@pytest.mark.parametrize("lattice,nw,nat,nR", [("fcc", 4, 1, 120), ("fcc", 2, 1, 40), ("sc", 1, 1, 27)])
+def test_bf16x3_random_models(epw, oracle_lib, lattice, nw, nat, nR):
+    rng = np.random.default_rng(300 + nw)
+    wm = W.make_model(lattice, nw, nat, [1.0], nR, nR, rng)
+    k = rng.random((7, 3))          # 7 k: a ragged last k-group
+    q = rng.random((300, 3))        # 3 q tiles, the last one ragged
+    wq = np.full(300, 1.0 / 300)
+    m = epw.Model(wm)
+    ref = oracle_lib.linewidth(wm, k, q, wq, 300.0, 0.1, 0.05)
+    got = m.linewidth(k, q, wq, T=300.0, EF=0.1, sigma=0.05, precision=epw.BF16X3)
+    assert _rel(got, ref) < BF16X3_TOL
+
+
+def test_bf16x3_c1_full(epw, oracle_lib):
+    wl = W.make_workload("sc_nw1")
+    m = epw.Model(wl.model)
+    got = m.linewidth(wl.k, wl.q, wl.wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.BF16X3)
+    ref = oracle_lib.linewidth(wl.model, wl.k, wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
+    assert _rel(got, ref) < BF16X3_TOL
+
+
+def test_bf16x3_unsupported_shape_reports(epw):
+    wm = _model(400, "hex", 5, 3, (1.0, 1.1, 1.2))
+    m = epw.Model(wm)
+    with pytest.raises(epw.EPWError) as e:
+        m.linewidth(np.zeros((2, 3)), np.zeros((4, 3)), T=300.0, EF=0.0, sigma=0.05, precision=epw.BF16X3)
+    assert e.value.status == 6
+
+
+def test_fcc_workload_full_size_bf16x3_sampled_k(epw, oracle_lib):
+    """The benchmark configuration (1000 k x 40^3 q, device buffers) in split-BF16, sampled k."""
+    import torch
+    wl = W.make_workload("fcc_nw4")
+    m = epw.Model(wl.model)
+    got = m.linewidth(torch.tensor(wl.k, device="cuda"), torch.tensor(wl.q, device="cuda"),
+                      torch.tensor(wl.wq, device="cuda"), T=wl.T, EF=wl.EF, sigma=wl.sigma,
+                      precision=epw.BF16X3).cpu().numpy()
+    m.sync()
+    idx = np.array([3, 500, 998])
+    ref = oracle_lib.linewidth(wl.model, wl.k[idx], wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
+    assert _rel(got[idx], ref) < BF16X3_TOL
     assert np.all(got >= 0)
