@@ -82,8 +82,13 @@ typedef enum {
  *   EPW_BF16X3 : contractions on the tensor cores (tcgen05) with operands split
  *                into two bfloat16 terms (x = hi + lo; hi*hi + hi*lo + lo*hi,
  *                FP32 accumulation); per-pair eigensolves and rotations in
- *                FP32; phases, phonons, k-side work and the reduction in FP64. */
-typedef enum { EPW_FP64 = 0, EPW_FP32 = 1, EPW_BF16X3 = 2 } epw_precision;
+ *                FP32; phases, phonons, k-side work and the reduction in FP64.
+ *   EPW_TF32X3 : as EPW_BF16X3 with tf32 terms (about 16x smaller contraction
+ *                error, half the tensor throughput).
+ * The two tensor-core forms need Re == Rp (same vectors, same order) and a
+ * compiled (nw, 3nat) shape: (1,3), (2,3), (4,3); otherwise the call returns
+ * EPW_ERR_UNSUPPORTED and EPW_FP32 / EPW_FP64 serve every shape. */
+typedef enum { EPW_FP64 = 0, EPW_FP32 = 1, EPW_BF16X3 = 2, EPW_TF32X3 = 3 } epw_precision;
 
 typedef struct epw_model epw_model; /* opaque */
 

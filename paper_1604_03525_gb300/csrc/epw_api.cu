@@ -362,7 +362,7 @@ static epw_status check_params(const epw_params *p) {
   if (!(p->sigma_eV > 0.0) || !std::isfinite(p->sigma_eV)) return fail(EPW_ERR_INVALID_ARG, "sigma_eV must be > 0");
   if (!(p->omega_min_eV >= 0.0)) return fail(EPW_ERR_INVALID_ARG, "omega_min_eV must be >= 0");
   if (!std::isfinite(p->EF_eV)) return fail(EPW_ERR_INVALID_ARG, "EF_eV must be finite");
-  if (p->precision < EPW_FP64 || p->precision > EPW_BF16X3) return fail(EPW_ERR_INVALID_ARG, "unknown precision");
+  if (p->precision < EPW_FP64 || p->precision > EPW_TF32X3) return fail(EPW_ERR_INVALID_ARG, "unknown precision");
   if (p->reserved != 0) return fail(EPW_ERR_INVALID_ARG, "reserved field must be 0");
   return EPW_OK;
 }
@@ -394,10 +394,10 @@ struct LwPlan {
 
 static epw_status plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,
                                  bool sout, LwPlan &L) {
-  const bool tc = prec == EPW_BF16X3;
+  const bool tc = prec == EPW_BF16X3 || prec == EPW_TF32X3;
   plan_prep(A, m, nk, nq, tc ? EPW_FP32 : prec, sk, sq, swq, true, L.p);
   if (tc) {
-    CKS(tc_plan(A, m, nk, nq, L.tc));
+    CKS(tc_plan(A, m, nk, nq, prec == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32, L.tc));
     L.partial = nullptr;
   } else {
     int nqb = (nq + 127) / 128;
@@ -409,7 +409,7 @@ static epw_status plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, i
 
 extern "C" epw_status epw_reserve(epw_model *m, int nk, int nq, int precision) {
   CKS(check_common(m, nk, (const double *)1, nq, (const double *)1));
-  if (precision < EPW_FP64 || precision > EPW_BF16X3) return fail(EPW_ERR_INVALID_ARG, "unknown precision");
+  if (precision < EPW_FP64 || precision > EPW_TF32X3) return fail(EPW_ERR_INVALID_ARG, "unknown precision");
   Arena A{nullptr, 0, 0};
   LwPlan L;
   CKS(plan_linewidth(A, m, nk, nq, precision, true, true, true, true, L));
@@ -457,7 +457,7 @@ extern "C" epw_status epw_linewidth(const epw_model *mc, int nk, const double *k
     wqd = p.wqd;
   }
   double *out = sout ? L.out_d : imsigma;
-  if (prec == EPW_BF16X3) {
+  if (prec == EPW_BF16X3 || prec == EPW_TF32X3) {
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
     epw_status s = tc_linewidth(m, nk, kd, nq, qd, wqd, par, p.PkRM, p.epsk, p.Uk, p.omegaT, (const cx<float> *)p.ET,
                                 (const cx<float> *)p.Bg, (const cx<float> *)p.BH, L.tc, out, st);
@@ -585,7 +585,7 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   CKS(check_params(par));
   if (!(par->T_K > 0.0)) return fail(EPW_ERR_INVALID_ARG, "the adjoint needs T_K > 0");
   if (nk > 0 && !cot) return fail(EPW_ERR_INVALID_ARG, "null grad_imsigma");
-  const int prec = par->precision == EPW_BF16X3 ? EPW_FP32 : par->precision;
+  const int prec = par->precision >= EPW_BF16X3 ? EPW_FP32 : par->precision;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nw2 = (size_t)m->nw * m->nw, per = (size_t)m->nm * nw2;
   const size_t ng = (size_t)m->nRe * m->nRp * per;

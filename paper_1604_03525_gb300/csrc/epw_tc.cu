@@ -7,12 +7,14 @@
 //   C[q][c] = sum_R P_q(R) B_k[R][c],   c = (H(k+q)_ij | (g_a(k,q) U_k)_jn)
 //
 // with P_q(R) = e^{2 pi i q.R}.  It runs as a real GEMM with K = 2 nR (re/im
-// interleaved) on tcgen05: operands are split into two bfloat16 terms
-// (x = hi + lo) and three MMAs (hi*hi + hi*lo + lo*hi) accumulate in FP32 in
-// tensor memory.  The epilogue of each 128 x 256 tile (128 q rows x 2 k) is the
+// interleaved) on tcgen05.  Each operand is split into two terms x = hi + lo
+// and three MMAs (lo*hi + hi*lo + hi*hi) accumulate in FP32 in tensor memory:
+//   OP_BF16: bfloat16 terms, kind::f16   (about 2^-17 relative per product)
+//   OP_TF32: tf32 terms,     kind::tf32  (about 2^-21 relative per product)
+// The epilogue of each 128 x 256 tile (128 q rows x a group of k) is the
 // per-pair work of Eq. (linewidthel): a Jacobi eigensolve of H(k+q), the mode
-// projection with e_q/sqrt(2 M w), the U_k+q^dagger rotation, |g|^2, Gaussian
-// deltas and occupations, reduced over the tile's q rows.
+// projection with e_q / sqrt(2 M w), the U_k+q^dagger rotation, |g|^2, the
+// Gaussian deltas and occupations, summed over each warp's 32 q rows.
 //
 // CTA layout (persistent, one CTA per SM, 10 warps):
 //   warp 0      TMA producer (A = q-phase tile, B = k-vertex tile, 2 stages)
@@ -20,6 +22,8 @@
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32*(w%4).., k-slot (w-2)/4
 // Tensor memory holds two accumulator stages of 256 columns (512 in total),
 // so the MMA of the next tile overlaps the epilogue of the current one.
+// Tiles are visited in q-blocks (so that a block of A stays in L2) and, inside
+// a block, k-group-major (so that the CTAs running together share one B tile).
 // Every wait is bounded; a wait that runs out raises EPW_DEV_TIMEOUT, drains
 // outstanding copies and MMAs, frees tensor memory and returns.
 #include <cuda.h>
@@ -32,12 +36,12 @@
 
 namespace {
 
-constexpr int BM = 128;                      // q rows per tile
-constexpr int BN = 256;                      // real accumulator columns per tile
-constexpr int BK = 64;                       // K elements per stage (128 B of bf16)
+constexpr int BM = 128;               // q rows per tile
+constexpr int BN = 256;               // real accumulator columns per tile
+constexpr int ROWB = 128;             // bytes per smem operand row (one 128-byte swizzle row)
 constexpr int STAGES = 2;
-constexpr int A_BYTES = BM * BK * 2;         // 16 KiB
-constexpr int B_BYTES = BN * BK * 2;         // 32 KiB
+constexpr int A_BYTES = BM * ROWB;    // 16 KiB
+constexpr int B_BYTES = BN * ROWB;    // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr int NTHREADS = 320;
@@ -45,10 +49,30 @@ constexpr int EPI_WARP0 = 2;
 constexpr int NEPI_WARPS = 8;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr size_t A_BLOCK_BYTES = 48u << 20;      // q-block size target (A operand bytes)
 
-// kind::f16 instruction descriptor: D=F32, A=B=BF16, K-major A and B, N=256, M=128.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+template <int OP>
+struct OpT;
+template <>
+struct OpT<TC_OP_BF16> {
+  using T = __nv_bfloat16;
+  static constexpr int ESZ = 2;
+  static constexpr int BK = ROWB / ESZ;  // 64 elements per stage
+  static constexpr int KSTEP = 16;      // K per MMA (32 bytes)
+  // kind::f16 instruction descriptor: D=F32, A=B=BF16, K-major, N=256, M=128
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+template <>
+struct OpT<TC_OP_TF32> {
+  using T = float;
+  static constexpr int ESZ = 4;
+  static constexpr int BK = ROWB / ESZ;  // 32 elements per stage
+  static constexpr int KSTEP = 8;       // K per MMA (32 bytes)
+  // kind::tf32 instruction descriptor: D=F32, A=B=TF32, K-major, N=256, M=128
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
 
 // ------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -88,12 +112,21 @@ __device__ __forceinline__ void tmem_relinquish() {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc)
-      : "memory");
+template <int OP>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  if constexpr (OP == TC_OP_BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(OpT<OP>::IDESC), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(OpT<OP>::IDESC), "r"(acc)
+        : "memory");
+  }
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -102,7 +135,7 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // 32 lanes x 32 bit, 8 consecutive columns per thread; waits for completion.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *r) {
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&r)[8]) {
   uint32_t u0, u1, u2, u3, u4, u5, u6, u7;
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
@@ -119,8 +152,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *r) {
   r[6] = __uint_as_float(u6);
   r[7] = __uint_as_float(u7);
 }
-// 32 consecutive columns per thread.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *r) {
+// 32 consecutive columns per thread; waits for completion.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32]) {
   uint32_t u[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -135,15 +168,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *r) {
 #pragma unroll
   for (int i = 0; i < 32; i++) r[i] = __uint_as_float(u[i]);
 }
-// n (multiple of 8) consecutive columns
+// NCOL (multiple of 8, at most 32) consecutive columns into a register array.
 template <int NCOL>
-__device__ __forceinline__ void tmem_load(uint32_t taddr, float *r) {
-  static_assert(NCOL % 8 == 0, "columns come in groups of 8");
-  int c = 0;
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float (&r)[NCOL]) {
+  static_assert(NCOL % 8 == 0 && NCOL <= 32, "8..32 columns in groups of 8");
+  if constexpr (NCOL == 32) {
+    tmem_ld32(taddr, r);
+  } else {
 #pragma unroll
-  for (; c + 32 <= NCOL; c += 32) tmem_ld32(taddr + c, r + c);
+    for (int c = 0; c < NCOL; c += 8) {
+      float t[8];
+      tmem_ld8(taddr + c, t);
 #pragma unroll
-  for (; c < NCOL; c += 8) tmem_ld8(taddr + c, r + c);
+      for (int i = 0; i < 8; i++) r[c + i] = t[i];
+    }
+  }
 }
 
 // K-major, 128-byte-swizzled smem operand: rows of 128 B, 8-row groups 1024 B apart.
@@ -155,6 +194,16 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
@@ -182,8 +231,129 @@ __device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity) {
     if (clock64() - t0 > WAIT_CYCLES) break;
 }
 
+// ---------------------------------------------------- FP32 Jacobi (epilogue)
+// Hermitian N x N in registers, upper triangle stored (A[i][j], i < j; the
+// diagonal's real part).  One rotation of the (p,q) plane, parameters without
+// a division by |a_pq| (branch-free, so a zero a_pq gives the identity):
+//   d = a_qq - a_pp,  den = |d| + sqrt(d^2 + 4|a_pq|^2),  t = 2|a_pq| sgn(d) / den,
+//   c = 1/sqrt(1+t^2),  s e = 2 sgn(d) c a_pq / den,  a_pp -= t|a_pq|,  a_qq += t|a_pq|.
+template <int N>
+struct Herm {
+  cx<float> a[N][N];  // only i < j used, plus a[i][i].x
+  __device__ __forceinline__ cx<float> get(int i, int j) const { return i < j ? a[i][j] : conjc(a[j][i]); }
+  __device__ __forceinline__ void set(int i, int j, cx<float> v) {
+    if (i < j)
+      a[i][j] = v;
+    else
+      a[j][i] = conjc(v);
+  }
+};
+
+struct Rot {
+  float c, tb;
+  cx<float> se;
+};
+
+template <int N>
+__device__ __forceinline__ Rot rot_params(const Herm<N> &H, int p, int q) {
+  const cx<float> apq = H.a[p][q];
+  const float d = H.a[q][q].x - H.a[p][p].x;
+  const float m2 = fmaf(apq.x, apq.x, apq.y * apq.y);
+  const float x = fmaf(d, d, 4.0f * m2);
+  const float sq = x * rsqrt_approx(fmaxf(x, 1e-37f));
+  const float den = fmaxf(fabsf(d) + sq, 1e-30f);
+  const float rden = rcp_approx(den);
+  const float sg = d >= 0.0f ? 2.0f : -2.0f;
+  const float tmag = 2.0f * m2 * rden;  // |t| |a_pq|
+  const float t2 = tmag * (2.0f * rden);
+  Rot r;
+  r.c = rsqrt_approx(1.0f + t2);
+  r.tb = 0.5f * sg * tmag;
+  const float kap = sg * rden * r.c;
+  r.se = mkc(kap * apq.x, kap * apq.y);
+  return r;
+}
+
+template <int N>
+__device__ __forceinline__ void rot_apply(Herm<N> &H, cx<float> (&V)[N][N], int p, int q, const Rot &r) {
+  H.a[p][p].x -= r.tb;
+  H.a[q][q].x += r.tb;
+  H.a[p][q] = mkc(0.0f, 0.0f);
+  const cx<float> sec = conjc(r.se);
+#pragma unroll
+  for (int k = 0; k < N; k++) {
+    if (k == p || k == q) continue;
+    const cx<float> akp = H.get(k, p), akq = H.get(k, q);
+    cx<float> nkp = mkc(r.c * akp.x, r.c * akp.y);
+    cx<float> nkq = mkc(r.c * akq.x, r.c * akq.y);
+    cfma(nkp, mkc(-sec.x, -sec.y), akq);
+    cfma(nkq, r.se, akp);
+    H.set(k, p, nkp);
+    H.set(k, q, nkq);
+  }
+#pragma unroll
+  for (int k = 0; k < N; k++) {
+    const cx<float> vp = V[k][p], vq = V[k][q];
+    cx<float> np = mkc(r.c * vp.x, r.c * vp.y);
+    cx<float> nq = mkc(r.c * vq.x, r.c * vq.y);
+    cfma(np, mkc(-sec.x, -sec.y), vq);
+    cfma(nq, r.se, vp);
+    V[k][p] = np;
+    V[k][q] = nq;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ float offdiag_frac(const Herm<N> &H) {
+  float off = 0.0f, dg = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    dg = fmaf(H.a[i][i].x, H.a[i][i].x, dg);
+#pragma unroll
+    for (int j = i + 1; j < N; j++) off += cabs2(H.a[i][j]);
+  }
+  return off / fmaxf(dg + 2.0f * off, 1e-37f);
+}
+
+// Sweeps until every lane of the warp has converged (warp-uniform exit).
+template <int N>
+__device__ __forceinline__ bool jacobi_fast(Herm<N> &H, cx<float> (&V)[N][N]) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+#pragma unroll
+    for (int j = 0; j < N; j++) V[i][j] = mkc(i == j ? 1.0f : 0.0f, 0.0f);
+  if constexpr (N == 1) return true;
+  constexpr float TOL2 = 1e-12f;
+  constexpr int MAXSWEEP = 12;
+  for (int sweep = 0; sweep < MAXSWEEP; sweep++) {
+    const bool conv = offdiag_frac(H) <= TOL2;
+    if (__all_sync(0xffffffffu, conv)) return true;
+    if constexpr (N == 4) {
+      // parallel ordering: the two rotations of a round touch disjoint planes
+      const Rot r01 = rot_params(H, 0, 1), r23 = rot_params(H, 2, 3);
+      rot_apply(H, V, 0, 1, r01);
+      rot_apply(H, V, 2, 3, r23);
+      const Rot r02 = rot_params(H, 0, 2), r13 = rot_params(H, 1, 3);
+      rot_apply(H, V, 0, 2, r02);
+      rot_apply(H, V, 1, 3, r13);
+      const Rot r03 = rot_params(H, 0, 3), r12 = rot_params(H, 1, 2);
+      rot_apply(H, V, 0, 3, r03);
+      rot_apply(H, V, 1, 2, r12);
+    } else {
+#pragma unroll
+      for (int p = 0; p < N - 1; p++)
+#pragma unroll
+        for (int q = p + 1; q < N; q++) {
+          const Rot r = rot_params(H, p, q);
+          rot_apply(H, V, p, q, r);
+        }
+    }
+  }
+  return offdiag_frac(H) <= TOL2;
+}
+
 struct TcArgs {
-  int nk, nq, nqt, nkg, kpad, nkb;
+  int nk, nq, nqt, nkg, kpad, nkb, qblock;
   const double *epsk;    // [nk][nw]
   const double *omegaT;  // [nm][nq]
   const float *nbT;      // [nm][nq]
@@ -201,113 +371,150 @@ struct Shape {
   static constexpr int CPK = CPK_RAW <= 8 ? 8 : CPK_RAW <= 16 ? 16 : CPK_RAW <= 32 ? 32 : CPK_RAW <= 64 ? 64 : 128;
   static constexpr int KPS = 128 / CPK;  // k per slot (per epilogue warp)
   static constexpr int KPT = 2 * KPS;    // k per tile
+  static constexpr int H2 = 2 * NW * NW; // real columns of one NW x NW complex block
   static_assert(CPK_RAW <= 128, "one k must fit in a 128-column slot");
+  static_assert(CPK <= 32 || H2 == 32, "wide shapes read 32-column blocks");
 };
 
+// Tile -> (k group, q tile) in q-blocks of `qblock` tiles, k-group-major inside a block.
+__device__ __forceinline__ void item_coords(const TcArgs &a, int item, int &kg, int &qt) {
+  const int per = a.qblock * a.nkg;
+  const int nb = (a.nqt + a.qblock - 1) / a.qblock;
+  int b = item / per;
+  if (b > nb - 1) b = nb - 1;
+  const int r = item - b * per;
+  const int qbs = min(a.qblock, a.nqt - b * a.qblock);
+  kg = r / qbs;
+  qt = b * a.qblock + r % qbs;
+}
+
 // ------------------------------------------------------------------ epilogue
+// One (k,q) pair per thread; the accumulator holds [H(k+q) | (g_a U_k)_a=0..NM-1].
 template <int NW, int NM>
 __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, int q, int k, bool valid, int quad,
                                               int qt) {
   using S = Shape<NW, NM>;
-  constexpr int H2 = 2 * NW * NW;  // real columns of one NW x NW complex block
-  constexpr int UR = NW <= 4 ? NW : 1;
+  constexpr int H2 = S::H2;
   const int qq = q < a.nq ? q : 0;
   const int kk = k < a.nk ? k : 0;
-  // H(k+q) (and, for small shapes, every column of this k) from the accumulator
+  // per-q and per-k data first, so their latency overlaps the eigensolve
+  float w[NM], nb[NM];
+  cx<float> E[NM][NM];
+#pragma unroll
+  for (int v = 0; v < NM; v++) {
+    w[v] = (float)__ldg(a.omegaT + (size_t)v * a.nq + qq);
+    nb[v] = __ldg(a.nbT + (size_t)v * a.nq + qq);
+  }
+#pragma unroll
+  for (int al = 0; al < NM; al++)
+#pragma unroll
+    for (int v = 0; v < NM; v++) {
+      const float2 e = __ldg(a.ET + ((size_t)al * NM + v) * a.nq + qq);
+      E[al][v] = mkc(e.x, e.y);
+    }
+  float ek[NW];
+#pragma unroll
+  for (int n = 0; n < NW; n++) ek[n] = (float)__ldg(a.epsk + (size_t)kk * NW + n);
+  const double wqi = valid ? (a.wq ? a.wq[q] : 1.0 / a.nq) * (double)a.gnorm : 0.0;
+
   constexpr bool ONE_LOAD = S::CPK <= 32;
-  float all[ONE_LOAD ? S::CPK : 1];
-  float hbuf[ONE_LOAD ? 1 : H2];
-  const float *h;
+  float all[ONE_LOAD ? S::CPK : 8];
+  float hb[ONE_LOAD ? 8 : H2];
   if constexpr (ONE_LOAD) {
     tmem_load<S::CPK>(tcol, all);
-    h = all;
   } else {
-    tmem_load<H2>(tcol, hbuf);
-    h = hbuf;
+    tmem_load<H2>(tcol, hb);
   }
-  cx<float> A[NW][NW], V[NW][NW];
+  Herm<NW> H;
 #pragma unroll
   for (int i = 0; i < NW; i++)
 #pragma unroll
-    for (int j = 0; j < NW; j++) A[i][j] = mkc(h[2 * (i * NW + j)], h[2 * (i * NW + j) + 1]);
-  bool nc = false;
-  jacobi_herm<float, NW>(A, V, NW, jacobi_tol<float>::tol2, jacobi_tol<float>::maxsweep, nc);
-  if (nc && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
-  float em[NW], cpf[NW];
-#pragma unroll UR
+    for (int j = i; j < NW; j++) {
+      const int o = 2 * (i * NW + j);
+      const int o2 = 2 * (j * NW + i);
+      float re, im;
+      if constexpr (ONE_LOAD) {
+        re = 0.5f * (all[o] + all[o2]);
+        im = 0.5f * (all[o + 1] - all[o2 + 1]);
+      } else {
+        re = 0.5f * (hb[o] + hb[o2]);
+        im = 0.5f * (hb[o + 1] - hb[o2 + 1]);
+      }
+      H.a[i][j] = mkc(re, i == j ? 0.0f : im);
+    }
+  cx<float> V[NW][NW];
+  const bool conv = jacobi_fast<NW>(H, V);
+  if (!conv && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
+  float em[NW], fm[NW];
+#pragma unroll
   for (int m = 0; m < NW; m++) {
-    em[m] = A[m][m].x;
-    cpf[m] = fermi_f(em[m] - a.EF, a.invkT);
+    em[m] = H.a[m][m].x;
+    fm[m] = fermi_f(em[m] - a.EF, a.invkT);
   }
-  float ek[NW];
-#pragma unroll UR
-  for (int n = 0; n < NW; n++) ek[n] = (float)a.epsk[(size_t)kk * NW + n];
   float acc[NW];
-#pragma unroll UR
+#pragma unroll
   for (int n = 0; n < NW; n++) acc[n] = 0.0f;
-  const float LOG2E = 1.4426950408889634f;
-  const float s2 = a.inv_sigma * a.inv_sigma * LOG2E;
-#pragma unroll 1
+  const float s2 = a.inv_sigma * a.inv_sigma * 1.4426950408889634f;
+#pragma unroll
   for (int nu = 0; nu < NM; nu++) {
-    const float w = (float)a.omegaT[(size_t)nu * a.nq + qq];
-    const bool keep = (w >= a.omega_min) && (w > 0.0f);
-    const float nb = a.nbT[(size_t)nu * a.nq + qq];
+    const bool keep = (w[nu] >= a.omega_min) && (w[nu] > 0.0f);
     cx<float> G[NW][NW];
 #pragma unroll
     for (int i = 0; i < NW; i++)
 #pragma unroll
       for (int j = 0; j < NW; j++) G[i][j] = mkc(0.0f, 0.0f);
-#pragma unroll 1
+#pragma unroll
     for (int al = 0; al < NM; al++) {
-      float xbuf[ONE_LOAD ? 1 : H2];
-      const float *x;
       if constexpr (ONE_LOAD) {
-        x = all + H2 * (1 + al);
+#pragma unroll
+        for (int i = 0; i < NW; i++)
+#pragma unroll
+          for (int j = 0; j < NW; j++) {
+            const int o = H2 * (1 + al) + 2 * (i * NW + j);
+            cfma(G[i][j], E[al][nu], mkc(all[o], all[o + 1]));
+          }
       } else {
-        tmem_load<H2>(tcol + H2 * (1 + al), xbuf);
-        x = xbuf;
+        float x[H2];
+        tmem_load<H2>(tcol + H2 * (1 + al), x);
+#pragma unroll
+        for (int i = 0; i < NW; i++)
+#pragma unroll
+          for (int j = 0; j < NW; j++) cfma(G[i][j], E[al][nu], mkc(x[2 * (i * NW + j)], x[2 * (i * NW + j) + 1]));
       }
-      float2 e2 = a.ET[((size_t)al * NM + nu) * a.nq + qq];
-      cx<float> e = mkc(e2.x, e2.y);
-#pragma unroll
-      for (int i = 0; i < NW; i++)
-#pragma unroll
-        for (int j = 0; j < NW; j++) cfma(G[i][j], e, mkc(x[2 * (i * NW + j)], x[2 * (i * NW + j) + 1]));
     }
     // |(U^dagger G)_mn|^2 with the delta terms of Eq. (linewidthel)
-#pragma unroll UR
+#pragma unroll
     for (int m = 0; m < NW; m++) {
-      const float f = cpf[m];
-      const float cp = keep ? nb + f : 0.0f, cm = keep ? nb + 1.0f - f : 0.0f;
-#pragma unroll UR
+      const float cp = keep ? nb[nu] + fm[m] : 0.0f;
+      const float cm = keep ? nb[nu] + 1.0f - fm[m] : 0.0f;
+#pragma unroll
       for (int n = 0; n < NW; n++) {
         cx<float> y = mkc(0.0f, 0.0f);
 #pragma unroll
         for (int i = 0; i < NW; i++) cfma(y, conjc(V[i][m]), G[i][n]);
         const float g2 = cabs2(y);
         const float xd = ek[n] - em[m];
-        const float xp = xd + w, xm = xd - w;
+        const float xp = xd + w[nu], xm = xd - w[nu];
         const float d = cp * ex2_approx(-xp * xp * s2) + cm * ex2_approx(-xm * xm * s2);
         acc[n] = fmaf(g2, d, acc[n]);
       }
     }
   }
-  const double wqi = valid ? (a.wq ? a.wq[q] : 1.0 / a.nq) * (double)a.gnorm : 0.0;
-#pragma unroll UR
+#pragma unroll
   for (int n = 0; n < NW; n++) {
     double v = (double)acc[n] * wqi;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && k < a.nk)
-      a.partial[((size_t)k * (4 * a.nqt) + qt * 4 + quad) * NW + n] = v;
+    if ((threadIdx.x & 31) == 0 && k < a.nk) a.partial[((size_t)k * (4 * a.nqt) + qt * 4 + quad) * NW + n] = v;
   }
 }
 
-template <int NW, int NM>
+template <int OP, int NW, int NM>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_linewidth(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                    const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcArgs a) {
   using S = Shape<NW, NM>;
+  using O = OpT<OP>;
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_tfull[2], bar_tempty[2], bar_final;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
@@ -342,11 +549,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     // The whole warp walks the schedule; lane 0 waits and issues the copies.
-    int issued[STAGES] = {0, 0};
+    int issued0 = 0, issued1 = 0;
     uint32_t it = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-      const int kg = item / a.nqt, qt = item % a.nqt;
+      int kg, qt;
+      item_coords(a, item, kg, qt);
       for (int kb = 0; kb < a.nkb; kb++, it++) {
         const int s = it % STAGES;
         const uint32_t par = ((it / STAGES) & 1u) ^ 1u;
@@ -356,11 +564,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t base = smem0 + s * STAGE_BYTES;
             const uint32_t fb = smem_u32(&bar_full[s]);
             mbar_expect_tx(fb, STAGE_BYTES);
-            tma_load_2d(base, &mAhi, kb * BK, qt * BM, fb);
-            tma_load_2d(base + A_BYTES, &mAlo, kb * BK, qt * BM, fb);
-            tma_load_2d(base + 2 * A_BYTES, &mBhi, kb * BK, kg * (S::KPT * S::CPK), fb);
-            tma_load_2d(base + 2 * A_BYTES + B_BYTES, &mBlo, kb * BK, kg * (S::KPT * S::CPK), fb);
-            issued[s] = (int)(it / STAGES) + 1;
+            tma_load_2d(base, &mAhi, kb * O::BK, qt * BM, fb);
+            tma_load_2d(base + A_BYTES, &mAlo, kb * O::BK, qt * BM, fb);
+            tma_load_2d(base + 2 * A_BYTES, &mBhi, kb * O::BK, kg * (S::KPT * S::CPK), fb);
+            tma_load_2d(base + 2 * A_BYTES + B_BYTES, &mBlo, kb * O::BK, kg * (S::KPT * S::CPK), fb);
+            if (s == 0)
+              issued0 = (int)(it / STAGES) + 1;
+            else
+              issued1 = (int)(it / STAGES) + 1;
           }
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -368,9 +579,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
     // drain: every issued copy must land before the CTA exits
-    if (lane == 0)
-      for (int s = 0; s < STAGES; s++)
-        if (issued[s] > 0) drain_bar(smem_u32(&bar_full[s]), (uint32_t)((issued[s] - 1) & 1));
+    if (lane == 0) {
+      if (issued0 > 0) drain_bar(smem_u32(&bar_full[0]), (uint32_t)((issued0 - 1) & 1));
+      if (issued1 > 0) drain_bar(smem_u32(&bar_full[1]), (uint32_t)((issued1 - 1) & 1));
+    }
     __syncwarp();
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
@@ -396,13 +608,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t base = smem0 + s * STAGE_BYTES;
             const uint64_t dAh = sdesc_sw128(base), dAl = sdesc_sw128(base + A_BYTES);
             const uint64_t dBh = sdesc_sw128(base + 2 * A_BYTES), dBl = sdesc_sw128(base + 2 * A_BYTES + B_BYTES);
-            const int ksteps = min(BK, a.kpad - kb * BK) / 16;
+            const int ksteps = min(O::BK, a.kpad - kb * O::BK) / O::KSTEP;
             for (int ks = 0; ks < ksteps; ks++) {
-              const uint64_t off = (uint64_t)((ks * 32) >> 4);
+              const uint64_t off = (uint64_t)((ks * 32) >> 4);  // 32 bytes of K per MMA
               const uint32_t acc = (kb == 0 && ks == 0) ? 0u : 1u;
-              umma_bf16(dcol, dAl + off, dBh + off, acc);
-              umma_bf16(dcol, dAh + off, dBl + off, 1u);
-              umma_bf16(dcol, dAh + off, dBh + off, 1u);
+              umma<OP>(dcol, dAl + off, dBh + off, acc);
+              umma<OP>(dcol, dAh + off, dBl + off, 1u);
+              umma<OP>(dcol, dAh + off, dBh + off, 1u);
             }
             umma_commit(smem_u32(&bar_empty[s]));
           }
@@ -431,7 +643,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool ok = wait_bar(smem_u32(&bar_tfull[ts]), tpar, abort_flag, a.dstatus);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      const int kg = item / a.nqt, qt = item % a.nqt;
+      int kg, qt;
+      item_coords(a, item, kg, qt);
       const int q = qt * BM + quad * 32 + lane;
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + ts * BN + slot * 128;
 #pragma unroll 1
@@ -453,38 +666,55 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ------------------------------------------------------- operand builders
-// A[q][kk] (K-major bf16 hi/lo): kk = 2r + t, value cos / sin of 2 pi (q.R_r mod 1).
-__global__ void k_build_a(int nq, int nR, int kpad, const double *__restrict__ q, const int *__restrict__ R,
-                          __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+template <typename T>
+__device__ __forceinline__ void split_store(double v, T *hi, T *lo, size_t i);
+template <>
+__device__ __forceinline__ void split_store<__nv_bfloat16>(double v, __nv_bfloat16 *hi, __nv_bfloat16 *lo, size_t i) {
+  const __nv_bfloat16 h = __double2bfloat16(v);
+  hi[i] = h;
+  lo[i] = __double2bfloat16(v - (double)__bfloat162float(h));
+}
+// tf32 term: an fp32 with its 13 low mantissa bits cleared after rounding to nearest
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+  return __uint_as_float(u);
+}
+template <>
+__device__ __forceinline__ void split_store<float>(double v, float *hi, float *lo, size_t i) {
+  const float h = tf32_round((float)v);
+  hi[i] = h;
+  lo[i] = tf32_round((float)(v - (double)h));
+}
+
+// A[q][kk] (K-major hi/lo): kk = 2r + t, value cos / sin of 2 pi (q.R_r mod 1).
+template <typename T>
+__global__ void k_build_a(int nq, int nR, int kpad, const double *__restrict__ q, const int *__restrict__ R, T *hi,
+                          T *lo) {
   size_t n = (size_t)nq * kpad;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
     int kk = (int)(idx % kpad);
     int iq = (int)(idx / kpad);
-    float v = 0.0f;
+    double d = 0.0;
     if (kk < 2 * nR) {
       int r = kk >> 1;
       double x = q[3 * iq] * R[3 * r] + q[3 * iq + 1] * R[3 * r + 1] + q[3 * iq + 2] * R[3 * r + 2];
       x -= rint(x);
       double s, c;
       sincospi(2.0 * x, &s, &c);
-      double d = (kk & 1) ? s : c;
-      __nv_bfloat16 h = __double2bfloat16(d);
-      hi[idx] = h;
-      lo[idx] = __double2bfloat16(d - (double)__bfloat162float(h));
-      continue;
+      d = (kk & 1) ? s : c;
     }
-    hi[idx] = __float2bfloat16(v);
-    lo[idx] = __float2bfloat16(v);
+    split_store<T>(d, hi, lo, idx);
   }
 }
 
-// B[k][col][kk] (K-major bf16 hi/lo) of the real GEMM:
+// B[k][col][kk] (K-major hi/lo) of the real GEMM:
 //   col = 2c + s (s: re/im of output column c), kk = 2r + t (t: re/im of P_q(R_r)),
 //   (s,t) = (0,0): Re b, (0,1): -Im b, (1,0): Im b, (1,1): Re b,  b = B_k[r][c].
 // Output columns c: [0, nw^2) H(k+q)_ij, then (a, j, n) of g_a(k,q) U_k.
+template <typename T>
 __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad,
-                          const cx<float> *__restrict__ BH, const cx<float> *__restrict__ Bg, __nv_bfloat16 *hi,
-                          __nv_bfloat16 *lo) {
+                          const cx<float> *__restrict__ BH, const cx<float> *__restrict__ Bg, T *hi, T *lo) {
   const int nw2 = nw * nw;
   const int nc = nw2 * (nm + 1);
   size_t n = (size_t)nk_pad * cpk * kpad;
@@ -499,9 +729,7 @@ __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, i
       cx<float> b = c < nw2 ? BH[((size_t)k * nR + r) * nw2 + c] : Bg[((size_t)k * nR + r) * nm * nw2 + (c - nw2)];
       v = s == 0 ? (t == 0 ? b.x : -b.y) : (t == 0 ? b.y : b.x);
     }
-    __nv_bfloat16 h = __float2bfloat16(v);
-    hi[idx] = h;
-    lo[idx] = __float2bfloat16(v - __bfloat162float(h));
+    split_store<T>((double)v, hi, lo, idx);
   }
 }
 
@@ -530,26 +758,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D bf16 tensor [rows][inner] (inner contiguous), box [box_rows][64], 128-byte swizzle.
-bool make_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+// 2D tensor [rows][inner] (inner contiguous), box [box_rows][128 bytes], 128-byte swizzle.
+bool make_map(CUtensorMap *map, const void *base, int op, uint64_t inner, uint64_t rows, uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
+  const int esz = op == TC_OP_BF16 ? 2 : 4;
   cuuint64_t dims[2] = {inner, rows};
-  cuuint64_t strides[1] = {inner * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  cuuint64_t strides[1] = {inner * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(ROWB / esz), box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(map, op == TC_OP_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
 bool shape_info(int nw, int nm, int &cpk, int &kpt) {
-#define EPW_TC_SHAPE(W, M)            \
-  if (nw == W && nm == M) {           \
-    cpk = Shape<W, M>::CPK;           \
-    kpt = Shape<W, M>::KPT;           \
-    return true;                      \
+#define EPW_TC_SHAPE(W, M)  \
+  if (nw == W && nm == M) { \
+    cpk = Shape<W, M>::CPK; \
+    kpt = Shape<W, M>::KPT; \
+    return true;            \
   }
   EPW_TC_SHAPE(4, 3)
   EPW_TC_SHAPE(1, 3)
@@ -558,13 +787,13 @@ bool shape_info(int nw, int nm, int &cpk, int &kpt) {
   return false;
 }
 
-template <int NW, int NM>
+template <int OP, int NW, int NM>
 cudaError_t launch_tc(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
                       const TcArgs &a, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_tc_linewidth<NW, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        cudaFuncSetAttribute(k_tc_linewidth<OP, NW, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -573,23 +802,40 @@ cudaError_t launch_tc(const CUtensorMap &ah, const CUtensorMap &al, const CUtens
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int items = a.nkg * a.nqt;
   int grid = items < sms ? items : sms;
-  k_tc_linewidth<NW, NM><<<grid, NTHREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
+  k_tc_linewidth<OP, NW, NM><<<grid, NTHREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
   return cudaGetLastError();
+}
+
+template <int OP>
+cudaError_t launch_tc_shape(int nw, int nm, const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh,
+                            const CUtensorMap &bl, const TcArgs &a, cudaStream_t st) {
+  if (nw == 4 && nm == 3) return launch_tc<OP, 4, 3>(ah, al, bh, bl, a, st);
+  if (nw == 1 && nm == 3) return launch_tc<OP, 1, 3>(ah, al, bh, bl, a, st);
+  if (nw == 2 && nm == 3) return launch_tc<OP, 2, 3>(ah, al, bh, bl, a, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, TcBuffers &b) {
+bool tc_supported(const epw_model *m) {
+  int cpk, kpt;
+  return m->same_ep && shape_info(m->nw, m->nm, cpk, kpt);
+}
+
+epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffers &b) {
   b = TcBuffers{};
+  b.op = op;
   b.ok = m->same_ep && shape_info(m->nw, m->nm, b.cpk, b.kpt);
   if (!b.ok) return EPW_OK;
-  b.kpad = (2 * m->nRe + 15) / 16 * 16;
+  const int esz = op == TC_OP_BF16 ? 2 : 4;
+  const int kal = op == TC_OP_BF16 ? 16 : 8;  // K per MMA
+  b.kpad = (2 * m->nRe + kal - 1) / kal * kal;
   b.nk_pad = (nk + b.kpt - 1) / b.kpt * b.kpt;
   b.nqt = (nq + BM - 1) / BM;
-  b.Ahi = A.take<__nv_bfloat16>((size_t)nq * b.kpad);
-  b.Alo = A.take<__nv_bfloat16>((size_t)nq * b.kpad);
-  b.Bhi = A.take<__nv_bfloat16>((size_t)b.nk_pad * b.cpk * b.kpad);
-  b.Blo = A.take<__nv_bfloat16>((size_t)b.nk_pad * b.cpk * b.kpad);
+  b.Ahi = A.take<char>((size_t)nq * b.kpad * esz);
+  b.Alo = A.take<char>((size_t)nq * b.kpad * esz);
+  b.Bhi = A.take<char>((size_t)b.nk_pad * b.cpk * b.kpad * esz);
+  b.Blo = A.take<char>((size_t)b.nk_pad * b.cpk * b.kpad * esz);
   b.nbT = A.take<float>((size_t)nq * m->nm);
   b.partial = A.take<double>((size_t)nk * 4 * b.nqt * m->nw);
   return EPW_OK;
@@ -604,14 +850,23 @@ epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, con
   (void)Uk;
   if (!b.ok) return EPW_ERR_UNSUPPORTED;
   const int nR = m->nRe;
+  const int op = b.op;
+  const int esz = op == TC_OP_BF16 ? 2 : 4;
   {
     size_t n = (size_t)nq * b.kpad;
-    k_build_a<<<grid_for(n, 256), 256, 0, st>>>(nq, nR, b.kpad, q, m->Re, (__nv_bfloat16 *)b.Ahi,
-                                                 (__nv_bfloat16 *)b.Alo);
+    if (op == TC_OP_BF16)
+      k_build_a<__nv_bfloat16><<<grid_for(n, 256), 256, 0, st>>>(nq, nR, b.kpad, q, m->Re, (__nv_bfloat16 *)b.Ahi,
+                                                                  (__nv_bfloat16 *)b.Alo);
+    else
+      k_build_a<float><<<grid_for(n, 256), 256, 0, st>>>(nq, nR, b.kpad, q, m->Re, (float *)b.Ahi, (float *)b.Alo);
     epw_count_launch();
     n = (size_t)b.nk_pad * b.cpk * b.kpad;
-    k_build_b<<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, BH32, Bg32,
-                                                 (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo);
+    if (op == TC_OP_BF16)
+      k_build_b<__nv_bfloat16><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, BH32,
+                                                                  Bg32, (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo);
+    else
+      k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, BH32, Bg32,
+                                                          (float *)b.Bhi, (float *)b.Blo);
     epw_count_launch();
     n = (size_t)nq * m->nm;
     k_bose_table<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nm, omegaT, par->T_K, b.nbT);
@@ -619,9 +874,9 @@ epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, con
   }
   CUtensorMap ah, al, bh, bl;
   std::memset(&ah, 0, sizeof(ah));
-  if (!make_map(&ah, b.Ahi, b.kpad, nq, BM) || !make_map(&al, b.Alo, b.kpad, nq, BM) ||
-      !make_map(&bh, b.Bhi, b.kpad, (uint64_t)b.nk_pad * b.cpk, BN) ||
-      !make_map(&bl, b.Blo, b.kpad, (uint64_t)b.nk_pad * b.cpk, BN))
+  if (!make_map(&ah, b.Ahi, op, b.kpad, nq, BM) || !make_map(&al, b.Alo, op, b.kpad, nq, BM) ||
+      !make_map(&bh, b.Bhi, op, b.kpad, (uint64_t)b.nk_pad * b.cpk, BN) ||
+      !make_map(&bl, b.Blo, op, b.kpad, (uint64_t)b.nk_pad * b.cpk, BN))
     return EPW_ERR_CUDA;
   TcArgs a;
   a.nk = nk;
@@ -629,7 +884,15 @@ epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, con
   a.nqt = b.nqt;
   a.nkg = b.nk_pad / b.kpt;
   a.kpad = b.kpad;
-  a.nkb = (b.kpad + BK - 1) / BK;
+  const int bk = ROWB / esz;
+  a.nkb = (b.kpad + bk - 1) / bk;
+  {
+    const size_t atile = (size_t)BM * b.kpad * esz * 2;
+    int qb = (int)(A_BLOCK_BYTES / atile);
+    if (qb < 152) qb = 152;
+    if (qb > b.nqt) qb = b.nqt;
+    a.qblock = qb < 1 ? 1 : qb;
+  }
   a.epsk = epsk;
   a.omegaT = omegaT;
   a.nbT = b.nbT;
@@ -642,16 +905,9 @@ epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, con
   a.omega_min = (float)par->omega_min_eV;
   a.partial = b.partial;
   a.dstatus = m->dstatus;
-  cudaError_t e = cudaSuccess;
   epw_timing_begin(const_cast<epw_model *>(m), st);
-  if (m->nw == 4 && m->nm == 3)
-    e = launch_tc<4, 3>(ah, al, bh, bl, a, st);
-  else if (m->nw == 1 && m->nm == 3)
-    e = launch_tc<1, 3>(ah, al, bh, bl, a, st);
-  else if (m->nw == 2 && m->nm == 3)
-    e = launch_tc<2, 3>(ah, al, bh, bl, a, st);
-  else
-    return EPW_ERR_UNSUPPORTED;
+  cudaError_t e = op == TC_OP_BF16 ? launch_tc_shape<TC_OP_BF16>(m->nw, m->nm, ah, al, bh, bl, a, st)
+                                   : launch_tc_shape<TC_OP_TF32>(m->nw, m->nm, ah, al, bh, bl, a, st);
   epw_timing_end(const_cast<epw_model *>(m), st);
   epw_count_launch();
   if (e != cudaSuccess) return EPW_ERR_CUDA;

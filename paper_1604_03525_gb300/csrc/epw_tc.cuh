@@ -1,18 +1,25 @@
-// Tensor-core (tcgen05, split-BF16) form of the fused linewidth kernel.
+// Tensor-core (tcgen05) form of the fused linewidth kernel.
 #pragma once
 #include "epw_internal.cuh"
 
+// Operand split of the tensor-core contraction.
+#define TC_OP_BF16 0  // two bfloat16 terms, kind::f16
+#define TC_OP_TF32 1  // two tf32 terms, kind::tf32
+
 struct TcBuffers {
-  void *Ahi, *Alo;   // q phases, bf16 split, K-major [nq][kpad]
-  void *Bhi, *Blo;   // k-side vertex, bf16 split, K-major [nk_pad][cpk][kpad]
+  void *Ahi, *Alo;   // q phases, split, K-major [nq][kpad]
+  void *Bhi, *Blo;   // k-side vertex, split, K-major [nk_pad][cpk][kpad]
   float *nbT;        // Bose factors [nm][nq]
   double *partial;   // [nk][4*nqt][nw]
-  int kpad, cpk, nk_pad, nqt, kpt;
+  int op, kpad, cpk, nk_pad, nqt, kpt;
   bool ok;           // shape has a tensor-core kernel
 };
 
+// True when the model's shape has a tensor-core kernel (Re == Rp sets and a
+// compiled (nw, 3nat) pair).
+bool tc_supported(const epw_model *m);
 // Lay out (or measure, with a null arena base) the buffers of the tensor-core path.
-epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, TcBuffers &b);
+epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffers &b);
 // Im Sigma [nk][nw] into `out` (device) from the shared preparation outputs.
 epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, const double *q, const double *wq,
                         const epw_params *par, const cx<double> *PkRM, const double *epsk, const cx<double> *Uk,
