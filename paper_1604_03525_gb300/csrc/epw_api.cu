@@ -508,8 +508,11 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
   g_err[0] = 0;
   epw_model *m = const_cast<epw_model *>(mc);
   CKS(check_common(m, nk, k, nq, q));
-  if (precision != EPW_FP64 && precision != EPW_FP32)
-    return fail(EPW_ERR_UNSUPPORTED, "epw_interp_g supports EPW_FP64 and EPW_FP32");
+  if (precision < EPW_FP64 || precision > EPW_TF32X3) return fail(EPW_ERR_INVALID_ARG, "unknown precision");
+  const bool tc = precision == EPW_BF16X3 || precision == EPW_TF32X3;
+  if (tc && !tc_supported(m))
+    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core kernel for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
+  const int wprec = tc ? EPW_FP32 : precision;  // precision of the shared preparation
   if (!(omega_min >= 0.0)) return fail(EPW_ERR_INVALID_ARG, "omega_min must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
   if (nk == 0 && nq == 0) return EPW_OK;
@@ -517,20 +520,24 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
   const size_t nw = m->nw, nm = m->nm;
   const bool s_ek = eps_k && !is_device_ptr(eps_k), s_ekq = eps_kq && !is_device_ptr(eps_kq);
   const bool s_om = omega && !is_device_ptr(omega), s_g = g && !is_device_ptr(g);
-  auto plan = [&](Arena &A, Prep &p, double *&ekd, double *&ekqd, double *&omd, double *&gd) {
-    plan_prep(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, precision, sk, sq, false, true, p);
+  TcBuffers tcb;
+  auto plan = [&](Arena &A, Prep &p, double *&ekd, double *&ekqd, double *&omd, double *&gd) -> epw_status {
+    plan_prep(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, wprec, sk, sq, false, true, p);
     ekd = s_ek ? A.take<double>((size_t)nk * nw) : eps_k;
     ekqd = s_ekq ? A.take<double>((size_t)nk * nq * nw) : eps_kq;
     omd = s_om ? A.take<double>((size_t)nq * nm) : omega;
     gd = s_g ? (double *)A.take<cx<double>>((size_t)nk * nq * nm * nw * nw) : g;
+    if (tc) return tc_plan(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, precision == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32,
+                           tcb);
+    return EPW_OK;
   };
   Arena A{nullptr, 0, 0};
   Prep p;
   double *ekd, *ekqd, *omd, *gd;
-  plan(A, p, ekd, ekqd, omd, gd);
+  CKS(plan(A, p, ekd, ekqd, omd, gd));
   CKS(ensure_ws(m, A.off));
   A = Arena{(char *)m->ws, m->ws_bytes, 0};
-  plan(A, p, ekd, ekqd, omd, gd);
+  CKS(plan(A, p, ekd, ekqd, omd, gd));
   const double *kd = k, *qd = q;
   if (sk) {
     CK(cudaMemcpyAsync(p.kd, k, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
@@ -540,9 +547,13 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
     CK(cudaMemcpyAsync(p.qd, q, sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, st));
     qd = p.qd;
   }
-  CKS(run_prep(m, nk, kd, nq, qd, precision, omega_min, nk > 0, p, omd, st));
+  CKS(run_prep(m, nk, kd, nq, qd, wprec, omega_min, nk > 0, p, omd, st));
   if (ekd && nk > 0) CK(cudaMemcpyAsync(ekd, p.epsk, sizeof(double) * nk * nw, cudaMemcpyDeviceToDevice, st));
-  if (nk > 0 && nq > 0 && (ekqd || gd)) {
+  if (tc && nk > 0 && nq > 0 && (ekqd || gd)) {
+    epw_status s = tc_interp(m, nk, nq, qd, omega_min, p.epsk, p.omegaT, (const cx<float> *)p.ET,
+                             (const cx<float> *)p.Bg, (const cx<float> *)p.BH, tcb, ekqd, gd, st);
+    if (s != EPW_OK) return fail(s, "tensor-core interpolation failed");
+  } else if (nk > 0 && nq > 0 && (ekqd || gd)) {
     PairArgs a;
     std::memset(&a, 0, sizeof(a));
     a.nk = nk;

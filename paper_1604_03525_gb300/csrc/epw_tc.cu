@@ -360,7 +360,9 @@ struct TcArgs {
   const float2 *ET;      // [nm*nm][nq]
   const double *wq;      // [nq] or null
   float EF, invkT, inv_sigma, gnorm, omega_min;
-  double *partial;  // [nk][4*nqt][nw]
+  double *partial;  // [nk][4*nqt][nw]            (linewidth)
+  double *eps_kq;   // [nk][nq][nw] or null        (interp)
+  double2 *gout;    // [nk][nq][nm][nw][nw] or null (interp)
   unsigned *dstatus;
 };
 
@@ -390,7 +392,9 @@ __device__ __forceinline__ void item_coords(const TcArgs &a, int item, int &kg, 
 
 // ------------------------------------------------------------------ epilogue
 // One (k,q) pair per thread; the accumulator holds [H(k+q) | (g_a U_k)_a=0..NM-1].
-template <int NW, int NM>
+// MODE 0: linewidth terms summed over the warp's q rows; MODE 1: write e_k+q
+// (ascending) and g_mn,nu.
+template <int NW, int NM, int MODE>
 __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, int q, int k, bool valid, int quad,
                                               int qt) {
   using S = Shape<NW, NM>;
@@ -447,10 +451,31 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   if (!conv && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
   float em[NW], fm[NW];
 #pragma unroll
-  for (int m = 0; m < NW; m++) {
-    em[m] = H.a[m][m].x;
-    fm[m] = fermi_f(em[m] - a.EF, a.invkT);
+  for (int m = 0; m < NW; m++) em[m] = H.a[m][m].x;
+  if constexpr (MODE == 1) {
+    // ascending order (odd-even transposition network), eigenvector columns follow
+#pragma unroll
+    for (int r = 0; r < NW; r++)
+#pragma unroll
+      for (int m = r & 1; m + 1 < NW; m += 2) {
+        const bool sw = em[m + 1] < em[m];
+        const float lo = sw ? em[m + 1] : em[m], hi = sw ? em[m] : em[m + 1];
+        em[m] = lo;
+        em[m + 1] = hi;
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+          const cx<float> v0 = V[i][m], v1 = V[i][m + 1];
+          V[i][m] = sw ? v1 : v0;
+          V[i][m + 1] = sw ? v0 : v1;
+        }
+      }
+    if (valid && a.eps_kq) {
+#pragma unroll
+      for (int m = 0; m < NW; m++) a.eps_kq[((size_t)k * a.nq + q) * NW + m] = (double)em[m];
+    }
   }
+#pragma unroll
+  for (int m = 0; m < NW; m++) fm[m] = fermi_f(em[m] - a.EF, a.invkT);
   float acc[NW];
 #pragma unroll
   for (int n = 0; n < NW; n++) acc[n] = 0.0f;
@@ -492,6 +517,11 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
         cx<float> y = mkc(0.0f, 0.0f);
 #pragma unroll
         for (int i = 0; i < NW; i++) cfma(y, conjc(V[i][m]), G[i][n]);
+        if constexpr (MODE == 1) {
+          if (valid && a.gout)
+            a.gout[(((size_t)k * a.nq + q) * NM + nu) * NW * NW + m * NW + n] = make_double2(y.x, y.y);
+          continue;
+        }
         const float g2 = cabs2(y);
         const float xd = ek[n] - em[m];
         const float xp = xd + w[nu], xm = xd - w[nu];
@@ -500,6 +530,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
       }
     }
   }
+  if constexpr (MODE == 1) return;
 #pragma unroll
   for (int n = 0; n < NW; n++) {
     double v = (double)acc[n] * wqi;
@@ -509,7 +540,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   }
 }
 
-template <int OP, int NW, int NM>
+template <int OP, int NW, int NM, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_linewidth(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                    const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcArgs a) {
@@ -650,7 +681,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll 1
       for (int j = 0; j < S::KPS; j++) {
         const int k = kg * S::KPT + slot * S::KPS + j;
-        epilogue_pair<NW, NM>(a, tbase + j * S::CPK, q, k, q < a.nq && k < a.nk, quad, qt);
+        epilogue_pair<NW, NM, MODE>(a, tbase + j * S::CPK, q, k, q < a.nq && k < a.nk, quad, qt);
       }
       tc_fence_before();
       __syncwarp();
@@ -787,13 +818,13 @@ bool shape_info(int nw, int nm, int &cpk, int &kpt) {
   return false;
 }
 
-template <int OP, int NW, int NM>
+template <int OP, int NW, int NM, int MODE>
 cudaError_t launch_tc(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
                       const TcArgs &a, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_tc_linewidth<OP, NW, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_linewidth<OP, NW, NM, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -802,16 +833,16 @@ cudaError_t launch_tc(const CUtensorMap &ah, const CUtensorMap &al, const CUtens
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int items = a.nkg * a.nqt;
   int grid = items < sms ? items : sms;
-  k_tc_linewidth<OP, NW, NM><<<grid, NTHREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
+  k_tc_linewidth<OP, NW, NM, MODE><<<grid, NTHREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
   return cudaGetLastError();
 }
 
-template <int OP>
+template <int OP, int MODE>
 cudaError_t launch_tc_shape(int nw, int nm, const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh,
                             const CUtensorMap &bl, const TcArgs &a, cudaStream_t st) {
-  if (nw == 4 && nm == 3) return launch_tc<OP, 4, 3>(ah, al, bh, bl, a, st);
-  if (nw == 1 && nm == 3) return launch_tc<OP, 1, 3>(ah, al, bh, bl, a, st);
-  if (nw == 2 && nm == 3) return launch_tc<OP, 2, 3>(ah, al, bh, bl, a, st);
+  if (nw == 4 && nm == 3) return launch_tc<OP, 4, 3, MODE>(ah, al, bh, bl, a, st);
+  if (nw == 1 && nm == 3) return launch_tc<OP, 1, 3, MODE>(ah, al, bh, bl, a, st);
+  if (nw == 2 && nm == 3) return launch_tc<OP, 2, 3, MODE>(ah, al, bh, bl, a, st);
   return cudaErrorInvalidValue;
 }
 
@@ -841,13 +872,10 @@ epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffe
   return EPW_OK;
 }
 
-epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, const double *q, const double *wq,
-                        const epw_params *par, const cx<double> *PkRM, const double *epsk, const cx<double> *Uk,
-                        const double *omegaT, const cx<float> *ET32, const cx<float> *Bg32, const cx<float> *BH32,
-                        TcBuffers &b, double *out, cudaStream_t st) {
-  (void)k;
-  (void)PkRM;
-  (void)Uk;
+static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const double *q, const double *wq,
+                         const epw_params *par, const double *epsk, const double *omegaT, const cx<float> *ET32,
+                         const cx<float> *Bg32, const cx<float> *BH32, TcBuffers &b, double *out, double *eps_kq,
+                         double *gout, cudaStream_t st) {
   if (!b.ok) return EPW_ERR_UNSUPPORTED;
   const int nR = m->nRe;
   const int op = b.op;
@@ -904,15 +932,44 @@ epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, con
   a.gnorm = (float)(1.0 / (par->sigma_eV * 1.7724538509055160273));
   a.omega_min = (float)par->omega_min_eV;
   a.partial = b.partial;
+  a.eps_kq = eps_kq;
+  a.gout = (double2 *)gout;
   a.dstatus = m->dstatus;
-  epw_timing_begin(const_cast<epw_model *>(m), st);
-  cudaError_t e = op == TC_OP_BF16 ? launch_tc_shape<TC_OP_BF16>(m->nw, m->nm, ah, al, bh, bl, a, st)
-                                   : launch_tc_shape<TC_OP_TF32>(m->nw, m->nm, ah, al, bh, bl, a, st);
-  epw_timing_end(const_cast<epw_model *>(m), st);
+  cudaError_t e;
+  if (mode == 0) {
+    epw_timing_begin(const_cast<epw_model *>(m), st);
+    e = op == TC_OP_BF16 ? launch_tc_shape<TC_OP_BF16, 0>(m->nw, m->nm, ah, al, bh, bl, a, st)
+                         : launch_tc_shape<TC_OP_TF32, 0>(m->nw, m->nm, ah, al, bh, bl, a, st);
+    epw_timing_end(const_cast<epw_model *>(m), st);
+  } else {
+    e = op == TC_OP_BF16 ? launch_tc_shape<TC_OP_BF16, 1>(m->nw, m->nm, ah, al, bh, bl, a, st)
+                         : launch_tc_shape<TC_OP_TF32, 1>(m->nw, m->nm, ah, al, bh, bl, a, st);
+  }
   epw_count_launch();
   if (e != cudaSuccess) return EPW_ERR_CUDA;
-  launch_finalize(nk, 4 * b.nqt, m->nw, b.partial, out, st);
+  if (mode == 0) launch_finalize(nk, 4 * b.nqt, m->nw, b.partial, out, st);
   return EPW_OK;
+}
+
+epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, const double *q, const double *wq,
+                        const epw_params *par, const cx<double> *PkRM, const double *epsk, const cx<double> *Uk,
+                        const double *omegaT, const cx<float> *ET32, const cx<float> *Bg32, const cx<float> *BH32,
+                        TcBuffers &b, double *out, cudaStream_t st) {
+  (void)k;
+  (void)PkRM;
+  (void)Uk;
+  return tc_run(0, m, nk, nq, q, wq, par, epsk, omegaT, ET32, Bg32, BH32, b, out, nullptr, nullptr, st);
+}
+
+epw_status tc_interp(const epw_model *m, int nk, int nq, const double *q, double omega_min, const double *epsk,
+                     const double *omegaT, const cx<float> *ET32, const cx<float> *Bg32, const cx<float> *BH32,
+                     TcBuffers &b, double *eps_kq, double *g, cudaStream_t st) {
+  epw_params par;
+  std::memset(&par, 0, sizeof(par));
+  par.T_K = 0.0;
+  par.sigma_eV = 1.0;
+  par.omega_min_eV = omega_min;
+  return tc_run(1, m, nk, nq, q, nullptr, &par, epsk, omegaT, ET32, Bg32, BH32, b, nullptr, eps_kq, g, st);
 }
 
 void tc_free(epw_model *) {}

@@ -25,4 +25,9 @@ epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, con
                         const epw_params *par, const cx<double> *PkRM, const double *epsk, const cx<double> *Uk,
                         const double *omegaT, const cx<float> *ET32, const cx<float> *Bg32, const cx<float> *BH32,
                         TcBuffers &b, double *out, cudaStream_t st);
+// e_k+q [nk][nq][nw] (ascending) and g [nk][nq][nm][nw][nw] (device, either may be
+// null) from the same contraction and eigensolve as tc_linewidth.
+epw_status tc_interp(const epw_model *m, int nk, int nq, const double *q, double omega_min, const double *epsk,
+                     const double *omegaT, const cx<float> *ET32, const cx<float> *Bg32, const cx<float> *BH32,
+                     TcBuffers &b, double *eps_kq, double *g, cudaStream_t st);
 void tc_free(epw_model *m);
