@@ -260,14 +260,22 @@ __device__ __forceinline__ Rot rot_params(const Herm<N> &H, int p, int q) {
   const float d = H.a[q][q].x - H.a[p][p].x;
   const float m2 = fmaf(apq.x, apq.x, apq.y * apq.y);
   const float x = fmaf(d, d, 4.0f * m2);
-  const float sq = x * rsqrt_approx(fmaxf(x, 1e-37f));
+  // hardware approximations refined by one Newton step each (to ~1 ulp), so
+  // that the rotation stays unitary and consistent with the diagonal update
+  const float xs = fmaxf(x, 1e-37f);
+  float ri = rsqrt_approx(xs);
+  ri = ri * fmaf(-0.5f * xs * ri, ri, 1.5f);
+  const float sq = x * ri;
   const float den = fmaxf(fabsf(d) + sq, 1e-30f);
-  const float rden = rcp_approx(den);
+  float rden = rcp_approx(den);
+  rden = rden * fmaf(-den, rden, 2.0f);
   const float sg = d >= 0.0f ? 2.0f : -2.0f;
   const float tmag = 2.0f * m2 * rden;  // |t| |a_pq|
   const float t2 = tmag * (2.0f * rden);
   Rot r;
-  r.c = rsqrt_approx(1.0f + t2);
+  const float u = 1.0f + t2;
+  float c = rsqrt_approx(u);
+  r.c = c * fmaf(-0.5f * u * c, c, 1.5f);
   r.tb = 0.5f * sg * tmag;
   const float kap = sg * rden * r.c;
   r.se = mkc(kap * apq.x, kap * apq.y);
