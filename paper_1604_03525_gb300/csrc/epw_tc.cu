@@ -410,24 +410,10 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   const int qq = q < a.nq ? q : 0;
   const int kk = k < a.nk ? k : 0;
   // per-q and per-k data first, so their latency overlaps the eigensolve
-  float w[NM], nb[NM];
-  cx<float> E[NM][NM];
-#pragma unroll
-  for (int v = 0; v < NM; v++) {
-    w[v] = (float)__ldg(a.omegaT + (size_t)v * a.nq + qq);
-    nb[v] = __ldg(a.nbT + (size_t)v * a.nq + qq);
-  }
-#pragma unroll
-  for (int al = 0; al < NM; al++)
-#pragma unroll
-    for (int v = 0; v < NM; v++) {
-      const float2 e = __ldg(a.ET + ((size_t)al * NM + v) * a.nq + qq);
-      E[al][v] = mkc(e.x, e.y);
-    }
   float ek[NW];
 #pragma unroll
   for (int n = 0; n < NW; n++) ek[n] = (float)__ldg(a.epsk + (size_t)kk * NW + n);
-  const double wqi = valid ? (a.wq ? a.wq[q] : 1.0 / a.nq) * (double)a.gnorm : 0.0;
+  const float wqf = valid ? (float)(a.wq ? a.wq[q] : 1.0 / a.nq) : 0.0f;
 
   constexpr bool ONE_LOAD = S::CPK <= 32;
   float all[ONE_LOAD ? S::CPK : 8];
@@ -488,9 +474,18 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
 #pragma unroll
   for (int n = 0; n < NW; n++) acc[n] = 0.0f;
   const float s2 = a.inv_sigma * a.inv_sigma * 1.4426950408889634f;
-#pragma unroll
+  // one mode per iteration (not unrolled: keeps the code within the instruction cache)
+#pragma unroll 1
   for (int nu = 0; nu < NM; nu++) {
-    const bool keep = (w[nu] >= a.omega_min) && (w[nu] > 0.0f);
+    const float wnu = (float)__ldg(a.omegaT + (size_t)nu * a.nq + qq);
+    const float nbnu = __ldg(a.nbT + (size_t)nu * a.nq + qq);
+    cx<float> E[NM];
+#pragma unroll
+    for (int al = 0; al < NM; al++) {
+      const float2 e = __ldg(a.ET + ((size_t)al * NM + nu) * a.nq + qq);
+      E[al] = mkc(e.x, e.y);
+    }
+    const bool keep = (wnu >= a.omega_min) && (wnu > 0.0f);
     cx<float> G[NW][NW];
 #pragma unroll
     for (int i = 0; i < NW; i++)
@@ -504,7 +499,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
 #pragma unroll
           for (int j = 0; j < NW; j++) {
             const int o = H2 * (1 + al) + 2 * (i * NW + j);
-            cfma(G[i][j], E[al][nu], mkc(all[o], all[o + 1]));
+            cfma(G[i][j], E[al], mkc(all[o], all[o + 1]));
           }
       } else {
         float x[H2];
@@ -512,14 +507,14 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
 #pragma unroll
         for (int i = 0; i < NW; i++)
 #pragma unroll
-          for (int j = 0; j < NW; j++) cfma(G[i][j], E[al][nu], mkc(x[2 * (i * NW + j)], x[2 * (i * NW + j) + 1]));
+          for (int j = 0; j < NW; j++) cfma(G[i][j], E[al], mkc(x[2 * (i * NW + j)], x[2 * (i * NW + j) + 1]));
       }
     }
     // |(U^dagger G)_mn|^2 with the delta terms of Eq. (linewidthel)
 #pragma unroll
     for (int m = 0; m < NW; m++) {
-      const float cp = keep ? nb[nu] + fm[m] : 0.0f;
-      const float cm = keep ? nb[nu] + 1.0f - fm[m] : 0.0f;
+      const float cp = keep ? nbnu + fm[m] : 0.0f;
+      const float cm = keep ? nbnu + 1.0f - fm[m] : 0.0f;
 #pragma unroll
       for (int n = 0; n < NW; n++) {
         cx<float> y = mkc(0.0f, 0.0f);
@@ -532,7 +527,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
         }
         const float g2 = cabs2(y);
         const float xd = ek[n] - em[m];
-        const float xp = xd + w[nu], xm = xd - w[nu];
+        const float xp = xd + wnu, xm = xd - wnu;
         const float d = cp * ex2_approx(-xp * xp * s2) + cm * ex2_approx(-xm * xm * s2);
         acc[n] = fmaf(g2, d, acc[n]);
       }
@@ -541,10 +536,12 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   if constexpr (MODE == 1) return;
 #pragma unroll
   for (int n = 0; n < NW; n++) {
-    double v = (double)acc[n] * wqi;
+    // 32 positive terms: an FP32 tree sum is accurate to a few ulp
+    float v = acc[n] * wqf;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && k < a.nk) a.partial[((size_t)k * (4 * a.nqt) + qt * 4 + quad) * NW + n] = v;
+    if ((threadIdx.x & 31) == 0 && k < a.nk)
+      a.partial[((size_t)k * (4 * a.nqt) + qt * 4 + quad) * NW + n] = (double)v * (double)a.gnorm;
   }
 }
 
@@ -736,7 +733,7 @@ __global__ void k_build_a(int nq, int nR, int kpad, const double *__restrict__ q
     int iq = (int)(idx / kpad);
     double d = 0.0;
     if (kk < 2 * nR) {
-      int r = kk >> 1;
+      int r = nR - 1 - (kk >> 1);
       double x = q[3 * iq] * R[3 * r] + q[3 * iq + 1] * R[3 * r + 1] + q[3 * iq + 2] * R[3 * r + 2];
       x -= rint(x);
       double s, c;
@@ -764,7 +761,7 @@ __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, i
     int k = (int)(rest / cpk);
     float v = 0.0f;
     if (k < nk && col < 2 * nc && kk < 2 * nR) {
-      int c = col >> 1, s = col & 1, r = kk >> 1, t = kk & 1;
+      int c = col >> 1, s = col & 1, r = nR - 1 - (kk >> 1), t = kk & 1;
       cx<float> b = c < nw2 ? BH[((size_t)k * nR + r) * nw2 + c] : Bg[((size_t)k * nR + r) * nm * nw2 + (c - nw2)];
       v = s == 0 ? (t == 0 ? b.x : -b.y) : (t == 0 ? b.y : b.x);
     }
