@@ -533,15 +533,16 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
       }
     }
   }
-  if constexpr (MODE == 1) return;
+  if constexpr (MODE == 0) {
 #pragma unroll
-  for (int n = 0; n < NW; n++) {
-    // 32 positive terms: an FP32 tree sum is accurate to a few ulp
-    float v = acc[n] * wqf;
+    for (int n = 0; n < NW; n++) {
+      // 32 positive terms: an FP32 tree sum is accurate to a few ulp
+      float v = acc[n] * wqf;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && k < a.nk)
-      a.partial[((size_t)k * (4 * a.nqt) + qt * 4 + quad) * NW + n] = (double)v * (double)a.gnorm;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0 && k < a.nk)
+        a.partial[((size_t)k * (4 * a.nqt) + qt * 4 + quad) * NW + n] = (double)v * (double)a.gnorm;
+    }
   }
 }
 
