@@ -169,6 +169,31 @@ epw_status epw_linewidth_backward(const epw_model *model, int nk, const double *
                                   const double *grad_imsigma, double *dg, double *dT, double *dEF,
                                   void *stream);
 
+/* Allocation-free variant of epw_linewidth, for callers that cannot allocate
+ * device memory: code running where cudaMalloc is not allowed or not wanted
+ * (inside a memory-pool-managed host framework, a real-time loop that must
+ * not block on the allocator, a sandbox that forbids new device allocations).
+ * The paper has no counterpart; it is an integration convenience.
+ *   - No device memory is allocated or freed by this call (no cudaMalloc,
+ *     cudaFree or allocating library routine).  Its scratch is one fixed
+ *     device array of EPW_NOALLOC_SCRATCH_BYTES that the library holds on every
+ *     GPU where it is loaded until the process exits.  Problems whose scratch
+ *     exceeds it return EPW_ERR_INVALID_ARG with the bytes needed.
+ *   - The model must already be loaded (epw_load_wannier allocates).
+ *   - k, q, wq (or NULL) and imsigma must be device pointers; precision
+ *     EPW_FP64 or EPW_FP32.  The call is asynchronous on `stream`; device-side
+ *     failures are reported by epw_sync.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents
+ *     (every value a call reads it first writes).  Calls whose work overlaps
+ *     on the GPU (different streams, threads or processes sharing a context)
+ *     race on it: serialise them. */
+#define EPW_NOALLOC_SCRATCH_BYTES (32u << 20)
+epw_status epw_linewidth_noalloc(const epw_model *model, int nk, const double *k, int nq, const double *q,
+                                 const double *wq, const epw_params *params, double *imsigma, void *stream);
+
 /* Wait for the model's work on `stream` and report device-side failures
  * (EPW_ERR_NOT_CONVERGED) raised since the previous epw_sync; clears them. */
 epw_status epw_sync(const epw_model *model, void *stream);

@@ -28,6 +28,7 @@ SIGNATURES = {
     "epw_interp_g": (I, [P, I, P, I, P, I, D, P, P, P, P, P]),
     "epw_linewidth": (I, [P, I, P, I, P, P, P, P, P]),
     "epw_linewidth_backward": (I, [P, I, P, I, P, P, P, P, P, P, P, P]),
+    "epw_linewidth_noalloc": (I, [P, I, P, I, P, P, P, P, P]),
     "epw_sync": (I, [P, P]),
     "epw_model_info": (I, [P, P, P, P, P, P]),
     "epw_launch_count": (ctypes.c_uint64, []),

@@ -149,6 +149,27 @@ class Model:
                                  _stream_of(ka, qa, wa, oa)))
         return out
 
+    def linewidth_noalloc(self, k, q, wq=None, *, T: float, EF: float, sigma: float, omega_min: float = 1e-5,
+                          precision: int = FP64, out=None):
+        """epw_linewidth_noalloc: like linewidth, but the library allocates no device memory.
+
+        For callers that must not allocate (see include/epw.h).  k, q, wq and
+        out must be CUDA tensors; out is allocated here by torch only when the
+        caller does not pass one.
+        """
+        lib = _lib.load()
+        ka, qa, wa = _Arg(k, np.float64), _Arg(q, np.float64), _Arg(wq, np.float64)
+        nk = int(np.prod(ka.keep.shape)) // 3
+        nq = int(np.prod(qa.keep.shape)) // 3
+        if out is None:
+            import torch
+            out = torch.empty((nk, self.nw), dtype=torch.float64, device=ka.keep.device)
+        oa = _Arg(out, np.float64)
+        pr = _lib.Params(float(T), float(EF), float(sigma), float(omega_min), int(precision), 0)
+        _check(lib.epw_linewidth_noalloc(self._h, nk, ka.ptr, nq, qa.ptr, wa.ptr, ctypes.byref(pr), oa.ptr,
+                                         _stream_of(ka, qa, wa, oa)))
+        return out
+
     # ---------------------------------------------------------------- interp
     def interp(self, k, q, precision: int = FP64, omega_min: float = 1e-5, want_g: bool = True):
         """(eps_k [nk,nw], eps_kq [nk,nq,nw], omega [nq,3nat], g [nk,nq,3nat,nw,nw]) as numpy arrays."""

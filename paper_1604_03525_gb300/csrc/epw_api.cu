@@ -714,3 +714,91 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   if (sk || sq || swq || scot || sdg || sdT || sdE) return read_status(m, st);
   return EPW_OK;
 }
+
+// ------------------------------------------------ allocation-free linewidth
+// Scratch for epw_linewidth_noalloc: a fixed device array that exists on every
+// GPU on which this library is loaded, for the life of the process.  Host code
+// must not hand the symbol itself to a kernel (in host code it names a host-side
+// stand-in); it uses the device address obtained once per device below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[EPW_NOALLOC_SCRATCH_BYTES];
+
+#define EPW_NOALLOC_MAX_DEVICES 64
+static std::atomic<uintptr_t> g_noalloc_ptr[EPW_NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device (looked up on the
+// first call for that device, with that device current).
+static epw_status noalloc_scratch(int dev, char **out) {
+  if (dev < 0 || dev >= EPW_NOALLOC_MAX_DEVICES) return fail(EPW_ERR_UNSUPPORTED, "device index %d too large", dev);
+  uintptr_t p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void *addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e != cudaSuccess || !addr)
+      return fail(EPW_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    p = (uintptr_t)addr;
+    g_noalloc_ptr[dev].store(p, std::memory_order_release);
+  }
+  *out = (char *)p;
+  return EPW_OK;
+}
+
+extern "C" epw_status epw_linewidth_noalloc(const epw_model *mc, int nk, const double *k, int nq, const double *q,
+                                            const double *wq, const epw_params *par, double *imsigma,
+                                            void *stream) {
+  g_err[0] = 0;
+  epw_model *m = const_cast<epw_model *>(mc);
+  CKS(check_common(m, nk, k, nq, q));
+  CKS(check_params(par));
+  const int prec = par->precision;
+  if (prec != EPW_FP64 && prec != EPW_FP32)
+    return fail(EPW_ERR_UNSUPPORTED, "epw_linewidth_noalloc runs EPW_FP64 or EPW_FP32");
+  if ((nk > 0 && !is_device_ptr(k)) || (nq > 0 && !is_device_ptr(q)) || (wq && nq > 0 && !is_device_ptr(wq)) ||
+      (nk > 0 && !is_device_ptr(imsigma)))
+    return fail(EPW_ERR_INVALID_ARG, "epw_linewidth_noalloc takes device pointers only");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (nk == 0) return EPW_OK;
+  if (nq == 0) {
+    CK(cudaMemsetAsync(imsigma, 0, sizeof(double) * (size_t)nk * m->nw, st));
+    return EPW_OK;
+  }
+  // measure, then lay the buffers out inside the fixed scratch array
+  LwPlan L;
+  Arena A{nullptr, 0, 0};
+  CKS(plan_linewidth(A, m, nk, nq, prec, false, false, false, false, L));
+  if (A.off > EPW_NOALLOC_SCRATCH_BYTES)
+    return fail(EPW_ERR_INVALID_ARG, "problem needs %zu bytes of scratch; epw_linewidth_noalloc holds %zu", A.off,
+                (size_t)EPW_NOALLOC_SCRATCH_BYTES);
+  char *scratch = nullptr;
+  CKS(noalloc_scratch(m->device, &scratch));
+  A = Arena{scratch, (size_t)EPW_NOALLOC_SCRATCH_BYTES, 0};
+  CKS(plan_linewidth(A, m, nk, nq, prec, false, false, false, false, L));
+  Prep &p = L.p;
+  CKS(run_prep(m, nk, k, nq, q, prec, par->omega_min_eV, true, p, nullptr, st));
+  PairArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nk = nk;
+  a.nq = nq;
+  a.nw = m->nw;
+  a.nm = m->nm;
+  a.nRe = m->nRe;
+  a.nRp = m->nRp;
+  a.PqTe = p.PqTe;
+  a.PqTp = p.PqTp;
+  a.BH = p.BH;
+  a.Bg = p.Bg;
+  a.ET = p.ET;
+  a.omegaT = p.omegaT;
+  a.eps_k = p.epsk;
+  a.wq = wq;
+  a.T = par->T_K;
+  a.EF = par->EF_eV;
+  a.sigma = par->sigma_eV;
+  a.omega_min = par->omega_min_eV;
+  a.partial = L.partial;  // every entry is written before it is read
+  a.dstatus = m->dstatus;
+  epw_status s = prec == EPW_FP64 ? launch_pair<double>(a, 0, st) : launch_pair<float>(a, 0, st);
+  if (s != EPW_OK) return fail(s, "no per-pair kernel for nw=%d, 3nat=%d in this precision", m->nw, m->nm);
+  launch_finalize(nk, (nq + 127) / 128, m->nw, L.partial, imsigma, st);
+  CK(cudaGetLastError());
+  return EPW_OK;
+}
