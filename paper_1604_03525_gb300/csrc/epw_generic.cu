@@ -449,19 +449,30 @@ __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
   }
 }
 
-// out[k][n] = pi * sum_qb partial[k][qb][n], compensated (Neumaier), fixed order.
+__device__ __forceinline__ void neumaier_add(double &s, double &c, double x) {
+  const double u = s + x;
+  c += fabs(s) >= fabs(x) ? (s - u) + x : (x - u) + s;
+  s = u;
+}
+
+// out[k][n] = pi * sum_qb partial[k][qb][n], compensated (Neumaier).  One warp
+// per (k, n): lane l sums qb = l, l+32, ... in order, then the 32 partial sums
+// are combined by a fixed shuffle tree, so the result does not depend on timing.
 __global__ void k_finalize(int nk, int nqb, int nw, const double *__restrict__ partial, double *out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nk * nw) return;
-  int k = t / nw, n = t % nw;
+  const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= nk * nw) return;
+  const int k = w / nw, n = w % nw;
   double s = 0.0, c = 0.0;
-  for (int b = 0; b < nqb; b++) {
-    double x = partial[((size_t)k * nqb + b) * nw + n];
-    double u = s + x;
-    c += fabs(s) >= fabs(x) ? (s - u) + x : (x - u) + s;
-    s = u;
+  for (int b = lane; b < nqb; b += 32) neumaier_add(s, c, partial[((size_t)k * nqb + b) * nw + n]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, s, o);
+    const double c2 = __shfl_down_sync(0xffffffffu, c, o);
+    neumaier_add(s, c, s2);
+    c += c2;
   }
-  out[t] = EPW_PI * (s + c);
+  if (lane == 0) out[w] = EPW_PI * (s + c);
 }
 
 // out[0] (+)= scale * sum_i partial[i], one block, fixed order, compensated.
@@ -640,9 +651,9 @@ template epw_status launch_pair<double>(const PairArgs &, int, cudaStream_t);
 template epw_status launch_pair<float>(const PairArgs &, int, cudaStream_t);
 
 void launch_finalize(int nk, int nqb, int nw, const double *partial, double *out, cudaStream_t st) {
-  int n = nk * nw;
+  int n = nk * nw;  // one warp each
   if (!n) return;
-  k_finalize<<<(n + 127) / 128, 128, 0, st>>>(nk, nqb, nw, partial, out);
+  k_finalize<<<(n + 3) / 4, 128, 0, st>>>(nk, nqb, nw, partial, out);
   epw_count_launch();
 }
 

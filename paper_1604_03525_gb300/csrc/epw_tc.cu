@@ -362,11 +362,11 @@ __device__ __forceinline__ bool jacobi_fast(Herm<N> &H, cx<float> (&V)[N][N]) {
 
 struct TcArgs {
   int nk, nq, nqt, nkg, kpad, nkb, qblock;
-  const double *epsk;    // [nk][nw]
-  const double *omegaT;  // [nm][nq]
+  const float *epsk;     // [nk][nw]
+  const float *omegaT;   // [nm][nq]
   const float *nbT;      // [nm][nq]
   const float2 *ET;      // [nm*nm][nq]
-  const double *wq;      // [nq] or null
+  const float *wq;       // [nq]
   float EF, invkT, inv_sigma, gnorm, omega_min;
   double *partial;  // [nk][4*nqt][nw]            (linewidth)
   double *eps_kq;   // [nk][nq][nw] or null        (interp)
@@ -412,8 +412,16 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   // per-q and per-k data first, so their latency overlaps the eigensolve
   float ek[NW];
 #pragma unroll
-  for (int n = 0; n < NW; n++) ek[n] = (float)__ldg(a.epsk + (size_t)kk * NW + n);
-  const float wqf = valid ? (float)(a.wq ? a.wq[q] : 1.0 / a.nq) : 0.0f;
+  for (int n = 0; n < NW; n++) ek[n] = __ldg(a.epsk + (size_t)kk * NW + n);
+  const float wqf = valid ? __ldg(a.wq + q) : 0.0f;
+  // data of the first mode (each later mode is fetched one iteration ahead)
+  float wn = __ldg(a.omegaT + qq), nbn = __ldg(a.nbT + qq);
+  cx<float> En[NM];
+#pragma unroll
+  for (int al = 0; al < NM; al++) {
+    const float2 e = __ldg(a.ET + (size_t)al * NM * a.nq + qq);
+    En[al] = mkc(e.x, e.y);
+  }
 
   constexpr bool ONE_LOAD = S::CPK <= 32;
   float all[ONE_LOAD ? S::CPK : 8];
@@ -477,13 +485,18 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   // one mode per iteration (not unrolled: keeps the code within the instruction cache)
 #pragma unroll 1
   for (int nu = 0; nu < NM; nu++) {
-    const float wnu = (float)__ldg(a.omegaT + (size_t)nu * a.nq + qq);
-    const float nbnu = __ldg(a.nbT + (size_t)nu * a.nq + qq);
+    const float wnu = wn, nbnu = nbn;
     cx<float> E[NM];
 #pragma unroll
-    for (int al = 0; al < NM; al++) {
-      const float2 e = __ldg(a.ET + ((size_t)al * NM + nu) * a.nq + qq);
-      E[al] = mkc(e.x, e.y);
+    for (int al = 0; al < NM; al++) E[al] = En[al];
+    if (nu + 1 < NM) {
+      wn = __ldg(a.omegaT + (size_t)(nu + 1) * a.nq + qq);
+      nbn = __ldg(a.nbT + (size_t)(nu + 1) * a.nq + qq);
+#pragma unroll
+      for (int al = 0; al < NM; al++) {
+        const float2 e = __ldg(a.ET + ((size_t)al * NM + nu + 1) * a.nq + qq);
+        En[al] = mkc(e.x, e.y);
+      }
     }
     const bool keep = (wnu >= a.omega_min) && (wnu > 0.0f);
     cx<float> G[NW][NW];
@@ -735,11 +748,17 @@ __global__ void k_build_a(int nq, int nR, int kpad, const double *__restrict__ q
     double d = 0.0;
     if (kk < 2 * nR) {
       int r = nR - 1 - (kk >> 1);
+      // argument q.R reduced to [-1/2, 1/2] in FP64; 2x = xh + xl with xh in FP32,
+      // then sin/cos(pi xh) in FP32 and the first-order correction in pi xl
+      // (|xl| <= 2^-25): about 1 FP32 ulp, below the 2^-22 of the two-term split.
       double x = q[3 * iq] * R[3 * r] + q[3 * iq + 1] * R[3 * r + 1] + q[3 * iq + 2] * R[3 * r + 2];
       x -= rint(x);
-      double s, c;
-      sincospi(2.0 * x, &s, &c);
-      d = (kk & 1) ? s : c;
+      const double x2 = 2.0 * x;
+      const float xh = (float)x2;
+      const float xl = (float)(x2 - (double)xh) * 3.14159265358979f;
+      float s, c;
+      sincospif(xh, &s, &c);
+      d = (kk & 1) ? (double)fmaf(xl, c, s) : (double)fmaf(-xl, s, c);
     }
     split_store<T>(d, hi, lo, idx);
   }
@@ -770,11 +789,25 @@ __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, i
   }
 }
 
-__global__ void k_bose_table(int nq, int nm, const double *__restrict__ omegaT, double T, float *nbT) {
-  size_t n = (size_t)nq * nm;
+// FP32 tables of the epilogue, evaluated once per call: Bose factors n(w_qnu, T)
+// (in FP64), frequencies, q weights (wq null: 1/nq) and band energies at k.
+__global__ void k_tc_tables(int nq, int nm, int nk, int nw, const double *__restrict__ omegaT, double T,
+                            const double *__restrict__ wq, const double *__restrict__ epsk, float *nbT, float *omF,
+                            float *wqF, float *ekF) {
+  const size_t nqm = (size_t)nq * nm, nkw = (size_t)nk * nw;
+  const size_t n = nqm + (size_t)nq + nkw;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    double w = omegaT[i];
-    nbT[i] = (w > 0.0) ? (float)bose_d(w, T) : 0.0f;
+    if (i < nqm) {
+      const double w = omegaT[i];
+      nbT[i] = (w > 0.0) ? (float)bose_d(w, T) : 0.0f;
+      omF[i] = (float)w;
+    } else if (i < nqm + nq) {
+      const size_t j = i - nqm;
+      wqF[j] = (float)(wq ? wq[j] : 1.0 / nq);
+    } else {
+      const size_t j = i - nqm - nq;
+      ekF[j] = (float)epsk[j];
+    }
   }
 }
 
@@ -874,6 +907,9 @@ epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffe
   b.Bhi = A.take<char>((size_t)b.nk_pad * b.cpk * b.kpad * esz);
   b.Blo = A.take<char>((size_t)b.nk_pad * b.cpk * b.kpad * esz);
   b.nbT = A.take<float>((size_t)nq * m->nm);
+  b.omF = A.take<float>((size_t)nq * m->nm);
+  b.wqF = A.take<float>((size_t)nq);
+  b.ekF = A.take<float>((size_t)nk * m->nw);
   b.partial = A.take<double>((size_t)nk * 4 * b.nqt * m->nw);
   return EPW_OK;
 }
@@ -902,8 +938,9 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
       k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, BH32, Bg32,
                                                           (float *)b.Bhi, (float *)b.Blo);
     epw_count_launch();
-    n = (size_t)nq * m->nm;
-    k_bose_table<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nm, omegaT, par->T_K, b.nbT);
+    n = (size_t)nq * m->nm + nq + (size_t)nk * m->nw;
+    k_tc_tables<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nm, nk, m->nw, omegaT, par->T_K, wq, epsk, b.nbT, b.omF,
+                                                   b.wqF, b.ekF);
     epw_count_launch();
   }
   CUtensorMap ah, al, bh, bl;
@@ -927,11 +964,11 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
     if (qb > b.nqt) qb = b.nqt;
     a.qblock = qb < 1 ? 1 : qb;
   }
-  a.epsk = epsk;
-  a.omegaT = omegaT;
+  a.epsk = b.ekF;
+  a.omegaT = b.omF;
   a.nbT = b.nbT;
   a.ET = (const float2 *)ET32;
-  a.wq = wq;
+  a.wq = b.wqF;
   a.EF = (float)par->EF_eV;
   a.invkT = par->T_K > 0.0 ? (float)(1.0 / (EPW_KB * par->T_K)) : 0.0f;
   a.inv_sigma = (float)(1.0 / par->sigma_eV);

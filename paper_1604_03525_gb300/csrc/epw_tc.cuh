@@ -10,6 +10,9 @@ struct TcBuffers {
   void *Ahi, *Alo;   // q phases, split, K-major [nq][kpad]
   void *Bhi, *Blo;   // k-side vertex, split, K-major [nk_pad][cpk][kpad]
   float *nbT;        // Bose factors [nm][nq]
+  float *omF;        // frequencies [nm][nq]
+  float *wqF;        // q weights [nq]
+  float *ekF;        // band energies at k [nk][nw]
   double *partial;   // [nk][4*nqt][nw]
   int op, kpad, cpk, nk_pad, nqt, kpt;
   bool ok;           // shape has a tensor-core kernel
