@@ -109,6 +109,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+TC_SOURCE = os.path.join(ROOT, "paper_1604_03525_gb300", "csrc", "epw_tc.cu")
+TC_PROFILE = os.path.join(ROOT, "profiles", "k_tc_linewidth_fcc_nw4.md")
+
+
+def profiled_traffic(form):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary.
+
+    The summary records `traffic <form> <bytes> source-sha256 <hash>` lines; a
+    value is used only while the kernel source still has that hash (otherwise
+    the counters describe an older kernel and the traffic is reported as null).
+    """
+    import hashlib
+    try:
+        sha = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
+        for line in open(TC_PROFILE):
+            parts = line.strip().strip("`").split()
+            if len(parts) == 5 and parts[0] == "traffic" and parts[1] == form and parts[3] == "source-sha256":
+                if parts[4] == sha:
+                    return float(parts[2]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/"
+                return None, "kernel changed since the ncu capture"
+    except OSError:
+        pass
+    return None, "no ncu capture recorded"
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -305,6 +330,8 @@ def main():
                 "traffic": None, "peak_source": "measured FMA throughput (FP32 73.55 / FP64 1.257 TFLOP/s)", "work": f"{tflops + sflops} algorithmic flops/pair x {pairs} pairs"}
     roof["kernel_ms"] = kern_ms
     roof["kernel_launches"] = kern_n
+    if prec in (epw.BF16X3, epw.TF32X3):
+        roof["traffic"], roof["traffic_source"] = profiled_traffic("bf16x3" if prec == epw.BF16X3 else "tf32x3")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -331,7 +331,7 @@ __device__ __forceinline__ bool jacobi_fast(Herm<N> &H, cx<float> (&V)[N][N]) {
 #pragma unroll
     for (int j = 0; j < N; j++) V[i][j] = mkc(i == j ? 1.0f : 0.0f, 0.0f);
   if constexpr (N == 1) return true;
-  constexpr float TOL2 = 1e-12f;
+  constexpr float TOL2 = 1e-10f;
   constexpr int MAXSWEEP = 12;
   for (int sweep = 0; sweep < MAXSWEEP; sweep++) {
     const bool conv = offdiag_frac(H) <= TOL2;
@@ -415,13 +415,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   for (int n = 0; n < NW; n++) ek[n] = __ldg(a.epsk + (size_t)kk * NW + n);
   const float wqf = valid ? __ldg(a.wq + q) : 0.0f;
   // data of the first mode (each later mode is fetched one iteration ahead)
-  float wn = __ldg(a.omegaT + qq), nbn = __ldg(a.nbT + qq);
-  cx<float> En[NM];
-#pragma unroll
-  for (int al = 0; al < NM; al++) {
-    const float2 e = __ldg(a.ET + (size_t)al * NM * a.nq + qq);
-    En[al] = mkc(e.x, e.y);
-  }
+
 
   constexpr bool ONE_LOAD = S::CPK <= 32;
   float all[ONE_LOAD ? S::CPK : 8];
@@ -485,18 +479,13 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   // one mode per iteration (not unrolled: keeps the code within the instruction cache)
 #pragma unroll 1
   for (int nu = 0; nu < NM; nu++) {
-    const float wnu = wn, nbnu = nbn;
+    const float wnu = __ldg(a.omegaT + (size_t)nu * a.nq + qq);
+    const float nbnu = __ldg(a.nbT + (size_t)nu * a.nq + qq);
     cx<float> E[NM];
 #pragma unroll
-    for (int al = 0; al < NM; al++) E[al] = En[al];
-    if (nu + 1 < NM) {
-      wn = __ldg(a.omegaT + (size_t)(nu + 1) * a.nq + qq);
-      nbn = __ldg(a.nbT + (size_t)(nu + 1) * a.nq + qq);
-#pragma unroll
-      for (int al = 0; al < NM; al++) {
-        const float2 e = __ldg(a.ET + ((size_t)al * NM + nu + 1) * a.nq + qq);
-        En[al] = mkc(e.x, e.y);
-      }
+    for (int al = 0; al < NM; al++) {
+      const float2 e = __ldg(a.ET + ((size_t)al * NM + nu) * a.nq + qq);
+      E[al] = mkc(e.x, e.y);
     }
     const bool keep = (wnu >= a.omega_min) && (wnu > 0.0f);
     cx<float> G[NW][NW];
