@@ -195,9 +195,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "tf32x3", "bf16x3", "fp32", "fp64"])
     ap.add_argument("--other-steps", type=int, default=2, help="timed steps of the other tensor-core/FP32 forms")
+    ap.add_argument("--backward-steps", type=int, default=1, help="timed adjoint calls (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU form (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nk", type=int, default=0, help="profiling only: use the first NK k-points of the workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -219,6 +221,8 @@ def main():
         torch.cuda.synchronize()
 
     wl = W.make_workload(WORKLOAD, T=T_SWEEP[rank % len(T_SWEEP)])
+    if args.nk > 0:
+        wl.k = wl.k[:args.nk]
     m = epw.Model(wl.model)
     dev = torch.device("cuda", local)
     k = torch.tensor(wl.k, device=dev)
@@ -297,6 +301,21 @@ def main():
         s64, k64, _, _ = timed_steps(args.fp64_steps, 1, epw.FP64)
         fp64 = {"value": pairs / (np.mean(s64) / 1e3), "unit": "pairs/s", "ms_per_step": float(np.mean(s64)),
                 "kernel_ms": k64}
+    backward = None
+    if args.backward_steps > 0:
+        # adjoint of sum_{k,n} Im Sigma_nk w.r.t. g(Re,Rp), T and E_F (FP32 SIMT form), device buffers
+        cot = torch.ones((len(wl.k), wl.model.nw), dtype=torch.float64, device=dev)
+        m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.FP32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.backward_steps):
+            m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.FP32)
+        e1.record()
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / args.backward_steps
+        backward = {"value": pairs / (bms / 1e3), "unit": "pairs/s", "ms_per_step": bms, "precision": "fp32",
+                    "what": "dL/dg(Re,Rp), dL/dT, dL/dE_F of L = sum Im Sigma; g(k,q) recomputed"}
     others = {}
     if args.other_steps > 0:
         for oname, op in (("bf16x3", epw.BF16X3), ("tf32x3", epw.TF32X3), ("fp32", epw.FP32)):
@@ -348,7 +367,7 @@ def main():
                                    f"T={T_SWEEP[0]:.0f} K (rank r: T_sweep[r])", "pairs_per_step_per_gpu": pairs,
                        "precision": name, "l2": "flushed between timed steps (256 MB write)"},
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof,
-            "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu_form": fp64, "other_forms": others,
+            "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu_form": fp64, "other_forms": others, "backward": backward,
         }
         print(json.dumps(line))
     m.close()

@@ -132,6 +132,13 @@ typedef struct {
  * sets, or a non-positive mass; EPW_ERR_OOM when device memory runs out. */
 epw_status epw_load_wannier(const epw_wannier_desc *desc, epw_model **out);
 
+/* Replace the vertex g(Re,Rp) of a loaded model (same layout and sizes as in
+ * epw_wannier_desc; weights are applied as at load).  g may be a host or a
+ * device pointer; complex128 unless g_is_c64.  Stream-ordered on `stream`:
+ * later calls on the same stream see the new vertex.  Used for gradient
+ * descent on g with epw_linewidth_backward. */
+epw_status epw_set_vertex(epw_model *model, const void *g, int g_is_c64, void *stream);
+
 /* Release a model and its device memory (NULL is a no-op).  Not stream-ordered:
  * the caller makes sure no work that uses the model is still running. */
 void epw_free_model(epw_model *model);

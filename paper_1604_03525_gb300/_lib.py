@@ -24,6 +24,7 @@ STATUS_NAMES = {
 SIGNATURES = {
     "epw_load_wannier": (I, [P, P]),
     "epw_free_model": (None, [P]),
+    "epw_set_vertex": (I, [P, P, I, P]),
     "epw_reserve": (I, [P, I, I, I]),
     "epw_interp_g": (I, [P, I, P, I, P, I, D, P, P, P, P, P]),
     "epw_linewidth": (I, [P, I, P, I, P, P, P, P, P]),

@@ -110,6 +110,13 @@ class Model:
     def handle(self):
         return self._h
 
+    def set_vertex(self, g):
+        """Replace g(Re,Rp) (layout of the model's g; host array or CUDA tensor)."""
+        ga = _Arg(g, np.complex128)
+        if tuple(ga.keep.shape) != self.g_shape:
+            raise ValueError(f"vertex shape {tuple(ga.keep.shape)} != {self.g_shape}")
+        _check(_lib.load().epw_set_vertex(self._h, ga.ptr, 0, _stream_of(ga)))
+
     def reserve(self, nk: int, nq: int, precision: int = FP64):
         _check(_lib.load().epw_reserve(self._h, int(nk), int(nq), int(precision)))
 

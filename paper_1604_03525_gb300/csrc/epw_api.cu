@@ -177,6 +177,28 @@ extern "C" void epw_free_model(epw_model *m) {
   cudaSetDevice(cur);
 }
 
+static epw_status ensure_ws(epw_model *m, size_t bytes);
+
+extern "C" epw_status epw_set_vertex(epw_model *m, const void *g, int g_is_c64, void *stream) {
+  g_err[0] = 0;
+  if (!m || !g) return fail(EPW_ERR_INVALID_ARG, "null model or vertex");
+  int cur = -1;
+  CK(cudaGetDevice(&cur));
+  if (cur != m->device) return fail(EPW_ERR_INVALID_ARG, "model lives on device %d, current device is %d", m->device, cur);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)m->nRe * m->nRp * m->nm * m->nw * m->nw * (g_is_c64 ? 8 : 16);
+  const void *gd = g;
+  if (!is_device_ptr(g)) {
+    CKS(ensure_ws(m, bytes));
+    CK(cudaMemcpyAsync(m->ws, g, bytes, cudaMemcpyHostToDevice, st));
+    gd = m->ws;
+  }
+  launch_set_vertex(m, gd, g_is_c64, st);
+  CK(cudaGetLastError());
+  if (gd != g) CK(cudaStreamSynchronize(st));
+  return EPW_OK;
+}
+
 extern "C" epw_status epw_model_info(const epw_model *m, int *nw, int *nat, int *nRe, int *nRp, int *nRph) {
   if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
   if (nw) *nw = m->nw;

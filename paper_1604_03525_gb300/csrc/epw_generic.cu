@@ -449,6 +449,26 @@ __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
   }
 }
 
+// gw[Re][Rp][...] = wRe wRp g   (g complex128 or, with is_c64, complex64)
+__global__ void k_set_vertex(int nRe, int nRp, size_t per, const void *__restrict__ g, int is_c64,
+                             const double *__restrict__ wRe, const double *__restrict__ wRp, cx<double> *gw) {
+  size_t n = (size_t)nRe * nRp * per;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    size_t rr = idx / per;
+    int a = (int)(rr / nRp), b = (int)(rr % nRp);
+    double s = wRe[a] * wRp[b];
+    double re, im;
+    if (is_c64) {
+      re = ((const float *)g)[2 * idx];
+      im = ((const float *)g)[2 * idx + 1];
+    } else {
+      re = ((const double *)g)[2 * idx];
+      im = ((const double *)g)[2 * idx + 1];
+    }
+    gw[idx] = mkc(s * re, s * im);
+  }
+}
+
 __device__ __forceinline__ void neumaier_add(double &s, double &c, double x) {
   const double u = s + x;
   c += fabs(s) >= fabs(x) ? (s - u) + x : (x - u) + s;
@@ -649,6 +669,14 @@ epw_status launch_pair(const PairArgs &a, int mode, cudaStream_t st) {
 }
 template epw_status launch_pair<double>(const PairArgs &, int, cudaStream_t);
 template epw_status launch_pair<float>(const PairArgs &, int, cudaStream_t);
+
+void launch_set_vertex(const epw_model *m, const void *g, int is_c64, cudaStream_t st) {
+  size_t per = (size_t)m->nm * m->nw * m->nw;
+  size_t n = (size_t)m->nRe * m->nRp * per;
+  if (!n) return;
+  k_set_vertex<<<nblocks(n, 256), 256, 0, st>>>(m->nRe, m->nRp, per, g, is_c64, m->wRe, m->wRp, m->gw);
+  epw_count_launch();
+}
 
 void launch_finalize(int nk, int nqb, int nw, const double *partial, double *out, cudaStream_t st) {
   int n = nk * nw;  // one warp each

@@ -310,6 +310,8 @@ struct PairArgs {
 template <typename R>
 epw_status launch_pair(const PairArgs &a, int mode, cudaStream_t st);
 void launch_finalize(int nk, int nqb, int nw, const double *partial, double *out, cudaStream_t st);
+// m->gw = wRe wRp g (g on the device)
+void launch_set_vertex(const epw_model *m, const void *g, int is_c64, cudaStream_t st);
 void launch_sum_scalar(int n, const double *partial, double scale, double *out, cudaStream_t st);
 // G1bar[k][Rp][a][j][i] = sum_n Bbar[Rp][k][a][j][n] conj(U_{k0+k}[i][n])
 template <typename R>

@@ -1,0 +1,68 @@
+"""Adjoint through torch.autograd: against the oracle gradient and central finite differences (FP64)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_03525_gb300 as epw
+    rng = np.random.default_rng(11)
+    wm = W.make_model("sc", 2, 1, [1.0], None, None, rng, box=1, omega_max=0.2)
+    k = rng.random((4, 3))
+    q = rng.random((160, 3))
+    cot = rng.random((4, 2))
+    return epw, wm, k, q, cot
+
+
+def test_autograd_matches_oracle_gradient(setup, oracle_lib):
+    import torch
+    from paper_1604_03525_gb300.autograd import linewidth
+    epw, wm, k, q, cot = setup
+    m = epw.Model(wm)
+    g = torch.tensor(wm.g, device="cuda", requires_grad=True)
+    T = torch.tensor(300.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    EF = torch.tensor(0.2, dtype=torch.float64, device="cuda", requires_grad=True)
+    kt, qt = torch.tensor(k, device="cuda"), torch.tensor(q, device="cuda")
+    out = linewidth(m, g, T, EF, kt, qt, sigma=0.2)
+    L = (out * torch.tensor(cot, device="cuda")).sum()
+    L.backward()
+    rdg, rdT, rdE = oracle_lib.linewidth_grad(wm, k, q, None, 300.0, 0.2, 0.2, cot=cot)
+    assert np.abs(g.grad.cpu().numpy() - rdg).max() <= 1e-9 * np.abs(rdg).max()
+    assert abs(T.grad.item() - rdT) <= 1e-9 * abs(rdT)
+    assert abs(EF.grad.item() - rdE) <= 1e-9 * abs(rdE)
+
+
+def test_autograd_directional_finite_differences(setup):
+    import torch
+    from paper_1604_03525_gb300.autograd import linewidth
+    epw, wm, k, q, cot = setup
+    m = epw.Model(wm)
+    kt, qt, ct = torch.tensor(k, device="cuda"), torch.tensor(q, device="cuda"), torch.tensor(cot, device="cuda")
+    g0 = torch.tensor(wm.g, device="cuda")
+    rng = np.random.default_rng(12)
+    d = torch.tensor(rng.standard_normal(wm.g.shape) + 1j * rng.standard_normal(wm.g.shape), device="cuda")
+
+    def L(g, T=300.0, EF=0.2):
+        Tt = torch.tensor(T, dtype=torch.float64, device="cuda")
+        Et = torch.tensor(EF, dtype=torch.float64, device="cuda")
+        return float((linewidth(m, g, Tt, Et, kt, qt, sigma=0.2) * ct).sum())
+
+    g = g0.clone().requires_grad_(True)
+    Tt = torch.tensor(300.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    Et = torch.tensor(0.2, dtype=torch.float64, device="cuda", requires_grad=True)
+    (linewidth(m, g, Tt, Et, kt, qt, sigma=0.2) * ct).sum().backward()
+    h = 1e-6
+    fd = (L(g0 + h * d) - L(g0 - h * d)) / (2 * h)
+    an = float((g.grad.conj() * d).real.sum())
+    assert abs(fd - an) <= 1e-6 * abs(an)
+    fdT = (L(g0, T=300.0 + 1e-3) - L(g0, T=300.0 - 1e-3)) / 2e-3
+    assert abs(fdT - Tt.grad.item()) <= 1e-6 * abs(fdT)
+    fdE = (L(g0, EF=0.2 + 1e-6) - L(g0, EF=0.2 - 1e-6)) / 2e-6
+    assert abs(fdE - Et.grad.item()) <= 1e-6 * abs(fdE)
