@@ -619,6 +619,8 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   if (!(par->T_K > 0.0)) return fail(EPW_ERR_INVALID_ARG, "the adjoint needs T_K > 0");
   if (nk > 0 && !cot) return fail(EPW_ERR_INVALID_ARG, "null grad_imsigma");
   const int prec = par->precision >= EPW_BF16X3 ? EPW_FP32 : par->precision;
+  // tensor-core adjoint (TF32 split) for shapes the fused kernel serves
+  const bool tcb = (par->precision == EPW_BF16X3 || par->precision == EPW_TF32X3) && tc_supported(m);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nw2 = (size_t)m->nw * m->nw, per = (size_t)m->nm * nw2;
   const size_t ng = (size_t)m->nRe * m->nRp * per;
@@ -633,24 +635,32 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   struct B {
     Prep p;
     double *cotd, *xbar, *Bbar, *G1bar, *gwbar, *pT, *pE, *sc, *dgd;
+    TcBuffers tc;
+    TcBwdBuffers tw;
   } b;
-  auto plan = [&](Arena &A) {
+  auto plan = [&](Arena &A) -> epw_status {
     plan_prep(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, prec, sk, sq, swq, true, b.p);
     b.cotd = scot ? A.take<double>((size_t)nk * m->nw) : (double *)cot;
-    b.xbar = (double *)A.take<char>(sR * (size_t)nq * nkc * per);
-    b.Bbar = (double *)A.take<char>(sR * (size_t)m->nRp * nkc * per);
-    b.G1bar = (double *)A.take<char>(sR * (size_t)m->nRp * nkc * per);
+    if (tcb) {
+      b.xbar = b.Bbar = b.G1bar = b.pT = b.pE = nullptr;
+      CKS(tc_bwd_plan(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, b.tc, b.tw));
+    } else {
+      b.xbar = (double *)A.take<char>(sR * (size_t)nq * nkc * per);
+      b.Bbar = (double *)A.take<char>(sR * (size_t)m->nRp * nkc * per);
+      b.G1bar = (double *)A.take<char>(sR * (size_t)m->nRp * nkc * per);
+      b.pT = A.take<double>((size_t)nkc * nqb);
+      b.pE = A.take<double>((size_t)nkc * nqb);
+    }
     b.gwbar = (double *)A.take<char>(sR * ng);
-    b.pT = A.take<double>((size_t)nkc * nqb);
-    b.pE = A.take<double>((size_t)nkc * nqb);
     b.sc = A.take<double>(2);
     b.dgd = sdg ? A.take<double>(2 * ng) : dg;
+    return EPW_OK;
   };
   Arena A{nullptr, 0, 0};
-  plan(A);
+  CKS(plan(A));
   CKS(ensure_ws(m, A.off));
   A = Arena{(char *)m->ws, m->ws_bytes, 0};
-  plan(A);
+  CKS(plan(A));
   Prep &p = b.p;
   const double *kd = k, *qd = q, *wqd = wq;
   if (sk) {
@@ -668,7 +678,13 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   if (scot) CK(cudaMemcpyAsync(b.cotd, cot, sizeof(double) * nk * m->nw, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(b.sc, 0, 2 * sizeof(double), st));
   CK(cudaMemsetAsync(b.gwbar, 0, sR * ng, st));
-  if (nk > 0 && nq > 0) {
+  if (nk > 0 && nq > 0 && tcb) {
+    CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
+    epw_status s = tc_linewidth_backward(m, nk, nq, qd, wqd, par, p.epsk, p.Uk, p.Pk32, p.omegaT,
+                                         (const cx<float> *)p.ET, (const cx<float> *)p.Bg, (const cx<float> *)p.BH,
+                                         b.cotd, b.tc, b.tw, (cx<float> *)b.gwbar, b.sc, st);
+    if (s != EPW_OK) return fail(s, "tensor-core adjoint failed");
+  } else if (nk > 0 && nq > 0) {
     CKS(run_prep(m, nk, kd, nq, qd, prec, par->omega_min_eV, true, p, nullptr, st));
     for (int k0 = 0; k0 < nk; k0 += nkc) {
       const int kc = std::min(nkc, nk - k0);

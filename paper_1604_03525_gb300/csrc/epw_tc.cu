@@ -30,6 +30,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "epw_tc.cuh"
@@ -371,8 +372,21 @@ struct TcArgs {
   double *partial;  // [nk][4*nqt][nw]            (linewidth)
   double *eps_kq;   // [nk][nq][nw] or null        (interp)
   double2 *gout;    // [nk][nq][nm][nw][nw] or null (interp)
+  // adjoint (MODE 2)
+  const float *cot;      // [nk][nw] cotangent of Im Sigma
+  float *xhi, *xlo;      // [nk*nm*nw*nw][ldx] conjugate-gradient rows, K = 2q+t (tf32 split)
+  int ldx;
+  double *partT, *partE;  // [nk][4*nqt] per-warp sums of dL/dT and dL/dE_F
+  float T;
   unsigned *dstatus;
 };
+
+// tf32 term: an fp32 with its 13 low mantissa bits cleared after rounding to nearest
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+  return __uint_as_float(u);
+}
 
 template <int NW, int NM>
 struct Shape {
@@ -401,7 +415,10 @@ __device__ __forceinline__ void item_coords(const TcArgs &a, int item, int &kg, 
 // ------------------------------------------------------------------ epilogue
 // One (k,q) pair per thread; the accumulator holds [H(k+q) | (g_a U_k)_a=0..NM-1].
 // MODE 0: linewidth terms summed over the warp's q rows; MODE 1: write e_k+q
-// (ascending) and g_mn,nu.
+// (ascending) and g_mn,nu; MODE 2: adjoint of L = sum c_nk Im Sigma_nk:
+//   W_nu,mn = c_nk pi w_q [(n+f) d+ + (n+1-f) d-],   Ybar_nu = 2 W_nu (U^dagger G_nu)
+//   Xbar_a  = sum_nu conj(E[a][nu]) U Ybar_nu   (= dL/d(g_a U_k)(k,q)*, written out)
+//   dL/dT, dL/dE_F through n(w, T) and f(e, T, E_F) (deltas hold neither).
 template <int NW, int NM, int MODE>
 __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, int q, int k, bool valid, int quad,
                                               int qt) {
@@ -476,6 +493,21 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
 #pragma unroll
   for (int n = 0; n < NW; n++) acc[n] = 0.0f;
   const float s2 = a.inv_sigma * a.inv_sigma * 1.4426950408889634f;
+  // adjoint state (MODE 2): c_nk pi w_q / (sigma sqrt(pi)) per n, Xbar accumulators, dT / dE_F sums
+  float cw[MODE == 2 ? NW : 1];
+  cx<float> Xb[MODE == 2 ? NM : 1][NW][NW];
+  float sT = 0.0f, sE = 0.0f;
+  if constexpr (MODE == 2) {
+#pragma unroll
+    for (int n = 0; n < NW; n++)
+      cw[n] = valid ? __ldg(a.cot + (size_t)kk * NW + n) * 3.14159265358979f * wqf * a.gnorm : 0.0f;
+#pragma unroll
+    for (int al = 0; al < NM; al++)
+#pragma unroll
+      for (int i = 0; i < NW; i++)
+#pragma unroll
+        for (int j = 0; j < NW; j++) Xb[al][i][j] = mkc(0.0f, 0.0f);
+  }
   // one mode per iteration (not unrolled: keeps the code within the instruction cache)
 #pragma unroll 1
   for (int nu = 0; nu < NM; nu++) {
@@ -512,27 +544,96 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
           for (int j = 0; j < NW; j++) cfma(G[i][j], E[al], mkc(x[2 * (i * NW + j)], x[2 * (i * NW + j) + 1]));
       }
     }
-    // |(U^dagger G)_mn|^2 with the delta terms of Eq. (linewidthel)
+    if constexpr (MODE == 2) {
+      const float kf = keep ? 1.0f : 0.0f;
+      const float dn = kf * nbnu * (nbnu + 1.0f) * wnu * a.invkT / a.T;
+      cx<float> Z[NW][NW];  // U Ybar_nu
 #pragma unroll
-    for (int m = 0; m < NW; m++) {
-      const float cp = keep ? nbnu + fm[m] : 0.0f;
-      const float cm = keep ? nbnu + 1.0f - fm[m] : 0.0f;
+      for (int i = 0; i < NW; i++)
 #pragma unroll
-      for (int n = 0; n < NW; n++) {
-        cx<float> y = mkc(0.0f, 0.0f);
+        for (int j = 0; j < NW; j++) Z[i][j] = mkc(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < NW; i++) cfma(y, conjc(V[i][m]), G[i][n]);
-        if constexpr (MODE == 1) {
-          if (valid && a.gout)
-            a.gout[(((size_t)k * a.nq + q) * NM + nu) * NW * NW + m * NW + n] = make_double2(y.x, y.y);
-          continue;
+      for (int m = 0; m < NW; m++) {
+        const float f = fm[m];
+        const float ff = f * (1.0f - f);
+        const float dfT = ff * (em[m] - a.EF) * a.invkT / a.T;
+        const float dfE = ff * a.invkT;
+        const float cp = kf * (nbnu + f), cm = kf * (nbnu + 1.0f - f);
+#pragma unroll
+        for (int n = 0; n < NW; n++) {
+          cx<float> y = mkc(0.0f, 0.0f);
+#pragma unroll
+          for (int i = 0; i < NW; i++) cfma(y, conjc(V[i][m]), G[i][n]);
+          const float g2 = cabs2(y);
+          const float xd = ek[n] - em[m];
+          const float xp = xd + wnu, xm = xd - wnu;
+          const float ep = ex2_approx(-xp * xp * s2), en = ex2_approx(-xm * xm * s2);
+          const float wv = 2.0f * cw[n] * (cp * ep + cm * en);
+          sT = fmaf(kf * cw[n] * g2, (dn + dfT) * ep + (dn - dfT) * en, sT);
+          sE = fmaf(kf * cw[n] * g2, dfE * (ep - en), sE);
+          const cx<float> yb = mkc(wv * y.x, wv * y.y);
+#pragma unroll
+          for (int j = 0; j < NW; j++) cfma(Z[j][n], V[j][m], yb);
         }
-        const float g2 = cabs2(y);
-        const float xd = ek[n] - em[m];
-        const float xp = xd + wnu, xm = xd - wnu;
-        const float d = cp * ex2_approx(-xp * xp * s2) + cm * ex2_approx(-xm * xm * s2);
-        acc[n] = fmaf(g2, d, acc[n]);
       }
+#pragma unroll
+      for (int al = 0; al < NM; al++) {
+        const cx<float> ec = conjc(E[al]);
+#pragma unroll
+        for (int j = 0; j < NW; j++)
+#pragma unroll
+          for (int n = 0; n < NW; n++) cfma(Xb[al][j][n], ec, Z[j][n]);
+      }
+    } else {
+      // |(U^dagger G)_mn|^2 with the delta terms of Eq. (linewidthel)
+#pragma unroll
+      for (int m = 0; m < NW; m++) {
+        const float cp = keep ? nbnu + fm[m] : 0.0f;
+        const float cm = keep ? nbnu + 1.0f - fm[m] : 0.0f;
+#pragma unroll
+        for (int n = 0; n < NW; n++) {
+          cx<float> y = mkc(0.0f, 0.0f);
+#pragma unroll
+          for (int i = 0; i < NW; i++) cfma(y, conjc(V[i][m]), G[i][n]);
+          if constexpr (MODE == 1) {
+            if (valid && a.gout)
+              a.gout[(((size_t)k * a.nq + q) * NM + nu) * NW * NW + m * NW + n] = make_double2(y.x, y.y);
+            continue;
+          }
+          const float g2 = cabs2(y);
+          const float xd = ek[n] - em[m];
+          const float xp = xd + wnu, xm = xd - wnu;
+          const float d = cp * ex2_approx(-xp * xp * s2) + cm * ex2_approx(-xm * xm * s2);
+          acc[n] = fmaf(g2, d, acc[n]);
+        }
+      }
+    }
+  }
+  if constexpr (MODE == 2) {
+    // Xbar rows (k, a, j, n), K index 2q + (re, im), split into two tf32 terms
+    if (valid) {
+#pragma unroll
+      for (int al = 0; al < NM; al++)
+#pragma unroll
+        for (int j = 0; j < NW; j++)
+#pragma unroll
+          for (int n = 0; n < NW; n++) {
+            const size_t row = (size_t)k * (NM * NW * NW) + (al * NW + j) * NW + n;
+            const float re = Xb[al][j][n].x, im = Xb[al][j][n].y;
+            const float hr = tf32_rn(re), hi = tf32_rn(im);
+            *reinterpret_cast<float2 *>(a.xhi + row * a.ldx + 2 * (size_t)q) = make_float2(hr, hi);
+            *reinterpret_cast<float2 *>(a.xlo + row * a.ldx + 2 * (size_t)q) =
+                make_float2(tf32_rn(re - hr), tf32_rn(im - hi));
+          }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sT += __shfl_down_sync(0xffffffffu, sT, o);
+      sE += __shfl_down_sync(0xffffffffu, sE, o);
+    }
+    if ((threadIdx.x & 31) == 0 && k < a.nk) {
+      a.partT[(size_t)k * (4 * a.nqt) + qt * 4 + quad] = (double)sT;
+      a.partE[(size_t)k * (4 * a.nqt) + qt * 4 + quad] = (double)sE;
     }
   }
   if constexpr (MODE == 0) {
@@ -1005,3 +1106,420 @@ epw_status tc_interp(const epw_model *m, int nk, int nq, const double *q, double
 }
 
 void tc_free(epw_model *) {}
+
+// ===================================================================== adjoint
+// dL/dg on the tensor cores, for L = sum_{k,n} c_nk Im Sigma_nk.  Per chunk of k:
+//  1. the fused kernel in MODE 2 recomputes the forward per pair and writes
+//     Xbar(k,q) = dL/d(g U_k)(k,q)* as rows (k, a, j, n) with K index 2q + (re,im);
+//  2. a split-K tcgen05 GEMM contracts them with conj(P_q(R)) over q:
+//     Bbar[R][k][a j n] = sum_q conj(e^{2 pi i q.R}) Xbar(k,q)_{a j n};
+//  3. the k-side adjoint (U_k rotation, conj(P_k(Re)) contraction) runs as in
+//     the SIMT form.
+namespace {
+
+constexpr int G_NT = 144;                          // N tile: rows of the conj-phase operand
+constexpr int G_A_BYTES = 128 * ROWB;              // 16 KiB
+constexpr int G_B_BYTES = G_NT * ROWB;             // 18 KiB
+constexpr int G_STAGE = 2 * G_A_BYTES + 2 * G_B_BYTES;
+constexpr int G_STAGES = 3;
+constexpr int G_SMEM = G_STAGES * G_STAGE + 1024;
+constexpr int G_THREADS = 192;                     // producer, MMA, 4 epilogue warps
+// kind::tf32: D=F32, A=B=TF32, K-major, N=144, M=128
+constexpr uint32_t G_IDESC =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(G_NT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+struct GemmArgs {
+  int mtiles, ntiles, splits, kblocks, kb_per_split;
+  int ldc;   // rows of Ct are padded to mtiles * 128
+  int npad;  // ntiles * G_NT
+  float *Ct; // [splits][npad][ldc]: transposed partial products
+  unsigned *dstatus;
+};
+
+__device__ __forceinline__ void umma_tf32_n144(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::
+          "r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(G_IDESC), "r"(acc)
+      : "memory");
+}
+
+// Ct[sp][n][m] = sum_{K blocks of split sp} A[m][K] B[n][K]   (two-term tf32 split, three MMAs)
+__global__ void __launch_bounds__(G_THREADS, 1)
+    k_tc_gemm_nt(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                 const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, GemmArgs g) {
+  __shared__ __align__(8) uint64_t bar_full[G_STAGES], bar_empty[G_STAGES], bar_tfull[2], bar_tempty[2], bar_final;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t smem0 = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int *abort_flag = &abort_sh;
+  const int nitems = g.mtiles * g.ntiles * g.splits;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G_STAGES; s++) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int s = 0; s < 2; s++) {
+      mbar_init(smem_u32(&bar_tfull[s]), 1);
+      mbar_init(smem_u32(&bar_tempty[s]), 4);
+    }
+    mbar_init(smem_u32(&bar_final), 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(&tmem_base_sh), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  auto coords = [&](int item, int &mt, int &nt, int &sp, int &kb0, int &kb1) {
+    sp = item % g.splits;
+    const int rest = item / g.splits;
+    nt = rest % g.ntiles;
+    mt = rest / g.ntiles;
+    kb0 = sp * g.kb_per_split;
+    kb1 = min(g.kblocks, kb0 + g.kb_per_split);
+  };
+  if (warp == 0) {
+    int issued[G_STAGES] = {0, 0, 0};
+    uint32_t it = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+      int mt, nt, sp, kb0, kb1;
+      coords(item, mt, nt, sp, kb0, kb1);
+      for (int kb = kb0; kb < kb1; kb++, it++) {
+        const int s = it % G_STAGES;
+        const uint32_t par = ((it / G_STAGES) & 1u) ^ 1u;
+        if (lane == 0) {
+          ok = wait_bar(smem_u32(&bar_empty[s]), par, abort_flag, g.dstatus);
+          if (ok) {
+            const uint32_t base = smem0 + s * G_STAGE;
+            const uint32_t fb = smem_u32(&bar_full[s]);
+            mbar_expect_tx(fb, G_STAGE);
+            tma_load_2d(base, &mAhi, kb * 32, mt * 128, fb);
+            tma_load_2d(base + G_A_BYTES, &mAlo, kb * 32, mt * 128, fb);
+            tma_load_2d(base + 2 * G_A_BYTES, &mBhi, kb * 32, nt * G_NT, fb);
+            tma_load_2d(base + 2 * G_A_BYTES + G_B_BYTES, &mBlo, kb * 32, nt * G_NT, fb);
+#pragma unroll
+            for (int z = 0; z < G_STAGES; z++)
+              if (z == s) issued[z] = (int)(it / G_STAGES) + 1;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int z = 0; z < G_STAGES; z++)
+        if (issued[z] > 0) drain_bar(smem_u32(&bar_full[z]), (uint32_t)((issued[z] - 1) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    uint32_t it = 0;
+    int titer = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, titer++) {
+      int mt, nt, sp, kb0, kb1;
+      coords(item, mt, nt, sp, kb0, kb1);
+      const int ts = titer & 1;
+      const uint32_t tpar = ((titer >> 1) & 1) ^ 1;
+      if (lane == 0) ok = wait_bar(smem_u32(&bar_tempty[ts]), tpar, abort_flag, g.dstatus);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t dcol = tmem + ts * 256;
+      for (int kb = kb0; kb < kb1; kb++, it++) {
+        const int s = it % G_STAGES;
+        const uint32_t par = (it / G_STAGES) & 1u;
+        if (lane == 0) {
+          ok = wait_bar(smem_u32(&bar_full[s]), par, abort_flag, g.dstatus);
+          if (ok) {
+            tc_fence_after();
+            const uint32_t base = smem0 + s * G_STAGE;
+            const uint64_t dAh = sdesc_sw128(base), dAl = sdesc_sw128(base + G_A_BYTES);
+            const uint64_t dBh = sdesc_sw128(base + 2 * G_A_BYTES), dBl = sdesc_sw128(base + 2 * G_A_BYTES + G_B_BYTES);
+#pragma unroll
+            for (int ks = 0; ks < 4; ks++) {  // 4 x 8 tf32 = 128 bytes of K
+              const uint64_t off = (uint64_t)((ks * 32) >> 4);
+              const uint32_t acc = (kb == kb0 && ks == 0) ? 0u : 1u;
+              umma_tf32_n144(dcol, dAl + off, dBh + off, acc);
+              umma_tf32_n144(dcol, dAh + off, dBl + off, 1u);
+              umma_tf32_n144(dcol, dAh + off, dBh + off, 1u);
+            }
+            umma_commit(smem_u32(&bar_empty[s]));
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+      }
+      if (!ok) break;
+      if (lane == 0) umma_commit(smem_u32(&bar_tfull[ts]));
+      __syncwarp();
+    }
+    if (lane == 0) {
+      umma_commit(smem_u32(&bar_final));
+      drain_bar(smem_u32(&bar_final), 0);
+    }
+    __syncwarp();
+  } else {
+    const int quad = warp & 3;
+    int titer = 0;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, titer++) {
+      int mt, nt, sp, kb0, kb1;
+      coords(item, mt, nt, sp, kb0, kb1);
+      const int ts = titer & 1;
+      const uint32_t tpar = (titer >> 1) & 1;
+      const bool ok = wait_bar(smem_u32(&bar_tfull[ts]), tpar, abort_flag, g.dstatus);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int m = mt * 128 + quad * 32 + lane;
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + ts * 256;
+      float *out = g.Ct + ((size_t)sp * g.npad + (size_t)nt * G_NT) * g.ldc + m;
+#pragma unroll 1
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        float v[32];
+        tmem_ld32(taddr + c0, v);
+#pragma unroll
+        for (int c = 0; c < 32; c++) out[(size_t)(c0 + c) * g.ldc] = v[c];
+      }
+#pragma unroll
+      for (int c0 = 128; c0 < G_NT; c0 += 8) {
+        float v[8];
+        tmem_ld8(taddr + c0, v);
+#pragma unroll
+        for (int c = 0; c < 8; c++) out[(size_t)(c0 + c) * g.ldc] = v[c];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[ts]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// conj-phase operand P[n][kk] (tf32 hi/lo), n = 2r + s, kk = 2q + t:
+//   (s,t) = (0,0): cos, (0,1): sin, (1,0): -sin, (1,1): cos  of 2 pi (q.R_r mod 1)
+// so that row 2r of Xbar P^T is Re sum_q conj(P_q(R_r)) Xbar and row 2r+1 its Im.
+__global__ void k_build_pconj(int nq, int nR, int ld, const double *__restrict__ q, const int *__restrict__ R,
+                              float *hi, float *lo) {
+  size_t n = (size_t)nq * 2 * nR;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int iq = (int)(idx % nq);
+    const int row = (int)(idx / nq);
+    const int r = row >> 1, s = row & 1;
+    double x = q[3 * iq] * R[3 * r] + q[3 * iq + 1] * R[3 * r + 1] + q[3 * iq + 2] * R[3 * r + 2];
+    x -= rint(x);
+    const double x2 = 2.0 * x;
+    const float xh = (float)x2;
+    const float xl = (float)(x2 - (double)xh) * 3.14159265358979f;
+    float sn, cs;
+    sincospif(xh, &sn, &cs);
+    const float c = fmaf(-xl, sn, cs), sv = fmaf(xl, cs, sn);
+    const float v0 = s == 0 ? c : -sv, v1 = s == 0 ? sv : c;
+    const size_t o = (size_t)row * ld + 2 * (size_t)iq;
+    const float h0 = tf32_rn(v0), h1 = tf32_rn(v1);
+    *reinterpret_cast<float2 *>(hi + o) = make_float2(h0, h1);
+    *reinterpret_cast<float2 *>(lo + o) = make_float2(tf32_rn(v0 - h0), tf32_rn(v1 - h1));
+  }
+}
+
+// Bbar[r][kl][c] = sum_sp (Ct[sp][2r][m], Ct[sp][2r+1][m]),  m = kl*nc + c, fixed order.
+__global__ void k_xbar_reduce(int nR, int kc, int nc, int splits, int npad, int ldc, const float *__restrict__ Ct,
+                              cx<float> *Bbar) {
+  size_t n = (size_t)nR * kc * nc;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % nc);
+    const size_t rest = idx / nc;
+    const int kl = (int)(rest % kc);
+    const int r = (int)(rest / kc);
+    const size_t m = (size_t)kl * nc + c;
+    float re = 0.0f, im = 0.0f;
+    for (int sp = 0; sp < splits; sp++) {
+      re += Ct[((size_t)sp * npad + 2 * r) * ldc + m];
+      im += Ct[((size_t)sp * npad + 2 * r + 1) * ldc + m];
+    }
+    Bbar[idx] = mkc(re, im);
+  }
+}
+
+__global__ void k_cot_table(size_t n, const double *__restrict__ cot, float *cotF) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    cotF[i] = (float)cot[i];
+}
+
+bool make_map_f32(CUtensorMap *map, const void *base, uint64_t inner, uint64_t ld, uint64_t rows, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {ld * 4};
+  cuuint32_t box[2] = {32, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+epw_status tc_bwd_plan(Arena &A, const epw_model *m, int nk, int nq, TcBuffers &b, TcBwdBuffers &w) {
+  CKS_TC(tc_plan(A, m, nk, nq, TC_OP_TF32, b));
+  w = TcBwdBuffers{};
+  if (!b.ok) return EPW_OK;
+  const int nc = m->nm * m->nw * m->nw;
+  w.nc = nc;
+  w.ld = (2 * nq + 31) / 32 * 32;
+  const size_t row_bytes = (size_t)nc * w.ld * 4 * 2;  // per k, hi + lo
+  int kc = (int)std::min<size_t>((size_t)nk, std::max<size_t>(2, ((size_t)2 << 30) / std::max<size_t>(row_bytes, 1)));
+  kc = (kc + 1) / 2 * 2;
+  w.kc = kc;
+  w.mtiles = (kc * nc + 127) / 128;
+  w.ntiles = (2 * m->nRe + G_NT - 1) / G_NT;
+  w.kblocks = (2 * nq + 31) / 32;
+  const int tiles = w.mtiles * w.ntiles;
+  int splits = std::max(1, std::min(w.kblocks, (2 * 152 + tiles - 1) / tiles));
+  w.kb_per_split = (w.kblocks + splits - 1) / splits;
+  w.splits = (w.kblocks + w.kb_per_split - 1) / w.kb_per_split;
+  w.ldc = w.mtiles * 128;
+  w.npad = w.ntiles * G_NT;
+  w.phi = A.take<float>((size_t)2 * m->nRe * w.ld);
+  w.plo = A.take<float>((size_t)2 * m->nRe * w.ld);
+  w.xhi = A.take<float>((size_t)kc * nc * w.ld);
+  w.xlo = A.take<float>((size_t)kc * nc * w.ld);
+  w.Ct = A.take<float>((size_t)w.splits * w.npad * w.ldc);
+  w.Bbar = A.take<cx<float>>((size_t)m->nRp * kc * nc);
+  w.G1bar = A.take<cx<float>>((size_t)m->nRp * kc * nc);
+  w.cotF = A.take<float>((size_t)nk * m->nw);
+  w.partT = A.take<double>((size_t)kc * 4 * b.nqt);
+  w.partE = A.take<double>((size_t)kc * 4 * b.nqt);
+  return EPW_OK;
+}
+
+epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const double *q, const double *wq,
+                                 const epw_params *par, const double *epsk, const cx<double> *Uk,
+                                 const cx<float> *Pk32, const double *omegaT, const cx<float> *ET32,
+                                 const cx<float> *Bg32, const cx<float> *BH32, const double *cot, TcBuffers &b,
+                                 TcBwdBuffers &w, cx<float> *gwbar, double *scal, cudaStream_t st) {
+  if (!b.ok) return EPW_ERR_UNSUPPORTED;
+  const int nR = m->nRe, nw = m->nw, nc = w.nc;
+  // forward operands (tf32 split), epilogue tables, conj-phase operand, cotangent table
+  {
+    size_t n = (size_t)nq * b.kpad;
+    k_build_a<float><<<grid_for(n, 256), 256, 0, st>>>(nq, nR, b.kpad, q, m->Re, (float *)b.Ahi, (float *)b.Alo);
+    epw_count_launch();
+    n = (size_t)b.nk_pad * b.cpk * b.kpad;
+    k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, nw, m->nm, b.cpk, b.kpad, BH32, Bg32,
+                                                        (float *)b.Bhi, (float *)b.Blo);
+    epw_count_launch();
+    n = (size_t)nq * m->nm + nq + (size_t)nk * nw;
+    k_tc_tables<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nm, nk, nw, omegaT, par->T_K, wq, epsk, b.nbT, b.omF,
+                                                   b.wqF, b.ekF);
+    epw_count_launch();
+    n = (size_t)nq * 2 * nR;
+    k_build_pconj<<<grid_for(n, 256), 256, 0, st>>>(nq, nR, w.ld, q, m->Re, w.phi, w.plo);
+    epw_count_launch();
+    n = (size_t)nk * nw;
+    k_cot_table<<<grid_for(n, 256), 256, 0, st>>>(n, cot, w.cotF);
+    epw_count_launch();
+  }
+  CUtensorMap ah, al, ph, pl;
+  if (!make_map(&ah, b.Ahi, TC_OP_TF32, b.kpad, nq, BM) || !make_map(&al, b.Alo, TC_OP_TF32, b.kpad, nq, BM) ||
+      !make_map_f32(&ph, w.phi, 2 * (uint64_t)nq, w.ld, 2 * (uint64_t)nR, G_NT) ||
+      !make_map_f32(&pl, w.plo, 2 * (uint64_t)nq, w.ld, 2 * (uint64_t)nR, G_NT))
+    return EPW_ERR_CUDA;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_tc_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM) != cudaSuccess)
+      return EPW_ERR_CUDA;
+    attr = true;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int k0 = 0; k0 < nk; k0 += w.kc) {
+    const int kc = std::min(w.kc, nk - k0);
+    const int kc_pad = (kc + b.kpt - 1) / b.kpt * b.kpt;
+    CUtensorMap bh, bl;
+    const size_t boff = (size_t)k0 * b.cpk * b.kpad;
+    if (!make_map(&bh, (const float *)b.Bhi + boff, TC_OP_TF32, b.kpad, (uint64_t)kc_pad * b.cpk, BN) ||
+        !make_map(&bl, (const float *)b.Blo + boff, TC_OP_TF32, b.kpad, (uint64_t)kc_pad * b.cpk, BN))
+      return EPW_ERR_CUDA;
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nk = kc;
+    a.nq = nq;
+    a.nqt = b.nqt;
+    a.nkg = kc_pad / b.kpt;
+    a.kpad = b.kpad;
+    a.nkb = (b.kpad + 31) / 32;
+    {
+      const size_t atile = (size_t)BM * b.kpad * 4 * 2;
+      int qb = (int)(A_BLOCK_BYTES / atile);
+      qb = std::max(qb, 152);
+      qb = std::min(qb, b.nqt);
+      a.qblock = std::max(qb, 1);
+    }
+    a.epsk = b.ekF + (size_t)k0 * nw;
+    a.omegaT = b.omF;
+    a.nbT = b.nbT;
+    a.ET = (const float2 *)ET32;
+    a.wq = b.wqF;
+    a.EF = (float)par->EF_eV;
+    a.invkT = (float)(1.0 / (EPW_KB * par->T_K));
+    a.inv_sigma = (float)(1.0 / par->sigma_eV);
+    a.gnorm = (float)(1.0 / (par->sigma_eV * 1.7724538509055160273));
+    a.omega_min = (float)par->omega_min_eV;
+    a.cot = w.cotF + (size_t)k0 * nw;
+    a.xhi = w.xhi;
+    a.xlo = w.xlo;
+    a.ldx = w.ld;
+    a.partT = w.partT;
+    a.partE = w.partE;
+    a.T = (float)par->T_K;
+    a.dstatus = m->dstatus;
+    cudaError_t e = launch_tc_shape<TC_OP_TF32, 2>(nw, m->nm, ah, al, bh, bl, a, st);
+    epw_count_launch();
+    if (e != cudaSuccess) return EPW_ERR_CUDA;
+    launch_sum_scalar(kc * 4 * b.nqt, w.partT, 1.0, scal, st);
+    launch_sum_scalar(kc * 4 * b.nqt, w.partE, 1.0, scal + 1, st);
+    // q contraction on the tensor cores (split K), then the fixed-order reduction
+    const int M = kc * nc;
+    CUtensorMap xh, xl;
+    if (!make_map_f32(&xh, w.xhi, 2 * (uint64_t)nq, w.ld, (uint64_t)M, 128) ||
+        !make_map_f32(&xl, w.xlo, 2 * (uint64_t)nq, w.ld, (uint64_t)M, 128))
+      return EPW_ERR_CUDA;
+    GemmArgs g;
+    g.mtiles = (M + 127) / 128;
+    g.ntiles = w.ntiles;
+    g.kblocks = w.kblocks;
+    g.kb_per_split = w.kb_per_split;
+    g.splits = w.splits;
+    g.ldc = w.ldc;
+    g.npad = w.npad;
+    g.Ct = w.Ct;
+    g.dstatus = m->dstatus;
+    const int items = g.mtiles * g.ntiles * g.splits;
+    k_tc_gemm_nt<<<std::min(items, sms), G_THREADS, G_SMEM, st>>>(xh, xl, ph, pl, g);
+    epw_count_launch();
+    if (cudaGetLastError() != cudaSuccess) return EPW_ERR_CUDA;
+    const size_t nred = (size_t)m->nRp * kc * nc;
+    k_xbar_reduce<<<grid_for(nred, 256), 256, 0, st>>>(m->nRp, kc, nc, g.splits, g.npad, g.ldc, w.Ct, w.Bbar);
+    epw_count_launch();
+    // k side: rotation adjoint, then conj(P_k(Re)) contraction into gwbar
+    launch_bg_adjoint_rotate_k0<float>(kc, k0, m->nRp, m->nm, nw, w.Bbar, Uk, w.G1bar, st);
+    const int ncol2 = m->nRp * nc;
+    launch_cgemm<float>(m->nRe, ncol2, kc, Pk32 + (size_t)k0 * m->nRe, m->nRe, true, true, w.G1bar, ncol2, gwbar,
+                        ncol2, true, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
+}

@@ -34,3 +34,30 @@ epw_status tc_interp(const epw_model *m, int nk, int nq, const double *q, double
                      const double *omegaT, const cx<float> *ET32, const cx<float> *Bg32, const cx<float> *BH32,
                      TcBuffers &b, double *eps_kq, double *g, cudaStream_t st);
 void tc_free(epw_model *m);
+
+// Buffers of the tensor-core adjoint (per chunk of kc k-points).
+struct TcBwdBuffers {
+  float *phi, *plo;        // conj-phase operand [2nR][ld]
+  float *xhi, *xlo;        // Xbar rows [kc*nc][ld]
+  float *Ct;               // split-K partials [splits][npad][ldc]
+  cx<float> *Bbar, *G1bar; // [nRp][kc][nc], [kc][nRp][nc]
+  float *cotF;             // [nk][nw]
+  double *partT, *partE;   // [kc][4*nqt]
+  int nc, ld, kc, mtiles, ntiles, kblocks, kb_per_split, splits, ldc, npad;
+};
+
+#define CKS_TC(expr)              \
+  do {                            \
+    epw_status s_ = (expr);       \
+    if (s_ != EPW_OK) return s_;  \
+  } while (0)
+
+// Lay out the adjoint's buffers (forward operands at TF32 included).
+epw_status tc_bwd_plan(Arena &A, const epw_model *m, int nk, int nq, TcBuffers &b, TcBwdBuffers &w);
+// Accumulates dL/dgw into gwbar [nRe][nRp][nm][nw][nw] and (dL/dT, dL/dE_F) into scal[0..1],
+// for L = sum c_nk Im Sigma_nk with c = cot [nk][nw] (device).
+epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const double *q, const double *wq,
+                                 const epw_params *par, const double *epsk, const cx<double> *Uk,
+                                 const cx<float> *Pk32, const double *omegaT, const cx<float> *ET32,
+                                 const cx<float> *Bg32, const cx<float> *BH32, const double *cot, TcBuffers &b,
+                                 TcBwdBuffers &w, cx<float> *gwbar, double *scal, cudaStream_t st);

@@ -66,3 +66,44 @@ def test_autograd_directional_finite_differences(setup):
     assert abs(fdT - Tt.grad.item()) <= 1e-6 * abs(fdT)
     fdE = (L(g0, EF=0.2 + 1e-6) - L(g0, EF=0.2 - 1e-6)) / 2e-6
     assert abs(fdE - Et.grad.item()) <= 1e-6 * abs(fdE)
+
+
+@pytest.mark.parametrize("nw,nR", [(4, 40), (2, 30), (1, 27)])
+def test_tensor_core_adjoint_matches_oracle(nw, nR, oracle_lib):
+    """TF32x3 adjoint (fused recompute + tcgen05 q-contraction) against the FP64 oracle gradient."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_03525_gb300 as epw
+    rng = np.random.default_rng(40 + nw)
+    lat = "sc" if nw == 1 else "fcc"
+    wm = W.make_model(lat, nw, 1, [1.0], nR, nR, rng)
+    k = rng.random((5, 3))
+    q = rng.random((300, 3))
+    cot = rng.random((5, nw))
+    m = epw.Model(wm)
+    dg, dT, dE = m.linewidth_backward(k, q, cot, T=300.0, EF=0.1, sigma=0.05, precision=epw.TF32X3)
+    rdg, rdT, rdE = oracle_lib.linewidth_grad(wm, k, q, None, 300.0, 0.1, 0.05, cot=cot)
+    assert np.abs(dg - rdg).max() <= 2e-4 * np.abs(rdg).max()
+    assert abs(dT - rdT) <= 2e-4 * abs(rdT)
+    assert abs(dE - rdE) <= 2e-4 * abs(rdE)
+
+
+def test_tensor_core_adjoint_chunks_at_benchmark_q():
+    """Benchmark model and 40^3 q grid, 100 k (three k chunks): TF32x3 adjoint vs the FP32 SIMT adjoint."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_03525_gb300 as epw
+    wl = W.make_workload("fcc_nw4")
+    m = epw.Model(wl.model)
+    k = torch.tensor(wl.k[:100], device="cuda")
+    q = torch.tensor(wl.q, device="cuda")
+    wq = torch.tensor(wl.wq, device="cuda")
+    cot = torch.ones((100, 4), dtype=torch.float64, device="cuda")
+    a = m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.TF32X3)
+    b = m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.FP32)
+    ga, gb = a[0].cpu().numpy(), b[0].cpu().numpy()
+    assert np.abs(ga - gb).max() <= 1e-3 * np.abs(gb).max()
+    assert abs(a[1] - b[1]) <= 1e-3 * abs(b[1])
+    assert abs(a[2] - b[2]) <= 1e-3 * abs(b[2])
