@@ -195,7 +195,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "tf32x3", "bf16x3", "fp32", "fp64"])
     ap.add_argument("--other-steps", type=int, default=2, help="timed steps of the other tensor-core/FP32 forms")
-    ap.add_argument("--backward-steps", type=int, default=1, help="timed adjoint calls (0: skip)")
+    ap.add_argument("--backward-steps", type=int, default=3, help="timed adjoint calls (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU form (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -303,19 +303,26 @@ def main():
                 "kernel_ms": k64}
     backward = None
     if args.backward_steps > 0:
-        # adjoint of sum_{k,n} Im Sigma_nk w.r.t. g(Re,Rp), T and E_F (FP32 SIMT form), device buffers
+        # adjoint of sum_{k,n} Im Sigma_nk w.r.t. g(Re,Rp), T and E_F, device buffers, g(k,q)
+        # recomputed: the tensor-core form (TF32x3) timed, the FP32 SIMT form once beside it
         cot = torch.ones((len(wl.k), wl.model.nw), dtype=torch.float64, device=dev)
-        m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.FP32)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.backward_steps):
-            m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.FP32)
-        e1.record()
-        torch.cuda.synchronize()
-        bms = e0.elapsed_time(e1) / args.backward_steps
-        backward = {"value": pairs / (bms / 1e3), "unit": "pairs/s", "ms_per_step": bms, "precision": "fp32",
+
+        def time_backward(op, n):
+            m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=op)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(n):
+                m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=op)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / n
+
+        bms = time_backward(epw.TF32X3, args.backward_steps)
+        backward = {"value": pairs / (bms / 1e3), "unit": "pairs/s", "ms_per_step": bms, "precision": "tf32x3",
                     "what": "dL/dg(Re,Rp), dL/dT, dL/dE_F of L = sum Im Sigma; g(k,q) recomputed"}
+        fms = time_backward(epw.FP32, 1)
+        backward["fp32_simt"] = {"value": pairs / (fms / 1e3), "unit": "pairs/s", "ms_per_step": fms}
     others = {}
     if args.other_steps > 0:
         for oname, op in (("bf16x3", epw.BF16X3), ("tf32x3", epw.TF32X3), ("fp32", epw.FP32)):

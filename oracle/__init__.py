@@ -89,8 +89,9 @@ def _load():
             for name in ("oracle_bose", "oracle_gauss"):
                 getattr(lib, name).argtypes = [ctypes.c_double, ctypes.c_double]
                 getattr(lib, name).restype = ctypes.c_double
-            lib.oracle_fermi.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
-            lib.oracle_fermi.restype = ctypes.c_double
+            for name in ("oracle_fermi", "oracle_fermi_slope"):
+                getattr(lib, name).argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+                getattr(lib, name).restype = ctypes.c_double
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = I
             _lib = lib
@@ -239,6 +240,10 @@ def bose(w, T):
 
 def fermi(e, EF, T):
     return _load().oracle_fermi(float(e), float(EF), float(T))
+
+
+def fermi_slope(e, EF, T):
+    return _load().oracle_fermi_slope(float(e), float(EF), float(T))
 
 
 def gauss(x, sigma):

@@ -98,6 +98,14 @@ double oracle_fermi(double e, double EF, double T) {
   return 1.0 / (1.0 + exp(x));
 }
 
+/* f (1 - f) = -kT df/de, written as t / (1 + t)^2 with t = exp(-|x|): the same
+   value as forming 1 - f, but without its cancellation once f rounds to 1. */
+double oracle_fermi_slope(double e, double EF, double T) {
+  if (T <= 0.0) return 0.0;
+  double t = exp(-fabs((e - EF) / (KB_EV * T)));
+  return t / ((1.0 + t) * (1.0 + t));
+}
+
 double oracle_gauss(double x, double sigma) {
   double y = x / sigma;
   return exp(-y * y) / (sigma * sqrt(M_PI));
@@ -462,8 +470,9 @@ int oracle_linewidth_grad(const oracle_model *m, int nk, const double *k, int nq
               Wg[id] = W * gmn[id];
               double g2 = creal(gmn[id]) * creal(gmn[id]) + cimag(gmn[id]) * cimag(gmn[id]);
               double dn_dT = nb * (nb + 1.0) * w[nu] / (kT * pr->T);
-              double df_dT = f * (1.0 - f) * (ekq[mm] - pr->EF) / (kT * pr->T);
-              double df_dE = f * (1.0 - f) / kT;
+              double ff = oracle_fermi_slope(ekq[mm], pr->EF, pr->T);
+              double df_dT = ff * (ekq[mm] - pr->EF) / (kT * pr->T);
+              double df_dE = ff / kT;
               nsum_add(&sT[tid], c * M_PI * wqi * g2 * ((dn_dT + df_dT) * dp + (dn_dT - df_dT) * dm));
               nsum_add(&sE[tid], c * M_PI * wqi * g2 * (df_dE * dp - df_dE * dm));
             }

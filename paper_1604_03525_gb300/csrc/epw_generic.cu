@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
       for (int m = 0; m < MW; m++) {
         if (m >= nw) continue;
         R f = occ_fermi<R>(ekq[m], a.EF, a.T);
-        double ff = (double)f * (1.0 - (double)f);
+        double ff = fermi_ff_d((double)ekq[m] - a.EF, a.T);
         double dfT = ff * ((double)ekq[m] - a.EF) / (kT * a.T);
         double dfE = ff / kT;
 #pragma unroll UW

@@ -87,6 +87,21 @@ __device__ __forceinline__ float fermi_f(float d, float invkT) {
   return x > 0.0f ? t / (1.0f + t) : 1.0f / (1.0f + t);
 }
 
+// f (1 - f) = t / (1 + t)^2 with t = e^{-|e - EF|/kT}: no cancellation in the tails
+// (forming 1 - f from a rounded f loses everything once f rounds to 1).
+__device__ __forceinline__ float fermi_ff_f(float d, float invkT) {
+  if (invkT <= 0.0f) return 0.0f;
+  const float t = __expf(-fabsf(d * invkT));
+  const float u = 1.0f + t;
+  return t / (u * u);
+}
+__device__ __forceinline__ double fermi_ff_d(double d, double T) {
+  if (T <= 0.0) return 0.0;
+  const double t = exp(-fabs(d / (EPW_KB * T)));
+  const double u = 1.0 + t;
+  return t / (u * u);
+}
+
 // -------------------------------------------------------- Jacobi eigensolver
 // Hermitian N x N (runtime n <= N, compile-time N so that fully unrolled loops
 // keep the arrays in registers for small N).  Cyclic sweeps of two-sided

@@ -555,7 +555,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
 #pragma unroll
       for (int m = 0; m < NW; m++) {
         const float f = fm[m];
-        const float ff = f * (1.0f - f);
+        const float ff = fermi_ff_f(em[m] - a.EF, a.invkT);
         const float dfT = ff * (em[m] - a.EF) * a.invkT / a.T;
         const float dfE = ff * a.invkT;
         const float cp = kf * (nbnu + f), cm = kf * (nbnu + 1.0f - f);

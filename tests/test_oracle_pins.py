@@ -258,6 +258,18 @@ def test_occupations_and_delta(oracle_lib):
         assert math.isclose(oracle_lib.fermi(e, EF, T) + oracle_lib.fermi(2 * EF - e, EF, T), 1.0, rel_tol=1e-14)
     assert oracle_lib.fermi(-0.1, 0.0, 0.0) == 1.0 and oracle_lib.fermi(0.1, 0.0, 0.0) == 0.0
     assert oracle_lib.fermi(0.0, 0.0, 0.0) == 0.5
+    # f (1 - f) against the occupations where 1 - f is exact enough, against the
+    # slope -kT df/de by central differences, and against exp(-|x|) deep in the tails.
+    for e, EF, T in [(0.03, 0.0, 300.0), (-0.01, 0.02, 77.0)]:
+        f = oracle_lib.fermi(e, EF, T)
+        assert math.isclose(oracle_lib.fermi_slope(e, EF, T), f * (1 - f), rel_tol=1e-13)
+        h = 1e-7
+        d = (oracle_lib.fermi(e + h, EF, T) - oracle_lib.fermi(e - h, EF, T)) / (2 * h)
+        assert math.isclose(oracle_lib.fermi_slope(e, EF, T), -KB * T * d, rel_tol=1e-6)
+    for x in (40.0, -40.0, 300.0):
+        T = 300.0
+        assert math.isclose(oracle_lib.fermi_slope(x * KB * T, 0.0, T), math.exp(-abs(x)), rel_tol=1e-12)
+    assert oracle_lib.fermi_slope(0.1, 0.0, 0.0) == 0.0
     s = 0.02
     x = np.linspace(-12 * s, 12 * s, 20001)
     vals = np.array([oracle_lib.gauss(v, s) for v in x])
