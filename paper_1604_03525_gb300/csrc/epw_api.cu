@@ -412,16 +412,24 @@ struct LwPlan {
   double *partial;
   double *out_d;
   TcBuffers tc;
+  TcStaged sg;
 };
+
+// Contraction buffer of the staged tensor-core form (per chunk of k).
+static const size_t STAGED_CT_BYTES = (size_t)4 << 30;
 
 static epw_status plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,
                                  bool sout, LwPlan &L) {
   const bool tc = prec == EPW_BF16X3 || prec == EPW_TF32X3;
+  const int op = prec == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32;
   plan_prep(A, m, nk, nq, tc ? EPW_FP32 : prec, sk, sq, swq, true, L.p);
-  if (tc) {
-    CKS(tc_plan(A, m, nk, nq, prec == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32, L.tc));
+  L.sg = TcStaged{};
+  L.tc = TcBuffers{};
+  if (tc && tc_supported(m)) {
+    CKS(tc_plan(A, m, nk, nq, op, L.tc));
     L.partial = nullptr;
   } else {
+    if (tc) CKS(tc_staged_plan(A, m, nk, nq, op, STAGED_CT_BYTES, L.sg));
     int nqb = (nq + 127) / 128;
     L.partial = A.take<double>((size_t)nk * nqb * m->nw);
   }
@@ -479,11 +487,50 @@ extern "C" epw_status epw_linewidth(const epw_model *mc, int nk, const double *k
     wqd = p.wqd;
   }
   double *out = sout ? L.out_d : imsigma;
-  if (prec == EPW_BF16X3 || prec == EPW_TF32X3) {
+  const bool tcp = prec == EPW_BF16X3 || prec == EPW_TF32X3;
+  if (tcp && !L.tc.ok && !L.sg.ok)
+    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
+  if (tcp && L.tc.ok) {
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
     epw_status s = tc_linewidth(m, nk, kd, nq, qd, wqd, par, p.PkRM, p.epsk, p.Uk, p.omegaT, (const cx<float> *)p.ET,
                                 (const cx<float> *)p.Bg, (const cx<float> *)p.BH, L.tc, out, st);
     if (s != EPW_OK) return fail(s, "tensor-core path: %s", g_err[0] ? g_err : "unsupported shape");
+  } else if (tcp) {
+    // staged tensor-core form: contraction per chunk of k on the tensor cores, per-pair work from HBM
+    CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
+    CKS(tc_staged_phases(m, nq, qd, L.sg, st));
+    epw_timing_begin(m, st);
+    for (int k0 = 0; k0 < nk; k0 += L.sg.kc) {
+      const int kc = std::min(L.sg.kc, nk - k0);
+      epw_status s = tc_staged_contract(m, k0, kc, nq, (const cx<float> *)p.Bg, (const cx<float> *)p.BH, L.sg, st);
+      if (s != EPW_OK) return fail(s, "staged tensor-core contraction failed");
+      PairArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.nk = kc;
+      a.nq = nq;
+      a.nw = m->nw;
+      a.nm = m->nm;
+      a.nRe = m->nRe;
+      a.nRp = m->nRp;
+      a.k0 = k0;
+      a.ET = p.ET;
+      a.omegaT = p.omegaT;
+      a.eps_k = p.epsk;
+      a.wq = wqd;
+      a.T = par->T_K;
+      a.EF = par->EF_eV;
+      a.sigma = par->sigma_eV;
+      a.omega_min = par->omega_min_eV;
+      a.partial = L.partial;
+      a.dstatus = m->dstatus;
+      a.Cq = L.sg.Ct;
+      a.ldc = (size_t)L.sg.ldc;
+      a.cpk = L.sg.cpk;
+      s = launch_pair_staged(a, 0, st);
+      if (s != EPW_OK) return fail(s, "no staged per-pair kernel for nw=%d, 3nat=%d", m->nw, m->nm);
+    }
+    epw_timing_end(m, st);
+    launch_finalize(nk, (nq + 127) / 128, m->nw, L.partial, out, st);
   } else {
     CKS(run_prep(m, nk, kd, nq, qd, prec, par->omega_min_eV, true, p, nullptr, st));
     PairArgs a;
@@ -531,10 +578,11 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
   epw_model *m = const_cast<epw_model *>(mc);
   CKS(check_common(m, nk, k, nq, q));
   if (precision < EPW_FP64 || precision > EPW_TF32X3) return fail(EPW_ERR_INVALID_ARG, "unknown precision");
-  const bool tc = precision == EPW_BF16X3 || precision == EPW_TF32X3;
-  if (tc && !tc_supported(m))
-    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core kernel for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
-  const int wprec = tc ? EPW_FP32 : precision;  // precision of the shared preparation
+  const bool tcp = precision == EPW_BF16X3 || precision == EPW_TF32X3;
+  const bool tc = tcp && tc_supported(m), staged = tcp && tc_staged_supported(m);
+  if (tcp && !tc && !staged)
+    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
+  const int wprec = tcp ? EPW_FP32 : precision;  // precision of the shared preparation
   if (!(omega_min >= 0.0)) return fail(EPW_ERR_INVALID_ARG, "omega_min must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
   if (nk == 0 && nq == 0) return EPW_OK;
@@ -543,14 +591,16 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
   const bool s_ek = eps_k && !is_device_ptr(eps_k), s_ekq = eps_kq && !is_device_ptr(eps_kq);
   const bool s_om = omega && !is_device_ptr(omega), s_g = g && !is_device_ptr(g);
   TcBuffers tcb;
+  TcStaged sg{};
   auto plan = [&](Arena &A, Prep &p, double *&ekd, double *&ekqd, double *&omd, double *&gd) -> epw_status {
     plan_prep(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, wprec, sk, sq, false, true, p);
     ekd = s_ek ? A.take<double>((size_t)nk * nw) : eps_k;
     ekqd = s_ekq ? A.take<double>((size_t)nk * nq * nw) : eps_kq;
     omd = s_om ? A.take<double>((size_t)nq * nm) : omega;
     gd = s_g ? (double *)A.take<cx<double>>((size_t)nk * nq * nm * nw * nw) : g;
-    if (tc) return tc_plan(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, precision == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32,
-                           tcb);
+    const int op = precision == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32;
+    if (tc) return tc_plan(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, op, tcb);
+    if (staged) return tc_staged_plan(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, op, STAGED_CT_BYTES, sg);
     return EPW_OK;
   };
   Arena A{nullptr, 0, 0};
@@ -575,6 +625,35 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
     epw_status s = tc_interp(m, nk, nq, qd, omega_min, p.epsk, p.omegaT, (const cx<float> *)p.ET,
                              (const cx<float> *)p.Bg, (const cx<float> *)p.BH, tcb, ekqd, gd, st);
     if (s != EPW_OK) return fail(s, "tensor-core interpolation failed");
+  } else if (staged && nk > 0 && nq > 0 && (ekqd || gd)) {
+    CKS(tc_staged_phases(m, nq, qd, sg, st));
+    for (int k0 = 0; k0 < nk; k0 += sg.kc) {
+      const int kc = std::min(sg.kc, nk - k0);
+      epw_status s = tc_staged_contract(m, k0, kc, nq, (const cx<float> *)p.Bg, (const cx<float> *)p.BH, sg, st);
+      if (s != EPW_OK) return fail(s, "staged tensor-core contraction failed");
+      PairArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.nk = kc;
+      a.nq = nq;
+      a.nw = m->nw;
+      a.nm = m->nm;
+      a.nRe = m->nRe;
+      a.nRp = m->nRp;
+      a.k0 = k0;
+      a.ET = p.ET;
+      a.omegaT = p.omegaT;
+      a.eps_k = p.epsk;
+      a.omega_min = omega_min;
+      a.sigma = 1.0;
+      a.eps_kq = ekqd;
+      a.gout = (cx<double> *)gd;
+      a.dstatus = m->dstatus;
+      a.Cq = sg.Ct;
+      a.ldc = (size_t)sg.ldc;
+      a.cpk = sg.cpk;
+      s = launch_pair_staged(a, 1, st);
+      if (s != EPW_OK) return fail(s, "no staged per-pair kernel for nw=%d, 3nat=%d", m->nw, m->nm);
+    }
   } else if (nk > 0 && nq > 0 && (ekqd || gd)) {
     PairArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -620,7 +699,12 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   if (nk > 0 && !cot) return fail(EPW_ERR_INVALID_ARG, "null grad_imsigma");
   const int prec = par->precision >= EPW_BF16X3 ? EPW_FP32 : par->precision;
   // tensor-core adjoint (TF32 split) for shapes the fused kernel serves
-  const bool tcb = (par->precision == EPW_BF16X3 || par->precision == EPW_TF32X3) && tc_supported(m);
+  const bool tcp = par->precision == EPW_BF16X3 || par->precision == EPW_TF32X3;
+  const bool tcb = tcp && tc_supported(m);
+  // other shapes: the forward contraction of the recompute staged on the tensor cores
+  const bool staged = tcp && !tcb && tc_staged_supported(m);
+  if (tcp && !tcb && !staged)
+    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nw2 = (size_t)m->nw * m->nw, per = (size_t)m->nm * nw2;
   const size_t ng = (size_t)m->nRe * m->nRp * per;
@@ -637,7 +721,9 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
     double *cotd, *xbar, *Bbar, *G1bar, *gwbar, *pT, *pE, *sc, *dgd;
     TcBuffers tc;
     TcBwdBuffers tw;
+    TcStaged sg;
   } b;
+  b.sg = TcStaged{};
   auto plan = [&](Arena &A) -> epw_status {
     plan_prep(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, prec, sk, sq, swq, true, b.p);
     b.cotd = scot ? A.take<double>((size_t)nk * m->nw) : (double *)cot;
@@ -645,6 +731,11 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
       b.xbar = b.Bbar = b.G1bar = b.pT = b.pE = nullptr;
       CKS(tc_bwd_plan(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1, b.tc, b.tw));
     } else {
+      if (staged) {
+        CKS(tc_staged_plan(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1,
+                           par->precision == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32, (size_t)2 << 30, b.sg));
+        nkc = std::min(nkc, b.sg.kc);
+      }
       b.xbar = (double *)A.take<char>(sR * (size_t)nq * nkc * per);
       b.Bbar = (double *)A.take<char>(sR * (size_t)m->nRp * nkc * per);
       b.G1bar = (double *)A.take<char>(sR * (size_t)m->nRp * nkc * per);
@@ -686,8 +777,13 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
     if (s != EPW_OK) return fail(s, "tensor-core adjoint failed");
   } else if (nk > 0 && nq > 0) {
     CKS(run_prep(m, nk, kd, nq, qd, prec, par->omega_min_eV, true, p, nullptr, st));
+    if (staged) CKS(tc_staged_phases(m, nq, qd, b.sg, st));
     for (int k0 = 0; k0 < nk; k0 += nkc) {
       const int kc = std::min(nkc, nk - k0);
+      if (staged) {
+        epw_status s = tc_staged_contract(m, k0, kc, nq, (const cx<float> *)p.Bg, (const cx<float> *)p.BH, b.sg, st);
+        if (s != EPW_OK) return fail(s, "staged tensor-core contraction failed");
+      }
       PairArgs a;
       std::memset(&a, 0, sizeof(a));
       a.nk = nk;
@@ -715,7 +811,13 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
       a.partialE = b.pE;
       a.nkc = kc;
       a.dstatus = m->dstatus;
-      epw_status s = prec == EPW_FP64 ? launch_pair<double>(a, 2, st) : launch_pair<float>(a, 2, st);
+      if (staged) {
+        a.Cq = b.sg.Ct;
+        a.ldc = (size_t)b.sg.ldc;
+        a.cpk = b.sg.cpk;
+      }
+      epw_status s = staged ? launch_pair_staged(a, 2, st)
+                            : prec == EPW_FP64 ? launch_pair<double>(a, 2, st) : launch_pair<float>(a, 2, st);
       if (s != EPW_OK) return fail(s, "no per-pair kernel for nw=%d, 3nat=%d", m->nw, m->nm);
       launch_sum_scalar(kc * nqb, b.pT, 1.0, b.sc, st);
       launch_sum_scalar(kc * nqb, b.pE, 1.0, b.sc + 1, st);

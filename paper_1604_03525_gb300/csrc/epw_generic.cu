@@ -247,7 +247,7 @@ __device__ __forceinline__ double block_sum128(double v, double *sh /*[4]*/) {
 //   G_nu     = sum_a E_q[a][nu] U^dagger X_a                 (= g_mn,nu)
 // mode 0: linewidth terms of Eq. (linewidthel), reduced over the block;
 // mode 1: write e_k+q and g_mn,nu;  mode 2: adjoint (see launch_pair).
-template <typename R, int MW, int MM, int MODE>
+template <typename R, int MW, int MM, int MODE, bool FROMC = false>
 __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
   constexpr int UW = MW <= 4 ? MW : 1;
   constexpr int UM = MM <= 4 ? MM : 1;
@@ -269,14 +269,27 @@ __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
   for (int i = 0; i < MW; i++)
 #pragma unroll UW
     for (int j = 0; j < MW; j++) A[i][j] = mkc<R>(0, 0);
-  for (int r = 0; r < a.nRe; r++) {
-    cx<R> p = PqTe[(size_t)r * nq + qq];
-    const cx<R> *b = BH + (size_t)r * nw2;
+  if constexpr (FROMC) {
+    // Hermitian part of the staged H(k+q)
+    const float *C = a.Cq + (size_t)kl * a.cpk * a.ldc + qq;
 #pragma unroll UW
     for (int i = 0; i < MW; i++)
 #pragma unroll UW
       for (int j = 0; j < MW; j++)
-        if (i < nw && j < nw) cfma(A[i][j], p, b[i * nw + j]);
+        if (i < nw && j < nw) {
+          const size_t ij = 2 * (size_t)(i * nw + j), ji = 2 * (size_t)(j * nw + i);
+          A[i][j] = mkc<R>(R(0.5) * (C[ij * a.ldc] + C[ji * a.ldc]), R(0.5) * (C[(ij + 1) * a.ldc] - C[(ji + 1) * a.ldc]));
+        }
+  } else {
+    for (int r = 0; r < a.nRe; r++) {
+      cx<R> p = PqTe[(size_t)r * nq + qq];
+      const cx<R> *b = BH + (size_t)r * nw2;
+#pragma unroll UW
+      for (int i = 0; i < MW; i++)
+#pragma unroll UW
+        for (int j = 0; j < MW; j++)
+          if (i < nw && j < nw) cfma(A[i][j], p, b[i * nw + j]);
+    }
   }
   cx<R> U[MW][MW];
   bool nc = false;
@@ -298,14 +311,26 @@ __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
     for (int i = 0; i < MW; i++)
 #pragma unroll UW
       for (int j = 0; j < MW; j++) X[i][j] = mkc<R>(0, 0);
-    for (int r = 0; r < a.nRp; r++) {
-      cx<R> p = PqTp[(size_t)r * nq + qq];
-      const cx<R> *b = Bg + ((size_t)r * nm + al) * nw2;
+    if constexpr (FROMC) {
+      const float *C = a.Cq + ((size_t)kl * a.cpk + 2 * (size_t)nw2 * (1 + al)) * a.ldc + qq;
 #pragma unroll UW
       for (int i = 0; i < MW; i++)
 #pragma unroll UW
         for (int j = 0; j < MW; j++)
-          if (i < nw && j < nw) cfma(X[i][j], p, b[i * nw + j]);
+          if (i < nw && j < nw) {
+            const size_t ij = 2 * (size_t)(i * nw + j);
+            X[i][j] = mkc<R>(C[ij * a.ldc], C[(ij + 1) * a.ldc]);
+          }
+    } else {
+      for (int r = 0; r < a.nRp; r++) {
+        cx<R> p = PqTp[(size_t)r * nq + qq];
+        const cx<R> *b = Bg + ((size_t)r * nm + al) * nw2;
+#pragma unroll UW
+        for (int i = 0; i < MW; i++)
+#pragma unroll UW
+          for (int j = 0; j < MW; j++)
+            if (i < nw && j < nw) cfma(X[i][j], p, b[i * nw + j]);
+      }
     }
     // Y = U^dagger X, then G_nu += E[al][nu] Y
 #pragma unroll UW
@@ -669,6 +694,21 @@ epw_status launch_pair(const PairArgs &a, int mode, cudaStream_t st) {
 }
 template epw_status launch_pair<double>(const PairArgs &, int, cudaStream_t);
 template epw_status launch_pair<float>(const PairArgs &, int, cudaStream_t);
+
+epw_status launch_pair_staged(const PairArgs &a, int mode, cudaStream_t st) {
+  int nkl = (mode == 2) ? a.nkc : a.nk;
+  if (nkl <= 0 || a.nq <= 0) return EPW_OK;
+  if (!a.Cq || a.nw > 8 || a.nm > 9) return EPW_ERR_UNSUPPORTED;
+  dim3 grid((a.nq + 127) / 128, nkl);
+  if (mode == 0)
+    k_pair<float, 8, 9, 0, true><<<grid, 128, 0, st>>>(a);
+  else if (mode == 1)
+    k_pair<float, 8, 9, 1, true><<<grid, 128, 0, st>>>(a);
+  else
+    k_pair<float, 8, 9, 2, true><<<grid, 128, 0, st>>>(a);
+  epw_count_launch();
+  return EPW_OK;
+}
 
 void launch_set_vertex(const epw_model *m, const void *g, int is_c64, cudaStream_t st) {
   size_t per = (size_t)m->nm * m->nw * m->nw;

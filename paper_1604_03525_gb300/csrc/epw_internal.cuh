@@ -320,10 +320,17 @@ struct PairArgs {
   double *partialE;    // backward: [nkc][nqb]
   int nkc;             // backward: k in this chunk
   unsigned *dstatus;
+  // staged tensor-core form: contraction read from Cq[(kl*cpk + 2c + s)*ldc + q]
+  // (kl = k - k0; c over [H(k+q)_ij | (g_a(k,q) U_k)_jn], s = re/im) instead of computed
+  const float *Cq;
+  size_t ldc;
+  int cpk;
 };
 // mode: 0 linewidth, 1 interp, 2 backward
 template <typename R>
 epw_status launch_pair(const PairArgs &a, int mode, cudaStream_t st);
+// per-pair kernel on a staged contraction (a.Cq set; FP32)
+epw_status launch_pair_staged(const PairArgs &a, int mode, cudaStream_t st);
 void launch_finalize(int nk, int nqb, int nw, const double *partial, double *out, cudaStream_t st);
 // m->gw = wRe wRp g (g on the device)
 void launch_set_vertex(const epw_model *m, const void *g, int is_c64, cudaStream_t st);

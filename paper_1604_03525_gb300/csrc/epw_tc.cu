@@ -1124,9 +1124,12 @@ constexpr int G_STAGE = 2 * G_A_BYTES + 2 * G_B_BYTES;
 constexpr int G_STAGES = 3;
 constexpr int G_SMEM = G_STAGES * G_STAGE + 1024;
 constexpr int G_THREADS = 192;                     // producer, MMA, 4 epilogue warps
-// kind::tf32: D=F32, A=B=TF32, K-major, N=144, M=128
-constexpr uint32_t G_IDESC =
-    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(G_NT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// D=F32, K-major, N=144, M=128; A=B=TF32 (kind::tf32) or BF16 (kind::f16)
+template <int OP>
+constexpr uint32_t g_idesc() {
+  return (1u << 4) | ((OP == TC_OP_BF16 ? 1u : 2u) << 7) | ((OP == TC_OP_BF16 ? 1u : 2u) << 10) |
+         ((uint32_t)(G_NT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
 
 struct GemmArgs {
   int mtiles, ntiles, splits, kblocks, kb_per_split;
@@ -1136,15 +1139,26 @@ struct GemmArgs {
   unsigned *dstatus;
 };
 
-__device__ __forceinline__ void umma_tf32_n144(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::
-          "r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(G_IDESC), "r"(acc)
-      : "memory");
+template <int OP>
+__device__ __forceinline__ void umma_n144(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  if constexpr (OP == TC_OP_BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(g_idesc<OP>()), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(g_idesc<OP>()), "r"(acc)
+        : "memory");
+  }
 }
 
-// Ct[sp][n][m] = sum_{K blocks of split sp} A[m][K] B[n][K]   (two-term tf32 split, three MMAs)
+// Ct[sp][n][m] = sum_{K blocks of split sp} A[m][K] B[n][K]   (two-term split, three MMAs;
+// a K block is one 128-byte row: 32 tf32 or 64 bf16 elements)
+template <int OP>
 __global__ void __launch_bounds__(G_THREADS, 1)
     k_tc_gemm_nt(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                  const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, GemmArgs g) {
@@ -1201,10 +1215,11 @@ __global__ void __launch_bounds__(G_THREADS, 1)
             const uint32_t base = smem0 + s * G_STAGE;
             const uint32_t fb = smem_u32(&bar_full[s]);
             mbar_expect_tx(fb, G_STAGE);
-            tma_load_2d(base, &mAhi, kb * 32, mt * 128, fb);
-            tma_load_2d(base + G_A_BYTES, &mAlo, kb * 32, mt * 128, fb);
-            tma_load_2d(base + 2 * G_A_BYTES, &mBhi, kb * 32, nt * G_NT, fb);
-            tma_load_2d(base + 2 * G_A_BYTES + G_B_BYTES, &mBlo, kb * 32, nt * G_NT, fb);
+            const int kx = kb * OpT<OP>::BK;
+            tma_load_2d(base, &mAhi, kx, mt * 128, fb);
+            tma_load_2d(base + G_A_BYTES, &mAlo, kx, mt * 128, fb);
+            tma_load_2d(base + 2 * G_A_BYTES, &mBhi, kx, nt * G_NT, fb);
+            tma_load_2d(base + 2 * G_A_BYTES + G_B_BYTES, &mBlo, kx, nt * G_NT, fb);
 #pragma unroll
             for (int z = 0; z < G_STAGES; z++)
               if (z == s) issued[z] = (int)(it / G_STAGES) + 1;
@@ -1245,12 +1260,12 @@ __global__ void __launch_bounds__(G_THREADS, 1)
             const uint64_t dAh = sdesc_sw128(base), dAl = sdesc_sw128(base + G_A_BYTES);
             const uint64_t dBh = sdesc_sw128(base + 2 * G_A_BYTES), dBl = sdesc_sw128(base + 2 * G_A_BYTES + G_B_BYTES);
 #pragma unroll
-            for (int ks = 0; ks < 4; ks++) {  // 4 x 8 tf32 = 128 bytes of K
+            for (int ks = 0; ks < 4; ks++) {  // 4 MMAs of 32 bytes of K each
               const uint64_t off = (uint64_t)((ks * 32) >> 4);
               const uint32_t acc = (kb == kb0 && ks == 0) ? 0u : 1u;
-              umma_tf32_n144(dcol, dAl + off, dBh + off, acc);
-              umma_tf32_n144(dcol, dAh + off, dBl + off, 1u);
-              umma_tf32_n144(dcol, dAh + off, dBh + off, 1u);
+              umma_n144<OP>(dcol, dAl + off, dBh + off, acc);
+              umma_n144<OP>(dcol, dAh + off, dBl + off, 1u);
+              umma_n144<OP>(dcol, dAh + off, dBh + off, 1u);
             }
             umma_commit(smem_u32(&bar_empty[s]));
           }
@@ -1439,7 +1454,8 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
     return EPW_ERR_CUDA;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_tc_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_tc_gemm_nt<TC_OP_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM) !=
+        cudaSuccess)
       return EPW_ERR_CUDA;
     attr = true;
   }
@@ -1509,7 +1525,7 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
     g.Ct = w.Ct;
     g.dstatus = m->dstatus;
     const int items = g.mtiles * g.ntiles * g.splits;
-    k_tc_gemm_nt<<<std::min(items, sms), G_THREADS, G_SMEM, st>>>(xh, xl, ph, pl, g);
+    k_tc_gemm_nt<TC_OP_TF32><<<std::min(items, sms), G_THREADS, G_SMEM, st>>>(xh, xl, ph, pl, g);
     epw_count_launch();
     if (cudaGetLastError() != cudaSuccess) return EPW_ERR_CUDA;
     const size_t nred = (size_t)m->nRp * kc * nc;
@@ -1521,5 +1537,102 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
     launch_cgemm<float>(m->nRe, ncol2, kc, Pk32 + (size_t)k0 * m->nRe, m->nRe, true, true, w.G1bar, ncol2, gwbar,
                         ncol2, true, st);
   }
+  return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
+}
+
+// =============================================================== staged form
+// Shapes whose per-k columns 2 nw^2 (3nat + 1) exceed one 128-column slot of the
+// fused kernel (e.g. nw = 5 or 8 with 6 to 9 modes) run the same real GEMM on
+// the tensor cores per chunk of k with its result written to HBM,
+//   Ct[kl cpk + col][q] = sum_kk A[q][kk] B[kl][col][kk],
+// and the per-pair kernel (eigensolve, rotation, deltas) reads it from there.
+bool tc_staged_supported(const epw_model *m) { return m->same_ep && !tc_supported(m) && m->nw <= 8 && m->nm <= 9; }
+
+epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t ct_budget, TcStaged &s) {
+  s = TcStaged{};
+  s.op = op;
+  s.ok = tc_staged_supported(m);
+  if (!s.ok) return EPW_OK;
+  const int esz = op == TC_OP_BF16 ? 2 : 4;
+  const int kal = op == TC_OP_BF16 ? 16 : 8;  // K per MMA
+  s.kpad = (2 * m->nRe + kal - 1) / kal * kal;
+  s.cpk = 2 * m->nw * m->nw * (m->nm + 1);
+  s.mtiles = (std::max(nq, 1) + 127) / 128;
+  s.ldc = s.mtiles * 128;
+  const size_t per_k = (size_t)s.cpk * s.ldc * 4;
+  s.kc = (int)std::min<size_t>((size_t)std::max(nk, 1), std::max<size_t>(1, ct_budget / per_k));
+  const int ntiles = (s.kc * s.cpk + G_NT - 1) / G_NT;
+  s.Ahi = A.take<char>((size_t)std::max(nq, 1) * s.kpad * esz);
+  s.Alo = A.take<char>((size_t)std::max(nq, 1) * s.kpad * esz);
+  s.Bhi = A.take<char>((size_t)s.kc * s.cpk * s.kpad * esz);
+  s.Blo = A.take<char>((size_t)s.kc * s.cpk * s.kpad * esz);
+  s.Ct = A.take<float>((size_t)ntiles * G_NT * s.ldc);
+  return EPW_OK;
+}
+
+epw_status tc_staged_phases(const epw_model *m, int nq, const double *q, TcStaged &s, cudaStream_t st) {
+  if (!s.ok) return EPW_ERR_UNSUPPORTED;
+  const size_t n = (size_t)nq * s.kpad;
+  if (s.op == TC_OP_BF16)
+    k_build_a<__nv_bfloat16><<<grid_for(n, 256), 256, 0, st>>>(nq, m->nRe, s.kpad, q, m->Re,
+                                                                (__nv_bfloat16 *)s.Ahi, (__nv_bfloat16 *)s.Alo);
+  else
+    k_build_a<float><<<grid_for(n, 256), 256, 0, st>>>(nq, m->nRe, s.kpad, q, m->Re, (float *)s.Ahi, (float *)s.Alo);
+  epw_count_launch();
+  return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
+}
+
+epw_status tc_staged_contract(const epw_model *m, int k0, int kc, int nq, const cx<float> *Bg32,
+                              const cx<float> *BH32, TcStaged &s, cudaStream_t st) {
+  if (!s.ok || kc > s.kc) return EPW_ERR_UNSUPPORTED;
+  const int nR = m->nRe, nw2 = m->nw * m->nw;
+  const size_t nb = (size_t)kc * s.cpk * s.kpad;
+  const cx<float> *bh = BH32 + (size_t)k0 * nR * nw2, *bg = Bg32 + (size_t)k0 * nR * m->nm * nw2;
+  if (s.op == TC_OP_BF16)
+    k_build_b<__nv_bfloat16><<<grid_for(nb, 256), 256, 0, st>>>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, bh, bg,
+                                                                 (__nv_bfloat16 *)s.Bhi, (__nv_bfloat16 *)s.Blo);
+  else
+    k_build_b<float><<<grid_for(nb, 256), 256, 0, st>>>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, bh, bg,
+                                                         (float *)s.Bhi, (float *)s.Blo);
+  epw_count_launch();
+  const int rows = kc * s.cpk;
+  CUtensorMap ah, al, bh_m, bl_m;
+  if (!make_map(&ah, s.Ahi, s.op, s.kpad, nq, 128) || !make_map(&al, s.Alo, s.op, s.kpad, nq, 128) ||
+      !make_map(&bh_m, s.Bhi, s.op, s.kpad, rows, G_NT) || !make_map(&bl_m, s.Blo, s.op, s.kpad, rows, G_NT))
+    return EPW_ERR_CUDA;
+  GemmArgs g;
+  g.mtiles = (nq + 127) / 128;
+  g.ntiles = (rows + G_NT - 1) / G_NT;
+  g.kblocks = (s.kpad * (s.op == TC_OP_BF16 ? 2 : 4) + ROWB - 1) / ROWB;
+  g.kb_per_split = g.kblocks;
+  g.splits = 1;
+  g.ldc = s.ldc;
+  g.npad = g.ntiles * G_NT;
+  g.Ct = s.Ct;
+  g.dstatus = m->dstatus;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int items = g.mtiles * g.ntiles;
+  if (s.op == TC_OP_BF16) {
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_tc_gemm_nt<TC_OP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM) !=
+          cudaSuccess)
+        return EPW_ERR_CUDA;
+      attr = true;
+    }
+    k_tc_gemm_nt<TC_OP_BF16><<<std::min(items, sms), G_THREADS, G_SMEM, st>>>(ah, al, bh_m, bl_m, g);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_tc_gemm_nt<TC_OP_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM) !=
+          cudaSuccess)
+        return EPW_ERR_CUDA;
+      attr = true;
+    }
+    k_tc_gemm_nt<TC_OP_TF32><<<std::min(items, sms), G_THREADS, G_SMEM, st>>>(ah, al, bh_m, bl_m, g);
+  }
+  epw_count_launch();
   return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
 }

@@ -61,3 +61,23 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
                                  const cx<float> *Pk32, const double *omegaT, const cx<float> *ET32,
                                  const cx<float> *Bg32, const cx<float> *BH32, const double *cot, TcBuffers &b,
                                  TcBwdBuffers &w, cx<float> *gwbar, double *scal, cudaStream_t st);
+
+// Staged tensor-core form for shapes the fused kernel cannot hold (Re == Rp,
+// nw <= 8, 3nat <= 9): per chunk of k, a tcgen05 GEMM writes
+// Ct[kl*cpk + 2c + s][q] (c over [H(k+q)_ij | (g_a(k,q) U_k)_jn], s = re/im),
+// which the per-pair kernel reads.
+struct TcStaged {
+  void *Ahi, *Alo;  // q phases [nq][kpad]
+  void *Bhi, *Blo;  // k-side operand of one chunk [kc][cpk][kpad]
+  float *Ct;        // [ntiles*144 rows][ldc]
+  int op, kpad, cpk, kc, mtiles, ldc;
+  bool ok;
+};
+bool tc_staged_supported(const epw_model *m);
+// Buffers for chunks of up to `kc` k-points, kc chosen so Ct stays within ct_budget bytes.
+epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t ct_budget, TcStaged &s);
+// Split q-phase operand (once per call).
+epw_status tc_staged_phases(const epw_model *m, int nq, const double *q, TcStaged &s, cudaStream_t st);
+// Contraction of k-points [k0, k0 + kc) into s.Ct.
+epw_status tc_staged_contract(const epw_model *m, int k0, int kc, int nq, const cx<float> *Bg32,
+                              const cx<float> *BH32, TcStaged &s, cudaStream_t st);

@@ -187,15 +187,6 @@ def test_tc_c1_full(epw, oracle_lib, prec, tol):
     assert _rel(got, ref) < tol
 
 
-def test_tc_unsupported_shape_reports(epw):
-    wm = _model(400, "hex", 5, 3, (1.0, 1.1, 1.2))
-    m = epw.Model(wm)
-    for prec in (epw.BF16X3, epw.TF32X3):
-        with pytest.raises(epw.EPWError) as e:
-            m.linewidth(np.zeros((2, 3)), np.zeros((4, 3)), T=300.0, EF=0.0, sigma=0.05, precision=prec)
-        assert e.value.status == 6
-
-
 @pytest.mark.parametrize("prec,tol", TC_CASES)
 def test_fcc_workload_full_size_tc_sampled_k(epw, oracle_lib, prec, tol):
     """The benchmark configuration (1000 k x 40^3 q, device buffers) on the tensor cores, sampled k."""

@@ -352,6 +352,23 @@ def _c2(nq_sub=None, kfile="kwindow_fcc_nw4.txt", T=300.0):
     return Workload("fcc_nw4_nat1_k1000win_q40^3", m, k, q, np.full(len(q), 1.0 / nq_full), T, EF, 0.020)
 
 
+def diamond_nw8_model():
+    """Diamond two-atom basis, nw=8, masses 1 and 1.2, 249 Re = Rp (whole fcc shells)."""
+    rng = np.random.default_rng(SEED_BASE + 2)
+    return make_model("diamond", 8, 2, [1.0, 1.2], 249, 249, rng)
+
+
+def _c3(nq_sub=None, kfile="kwindow_diamond_nw8.txt", T=300.0):
+    """2000 k near the band edges; 60^3 grid plus 10^5 random q, equal weights; sigma 10 meV."""
+    m = diamond_nw8_model()
+    k, EF = load_kpoint_file(os.path.join(GOLDEN_DIR, kfile))
+    q = np.concatenate([uniform_grid(60), random_points(np.random.default_rng(SEED_BASE + 302), 100000)])
+    nq_full = len(q)
+    if nq_sub:
+        q = q[np.random.default_rng(SEED_BASE + 102).choice(nq_full, nq_sub, replace=False)]
+    return Workload("diamond_nw8_nat2_k2000edge_q60^3+1e5", m, k, q, np.full(len(q), 1.0 / nq_full), T, EF, 0.010)
+
+
 def _c5(nq_sub=None):
     rng = np.random.default_rng(SEED_BASE + 4)
     m = make_model("hex", 5, 3, [1.0, 1.1, 1.2], 300, 300, rng)
@@ -366,6 +383,7 @@ def _c5(nq_sub=None):
 WORKLOADS = {
     "sc_nw1": _c1,
     "fcc_nw4": _c2,
+    "diamond_nw8": _c3,
     "hex_nw5": _c5,
 }
 
