@@ -201,6 +201,46 @@ epw_status epw_linewidth_backward(const epw_model *model, int nk, const double *
 epw_status epw_linewidth_noalloc(const epw_model *model, int nk, const double *k, int nq, const double *q,
                                  const double *wq, const epw_params *params, double *imsigma, void *stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many linewidth problems of Eq. (linewidthel) at once, on systems that may
+ * differ in every size (nw, nat, nRe, nRp, nk, nq), precision and parameter.
+ * One job is one epw_linewidth call; all its pointers are DEVICE pointers:
+ *   k [nk][3], q [nq][3], wq [nq] or NULL (1/nq), imsigma [nk][nw] (output).
+ * Several jobs may share a model.  Shapes, pointers and params are fixed when
+ * the batch is created; the contents of k, q and wq may change between runs. */
+typedef struct {
+  const epw_model *model;
+  int nk, nq;
+  const double *k, *q, *wq;
+  epw_params params;
+  double *imsigma;
+} epw_linewidth_job;
+
+typedef struct epw_batch epw_batch;
+
+/* Plans the jobs and allocates one device workspace for all of them (owned by
+ * the batch), picks each job's tile parameters with the autotuner, and
+ * captures the whole batch as one CUDA graph whose jobs run on parallel
+ * branches (the branch count is chosen by timing the candidate graphs).
+ * Autotuning runs timed trials of a job shape the first time the process
+ * sees it (kept per process; with the environment variable EPW_TUNE_CACHE
+ * naming a file, also read from and appended to it).  Creating a batch runs
+ * every job at least once, so each imsigma holds a result on return.
+ * Errors: EPW_ERR_INVALID_ARG (null/host pointers, bad params, models on
+ * another device), EPW_ERR_UNSUPPORTED (a job shape with no kernel for its
+ * precision), EPW_ERR_OOM, EPW_ERR_CUDA.  No model may have timing enabled. */
+epw_status epw_batch_create(int njobs, const epw_linewidth_job *jobs, epw_batch **out);
+/* Replays the batch's graph on `stream` (asynchronous); epw_sync on a job's
+ * model reports device-side failures. */
+epw_status epw_batch_run(epw_batch *batch, void *stream);
+/* Graph branches, workspace bytes and number of graph nodes (any may be NULL). */
+epw_status epw_batch_info(const epw_batch *batch, int *branches, size_t *workspace_bytes, size_t *graph_nodes);
+/* Waits for the batch's work and releases its graph, streams and workspace. */
+void epw_batch_free(epw_batch *batch);
+/* One-shot form: create, run on `stream`, wait, check every model's device
+ * status, free. */
+epw_status epw_linewidth_batched(int njobs, const epw_linewidth_job *jobs, void *stream);
+
 /* Wait for the model's work on `stream` and report device-side failures
  * (EPW_ERR_NOT_CONVERGED) raised since the previous epw_sync; clears them. */
 epw_status epw_sync(const epw_model *model, void *stream);

@@ -30,6 +30,11 @@ SIGNATURES = {
     "epw_linewidth": (I, [P, I, P, I, P, P, P, P, P]),
     "epw_linewidth_backward": (I, [P, I, P, I, P, P, P, P, P, P, P, P]),
     "epw_linewidth_noalloc": (I, [P, I, P, I, P, P, P, P, P]),
+    "epw_batch_create": (I, [I, P, P]),
+    "epw_batch_run": (I, [P, P]),
+    "epw_batch_info": (I, [P, P, P, P]),
+    "epw_batch_free": (None, [P]),
+    "epw_linewidth_batched": (I, [I, P, P]),
     "epw_sync": (I, [P, P]),
     "epw_model_info": (I, [P, P, P, P, P, P]),
     "epw_launch_count": (ctypes.c_uint64, []),
@@ -52,6 +57,11 @@ class WannierDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("T_K", D), ("EF_eV", D), ("sigma_eV", D), ("omega_min_eV", D),
                 ("precision", I), ("reserved", I)]
+
+
+class LinewidthJob(ctypes.Structure):
+    _fields_ = [("model", P), ("nk", I), ("nq", I), ("k", P), ("q", P), ("wq", P),
+                ("params", Params), ("imsigma", P)]
 
 
 def library_path() -> str:

@@ -219,3 +219,66 @@ class Model:
 
 def launch_count() -> int:
     return int(_lib.load().epw_launch_count())
+
+
+class Batch:
+    """Many linewidth problems (possibly different models and sizes) as one CUDA graph.
+
+    ``jobs`` is a list of dicts with keys model (Model), k, q (CUDA float64
+    tensors [n, 3]), wq (CUDA tensor or None), T, EF, sigma, optional
+    omega_min and precision, and optional out (CUDA float64 [nk, nw]; made
+    here when absent).  Creating the batch autotunes, captures the graph and
+    runs every job once; ``run()`` replays it on the current torch stream.
+    Shapes and buffers are fixed; the contents of k, q, wq may change.
+    """
+
+    def __init__(self, jobs):
+        import torch
+        lib = _lib.load()
+        self._keep = []
+        self.outputs = []
+        arr = (_lib.LinewidthJob * max(len(jobs), 1))()
+        for i, j in enumerate(jobs):
+            m = j["model"]
+            ka, qa, wa = _Arg(j["k"], np.float64), _Arg(j["q"], np.float64), _Arg(j.get("wq"), np.float64)
+            for a in (ka, qa) + ((wa,) if wa.keep is not None else ()):
+                if not a.device:
+                    raise ValueError("batch jobs take CUDA tensors")
+            nk = int(np.prod(ka.keep.shape)) // 3
+            nq = int(np.prod(qa.keep.shape)) // 3
+            out = j.get("out")
+            if out is None:
+                out = torch.empty((nk, m.nw), dtype=torch.float64, device=ka.keep.device)
+            oa = _Arg(out, np.float64)
+            self._keep += [ka, qa, wa, oa, m]
+            self.outputs.append(oa.keep)
+            pr = _lib.Params(float(j["T"]), float(j["EF"]), float(j["sigma"]), float(j.get("omega_min", 1e-5)),
+                             int(j.get("precision", FP64)), 0)
+            arr[i] = _lib.LinewidthJob(m.handle, nk, nq, ka.ptr, qa.ptr, wa.ptr, pr, oa.ptr)
+        self._jobs = arr
+        h = ctypes.c_void_p()
+        torch.cuda.synchronize()
+        _check(lib.epw_batch_create(len(jobs), arr, ctypes.byref(h)))
+        self._h = h
+
+    def run(self):
+        import torch
+        _check(_lib.load().epw_batch_run(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        return self.outputs
+
+    def info(self):
+        """(graph branches, workspace bytes, graph nodes)."""
+        b, w, n = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_size_t()
+        _check(_lib.load().epw_batch_info(self._h, ctypes.byref(b), ctypes.byref(w), ctypes.byref(n)))
+        return b.value, w.value, n.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().epw_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -10,8 +10,7 @@
 #include <cstring>
 #include <vector>
 
-#include "epw_internal.cuh"
-#include "epw_tc.cuh"
+#include "epw_host.cuh"
 
 // ------------------------------------------------------------------ errors
 static thread_local char g_err[512] = "";
@@ -20,6 +19,13 @@ static std::atomic<uint64_t> g_launches{0};
 void epw_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static epw_status fail(epw_status s, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+epw_status epwi_fail(epw_status s, const char *fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
@@ -42,7 +48,7 @@ static epw_status fail(epw_status s, const char *fmt, ...) {
     if (s_ != EPW_OK) return s_;       \
   } while (0)
 
-static bool is_device_ptr(const void *p) {
+bool epwi_is_device_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -51,6 +57,8 @@ static bool is_device_ptr(const void *p) {
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
+
+static bool is_device_ptr(const void *p) { return epwi_is_device_ptr(p); }
 
 // ------------------------------------------------------------------ model
 static bool same_set(int n1, const int32_t *a, int n2, const int32_t *b) {
@@ -264,24 +272,6 @@ static epw_status ensure_ws(epw_model *m, size_t bytes) {
   return EPW_OK;
 }
 
-// Per-call device state of the preparation steps shared by every entry point.
-struct Prep {
-  double *kd, *qd, *wqd;
-  cx<double> *PkRM, *PkT;  // k phases [nk][nRe], [nRe][nk]
-  cx<double> *Hk;          // [nk][nw][nw]
-  double *epsk;            // [nk][nw]
-  cx<double> *Uk;          // [nk][nw][nw]
-  void *PqTe, *PqTp;       // [nR][nq] in working precision
-  cx<double> *PqTph;       // [nRph][nq] FP64 (phonons)
-  cx<double> *D;           // [nq][nm][nm]
-  double *w2;              // [nq][nm]
-  cx<double> *ev;          // [nq][nm][nm]
-  double *omegaT;          // [nm][nq]
-  void *ET;                // [nm*nm][nq] working precision
-  void *G1, *Bg, *BH;      // working precision
-  cx<float> *Pk32, *gw32;  // FP32 copies for the k-side contraction
-};
-
 static size_t rsize(int prec) { return prec == EPW_FP64 ? sizeof(cx<double>) : sizeof(cx<float>); }
 
 // Lay out (or, with a null base, measure) the preparation buffers.
@@ -367,7 +357,7 @@ static epw_status run_prep(const epw_model *m, int nk, const double *k, int nq, 
   return EPW_OK;
 }
 
-static epw_status check_common(const epw_model *m, int nk, const double *k, int nq, const double *q) {
+epw_status epwi_check_common(const epw_model *m, int nk, const double *k, int nq, const double *q) {
   if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
   if (nk < 0 || nq < 0) return fail(EPW_ERR_INVALID_ARG, "negative nk or nq");
   if ((nk > 0 && !k) || (nq > 0 && !q)) return fail(EPW_ERR_INVALID_ARG, "null k or q");
@@ -378,7 +368,7 @@ static epw_status check_common(const epw_model *m, int nk, const double *k, int 
   return EPW_OK;
 }
 
-static epw_status check_params(const epw_params *p) {
+epw_status epwi_check_params(const epw_params *p) {
   if (!p) return fail(EPW_ERR_INVALID_ARG, "null params");
   if (!(p->T_K >= 0.0) || !std::isfinite(p->T_K)) return fail(EPW_ERR_INVALID_ARG, "T_K must be finite and >= 0");
   if (!(p->sigma_eV > 0.0) || !std::isfinite(p->sigma_eV)) return fail(EPW_ERR_INVALID_ARG, "sigma_eV must be > 0");
@@ -388,6 +378,11 @@ static epw_status check_params(const epw_params *p) {
   if (p->reserved != 0) return fail(EPW_ERR_INVALID_ARG, "reserved field must be 0");
   return EPW_OK;
 }
+
+static epw_status check_common(const epw_model *m, int nk, const double *k, int nq, const double *q) {
+  return epwi_check_common(m, nk, k, nq, q);
+}
+static epw_status check_params(const epw_params *p) { return epwi_check_params(p); }
 
 static epw_status read_status(const epw_model *m, cudaStream_t st) {
   unsigned h[4] = {0, 0, 0, 0};
@@ -407,19 +402,13 @@ extern "C" epw_status epw_sync(const epw_model *m, void *stream) {
 }
 
 // ------------------------------------------------------------- linewidth
-struct LwPlan {
-  Prep p;
-  double *partial;
-  double *out_d;
-  TcBuffers tc;
-  TcStaged sg;
-};
-
 // Contraction buffer of the staged tensor-core form (per chunk of k).
 static const size_t STAGED_CT_BYTES = (size_t)4 << 30;
 
-static epw_status plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,
-                                 bool sout, LwPlan &L) {
+EpwTune epwi_default_tune() { return EpwTune{0, STAGED_CT_BYTES}; }
+
+epw_status epwi_plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,
+                               bool sout, const EpwTune &tune, LwPlan &L) {
   const bool tc = prec == EPW_BF16X3 || prec == EPW_TF32X3;
   const int op = prec == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32;
   plan_prep(A, m, nk, nq, tc ? EPW_FP32 : prec, sk, sq, swq, true, L.p);
@@ -427,14 +416,20 @@ static epw_status plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, i
   L.tc = TcBuffers{};
   if (tc && tc_supported(m)) {
     CKS(tc_plan(A, m, nk, nq, op, L.tc));
+    L.tc.a_block_bytes = tune.a_block_bytes;
     L.partial = nullptr;
   } else {
-    if (tc) CKS(tc_staged_plan(A, m, nk, nq, op, STAGED_CT_BYTES, L.sg));
+    if (tc) CKS(tc_staged_plan(A, m, nk, nq, op, tune.staged_ct_bytes ? tune.staged_ct_bytes : STAGED_CT_BYTES, L.sg));
     int nqb = (nq + 127) / 128;
     L.partial = A.take<double>((size_t)nk * nqb * m->nw);
   }
   L.out_d = sout ? A.take<double>((size_t)nk * m->nw) : nullptr;
   return EPW_OK;
+}
+
+static epw_status plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,
+                                 bool sout, LwPlan &L) {
+  return epwi_plan_linewidth(A, m, nk, nq, prec, sk, sq, swq, sout, epwi_default_tune(), L);
 }
 
 extern "C" epw_status epw_reserve(epw_model *m, int nk, int nq, int precision) {
@@ -487,6 +482,18 @@ extern "C" epw_status epw_linewidth(const epw_model *mc, int nk, const double *k
     wqd = p.wqd;
   }
   double *out = sout ? L.out_d : imsigma;
+  CKS(epwi_linewidth_exec(m, nk, kd, nq, qd, wqd, par, L, out, st));
+  if (sout) {
+    CK(cudaMemcpyAsync(imsigma, out, sizeof(double) * (size_t)nk * m->nw, cudaMemcpyDeviceToHost, st));
+  }
+  if (sk || sq || swq || sout) return read_status(m, st);
+  return EPW_OK;
+}
+
+epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, const double *qd, const double *wqd,
+                               const epw_params *par, LwPlan &L, double *out, cudaStream_t st) {
+  const int prec = par->precision;
+  Prep &p = L.p;
   const bool tcp = prec == EPW_BF16X3 || prec == EPW_TF32X3;
   if (tcp && !L.tc.ok && !L.sg.ok)
     return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
@@ -524,7 +531,7 @@ extern "C" epw_status epw_linewidth(const epw_model *mc, int nk, const double *k
       a.partial = L.partial;
       a.dstatus = m->dstatus;
       a.Cq = L.sg.Ct;
-      a.ldc = (size_t)L.sg.ldc;
+      a.ldc = L.sg.pair_ld();
       a.cpk = L.sg.cpk;
       s = launch_pair_staged(a, 0, st);
       if (s != EPW_OK) return fail(s, "no staged per-pair kernel for nw=%d, 3nat=%d", m->nw, m->nm);
@@ -563,10 +570,6 @@ extern "C" epw_status epw_linewidth(const epw_model *mc, int nk, const double *k
     launch_finalize(nk, (nq + 127) / 128, m->nw, L.partial, out, st);
   }
   CK(cudaGetLastError());
-  if (sout) {
-    CK(cudaMemcpyAsync(imsigma, out, sizeof(double) * (size_t)nk * m->nw, cudaMemcpyDeviceToHost, st));
-  }
-  if (sk || sq || swq || sout) return read_status(m, st);
   return EPW_OK;
 }
 
@@ -649,7 +652,7 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
       a.gout = (cx<double> *)gd;
       a.dstatus = m->dstatus;
       a.Cq = sg.Ct;
-      a.ldc = (size_t)sg.ldc;
+      a.ldc = sg.pair_ld();
       a.cpk = sg.cpk;
       s = launch_pair_staged(a, 1, st);
       if (s != EPW_OK) return fail(s, "no staged per-pair kernel for nw=%d, 3nat=%d", m->nw, m->nm);
@@ -705,6 +708,8 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   const bool staged = tcp && !tcb && tc_staged_supported(m);
   if (tcp && !tcb && !staged)
     return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
+  if (m->nw > 8 || m->nm > 9)
+    return fail(EPW_ERR_UNSUPPORTED, "the adjoint has no kernel for nw=%d, 3nat=%d (at most 8 and 9)", m->nw, m->nm);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nw2 = (size_t)m->nw * m->nw, per = (size_t)m->nm * nw2;
   const size_t ng = (size_t)m->nRe * m->nRp * per;
@@ -813,7 +818,7 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
       a.dstatus = m->dstatus;
       if (staged) {
         a.Cq = b.sg.Ct;
-        a.ldc = (size_t)b.sg.ldc;
+        a.ldc = b.sg.pair_ld();
         a.cpk = b.sg.cpk;
       }
       epw_status s = staged ? launch_pair_staged(a, 2, st)

@@ -201,29 +201,6 @@ __global__ void k_cast_c64_c32(size_t n, const cx<double> *__restrict__ in, cx<f
 }
 
 // ------------------------------------------------------------ per-pair kernel
-template <typename R>
-__device__ __forceinline__ R gauss_r(R x, R inv_sigma, R norm) {
-  R y = x * inv_sigma;
-  return norm * exp(-y * y);
-}
-
-template <typename R>
-__device__ __forceinline__ R occ_bose(R w, double T);
-template <>
-__device__ __forceinline__ double occ_bose<double>(double w, double T) { return bose_d(w, T); }
-template <>
-__device__ __forceinline__ float occ_bose<float>(float w, double T) {
-  return bose_f(w, T > 0.0 ? (float)(1.0 / (EPW_KB * T)) : 0.0f);
-}
-template <typename R>
-__device__ __forceinline__ R occ_fermi(R e, double EF, double T);
-template <>
-__device__ __forceinline__ double occ_fermi<double>(double e, double EF, double T) { return fermi_d(e, EF, T); }
-template <>
-__device__ __forceinline__ float occ_fermi<float>(float e, double EF, double T) {
-  return fermi_f((float)((double)e - EF), T > 0.0 ? (float)(1.0 / (EPW_KB * T)) : 0.0f);
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -689,7 +666,7 @@ epw_status launch_pair(const PairArgs &a, int mode, cudaStream_t st) {
   else if (a.nw <= 8 && a.nm <= 9)
     pair_dispatch_mode<R, 8, 9>(a, mode, grid, st);
   else
-    return EPW_ERR_UNSUPPORTED;
+    return launch_pair_wide<R>(a, mode, st);
   return EPW_OK;
 }
 template epw_status launch_pair<double>(const PairArgs &, int, cudaStream_t);
@@ -698,7 +675,8 @@ template epw_status launch_pair<float>(const PairArgs &, int, cudaStream_t);
 epw_status launch_pair_staged(const PairArgs &a, int mode, cudaStream_t st) {
   int nkl = (mode == 2) ? a.nkc : a.nk;
   if (nkl <= 0 || a.nq <= 0) return EPW_OK;
-  if (!a.Cq || a.nw > 8 || a.nm > 9) return EPW_ERR_UNSUPPORTED;
+  if (!a.Cq) return EPW_ERR_UNSUPPORTED;
+  if (a.nw > 8 || a.nm > 9) return launch_pair_wide<float>(a, mode, st);
   dim3 grid((a.nq + 127) / 128, nkl);
   if (mode == 0)
     k_pair<float, 8, 9, 0, true><<<grid, 128, 0, st>>>(a);

@@ -227,6 +227,31 @@ __device__ __forceinline__ void sort_eig(cx<R> (&A)[N][N], cx<R> (&V)[N][N], R (
   }
 }
 
+// Gaussian delta, exp(-(x/sigma)^2) / (sigma sqrt(pi)) with norm = 1/(sigma sqrt(pi)).
+template <typename R>
+__device__ __forceinline__ R gauss_r(R x, R inv_sigma, R norm) {
+  R y = x * inv_sigma;
+  return norm * exp(-y * y);
+}
+
+// Occupations in working precision (FP64 forms in FP64, FP32 forms with 1/kT).
+template <typename R>
+__device__ __forceinline__ R occ_bose(R w, double T);
+template <>
+__device__ __forceinline__ double occ_bose<double>(double w, double T) { return bose_d(w, T); }
+template <>
+__device__ __forceinline__ float occ_bose<float>(float w, double T) {
+  return bose_f(w, T > 0.0 ? (float)(1.0 / (EPW_KB * T)) : 0.0f);
+}
+template <typename R>
+__device__ __forceinline__ R occ_fermi(R e, double EF, double T);
+template <>
+__device__ __forceinline__ double occ_fermi<double>(double e, double EF, double T) { return fermi_d(e, EF, T); }
+template <>
+__device__ __forceinline__ float occ_fermi<float>(float e, double EF, double T) {
+  return fermi_f((float)((double)e - EF), T > 0.0 ? (float)(1.0 / (EPW_KB * T)) : 0.0f);
+}
+
 template <typename R>
 struct jacobi_tol;
 template <>
@@ -331,6 +356,10 @@ template <typename R>
 epw_status launch_pair(const PairArgs &a, int mode, cudaStream_t st);
 // per-pair kernel on a staged contraction (a.Cq set; FP32)
 epw_status launch_pair_staged(const PairArgs &a, int mode, cudaStream_t st);
+// warp-per-pair kernel for nw, 3nat up to 18 (modes 0 and 1; a.Cq set: staged
+// contraction in the q-major layout Cq[q*ldc + kl*cpk + 2c + s], FP32 only)
+template <typename R>
+epw_status launch_pair_wide(const PairArgs &a, int mode, cudaStream_t st);
 void launch_finalize(int nk, int nqb, int nw, const double *partial, double *out, cudaStream_t st);
 // m->gw = wRe wRp g (g on the device)
 void launch_set_vertex(const epw_model *m, const void *g, int is_c64, cudaStream_t st);

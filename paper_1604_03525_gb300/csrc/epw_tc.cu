@@ -1049,7 +1049,7 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
   a.nkb = (b.kpad + bk - 1) / bk;
   {
     const size_t atile = (size_t)BM * b.kpad * esz * 2;
-    int qb = (int)(A_BLOCK_BYTES / atile);
+    int qb = (int)((b.a_block_bytes ? b.a_block_bytes : A_BLOCK_BYTES) / atile);
     if (qb < 152) qb = 152;
     if (qb > b.nqt) qb = b.nqt;
     a.qblock = qb < 1 ? 1 : qb;
@@ -1136,6 +1136,8 @@ struct GemmArgs {
   int ldc;   // rows of Ct are padded to mtiles * 128
   int npad;  // ntiles * G_NT
   float *Ct; // [splits][npad][ldc]: transposed partial products
+  int qmajor;  // instead Ct[m][n] with row length ldn (one split)
+  size_t ldn;
   unsigned *dstatus;
 };
 
@@ -1295,20 +1297,29 @@ __global__ void __launch_bounds__(G_THREADS, 1)
       tc_fence_after();
       const int m = mt * 128 + quad * 32 + lane;
       const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + ts * 256;
-      float *out = g.Ct + ((size_t)sp * g.npad + (size_t)nt * G_NT) * g.ldc + m;
+      // column-major partials (stride ldc), or one q-major row per thread (32-byte stores)
+      const size_t cs = g.qmajor ? 1 : (size_t)g.ldc;
+      float *out = g.qmajor ? g.Ct + (size_t)m * g.ldn + (size_t)nt * G_NT
+                            : g.Ct + ((size_t)sp * g.npad + (size_t)nt * G_NT) * g.ldc + m;
 #pragma unroll 1
       for (int c0 = 0; c0 < 128; c0 += 32) {
         float v[32];
         tmem_ld32(taddr + c0, v);
+        if (g.qmajor) {
 #pragma unroll
-        for (int c = 0; c < 32; c++) out[(size_t)(c0 + c) * g.ldc] = v[c];
+          for (int c = 0; c < 32; c += 4)
+            *reinterpret_cast<float4 *>(out + c0 + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 32; c++) out[(size_t)(c0 + c) * cs] = v[c];
+        }
       }
 #pragma unroll
       for (int c0 = 128; c0 < G_NT; c0 += 8) {
         float v[8];
         tmem_ld8(taddr + c0, v);
 #pragma unroll
-        for (int c = 0; c < 8; c++) out[(size_t)(c0 + c) * g.ldc] = v[c];
+        for (int c = 0; c < 8; c++) out[(size_t)(c0 + c) * cs] = v[c];
       }
       tc_fence_before();
       __syncwarp();
@@ -1523,6 +1534,8 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
     g.ldc = w.ldc;
     g.npad = w.npad;
     g.Ct = w.Ct;
+    g.qmajor = 0;
+    g.ldn = 0;
     g.dstatus = m->dstatus;
     const int items = g.mtiles * g.ntiles * g.splits;
     k_tc_gemm_nt<TC_OP_TF32><<<std::min(items, sms), G_THREADS, G_SMEM, st>>>(xh, xl, ph, pl, g);
@@ -1546,7 +1559,7 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
 // the tensor cores per chunk of k with its result written to HBM,
 //   Ct[kl cpk + col][q] = sum_kk A[q][kk] B[kl][col][kk],
 // and the per-pair kernel (eigensolve, rotation, deltas) reads it from there.
-bool tc_staged_supported(const epw_model *m) { return m->same_ep && !tc_supported(m) && m->nw <= 8 && m->nm <= 9; }
+bool tc_staged_supported(const epw_model *m) { return m->same_ep && !tc_supported(m) && m->nw <= 18 && m->nm <= 18; }
 
 epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t ct_budget, TcStaged &s) {
   s = TcStaged{};
@@ -1562,6 +1575,10 @@ epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, 
   const size_t per_k = (size_t)s.cpk * s.ldc * 4;
   s.kc = (int)std::min<size_t>((size_t)std::max(nk, 1), std::max<size_t>(1, ct_budget / per_k));
   const int ntiles = (s.kc * s.cpk + G_NT - 1) / G_NT;
+  // shapes beyond the register-tile per-pair kernel read Ct q-major (a pair's
+  // columns contiguous) in the warp-per-pair kernel
+  s.qmajor = m->nw > 8 || m->nm > 9;
+  s.ldn = (size_t)ntiles * G_NT;
   s.Ahi = A.take<char>((size_t)std::max(nq, 1) * s.kpad * esz);
   s.Alo = A.take<char>((size_t)std::max(nq, 1) * s.kpad * esz);
   s.Bhi = A.take<char>((size_t)s.kc * s.cpk * s.kpad * esz);
@@ -1609,6 +1626,8 @@ epw_status tc_staged_contract(const epw_model *m, int k0, int kc, int nq, const 
   g.ldc = s.ldc;
   g.npad = g.ntiles * G_NT;
   g.Ct = s.Ct;
+  g.qmajor = s.qmajor ? 1 : 0;
+  g.ldn = s.ldn;
   g.dstatus = m->dstatus;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);

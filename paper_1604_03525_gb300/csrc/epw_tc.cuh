@@ -16,6 +16,7 @@ struct TcBuffers {
   double *partial;   // [nk][4*nqt][nw]
   int op, kpad, cpk, nk_pad, nqt, kpt;
   bool ok;           // shape has a tensor-core kernel
+  size_t a_block_bytes;  // q-block of the A operand visited by all k groups (0: default)
 };
 
 // True when the model's shape has a tensor-core kernel (Re == Rp sets and a
@@ -63,15 +64,20 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
                                  TcBwdBuffers &w, cx<float> *gwbar, double *scal, cudaStream_t st);
 
 // Staged tensor-core form for shapes the fused kernel cannot hold (Re == Rp,
-// nw <= 8, 3nat <= 9): per chunk of k, a tcgen05 GEMM writes
+// nw <= 18, 3nat <= 18): per chunk of k, a tcgen05 GEMM writes
 // Ct[kl*cpk + 2c + s][q] (c over [H(k+q)_ij | (g_a(k,q) U_k)_jn], s = re/im),
-// which the per-pair kernel reads.
+// or Ct[q][kl*cpk + 2c + s] for the warp-per-pair kernel, which the per-pair
+// kernel reads.
 struct TcStaged {
   void *Ahi, *Alo;  // q phases [nq][kpad]
   void *Bhi, *Blo;  // k-side operand of one chunk [kc][cpk][kpad]
-  float *Ct;        // [ntiles*144 rows][ldc]
+  float *Ct;        // [ntiles*144 rows][ldc], or q-major [ldc][ldn] when qmajor
   int op, kpad, cpk, kc, mtiles, ldc;
   bool ok;
+  bool qmajor;      // layout read by the warp-per-pair kernel (nw > 8 or 3nat > 9)
+  size_t ldn;
+  // leading dimension for the per-pair kernel's reads
+  size_t pair_ld() const { return qmajor ? ldn : (size_t)ldc; }
 };
 bool tc_staged_supported(const epw_model *m);
 // Buffers for chunks of up to `kc` k-points, kc chosen so Ct stays within ct_budget bytes.

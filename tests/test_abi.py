@@ -52,8 +52,35 @@ def test_null_arguments_rejected_without_gpu_work(lib):
     lib.epw_free_model(None)  # no-op
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
     from paper_1604_03525_gb300 import _lib
     # epw_wannier_desc: ints and pointers in declaration order (LP64)
     assert ctypes.sizeof(_lib.WannierDesc) == 120
     assert ctypes.sizeof(_lib.Params) == 4 * 8 + 2 * 4
+    # the C compiler's view of the header (plain C, no CUDA headers needed)
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "epw.h"\nint main(void){printf("%zu %zu %zu %zu %zu\\n",'
+                   ' sizeof(epw_wannier_desc), sizeof(epw_params), sizeof(epw_linewidth_job),'
+                   ' offsetof(epw_linewidth_job, params), offsetof(epw_linewidth_job, imsigma));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run([cc, "-include", "stddef.h", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    J = _lib.LinewidthJob
+    assert sizes == [ctypes.sizeof(_lib.WannierDesc), ctypes.sizeof(_lib.Params), ctypes.sizeof(J),
+                     J.params.offset, J.imsigma.offset]
+
+
+def test_batch_arguments_rejected_without_gpu_work(lib):
+    h = ctypes.c_void_p()
+    assert lib.epw_batch_create(-1, None, ctypes.byref(h)) == 1
+    assert lib.epw_batch_create(2, None, ctypes.byref(h)) == 1
+    assert lib.epw_batch_create(0, None, None) == 1
+    assert lib.epw_batch_run(None, None) == 1
+    assert lib.epw_batch_info(None, None, None, None) == 1
+    lib.epw_batch_free(None)  # no-op

@@ -1,0 +1,123 @@
+"""Batched linewidth (epw_batch_create / epw_batch_run): uneven systems in one CUDA graph.
+
+Every job of a batch runs the same kernels as a single epw_linewidth call; the
+tile choices only reorder independent work, so the batch must reproduce the
+single calls exactly (the per-(k, q-tile) partial sums are reduced in a fixed
+order either way).  A few jobs are also checked against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def epw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_03525_gb300 as epw
+    return epw
+
+
+def _job(m, k, q, prec, T=300.0, EF=0.1, sigma=0.05, wq=None):
+    import torch
+    return dict(model=m, k=torch.tensor(k, device="cuda"), q=torch.tensor(q, device="cuda"),
+                wq=None if wq is None else torch.tensor(wq, device="cuda"), T=T, EF=EF, sigma=sigma,
+                precision=prec)
+
+
+def _single(m, j):
+    return m.linewidth(j["k"], j["q"], j["wq"], T=j["T"], EF=j["EF"], sigma=j["sigma"],
+                       precision=j["precision"]).cpu().numpy()
+
+
+def test_uneven_batch_reproduces_single_calls(epw, oracle_lib):
+    import torch
+    rng = np.random.default_rng(700)
+    m_fcc = epw.Model(W.make_model("fcc", 4, 1, [1.0], 60, 60, rng))       # fused tensor-core kernel
+    hexm = W.make_model("hex", 5, 3, [1.0, 1.1, 1.2], 30, 30, rng)
+    m_hex = epw.Model(hexm)                                                 # staged form
+    scm = W.make_model("sc", 2, 1, [1.0], None, None, rng, box=1)
+    m_sc = epw.Model(scm)                                                   # SIMT forms
+    jobs = [
+        _job(m_fcc, rng.random((37, 3)), rng.random((700, 3)), epw.TF32X3),
+        _job(m_fcc, rng.random((5, 3)), rng.random((130, 3)), epw.BF16X3, T=100.0),
+        _job(m_hex, rng.random((9, 3)), rng.random((260, 3)), epw.TF32X3),
+        _job(m_hex, rng.random((3, 3)), rng.random((129, 3)), epw.BF16X3, sigma=0.03),
+        _job(m_sc, rng.random((11, 3)), rng.random((333, 3)), epw.FP64, wq=np.full(333, 2e-3)),
+        _job(m_sc, rng.random((4, 3)), rng.random((64, 3)), epw.FP32, EF=-0.2),
+        _job(m_sc, rng.random((6, 3)), np.zeros((0, 3)), epw.FP64),          # no q: zeros
+    ]
+    b = epw.Batch(jobs)
+    branches, ws, nodes = b.info()
+    assert branches in (1, 2, 4) and ws > 0 and nodes > 0
+    outs = [o.cpu().numpy() for o in b.run()]
+    torch.cuda.synchronize()
+    models = [m_fcc, m_fcc, m_hex, m_hex, m_sc, m_sc, m_sc]
+    for j, m, o in zip(jobs, models, outs):
+        if len(j["q"]) == 0:
+            assert np.all(o == 0)
+            continue
+        assert np.array_equal(o, _single(m, j))
+    # the oracle on two of them
+    ref = oracle_lib.linewidth(hexm, jobs[2]["k"].cpu().numpy(), jobs[2]["q"].cpu().numpy(), None, 300.0, 0.1, 0.05)
+    assert np.max(np.abs(outs[2] - ref)) <= 1e-4 * np.abs(ref).max()
+    ref = oracle_lib.linewidth(scm, jobs[4]["k"].cpu().numpy(), jobs[4]["q"].cpu().numpy(), np.full(333, 2e-3),
+                               300.0, 0.1, 0.05)
+    assert np.allclose(outs[4], ref, rtol=1e-9, atol=1e-14)
+    # new k contents, same buffers: the replay follows them
+    jobs[0]["k"].copy_(torch.tensor(rng.random((37, 3)), device="cuda"))
+    jobs[4]["q"].copy_(torch.tensor(rng.random((333, 3)), device="cuda"))
+    outs = [o.cpu().numpy() for o in b.run()]
+    torch.cuda.synchronize()
+    assert np.array_equal(outs[0], _single(m_fcc, jobs[0]))
+    assert np.array_equal(outs[4], _single(m_sc, jobs[4]))
+    b.close()
+    for m in (m_fcc, m_hex, m_sc):
+        m.sync()
+
+
+def test_drawn_uneven_batch_small_sizes(epw, oracle_lib):
+    """The uneven-systems draw (sizes scaled down so the oracle can follow) through one batch."""
+    import torch
+    specs = W.models.batch_specs(24, nR_range=(27, 60), nk_range=(3, 24), nq_range=(4, 7))
+    jobs, models, wms = [], [], []
+    for i, sp in enumerate(specs):
+        wm, k, q = W.models.batch_system(sp)
+        m = epw.Model(wm)
+        prec = (epw.TF32X3, epw.BF16X3, epw.FP32, epw.FP64)[i % 4]
+        jobs.append(_job(m, k, q, prec, EF=0.0, sigma=0.05))
+        models.append(m)
+        wms.append(wm)
+    b = epw.Batch(jobs)
+    outs = [o.cpu().numpy() for o in b.run()]
+    torch.cuda.synchronize()
+    for j, m, o in zip(jobs, models, outs):
+        assert np.array_equal(o, _single(m, j))
+    # With 4^3..7^3 q each state's sum rests on a handful of pairs, so the
+    # ~1e-5 eV e_k+q error of the split contraction (a relative change of
+    # ~2 x dx / sigma^2, up to 4e-4 at x ~ sigma = 50 meV per Gaussian) does
+    # not average out as on the benchmark grids: 1e-3 for both split forms.
+    tol = {epw.FP64: 1e-6, epw.FP32: 2e-3, epw.TF32X3: 1e-3, epw.BF16X3: 1e-3}
+    for i in range(min(4, len(jobs))):
+        j = jobs[i]
+        ref = oracle_lib.linewidth(wms[i], j["k"].cpu().numpy(), j["q"].cpu().numpy(), None, 300.0, 0.0, 0.05)
+        floor = 1e-6 * np.abs(ref).max()
+        rel = np.max(np.abs(outs[i] - ref) / np.maximum(np.abs(ref), floor))
+        print("drawn system", i, specs[i], "precision", j["precision"], "max rel err vs oracle", rel)
+        assert rel < tol[j["precision"]], (i, rel)
+    b.close()
+
+
+def test_batch_rejects_host_buffers_and_unsupported_shapes(epw):
+    rng = np.random.default_rng(710)
+    m = epw.Model(W.make_model("sc", 1, 1, [1.0], None, None, rng, box=1))
+    with pytest.raises(ValueError):
+        epw.Batch([dict(model=m, k=np.zeros((2, 3)), q=np.zeros((4, 3)), T=300.0, EF=0.0, sigma=0.05)])
+    big = epw.Model(W.make_model("hex", 5, 3, [1.0, 1.1, 1.2], 20, 40, rng))  # Re != Rp: no tensor-core form
+    with pytest.raises(epw.EPWError) as e:
+        epw.Batch([_job(big, rng.random((2, 3)), rng.random((8, 3)), epw.TF32X3)])
+    assert e.value.status == 6

@@ -100,13 +100,11 @@ def test_shapes_without_a_tensor_core_form_report(epw):
         with pytest.raises(epw.EPWError) as e:
             m.linewidth(np.zeros((2, 3)), np.zeros((4, 3)), T=300.0, EF=0.0, sigma=0.05, precision=prec)
         assert e.value.status == 6
-    # nw above the per-pair kernels' register tiles
-    wm = W.make_model("sc", 12, 1, [1.0], None, None, np.random.default_rng(531), box=1)
-    m = epw.Model(wm)
-    for prec in (epw.FP32, epw.TF32X3):
-        with pytest.raises(epw.EPWError) as e:
-            m.linewidth(np.zeros((2, 3)), np.zeros((4, 3)), T=300.0, EF=0.0, sigma=0.05, precision=prec)
-        assert e.value.status == 6
+    # nw above the widest per-pair kernel (18) is refused when the model is loaded
+    wm = W.make_model("sc", 20, 1, [1.0], None, None, np.random.default_rng(531), box=1)
+    with pytest.raises(epw.EPWError) as e:
+        epw.Model(wm)
+    assert e.value.status == 1
 
 
 @pytest.fixture(scope="module")
