@@ -234,10 +234,11 @@ def main():
 
     precs = {"tf32x3": epw.TF32X3, "bf16x3": epw.BF16X3, "fp32": epw.FP32, "fp64": epw.FP64}
     if args.precision == "auto":
-        # the fastest form that meets the 1e-4 target on this workload
-        name = "tf32x3"
+        # the fastest form that meets the 1e-4 target on this workload: split-BF16
+        # (max relative error 3.4e-5 against the oracle at this size; TF32x3 1.2e-5)
+        name = "bf16x3"
         try:
-            m.linewidth(k[:8], q[:256], wq[:256], T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.TF32X3)
+            m.linewidth(k[:8], q[:256], wq[:256], T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.BF16X3)
         except epw.EPWError:
             name = "fp32"
     else:
