@@ -79,6 +79,7 @@ def _load():
                 ("oracle_interp", [P, I, P, I, P, ctypes.c_double, P, P, P, P]),
                 ("oracle_linewidth", [P, I, P, I, P, P, P, P]),
                 ("oracle_linewidth_grad", [P, I, P, I, P, P, P, P, P, P, P]),
+                ("oracle_phonon_self", [P, I, P, P, I, P, P, P, P, P, P]),
             ]:
                 getattr(lib, name).argtypes = args
                 getattr(lib, name).restype = I
@@ -213,6 +214,26 @@ def linewidth(model, k, q, wq=None, T=300.0, EF=0.0, sigma=0.05, omega_min=1e-5)
     if rc != 0:
         raise RuntimeError("oracle linewidth: eigensolve did not converge")
     return out
+
+
+def phonon_self(model, k, q, wk=None, T=300.0, EF=0.0, sigma=0.05, omega_min=1e-5):
+    """(Pi''_qnu [nq, 3nat] (Eq. linewidthph, on shell), lambda_qnu [nq, 3nat] (Eq. lambdaEQ),
+    nesting zeta_q [nq] (Eq. nestingfct), N(E_F)) from sums over the k list (weights wk, default 1/nk)."""
+    lib = _load()
+    k, q = _pts(k), _pts(q)
+    b = _Bound(model)
+    nm = 3 * model.nat
+    wk_a = None if wk is None else np.ascontiguousarray(wk, dtype=np.float64)
+    pi = np.zeros((len(q), nm))
+    lam = np.zeros((len(q), nm))
+    zeta = np.zeros(len(q))
+    dos = np.zeros(1)
+    pr = _Params(T, EF, sigma, omega_min)
+    rc = lib.oracle_phonon_self(b.ptr, len(k), _p(k), None if wk_a is None else _p(wk_a), len(q), _p(q),
+                                ctypes.byref(pr), _p(pi), _p(lam), _p(zeta), _p(dos))
+    if rc != 0:
+        raise RuntimeError("oracle phonon self-energy: eigensolve did not converge")
+    return pi, lam, zeta, float(dos[0])
 
 
 def linewidth_grad(model, k, q, wq=None, T=300.0, EF=0.0, sigma=0.05, omega_min=1e-5, cot=None):

@@ -29,6 +29,10 @@
  *     Modes with w_qnu < omega_min are left out (w -> 0 at Gamma).
  *   - The adjoint of L = sum_{k,n} c_nk Im Sigma_nk with respect to g(Re,Rp)
  *     (reported as dL/dRe g + i dL/dIm g), the temperature and the Fermi level.
+ *   - Per (q, nu) sums over a k list of the same vertex: the phonon self-energy
+ *     Pi''_qnu of Eq. (linewidthph) on shell (w = w_qnu, sign as printed), the
+ *     coupling strength lambda_qnu of Eq. (lambdaEQ) with N(E_F) from the k
+ *     list, and the nesting function of Eq. (nestingfct).
  *
  * Every eigensolve is a plain cyclic complex Jacobi iteration on the Hermitian
  * part (X + X^dagger)/2, run to full double precision; eigenvalues ascend.
@@ -401,6 +405,85 @@ int oracle_linewidth(const oracle_model *m, int nk, const double *k, int nq, con
     imsig[i] = nsum_get(&s);
   }
   free(acc); free(epsk); free(Uk);
+  return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------- phonon self-energy */
+
+/* Per (q, nu), sums over k of the same interpolated vertex (Sec. "Theory"):
+ *   pi_im[q][nu] = Pi''_qnu(w_qnu) of Eq. (linewidthph), on shell, as printed:
+ *                  2 pi sum_k w_k sum_mn |g_mn,nu(k,q)|^2 (f_nk - f_mk+q) delta(e_nk - e_mk+q - w_qnu)
+ *   lam[q][nu]   = lambda_qnu of Eq. (lambdaEQ):
+ *                  sum_k w_k sum_mn |g|^2 delta(e_nk - E_F) delta(e_mk+q - E_F) / (N(E_F) w_qnu)
+ *   zeta[q]      = nesting function of Eq. (nestingfct): sum_k w_k sum_nm delta(e_nk - E_F) delta(e_mk+q - E_F)
+ *   dos[0]       = N(E_F) = sum_k w_k sum_n delta(e_nk - E_F)   (per spin)
+ * Modes below omega_min get 0 in pi_im and lam.  wk == NULL means 1/nk.
+ * Any of pi_im, lam, zeta, dos may be NULL. */
+int oracle_phonon_self(const oracle_model *m, int nk, const double *k, const double *wk, int nq, const double *q,
+                       const oracle_params *pr, double *pi_im, double *lam, double *zeta, double *dos) {
+  int nw = m->nw, nm = 3 * m->nat, nc = nm * nw * nw;
+  double *epsk = malloc(sizeof(double) * (long)nk * nw);
+  double *Uk = malloc(sizeof(cplx) * (long)nk * nw * nw);
+  int bad = oracle_bands(m, nk, k, epsk, Uk);
+  nsum nd = {0.0, 0.0};
+  for (int ik = 0; ik < nk; ik++)
+    for (int n = 0; n < nw; n++)
+      nsum_add(&nd, (wk ? wk[ik] : 1.0 / nk) * oracle_gauss(epsk[(long)ik * nw + n] - pr->EF, pr->sigma));
+  const double nef = nsum_get(&nd);
+  if (dos) dos[0] = nef;
+#pragma omp parallel reduction(+ : bad)
+  {
+    cplx *gReq = malloc(sizeof(cplx) * (long)m->nRe * nc);
+    cplx *gk = malloc(sizeof(cplx) * nc), *tmp = malloc(sizeof(cplx) * nc), *gmn = malloc(sizeof(cplx) * nc);
+    cplx *Hkq = malloc(sizeof(cplx) * nw * nw), *Ukq = malloc(sizeof(cplx) * nw * nw);
+    cplx *D = malloc(sizeof(cplx) * nm * nm), *ev = malloc(sizeof(cplx) * nm * nm), *E = malloc(sizeof(cplx) * nm * nm);
+    double w2[64], w[64], ekq[64];
+    nsum sp[64], sl[64], sz;
+#pragma omp for schedule(dynamic)
+    for (int iq = 0; iq < nq; iq++) {
+      const double *qq = q + 3 * iq;
+      oracle_dynmat(m, qq, D);
+      if (oracle_eigh(nm, D, w2, ev) < 0) bad++;
+      for (int j = 0; j < nm; j++) w[j] = (w2[j] >= 0 ? 1.0 : -1.0) * sqrt(fabs(w2[j]));
+      mode_factors(m, w, ev, pr->omega_min, E);
+      oracle_g_Re_q(m, qq, gReq);
+      for (int nu = 0; nu < nm; nu++) sp[nu] = sl[nu] = (nsum){0.0, 0.0};
+      sz = (nsum){0.0, 0.0};
+      for (int ik = 0; ik < nk; ik++) {
+        const double wki = wk ? wk[ik] : 1.0 / nk;
+        double kq[3] = {k[3 * ik] + qq[0], k[3 * ik + 1] + qq[1], k[3 * ik + 2] + qq[2]};
+        oracle_hk(m, kq, Hkq);
+        if (oracle_eigh(nw, Hkq, ekq, Ukq) < 0) bad++;
+        g_k_from_Re_q(m, gReq, k + 3 * ik, gk);
+        bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E, gmn, tmp);
+        for (int n = 0; n < nw; n++) {
+          const double en = epsk[(long)ik * nw + n];
+          const double fn = oracle_fermi(en, pr->EF, pr->T);
+          const double dn = oracle_gauss(en - pr->EF, pr->sigma);
+          for (int mm = 0; mm < nw; mm++) {
+            const double fm = oracle_fermi(ekq[mm], pr->EF, pr->T);
+            const double dd = dn * oracle_gauss(ekq[mm] - pr->EF, pr->sigma);
+            nsum_add(&sz, wki * dd);
+            for (int nu = 0; nu < nm; nu++) {
+              if (w[nu] < pr->omega_min) continue;
+              cplx gv = gmn[(nu * nw + mm) * nw + n];
+              double g2 = creal(gv) * creal(gv) + cimag(gv) * cimag(gv);
+              nsum_add(&sp[nu], wki * g2 * (fn - fm) * oracle_gauss(en - ekq[mm] - w[nu], pr->sigma));
+              nsum_add(&sl[nu], wki * g2 * dd);
+            }
+          }
+        }
+      }
+      for (int nu = 0; nu < nm; nu++) {
+        const int keep = w[nu] >= pr->omega_min;
+        if (pi_im) pi_im[(long)iq * nm + nu] = keep ? 2.0 * M_PI * nsum_get(&sp[nu]) : 0.0;
+        if (lam) lam[(long)iq * nm + nu] = (keep && nef > 0.0) ? nsum_get(&sl[nu]) / (nef * w[nu]) : 0.0;
+      }
+      if (zeta) zeta[iq] = nsum_get(&sz);
+    }
+    free(gReq); free(gk); free(tmp); free(gmn); free(Hkq); free(Ukq); free(D); free(ev); free(E);
+  }
+  free(epsk); free(Uk);
   return bad ? -1 : 0;
 }
 

@@ -17,6 +17,7 @@ sign or index, transposed operand):
 * occupations      closed forms, limits, n(-w) = -1 - n(w), unit-norm delta;
 * adjoint          central finite differences of the forward oracle.
 """
+import dataclasses
 import itertools
 import math
 
@@ -309,3 +310,100 @@ def test_adjoint_matches_finite_differences(oracle_lib):
     assert abs(fdT - dT) <= 1e-6 * abs(dT)
     fdE = (L(m, EF=EF + 1e-6) - L(m, EF=EF - 1e-6)) / 2e-6
     assert abs(fdE - dEF) <= 1e-6 * abs(dEF)
+
+
+# ------------------------------------------------- phonon self-energy (oracle)
+def _two_band_tb(eps=(-0.3, 0.4), t=0.5, K=0.01, M=1.3, c=((0.05, 0.03), (0.08, 0.02))):
+    """Two bands that never mix (H(k) diagonal, band 0 below band 1 everywhere) with
+    g_mn,a(Re=0, Rp=+-e_a) = -+ i c_mn / 2, so that g_mn,a(k,q) = c_mn sin(2 pi q_a)."""
+    m = W.tight_binding_model(eps0=0.0, t=t, K=K, g0=1.0, mass=M)
+    nR = len(m.Re)
+    H = np.zeros((nR, 2, 2), dtype=np.complex128)
+    g = np.zeros((nR, nR, 3, 2, 2), dtype=np.complex128)
+    for b in range(2):
+        H[:, b, b] = m.H[:, 0, 0]
+        i0 = [i for i, R in enumerate(m.Re) if not R.any()][0]
+        H[i0, b, b] = eps[b]
+    for mm in range(2):
+        for n in range(2):
+            g[:, :, :, mm, n] = m.g[:, :, :, 0, 0] * c[mm][n]
+    return dataclasses.replace(m, nw=2, H=H, g=g), eps, t, K, M, np.array(c)
+
+
+def _phonon_closed_form(k, q, T, EF, sigma, bands, K, M, c, wmin=1e-5):
+    """Pi'', lambda, zeta, N(E_F) for models with k-independent |g_mn,a|^2 = c_mn^2 sin^2(2 pi q_a) / (2 M w_a)
+    and band energies bands(k) -> [nw]; modes sorted by frequency like the oracle's."""
+    nk = len(k)
+    ek = np.array([bands(kk) for kk in k])
+    dos = sum(_gauss(e - EF, sigma) for row in ek for e in row) / nk
+    pi_out, lam_out, zeta = [], [], []
+    for qq in q:
+        ekq = np.array([bands(kk + qq) for kk in k])
+        w = 2 * math.sqrt(K / M) * np.abs(np.sin(np.pi * qq))
+        z = 0.0
+        P = np.zeros(3)
+        L = np.zeros(3)
+        for ik in range(nk):
+            for n in range(ek.shape[1]):
+                fn = _fermi(ek[ik, n], EF, T)
+                for mm in range(ek.shape[1]):
+                    fm = _fermi(ekq[ik, mm], EF, T)
+                    dd = _gauss(ek[ik, n] - EF, sigma) * _gauss(ekq[ik, mm] - EF, sigma)
+                    z += dd / nk
+                    for a in range(3):
+                        if w[a] < wmin:
+                            continue
+                        g2 = c[mm, n] ** 2 * math.sin(2 * math.pi * qq[a]) ** 2 / (2 * M * w[a])
+                        P[a] += g2 * (fn - fm) * _gauss(ek[ik, n] - ekq[ik, mm] - w[a], sigma) / nk
+                        L[a] += g2 * dd / nk
+        order = np.argsort(w)
+        pi_out.append(2 * math.pi * P[order])
+        lam_out.append(np.where(w[order] >= wmin, L[order] / (dos * np.maximum(w[order], wmin)), 0.0))
+        zeta.append(z)
+    return np.array(pi_out), np.array(lam_out), np.array(zeta), dos
+
+
+@pytest.mark.parametrize("T,EF,sigma", [(300.0, 0.1, 0.08), (50.0, -0.4, 0.05)])
+def test_phonon_self_energy_closed_form_one_band(oracle_lib, T, EF, sigma):
+    m = _tb()
+    rng = np.random.default_rng(70)
+    k = W.uniform_grid(6) + 0.03
+    q = rng.random((5, 3))  # generic q: three distinct frequencies
+    pi, lam, zeta, dos = oracle_lib.phonon_self(m, k, q, None, T, EF, sigma)
+    bands = lambda kk: [0.2 - 2 * 0.5 * np.cos(2 * np.pi * kk).sum()]
+    rpi, rlam, rz, rdos = _phonon_closed_form(k, q, T, EF, sigma, bands, 0.01, 1.3, np.array([[0.05]]))
+    assert math.isclose(dos, rdos, rel_tol=1e-12)
+    assert np.allclose(zeta, rz, rtol=1e-11, atol=1e-14 * np.abs(rz).max())
+    assert np.allclose(pi, rpi, rtol=1e-10, atol=1e-13 * np.abs(rpi).max())
+    assert np.allclose(lam, rlam, rtol=1e-10, atol=1e-13 * np.abs(rlam).max())
+    assert np.abs(rpi).max() > 0 and np.abs(rlam).max() > 0
+
+
+def test_phonon_self_energy_closed_form_two_bands(oracle_lib):
+    """Asymmetric interband couplings pin the band indices: n at k, m at k+q."""
+    m, eps, t, K, M, c = _two_band_tb()
+    rng = np.random.default_rng(71)
+    k = W.uniform_grid(5) + 0.02
+    q = rng.random((4, 3))
+    T, EF, sigma = 300.0, 0.05, 0.1
+    pi, lam, zeta, dos = oracle_lib.phonon_self(m, k, q, None, T, EF, sigma)
+    bands = lambda kk: [e - 2 * t * np.cos(2 * np.pi * kk).sum() for e in eps]
+    rpi, rlam, rz, rdos = _phonon_closed_form(k, q, T, EF, sigma, bands, K, M, c)
+    assert math.isclose(dos, rdos, rel_tol=1e-12)
+    assert np.allclose(zeta, rz, rtol=1e-11, atol=1e-14 * np.abs(rz).max())
+    assert np.allclose(pi, rpi, rtol=1e-10, atol=1e-13 * np.abs(rpi).max())
+    assert np.allclose(lam, rlam, rtol=1e-10, atol=1e-13 * np.abs(rlam).max())
+    # the transposed couplings give a different answer (the pin sees the index order)
+    tpi, _, _, _ = _phonon_closed_form(k, q, T, EF, sigma, bands, K, M, c.T)
+    assert not np.allclose(tpi, rpi, rtol=1e-3)
+
+
+def test_phonon_self_energy_time_reversal(oracle_lib):
+    rng = np.random.default_rng(72)
+    m = W.make_model("fcc", 2, 1, [1.0], 20, 20, rng, real=True)
+    k = W.uniform_grid(4) + 0.0
+    q = rng.random((3, 3))
+    a = oracle_lib.phonon_self(m, k, q, None, 300.0, 0.0, 0.1)
+    b = oracle_lib.phonon_self(m, k, -q, None, 300.0, 0.0, 0.1)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.allclose(x, y, rtol=1e-9, atol=1e-12 * (np.abs(x).max() + 1e-300))
