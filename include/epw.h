@@ -176,6 +176,26 @@ epw_status epw_linewidth_backward(const epw_model *model, int nk, const double *
                                   const double *grad_imsigma, double *dg, double *dT, double *dEF,
                                   void *stream);
 
+/* Phonon-side sums over a k list of the same interpolated vertex, for each q
+ * of the q list and each mode nu (Sec. "Theory", Eqs. (linewidthph),
+ * (lambdaEQ), (nestingfct)):
+ *   pi_imag[q][nu] = Pi''_qnu on shell (w = w_qnu), sign as printed:
+ *       2 pi sum_k w_k sum_mn |g_mn,nu(k,q)|^2 (f_nk - f_mk+q) delta(e_nk - e_mk+q - w_qnu)
+ *   lambda[q][nu]  = sum_k w_k sum_mn |g|^2 delta(e_nk - E_F) delta(e_mk+q - E_F) / (N(E_F) w_qnu)
+ *   nesting[q]     = sum_k w_k sum_mn delta(e_nk - E_F) delta(e_mk+q - E_F)
+ *   dos_ef[0]      = N(E_F) = sum_k w_k sum_n delta(e_nk - E_F)   (per spin)
+ * with the Gaussian delta and occupations of epw_linewidth (params: T_K,
+ * EF_eV, sigma_eV, omega_min_eV; modes below omega_min get 0).  k [nk][3],
+ * wk [nk] or NULL (1/nk), q [nq][3]; outputs [nq][3nat], [nq][3nat], [nq], [1]
+ * (eV for pi_imag; lambda and nesting dimensionless / per eV^2); any output may
+ * be NULL; pointers host or device.  precision: EPW_FP64, EPW_FP32 (CUDA
+ * cores) or EPW_TF32X3 / EPW_BF16X3 (contraction on the tensor cores, staged
+ * per chunk of k; needs Re == Rp).  Shapes up to nw = 8, 3nat = 9; others
+ * return EPW_ERR_UNSUPPORTED.  Per-q sums over k are formed in a fixed order. */
+epw_status epw_phonon_selfenergy(const epw_model *model, int nk, const double *k, const double *wk, int nq,
+                                 const double *q, const epw_params *params, double *pi_imag, double *lambda,
+                                 double *nesting, double *dos_ef, void *stream);
+
 /* Allocation-free variant of epw_linewidth, for callers that cannot allocate
  * device memory: code running where cudaMalloc is not allowed or not wanted
  * (inside a memory-pool-managed host framework, a real-time loop that must

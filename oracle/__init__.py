@@ -93,6 +93,8 @@ def _load():
             for name in ("oracle_fermi", "oracle_fermi_slope"):
                 getattr(lib, name).argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
                 getattr(lib, name).restype = ctypes.c_double
+            lib.oracle_fermi_diff.argtypes = [ctypes.c_double] * 4
+            lib.oracle_fermi_diff.restype = ctypes.c_double
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = I
             _lib = lib
@@ -265,6 +267,10 @@ def fermi(e, EF, T):
 
 def fermi_slope(e, EF, T):
     return _load().oracle_fermi_slope(float(e), float(EF), float(T))
+
+
+def fermi_diff(ea, eb, EF, T):
+    return _load().oracle_fermi_diff(float(ea), float(eb), float(EF), float(T))
 
 
 def gauss(x, sigma):

@@ -110,6 +110,19 @@ double oracle_fermi_slope(double e, double EF, double T) {
   return t / ((1.0 + t) * (1.0 + t));
 }
 
+/* f(ea) - f(eb) without the cancellation of subtracting two rounded occupations:
+   with a, b = (e - E_F)/kT, d = b - a and S = |a| + |b| (d + S >= 0, S - d >= 0),
+     f(a) - f(b) = 2 sinh(d/2) e^{-S/2} / ((1 + e^{-|a|}) (1 + e^{-|b|})),
+   the sinh written with expm1 of d or -d so that no exponent is positive.
+   T = 0: the step occupations (f(E_F) = 1/2). */
+double oracle_fermi_diff(double ea, double eb, double EF, double T) {
+  if (T <= 0.0) return oracle_fermi(ea, EF, T) - oracle_fermi(eb, EF, T);
+  const double a = (ea - EF) / (KB_EV * T), b = (eb - EF) / (KB_EV * T);
+  const double d = b - a, S = fabs(a) + fabs(b);
+  const double num = d >= 0.0 ? -exp(0.5 * (d - S)) * expm1(-d) : exp(-0.5 * (d + S)) * expm1(d);
+  return num / ((1.0 + exp(-fabs(a))) * (1.0 + exp(-fabs(b))));
+}
+
 double oracle_gauss(double x, double sigma) {
   double y = x / sigma;
   return exp(-y * y) / (sigma * sqrt(M_PI));
@@ -458,17 +471,16 @@ int oracle_phonon_self(const oracle_model *m, int nk, const double *k, const dou
         bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E, gmn, tmp);
         for (int n = 0; n < nw; n++) {
           const double en = epsk[(long)ik * nw + n];
-          const double fn = oracle_fermi(en, pr->EF, pr->T);
           const double dn = oracle_gauss(en - pr->EF, pr->sigma);
           for (int mm = 0; mm < nw; mm++) {
-            const double fm = oracle_fermi(ekq[mm], pr->EF, pr->T);
+            const double dfnm = oracle_fermi_diff(en, ekq[mm], pr->EF, pr->T);  /* f_nk - f_mk+q */
             const double dd = dn * oracle_gauss(ekq[mm] - pr->EF, pr->sigma);
             nsum_add(&sz, wki * dd);
             for (int nu = 0; nu < nm; nu++) {
               if (w[nu] < pr->omega_min) continue;
               cplx gv = gmn[(nu * nw + mm) * nw + n];
               double g2 = creal(gv) * creal(gv) + cimag(gv) * cimag(gv);
-              nsum_add(&sp[nu], wki * g2 * (fn - fm) * oracle_gauss(en - ekq[mm] - w[nu], pr->sigma));
+              nsum_add(&sp[nu], wki * g2 * dfnm * oracle_gauss(en - ekq[mm] - w[nu], pr->sigma));
               nsum_add(&sl[nu], wki * g2 * dd);
             }
           }

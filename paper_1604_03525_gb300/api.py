@@ -156,6 +156,26 @@ class Model:
                                  _stream_of(ka, qa, wa, oa)))
         return out
 
+    def phonon_selfenergy(self, k, q, wk=None, *, T: float, EF: float, sigma: float, omega_min: float = 1e-5,
+                          precision: int = FP64):
+        """(Pi''_qnu [nq, 3nat], lambda_qnu [nq, 3nat], nesting [nq], N(E_F)): per-q sums over the k list
+        (Eqs. linewidthph on shell, lambdaEQ, nestingfct)."""
+        lib = _lib.load()
+        ka, qa, wa = _Arg(k, np.float64), _Arg(q, np.float64), _Arg(wk, np.float64)
+        nk = int(np.prod(ka.keep.shape)) // 3
+        nq = int(np.prod(qa.keep.shape)) // 3
+        if qa.device:
+            import torch
+            mk = lambda *shape: torch.zeros(shape, dtype=torch.float64, device=qa.keep.device)
+        else:
+            mk = lambda *shape: np.zeros(shape)
+        pi, lam, zeta, dos = mk(nq, self.nm), mk(nq, self.nm), mk(nq), mk(1)
+        outs = [_Arg(x, np.float64) for x in (pi, lam, zeta, dos)]
+        pr = _lib.Params(float(T), float(EF), float(sigma), float(omega_min), int(precision), 0)
+        _check(lib.epw_phonon_selfenergy(self._h, nk, ka.ptr, wa.ptr, nq, qa.ptr, ctypes.byref(pr),
+                                         *[o.ptr for o in outs], _stream_of(ka, qa, wa, *outs)))
+        return pi, lam, zeta, (float(dos[0]) if not _is_torch(dos) else dos)
+
     def linewidth_noalloc(self, k, q, wq=None, *, T: float, EF: float, sigma: float, omega_min: float = 1e-5,
                           precision: int = FP64, out=None):
         """epw_linewidth_noalloc: like linewidth, but the library allocates no device memory.

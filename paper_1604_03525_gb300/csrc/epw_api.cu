@@ -860,6 +860,158 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   return EPW_OK;
 }
 
+// ------------------------------------------------- phonon self-energy
+// Per (q, nu) sums over the k list: Pi''_qnu (Eq. (linewidthph), on shell), lambda_qnu
+// (Eq. (lambdaEQ)) and the nesting function (Eq. (nestingfct)); see include/epw.h.
+extern "C" epw_status epw_phonon_selfenergy(const epw_model *mc, int nk, const double *k, const double *wk, int nq,
+                                            const double *q, const epw_params *par, double *pi_im, double *lam,
+                                            double *zeta, double *dos, void *stream) {
+  g_err[0] = 0;
+  epw_model *m = const_cast<epw_model *>(mc);
+  CKS(check_common(m, nk, k, nq, q));
+  CKS(check_params(par));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nm = m->nm;
+  const bool tcp = par->precision == EPW_BF16X3 || par->precision == EPW_TF32X3;
+  if (m->nw > 8 || nm > 9)
+    return fail(EPW_ERR_UNSUPPORTED, "the phonon-side sums have no kernel for nw=%d, 3nat=%d (at most 8 and 9)",
+                m->nw, nm);
+  if (tcp && !m->same_ep) return fail(EPW_ERR_UNSUPPORTED, "the tensor-core forms need Re == Rp");
+  const int wprec = tcp ? EPW_FP32 : par->precision;
+  const bool sk = nk > 0 && !is_device_ptr(k), sq = nq > 0 && !is_device_ptr(q);
+  const bool swk = wk && nk > 0 && !is_device_ptr(wk);
+  const bool spi = pi_im && nq > 0 && !is_device_ptr(pi_im), slam = lam && nq > 0 && !is_device_ptr(lam);
+  const bool sz = zeta && nq > 0 && !is_device_ptr(zeta), sd = dos && !is_device_ptr(dos);
+  // chunks of k per q block: enough blocks to fill the GPU a few times over
+  const int nqb = (std::max(nq, 1) + 127) / 128;
+  const int want = std::max(1, (4 * 152 + nqb - 1) / nqb);
+  const int kper = std::max(1, (std::max(nk, 1) + want - 1) / want);
+  struct B {
+    Prep p;
+    TcStaged sg;
+    double *partial, *pid, *lamd, *zd, *dosd, *terms, *wkd;
+    int nchunk;
+  } b;
+  auto plan = [&](Arena &A) -> epw_status {
+    plan_prep(A, m, std::max(nk, 1), std::max(nq, 1), wprec, sk, sq, false, true, b.p);
+    b.wkd = swk ? A.take<double>((size_t)nk) : nullptr;  // k weights staged from the host
+    b.sg = TcStaged{};
+    int nchunk = (std::max(nk, 1) + kper - 1) / kper;
+    if (tcp) {
+      CKS(tc_staged_plan(A, m, std::max(nk, 1), std::max(nq, 1), par->precision == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32,
+                         STAGED_CT_BYTES, b.sg, true));
+      if (!b.sg.ok) return fail(EPW_ERR_UNSUPPORTED, "no staged tensor-core form for this model");
+      nchunk = 0;  // chunks of kper inside each staged chunk of sg.kc
+      for (int k0 = 0; k0 < std::max(nk, 1); k0 += b.sg.kc) {
+        const int kc = std::min(b.sg.kc, std::max(nk, 1) - k0);
+        nchunk += (kc + kper - 1) / kper;
+      }
+    }
+    b.nchunk = nchunk;
+    b.partial = A.take<double>((size_t)nchunk * std::max(nq, 1) * (2 * nm + 1));
+    b.pid = spi ? A.take<double>((size_t)nq * nm) : pi_im;
+    b.lamd = slam ? A.take<double>((size_t)nq * nm) : lam;
+    b.zd = sz ? A.take<double>((size_t)nq) : zeta;
+    b.dosd = A.take<double>(1);
+    b.terms = A.take<double>((size_t)std::max(nk, 1));
+    return EPW_OK;
+  };
+  Arena A{nullptr, 0, 0};
+  CKS(plan(A));
+  CKS(ensure_ws(m, A.off));
+  A = Arena{(char *)m->ws, m->ws_bytes, 0};
+  CKS(plan(A));
+  Prep &p = b.p;
+  const double *kd = k, *qd = q, *wkd = wk;
+  if (sk) {
+    CK(cudaMemcpyAsync(p.kd, k, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
+    kd = p.kd;
+  }
+  if (sq) {
+    CK(cudaMemcpyAsync(p.qd, q, sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, st));
+    qd = p.qd;
+  }
+  if (swk) {
+    CK(cudaMemcpyAsync(b.wkd, wk, sizeof(double) * nk, cudaMemcpyHostToDevice, st));
+    wkd = b.wkd;
+  }
+  CK(cudaMemsetAsync(b.dosd, 0, sizeof(double), st));
+  if (nq > 0) {
+    if (b.pid) CK(cudaMemsetAsync(b.pid, 0, sizeof(double) * (size_t)nq * nm, st));
+    if (b.lamd) CK(cudaMemsetAsync(b.lamd, 0, sizeof(double) * (size_t)nq * nm, st));
+    if (b.zd) CK(cudaMemsetAsync(b.zd, 0, sizeof(double) * (size_t)nq, st));
+  }
+  if (nk > 0 && nq > 0) {
+    CKS(run_prep(m, nk, kd, nq, qd, wprec, par->omega_min_eV, true, p, nullptr, st));
+  } else if (nk > 0) {
+    // bands at k only (N(E_F))
+    launch_phases(nk, kd, m->nRe, m->Re, p.PkRM, p.PkT, nullptr, st);
+    launch_fourier_d(nk, m->nRe, p.PkT, m->Hw, m->nw * m->nw, p.Hk, st);
+    launch_eigh_d(nk, m->nw, p.Hk, p.epsk, p.Uk, m->dstatus, st);
+  }
+  if (nk > 0) {
+    launch_dos_terms(nk, m->nw, p.epsk, wkd, par->EF_eV, par->sigma_eV, b.terms, st);
+    launch_sum_scalar(nk, b.terms, 1.0, b.dosd, st);
+  }
+  if (nk > 0 && nq > 0) {
+    PairArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nq = nq;
+    a.nw = m->nw;
+    a.nm = nm;
+    a.nRe = m->nRe;
+    a.nRp = m->nRp;
+    a.PqTe = p.PqTe;
+    a.PqTp = p.PqTp;
+    a.BH = p.BH;
+    a.Bg = p.Bg;
+    a.ET = p.ET;
+    a.omegaT = p.omegaT;
+    a.eps_k = p.epsk;
+    a.wq = wkd;  // the k weights
+    a.nk_total = nk;
+    a.T = par->T_K;
+    a.EF = par->EF_eV;
+    a.sigma = par->sigma_eV;
+    a.omega_min = par->omega_min_eV;
+    a.dstatus = m->dstatus;
+    a.nkc = kper;
+    if (tcp) {
+      CKS(tc_staged_phases(m, nq, qd, b.sg, st));
+      int chunk0 = 0;
+      for (int k0 = 0; k0 < nk; k0 += b.sg.kc) {
+        const int kc = std::min(b.sg.kc, nk - k0);
+        epw_status s = tc_staged_contract(m, k0, kc, nq, (const cx<float> *)p.Bg, (const cx<float> *)p.BH, b.sg, st);
+        if (s != EPW_OK) return fail(s, "staged tensor-core contraction failed");
+        const int nch = (kc + kper - 1) / kper;
+        a.k0 = k0;
+        a.nk = kc;
+        a.Cq = b.sg.Ct;
+        a.ldc = b.sg.pair_ld();
+        a.cpk = b.sg.cpk;
+        a.partial = b.partial + (size_t)chunk0 * nq * (2 * nm + 1);
+        s = launch_pair_ph<float>(a, nch, st);
+        if (s != EPW_OK) return fail(s, "no phonon-side kernel for nw=%d, 3nat=%d", m->nw, nm);
+        chunk0 += nch;
+      }
+    } else {
+      a.k0 = 0;
+      a.nk = nk;
+      a.partial = b.partial;
+      epw_status s = wprec == EPW_FP64 ? launch_pair_ph<double>(a, b.nchunk, st) : launch_pair_ph<float>(a, b.nchunk, st);
+      if (s != EPW_OK) return fail(s, "no phonon-side kernel for nw=%d, 3nat=%d", m->nw, nm);
+    }
+    launch_ph_finalize(nq, nm, b.nchunk, b.partial, p.omegaT, par->omega_min_eV, b.dosd, b.pid, b.lamd, b.zd, st);
+  }
+  CK(cudaGetLastError());
+  if (spi) CK(cudaMemcpyAsync(pi_im, b.pid, sizeof(double) * (size_t)nq * nm, cudaMemcpyDeviceToHost, st));
+  if (slam) CK(cudaMemcpyAsync(lam, b.lamd, sizeof(double) * (size_t)nq * nm, cudaMemcpyDeviceToHost, st));
+  if (sz) CK(cudaMemcpyAsync(zeta, b.zd, sizeof(double) * (size_t)nq, cudaMemcpyDeviceToHost, st));
+  if (dos) CK(cudaMemcpyAsync(dos, b.dosd, sizeof(double), sd ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  if (sk || sq || swk || spi || slam || sz || sd) return read_status(m, st);
+  return EPW_OK;
+}
+
 // ------------------------------------------------ allocation-free linewidth
 // Scratch for epw_linewidth_noalloc: a fixed device array that exists on every
 // GPU on which this library is loaded, for the life of the process.  Host code

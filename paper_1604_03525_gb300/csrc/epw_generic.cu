@@ -218,29 +218,22 @@ __device__ __forceinline__ double block_sum128(double v, double *sh /*[4]*/) {
   return s;
 }
 
-// One thread per (k, q) pair; a block holds 128 consecutive q of one k.
-//   H(k+q)   = sum_Re P_q(Re) BH_k(Re)                      -> Jacobi -> e_m, U
+// The vertex of one pair (k, q) (kl = k - a.k0; qq a valid q):
+//   H(k+q)   = sum_Re P_q(Re) BH_k(Re)  (or the staged contraction)  -> Jacobi -> e_m (ascending), U
 //   X_a      = sum_Rp P_q(Rp) Bg_k(Rp, a)   (= g_a(k,q) U_k)
 //   G_nu     = sum_a E_q[a][nu] U^dagger X_a                 (= g_mn,nu)
-// mode 0: linewidth terms of Eq. (linewidthel), reduced over the block;
-// mode 1: write e_k+q and g_mn,nu;  mode 2: adjoint (see launch_pair).
-template <typename R, int MW, int MM, int MODE, bool FROMC = false>
-__global__ void __launch_bounds__(128) k_pair(PairArgs a) {
+// Returns false when the eigensolve did not converge.
+template <typename R, int MW, int MM, bool FROMC>
+__device__ __forceinline__ bool pair_vertex(const PairArgs &a, int kl, int k, int qq, R (&ekq)[MW], cx<R> (&U)[MW][MW],
+                                            cx<R> (&G)[MM][MW][MW]) {
   constexpr int UW = MW <= 4 ? MW : 1;
   constexpr int UM = MM <= 4 ? MM : 1;
-  __shared__ double sh[4];
-  const int q = blockIdx.x * 128 + threadIdx.x;
-  const int kl = blockIdx.y;
-  const int k = a.k0 + kl;
-  const bool valid = q < a.nq;
-  const int qq = valid ? q : 0;
   const int nw = a.nw, nm = a.nm, nw2 = nw * nw, nq = a.nq;
   const cx<R> *PqTe = (const cx<R> *)a.PqTe;
   const cx<R> *PqTp = (const cx<R> *)a.PqTp;
   const cx<R> *BH = (const cx<R> *)a.BH + (size_t)k * a.nRe * nw2;
   const cx<R> *Bg = (const cx<R> *)a.Bg + (size_t)k * a.nRp * nm * nw2;
   const cx<R> *ET = (const cx<R> *)a.ET;
-
   cx<R> A[MW][MW];
 #pragma unroll UW
   for (int i = 0; i < MW; i++)
@@ -268,14 +261,9 @@ __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
           if (i < nw && j < nw) cfma(A[i][j], p, b[i * nw + j]);
     }
   }
-  cx<R> U[MW][MW];
   bool nc = false;
   jacobi_herm<R, MW>(A, U, nw, jacobi_tol<R>::tol2, jacobi_tol<R>::maxsweep, nc);
-  R ekq[MW];
   sort_eig<R, MW>(A, U, ekq, nw);
-  if (nc && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
-
-  cx<R> G[MM][MW][MW];
 #pragma unroll UM
   for (int v = 0; v < MM; v++)
 #pragma unroll UW
@@ -326,6 +314,29 @@ __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
       }
     }
   }
+  return !nc;
+}
+
+// One thread per (k, q) pair; a block holds 128 consecutive q of one k.
+// mode 0: linewidth terms of Eq. (linewidthel), reduced over the block;
+// mode 1: write e_k+q and g_mn,nu;  mode 2: adjoint (see launch_pair).
+template <typename R, int MW, int MM, int MODE, bool FROMC = false>
+__global__ void __launch_bounds__(128) k_pair(PairArgs a) {
+  constexpr int UW = MW <= 4 ? MW : 1;
+  constexpr int UM = MM <= 4 ? MM : 1;
+  __shared__ double sh[4];
+  const int q = blockIdx.x * 128 + threadIdx.x;
+  const int kl = blockIdx.y;
+  const int k = a.k0 + kl;
+  const bool valid = q < a.nq;
+  const int qq = valid ? q : 0;
+  const int nw = a.nw, nm = a.nm, nw2 = nw * nw, nq = a.nq;
+  const cx<R> *ET = (const cx<R> *)a.ET;
+  R ekq[MW];
+  cx<R> U[MW][MW];
+  cx<R> G[MM][MW][MW];
+  const bool conv = pair_vertex<R, MW, MM, FROMC>(a, kl, k, qq, ekq, U, G);
+  if (!conv && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
 
   const double *ek = a.eps_k + (size_t)k * nw;
   const R inv_sigma = (R)(1.0 / a.sigma);
@@ -449,6 +460,134 @@ __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
     double tE = block_sum128(sE, sh);
     if (threadIdx.x == 0) a.partialE[(size_t)kl * nqb + blockIdx.x] = tE;
   }
+}
+
+// Per-(q, nu) sums over k (phonon self-energy, Eq. (linewidthph) on shell;
+// coupling strength, Eq. (lambdaEQ); nesting function, Eq. (nestingfct)):
+// one thread per q of a block of 128, looping over the a.nk k-points from
+// a.k0 in order; the block's chunk index is blockIdx.y (k = a.k0 + blockIdx.y *
+// a.nkc + j).  Writes, per q, the partial sums over its k chunk:
+//   out[chunk][q][nu]          sum_k w_k sum_mn |g|^2 (f_nk - f_mk+q) delta(e_nk - e_mk+q - w_qnu)
+//   out[chunk][q][nm + nu]     sum_k w_k sum_mn |g|^2 delta(e_nk - E_F) delta(e_mk+q - E_F)
+//   out[chunk][q][2 nm]        sum_k w_k sum_mn delta(e_nk - E_F) delta(e_mk+q - E_F)
+template <typename R, int MW, int MM, bool FROMC>
+__global__ void __launch_bounds__(128) k_pair_ph(PairArgs a) {
+  constexpr int UW = MW <= 4 ? MW : 1;
+  constexpr int UM = MM <= 4 ? MM : 1;
+  const int q = blockIdx.x * 128 + threadIdx.x;
+  if (q >= a.nq) return;
+  const int nw = a.nw, nm = a.nm, nq = a.nq;
+  const int kc0 = blockIdx.y * a.nkc;
+  const int kc1 = min(a.nk, kc0 + a.nkc);
+  const R inv_sigma = (R)(1.0 / a.sigma);
+  const R gnorm = (R)(1.0 / (a.sigma * 1.7724538509055160273));
+  R w[MM];
+  bool keep[MM];
+#pragma unroll UM
+  for (int v = 0; v < MM; v++) {
+    w[v] = v < nm ? (R)a.omegaT[(size_t)v * nq + q] : R(0);
+    keep[v] = v < nm && (w[v] >= (R)a.omega_min) && (w[v] > R(0));
+  }
+  double sp[MM], sl[MM], sz = 0.0;
+#pragma unroll UM
+  for (int v = 0; v < MM; v++) sp[v] = sl[v] = 0.0;
+  for (int kl = kc0; kl < kc1; kl++) {
+    const int k = a.k0 + kl;
+    R ekq[MW];
+    cx<R> U[MW][MW];
+    cx<R> G[MM][MW][MW];
+    const bool conv = pair_vertex<R, MW, MM, FROMC>(a, kl, k, q, ekq, U, G);
+    if (!conv) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
+    const double wk = a.wq ? a.wq[k] : 1.0 / a.nk_total;
+    R en[MW], dn[MW], dm[MW];
+#pragma unroll UW
+    for (int n = 0; n < MW; n++) {
+      en[n] = n < nw ? (R)a.eps_k[(size_t)k * nw + n] : R(0);
+      dn[n] = gauss_r<R>(en[n] - (R)a.EF, inv_sigma, gnorm);
+      dm[n] = gauss_r<R>(ekq[n] - (R)a.EF, inv_sigma, gnorm);
+    }
+    R z = R(0);
+    R fd[MW][MW];  // f_nk - f_mk+q
+#pragma unroll UW
+    for (int m = 0; m < MW; m++)
+#pragma unroll UW
+      for (int n = 0; n < MW; n++) {
+        fd[m][n] = R(0);
+        if (m < nw && n < nw) {
+          z += dn[n] * dm[m];
+          if constexpr (sizeof(R) == sizeof(double))
+            fd[m][n] = (R)fermi_diff_d((double)en[n], (double)ekq[m], a.EF, a.T);
+          else
+            fd[m][n] = (R)fermi_diff_f((float)en[n], (float)ekq[m], a.EF, a.T);
+        }
+      }
+    sz += wk * (double)z;
+#pragma unroll UM
+    for (int v = 0; v < MM; v++) {
+      if (!keep[v]) continue;
+      R p = R(0), l = R(0);
+#pragma unroll UW
+      for (int m = 0; m < MW; m++)
+#pragma unroll UW
+        for (int n = 0; n < MW; n++) {
+          if (m >= nw || n >= nw) continue;
+          const R g2 = cabs2(G[v][m][n]);
+          p += g2 * fd[m][n] * gauss_r<R>(en[n] - ekq[m] - w[v], inv_sigma, gnorm);
+          l += g2 * dn[n] * dm[m];
+        }
+      sp[v] += wk * (double)p;
+      sl[v] += wk * (double)l;
+    }
+  }
+  double *o = a.partial + ((size_t)blockIdx.y * nq + q) * (2 * nm + 1);
+  for (int v = 0; v < nm; v++) {
+    o[v] = sp[v < MM ? v : 0];
+    o[nm + v] = sl[v < MM ? v : 0];
+  }
+  o[2 * nm] = sz;
+}
+
+// Sum of the per-chunk partials in chunk order; Pi'' = 2 pi sum_p, lambda = sum_l / (N(E_F) w)
+// for kept modes (0 otherwise), zeta = sum_z.  dos: N(E_F) on the device.
+__global__ void k_ph_finalize(int nq, int nm, int nchunk, const double *__restrict__ partial,
+                              const double *__restrict__ omegaT, double omega_min, const double *__restrict__ dos,
+                              double *pi_im, double *lam, double *zeta) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int st = 2 * nm + 1;
+  for (int j = 0; j < st; j++) {
+    double s = 0.0, c = 0.0;  // Neumaier over chunks
+    for (int ch = 0; ch < nchunk; ch++) {
+      const double x = partial[((size_t)ch * nq + q) * st + j];
+      const double t = s + x;
+      c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+      s = t;
+    }
+    s += c;
+    if (j < nm) {
+      const double w = omegaT[(size_t)j * nq + q];
+      const bool keep = w >= omega_min && w > 0.0;
+      if (pi_im) pi_im[(size_t)q * nm + j] = keep ? 2.0 * EPW_PI * s : 0.0;
+    } else if (j < 2 * nm) {
+      const int v = j - nm;
+      const double w = omegaT[(size_t)v * nq + q];
+      const bool keep = w >= omega_min && w > 0.0 && dos[0] > 0.0;
+      if (lam) lam[(size_t)q * nm + v] = keep ? s / (dos[0] * w) : 0.0;
+    } else if (zeta) {
+      zeta[q] = s;
+    }
+  }
+}
+
+// Per-k terms of N(E_F) = sum_k w_k sum_n delta(e_nk - E_F).
+__global__ void k_dos_terms(int nk, int nw, const double *__restrict__ epsk, const double *__restrict__ wk,
+                            double EF, double sigma, double *terms) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const double inv = 1.0 / sigma, norm = 1.0 / (sigma * 1.7724538509055160273);
+  double s = 0.0;
+  for (int n = 0; n < nw; n++) s += gauss_r<double>(epsk[(size_t)k * nw + n] - EF, inv, norm);
+  terms[k] = (wk ? wk[k] : 1.0 / nk) * s;
 }
 
 // gw[Re][Rp][...] = wRe wRp g   (g complex128 or, with is_c64, complex64)
@@ -686,6 +825,47 @@ epw_status launch_pair_staged(const PairArgs &a, int mode, cudaStream_t st) {
     k_pair<float, 8, 9, 2, true><<<grid, 128, 0, st>>>(a);
   epw_count_launch();
   return EPW_OK;
+}
+
+template <typename R, bool FROMC>
+static epw_status ph_dispatch(const PairArgs &a, dim3 grid, cudaStream_t st) {
+  if (a.nw <= 1 && a.nm <= 3)
+    k_pair_ph<R, 1, 3, FROMC><<<grid, 128, 0, st>>>(a);
+  else if (a.nw <= 4 && a.nm <= 3)
+    k_pair_ph<R, 4, 3, FROMC><<<grid, 128, 0, st>>>(a);
+  else if (a.nw <= 8 && a.nm <= 9)
+    k_pair_ph<R, 8, 9, FROMC><<<grid, 128, 0, st>>>(a);
+  else
+    return EPW_ERR_UNSUPPORTED;
+  epw_count_launch();
+  return EPW_OK;
+}
+
+template <typename R>
+epw_status launch_pair_ph(const PairArgs &a, int nchunk, cudaStream_t st) {
+  if (a.nk <= 0 || a.nq <= 0) return EPW_OK;
+  dim3 grid((a.nq + 127) / 128, nchunk);
+  if (a.Cq) {
+    if constexpr (sizeof(R) == sizeof(float)) return ph_dispatch<float, true>(a, grid, st);
+    return EPW_ERR_UNSUPPORTED;
+  }
+  return ph_dispatch<R, false>(a, grid, st);
+}
+template epw_status launch_pair_ph<double>(const PairArgs &, int, cudaStream_t);
+template epw_status launch_pair_ph<float>(const PairArgs &, int, cudaStream_t);
+
+void launch_ph_finalize(int nq, int nm, int nchunk, const double *partial, const double *omegaT, double omega_min,
+                        const double *dos, double *pi_im, double *lam, double *zeta, cudaStream_t st) {
+  if (nq <= 0) return;
+  k_ph_finalize<<<(nq + 127) / 128, 128, 0, st>>>(nq, nm, nchunk, partial, omegaT, omega_min, dos, pi_im, lam, zeta);
+  epw_count_launch();
+}
+
+void launch_dos_terms(int nk, int nw, const double *epsk, const double *wk, double EF, double sigma, double *terms,
+                      cudaStream_t st) {
+  if (nk <= 0) return;
+  k_dos_terms<<<(nk + 127) / 128, 128, 0, st>>>(nk, nw, epsk, wk, EF, sigma, terms);
+  epw_count_launch();
 }
 
 void launch_set_vertex(const epw_model *m, const void *g, int is_c64, cudaStream_t st) {

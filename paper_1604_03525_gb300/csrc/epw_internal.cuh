@@ -102,6 +102,31 @@ __device__ __forceinline__ double fermi_ff_d(double d, double T) {
   return t / (u * u);
 }
 
+// f(ea) - f(eb) without subtracting two rounded occupations: with a, b the
+// arguments (e - E_F)/kT, d = b - a and S = |a| + |b|,
+//   f(a) - f(b) = 2 sinh(d/2) e^{-S/2} / ((1 + e^{-|a|}) (1 + e^{-|b|})),
+// the sinh through expm1 of d or -d so that no exponent is positive.
+__device__ __forceinline__ double fermi_diff_d(double ea, double eb, double EF, double T) {
+  if (T <= 0.0) return fermi_d(ea, EF, T) - fermi_d(eb, EF, T);
+  const double ikt = 1.0 / (EPW_KB * T);
+  const double a = (ea - EF) * ikt, b = (eb - EF) * ikt;
+  const double d = b - a, S = fabs(a) + fabs(b);
+  const double num = d >= 0.0 ? -exp(0.5 * (d - S)) * expm1(-d) : exp(-0.5 * (d + S)) * expm1(d);
+  return num / ((1.0 + exp(-fabs(a))) * (1.0 + exp(-fabs(b))));
+}
+__device__ __forceinline__ float fermi_diff_f(float ea, float eb, double EF, double T) {
+  if (T <= 0.0) {
+    const float fa = ea < (float)EF ? 1.0f : (ea > (float)EF ? 0.0f : 0.5f);
+    const float fb = eb < (float)EF ? 1.0f : (eb > (float)EF ? 0.0f : 0.5f);
+    return fa - fb;
+  }
+  const float ikt = (float)(1.0 / (EPW_KB * T));
+  const float a = (float)((double)ea - EF) * ikt, b = (float)((double)eb - EF) * ikt;
+  const float d = b - a, S = fabsf(a) + fabsf(b);
+  const float num = d >= 0.0f ? -expf(0.5f * (d - S)) * expm1f(-d) : expf(-0.5f * (d + S)) * expm1f(d);
+  return num / ((1.0f + expf(-fabsf(a))) * (1.0f + expf(-fabsf(b))));
+}
+
 // -------------------------------------------------------- Jacobi eigensolver
 // Hermitian N x N (runtime n <= N, compile-time N so that fully unrolled loops
 // keep the arrays in registers for small N).  Cyclic sweeps of two-sided
@@ -350,12 +375,22 @@ struct PairArgs {
   const float *Cq;
   size_t ldc;
   int cpk;
+  int nk_total;  // phonon side: all k-points of the call (the 1/nk weight when wq (= w_k) is null)
 };
 // mode: 0 linewidth, 1 interp, 2 backward
 template <typename R>
 epw_status launch_pair(const PairArgs &a, int mode, cudaStream_t st);
 // per-pair kernel on a staged contraction (a.Cq set; FP32)
 epw_status launch_pair_staged(const PairArgs &a, int mode, cudaStream_t st);
+// phonon side (per-(q, nu) sums over k, nw <= 8, 3nat <= 9): grid (q blocks, nchunk), each chunk
+// a.nkc k-points from a.k0 (a.nk of them in total in this launch); a.wq holds w_k here;
+// partials [nchunk][nq][2 nm + 1]
+template <typename R>
+epw_status launch_pair_ph(const PairArgs &a, int nchunk, cudaStream_t st);
+void launch_ph_finalize(int nq, int nm, int nchunk, const double *partial, const double *omegaT, double omega_min,
+                        const double *dos, double *pi_im, double *lam, double *zeta, cudaStream_t st);
+void launch_dos_terms(int nk, int nw, const double *epsk, const double *wk, double EF, double sigma, double *terms,
+                      cudaStream_t st);
 // warp-per-pair kernel for nw, 3nat up to 18 (modes 0 and 1; a.Cq set: staged
 // contraction in the q-major layout Cq[q*ldc + kl*cpk + 2c + s], FP32 only)
 template <typename R>

@@ -1787,10 +1787,11 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
 // and the per-pair kernel (eigensolve, rotation, deltas) reads it from there.
 bool tc_staged_supported(const epw_model *m) { return m->same_ep && !tc_supported(m) && m->nw <= 18 && m->nm <= 18; }
 
-epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t ct_budget, TcStaged &s) {
+epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t ct_budget, TcStaged &s,
+                          bool any_shape) {
   s = TcStaged{};
   s.op = op;
-  s.ok = tc_staged_supported(m);
+  s.ok = any_shape ? (m->same_ep && m->nw <= 18 && m->nm <= 18) : tc_staged_supported(m);
   if (!s.ok) return EPW_OK;
   const int esz = op == TC_OP_BF16 ? 2 : 4;
   const int kal = op == TC_OP_BF16 ? 16 : 8;  // K per MMA

@@ -81,7 +81,9 @@ struct TcStaged {
 };
 bool tc_staged_supported(const epw_model *m);
 // Buffers for chunks of up to `kc` k-points, kc chosen so Ct stays within ct_budget bytes.
-epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t ct_budget, TcStaged &s);
+// any_shape: also for shapes the fused kernel serves (per-q sums over k use the staged form).
+epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t ct_budget, TcStaged &s,
+                          bool any_shape = false);
 // Split q-phase operand (once per call).
 epw_status tc_staged_phases(const epw_model *m, int nq, const double *q, TcStaged &s, cudaStream_t st);
 // Contraction of k-points [k0, k0 + kc) into s.Ct.

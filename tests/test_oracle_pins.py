@@ -312,6 +312,26 @@ def test_adjoint_matches_finite_differences(oracle_lib):
     assert abs(fdE - dEF) <= 1e-6 * abs(dEF)
 
 
+def test_fermi_difference_without_cancellation(oracle_lib):
+    """f(ea) - f(eb) against 600-digit arithmetic (the plain difference of the two occupations),
+    where forming two rounded double occupations cancels."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 600
+    T, EF = 300.0, 0.1
+    kT = KB * T
+    for xa, xb in [(1.0, 2.0), (-3.0, 5.0), (40.0, 40.001), (-40.0, -40.0001), (-30.0, 29.0), (25.0, -31.0),
+                   (1e-3, -1e-3), (300.0, 301.0), (-500.0, -400.0)]:
+        ea, eb = EF + xa * kT, EF + xb * kT
+        # the same rounded arguments as the oracle forms (the conditioning of b - a is the input's)
+        a = mpmath.mpf((ea - EF) / (KB * T))
+        b = mpmath.mpf((eb - EF) / (KB * T))
+        ref = float(1 / (1 + mpmath.e ** a) - 1 / (1 + mpmath.e ** b))
+        got = oracle_lib.fermi_diff(ea, eb, EF, T)
+        assert abs(got - ref) <= 1e-13 * abs(ref) + 1e-300, (xa, xb, got, ref)
+    assert oracle_lib.fermi_diff(-0.1, 0.1, 0.0, 0.0) == 1.0
+    assert oracle_lib.fermi_diff(0.0, 0.1, 0.0, 0.0) == 0.5
+
+
 # ------------------------------------------------- phonon self-energy (oracle)
 def _two_band_tb(eps=(-0.3, 0.4), t=0.5, K=0.01, M=1.3, c=((0.05, 0.03), (0.08, 0.02))):
     """Two bands that never mix (H(k) diagonal, band 0 below band 1 everywhere) with
