@@ -196,6 +196,8 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "tf32x3", "bf16x3", "fp32", "fp64"])
     ap.add_argument("--other-steps", type=int, default=2, help="timed steps of the other tensor-core/FP32 forms")
     ap.add_argument("--backward-steps", type=int, default=3, help="timed adjoint calls (0: skip)")
+    ap.add_argument("--phonon-steps", type=int, default=2,
+                    help="timed phonon-side calls (Pi'', lambda, nesting over the same k x q; 0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU form (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -324,6 +326,21 @@ def main():
                     "what": "dL/dg(Re,Rp), dL/dT, dL/dE_F of L = sum Im Sigma; g(k,q) recomputed"}
         fms = time_backward(epw.FP32, 1)
         backward["fp32_simt"] = {"value": pairs / (fms / 1e3), "unit": "pairs/s", "ms_per_step": fms}
+    phonon = None
+    if args.phonon_steps > 0:
+        # per-(q, nu) sums over the k list on the same workload: Pi''_qnu, lambda_qnu, nesting, N(E_F)
+        pk = dict(T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=prec)
+        m.phonon_selfenergy(k, q, **pk)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.phonon_steps):
+            m.phonon_selfenergy(k, q, **pk)
+        e1.record()
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / args.phonon_steps
+        phonon = {"value": pairs / (pms / 1e3), "unit": "pairs/s", "ms_per_step": pms, "precision": name,
+                  "what": "Pi''_qnu (on shell), lambda_qnu, nesting zeta_q, N(E_F): per-q sums over the 1000 k"}
     others = {}
     if args.other_steps > 0:
         for oname, op in (("bf16x3", epw.BF16X3), ("tf32x3", epw.TF32X3), ("fp32", epw.FP32)):
@@ -375,7 +392,7 @@ def main():
                                    f"T={T_SWEEP[0]:.0f} K (rank r: T_sweep[r])", "pairs_per_step_per_gpu": pairs,
                        "precision": name, "l2": "flushed between timed steps (256 MB write)"},
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof,
-            "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu_form": fp64, "other_forms": others, "backward": backward,
+            "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu_form": fp64, "other_forms": others, "backward": backward, "phonon_side": phonon,
         }
         print(json.dumps(line))
     m.close()

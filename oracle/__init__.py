@@ -93,6 +93,8 @@ def _load():
             for name in ("oracle_fermi", "oracle_fermi_slope"):
                 getattr(lib, name).argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
                 getattr(lib, name).restype = ctypes.c_double
+            lib.oracle_eliashberg.argtypes = [I, I, P, P, P, I, P, ctypes.c_double, P]
+            lib.oracle_eliashberg.restype = None
             lib.oracle_fermi_diff.argtypes = [ctypes.c_double] * 4
             lib.oracle_fermi_diff.restype = ctypes.c_double
             lib.oracle_num_threads.argtypes = []
@@ -236,6 +238,19 @@ def phonon_self(model, k, q, wk=None, T=300.0, EF=0.0, sigma=0.05, omega_min=1e-
     if rc != 0:
         raise RuntimeError("oracle phonon self-energy: eigensolve did not converge")
     return pi, lam, zeta, float(dos[0])
+
+
+def eliashberg(omega, lam, grid, sigma_ph, wq=None):
+    """alpha^2 F(omega) on `grid` (Eq. isotropiceliash) from w_qnu, lambda_qnu [nq, nm]."""
+    lib = _load()
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    la = np.ascontiguousarray(lam, dtype=np.float64)
+    gr = np.ascontiguousarray(grid, dtype=np.float64)
+    wq_a = None if wq is None else np.ascontiguousarray(wq, dtype=np.float64)
+    out = np.zeros(len(gr))
+    lib.oracle_eliashberg(om.shape[0], om.shape[1], _p(om), _p(la), None if wq_a is None else _p(wq_a), len(gr),
+                          _p(gr), float(sigma_ph), _p(out))
+    return out
 
 
 def linewidth_grad(model, k, q, wq=None, T=300.0, EF=0.0, sigma=0.05, omega_min=1e-5, cot=None):

@@ -32,7 +32,8 @@
  *   - Per (q, nu) sums over a k list of the same vertex: the phonon self-energy
  *     Pi''_qnu of Eq. (linewidthph) on shell (w = w_qnu, sign as printed), the
  *     coupling strength lambda_qnu of Eq. (lambdaEQ) with N(E_F) from the k
- *     list, and the nesting function of Eq. (nestingfct).
+ *     list, and the nesting function of Eq. (nestingfct); the isotropic
+ *     Eliashberg function of Eq. (isotropiceliash) from w_qnu and lambda_qnu.
  *
  * Every eigensolve is a plain cyclic complex Jacobi iteration on the Hermitian
  * part (X + X^dagger)/2, run to full double precision; eigenvalues ascend.
@@ -497,6 +498,24 @@ int oracle_phonon_self(const oracle_model *m, int nk, const double *k, const dou
   }
   free(epsk); free(Uk);
   return bad ? -1 : 0;
+}
+
+/* Isotropic Eliashberg function of Eq. (isotropiceliash) on an omega grid:
+ *   a2f[i] = 1/2 sum_q w_q sum_nu w_qnu lambda_qnu delta_ph(omega_i - w_qnu),
+ * delta_ph the Gaussian of width sigma_ph; omega [nq][nm], lambda [nq][nm] (eV, 1);
+ * wq == NULL means 1/nq. */
+void oracle_eliashberg(int nq, int nm, const double *omega, const double *lambda, const double *wq, int nw,
+                       const double *grid, double sigma_ph, double *a2f) {
+  for (int i = 0; i < nw; i++) {
+    nsum s = {0.0, 0.0};
+    for (int iq = 0; iq < nq; iq++)
+      for (int nu = 0; nu < nm; nu++) {
+        const double w = omega[(long)iq * nm + nu];
+        nsum_add(&s, 0.5 * (wq ? wq[iq] : 1.0 / nq) * w * lambda[(long)iq * nm + nu] *
+                         oracle_gauss(grid[i] - w, sigma_ph));
+      }
+    a2f[i] = nsum_get(&s);
+  }
 }
 
 /* ------------------------------------------------------------- adjoint */

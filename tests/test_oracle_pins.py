@@ -427,3 +427,21 @@ def test_phonon_self_energy_time_reversal(oracle_lib):
     b = oracle_lib.phonon_self(m, k, -q, None, 300.0, 0.0, 0.1)
     for x, y in zip(a[:3], b[:3]):
         assert np.allclose(x, y, rtol=1e-9, atol=1e-12 * (np.abs(x).max() + 1e-300))
+
+
+def test_eliashberg_function_pins(oracle_lib):
+    """Eq. (isotropiceliash): one mode at w0 gives lambda w0 / 2 times a normalised Gaussian at w0;
+    for any spectrum, 2 int a2F(w)/w dw = sum_q w_q sum_nu lambda_qnu (widths small against w)."""
+    s = 1e-4
+    grid = np.linspace(0.0, 0.12, 24001)
+    a2f = oracle_lib.eliashberg(np.array([[0.05]]), np.array([[0.8]]), grid, s)
+    ref = 0.5 * 0.05 * 0.8 * np.exp(-((grid - 0.05) / s) ** 2) / (s * math.sqrt(math.pi))
+    assert np.allclose(a2f, ref, rtol=1e-13, atol=1e-13 * ref.max())
+    rng = np.random.default_rng(80)
+    om = 0.01 + 0.09 * rng.random((40, 6))
+    lam = rng.random((40, 6))
+    wq = rng.random(40)
+    wq /= wq.sum()
+    a2f = oracle_lib.eliashberg(om, lam, grid, s, wq)
+    integral = 2 * np.trapezoid(a2f / np.maximum(grid, 1e-12), grid)
+    assert abs(integral - (wq[:, None] * lam).sum()) < 1e-5 * (wq[:, None] * lam).sum()
