@@ -196,6 +196,16 @@ epw_status epw_phonon_selfenergy(const epw_model *model, int nk, const double *k
                                  const double *q, const epw_params *params, double *pi_imag, double *lambda,
                                  double *nesting, double *dos_ef, void *stream);
 
+/* Isotropic Eliashberg function of Eq. (isotropiceliash) on an omega grid:
+ *   a2f[i] = 1/2 sum_q w_q sum_nu omega[q][nu] lambda[q][nu] delta_ph(grid[i] - omega[q][nu])
+ * with delta_ph the Gaussian exp(-(x/sigma_ph)^2)/(sigma_ph sqrt(pi)); omega and lambda [nq][nmodes]
+ * (from epw_interp_g and epw_phonon_selfenergy), wq [nq] or NULL (1/nq), grid [ngrid] (eV) and
+ * a2f [ngrid] (dimensionless).  Host or device pointers; host inputs are staged through
+ * stream-ordered scratch of the call, and a host a2f is ready on return.
+ * Each grid point is a compensated sum over (q, nu) in a fixed order. */
+epw_status epw_eliashberg(int nq, int nmodes, const double *omega, const double *lambda, const double *wq,
+                          int ngrid, const double *grid, double sigma_ph, double *a2f, void *stream);
+
 /* Allocation-free variant of epw_linewidth, for callers that cannot allocate
  * device memory: code running where cudaMalloc is not allowed or not wanted
  * (inside a memory-pool-managed host framework, a real-time loop that must

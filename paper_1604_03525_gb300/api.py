@@ -241,6 +241,25 @@ def launch_count() -> int:
     return int(_lib.load().epw_launch_count())
 
 
+def eliashberg(omega, lam, grid, sigma_ph: float, wq=None):
+    """alpha^2 F on `grid` (Eq. isotropiceliash) from w_qnu and lambda_qnu [nq, 3nat] (epw_eliashberg)."""
+    lib = _lib.load()
+    oa, la, ga, wa = _Arg(omega, np.float64), _Arg(lam, np.float64), _Arg(grid, np.float64), _Arg(wq, np.float64)
+    nq, nm = (oa.keep.shape[0], oa.keep.shape[1]) if oa.keep.ndim == 2 else (0, 0)
+    if tuple(la.keep.shape) != tuple(oa.keep.shape):
+        raise ValueError("omega and lambda must have the same shape [nq, nmodes]")
+    ng = int(np.prod(ga.keep.shape))
+    if ga.device:
+        import torch
+        out = torch.zeros(ng, dtype=torch.float64, device=ga.keep.device)
+    else:
+        out = np.zeros(ng)
+    o = _Arg(out, np.float64)
+    _check(lib.epw_eliashberg(nq, nm, oa.ptr, la.ptr, wa.ptr, ng, ga.ptr, float(sigma_ph), o.ptr,
+                              _stream_of(oa, la, ga, wa, o)))
+    return out
+
+
 class Batch:
     """Many linewidth problems (possibly different models and sizes) as one CUDA graph.
 

@@ -1012,6 +1012,41 @@ extern "C" epw_status epw_phonon_selfenergy(const epw_model *mc, int nk, const d
   return EPW_OK;
 }
 
+// ---------------------------------------------------- Eliashberg function
+extern "C" epw_status epw_eliashberg(int nq, int nmodes, const double *omega, const double *lambda,
+                                     const double *wq, int ngrid, const double *grid, double sigma_ph, double *a2f,
+                                     void *stream) {
+  g_err[0] = 0;
+  if (nq < 0 || nmodes < 0 || ngrid < 0) return fail(EPW_ERR_INVALID_ARG, "negative size");
+  if (ngrid > 0 && (!grid || !a2f)) return fail(EPW_ERR_INVALID_ARG, "null grid or output");
+  if ((size_t)nq * nmodes > 0 && (!omega || !lambda)) return fail(EPW_ERR_INVALID_ARG, "null omega or lambda");
+  if (!(sigma_ph > 0.0) || !std::isfinite(sigma_ph)) return fail(EPW_ERR_INVALID_ARG, "sigma_ph must be > 0");
+  if (ngrid == 0) return EPW_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nt = (size_t)nq * nmodes;
+  const bool so = nt && !is_device_ptr(omega), sl = nt && !is_device_ptr(lambda);
+  const bool sw = wq && nq > 0 && !is_device_ptr(wq), sg = !is_device_ptr(grid), sa = !is_device_ptr(a2f);
+  // scratch of this call only (the function has no model and no workspace)
+  size_t bytes = 0;
+  auto room = [&](bool need, size_t n) { size_t o = bytes; if (need) bytes += (n * sizeof(double) + 255) & ~size_t(255); return o; };
+  const size_t oo = room(so, nt), ol = room(sl, nt), ow = room(sw, nq), og = room(sg, ngrid), oa = room(sa, ngrid);
+  char *buf = nullptr;
+  if (bytes) CK(cudaMallocAsync((void **)&buf, bytes, st));
+  const double *om = so ? (const double *)(buf + oo) : omega, *la = sl ? (const double *)(buf + ol) : lambda;
+  const double *w = sw ? (const double *)(buf + ow) : wq, *gr = sg ? (const double *)(buf + og) : grid;
+  double *out = sa ? (double *)(buf + oa) : a2f;
+  if (so) CK(cudaMemcpyAsync((void *)om, omega, nt * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (sl) CK(cudaMemcpyAsync((void *)la, lambda, nt * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (sw) CK(cudaMemcpyAsync((void *)w, wq, nq * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (sg) CK(cudaMemcpyAsync((void *)gr, grid, ngrid * sizeof(double), cudaMemcpyHostToDevice, st));
+  launch_eliashberg(nq, nmodes, om, la, w, ngrid, gr, sigma_ph, out, st);
+  CK(cudaGetLastError());
+  if (sa) CK(cudaMemcpyAsync(a2f, out, ngrid * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (buf) CK(cudaFreeAsync(buf, st));
+  if (sa) CK(cudaStreamSynchronize(st));
+  return EPW_OK;
+}
+
 // ------------------------------------------------ allocation-free linewidth
 // Scratch for epw_linewidth_noalloc: a fixed device array that exists on every
 // GPU on which this library is loaded, for the life of the process.  Host code

@@ -590,6 +590,33 @@ __global__ void k_dos_terms(int nk, int nw, const double *__restrict__ epsk, con
   terms[k] = (wk ? wk[k] : 1.0 / nk) * s;
 }
 
+// alpha^2 F on a grid (Eq. (isotropiceliash)): one block per grid point, each
+// thread a fixed stride of the (q, nu) terms (compensated), then a fixed tree.
+__global__ void k_eliashberg(int nq, int nm, const double *__restrict__ omega, const double *__restrict__ lam,
+                             const double *__restrict__ wq, const double *__restrict__ grid, double sigma_ph,
+                             double *a2f) {
+  __shared__ double ss[256];
+  const double x0 = grid[blockIdx.x];
+  const double inv = 1.0 / sigma_ph, norm = 1.0 / (sigma_ph * 1.7724538509055160273);
+  double s = 0.0, c = 0.0;
+  const size_t n = (size_t)nq * nm;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int iq = (int)(i / nm);
+    const double w = omega[i];
+    const double x = 0.5 * (wq ? wq[iq] : 1.0 / nq) * w * lam[i] * gauss_r<double>(x0 - w, inv, norm);
+    const double t = s + x;
+    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  ss[threadIdx.x] = s + c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) ss[threadIdx.x] += ss[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a2f[blockIdx.x] = ss[0];
+}
+
 // gw[Re][Rp][...] = wRe wRp g   (g complex128 or, with is_c64, complex64)
 __global__ void k_set_vertex(int nRe, int nRp, size_t per, const void *__restrict__ g, int is_c64,
                              const double *__restrict__ wRe, const double *__restrict__ wRp, cx<double> *gw) {
@@ -865,6 +892,13 @@ void launch_dos_terms(int nk, int nw, const double *epsk, const double *wk, doub
                       cudaStream_t st) {
   if (nk <= 0) return;
   k_dos_terms<<<(nk + 127) / 128, 128, 0, st>>>(nk, nw, epsk, wk, EF, sigma, terms);
+  epw_count_launch();
+}
+
+void launch_eliashberg(int nq, int nm, const double *omega, const double *lam, const double *wq, int ngrid,
+                       const double *grid, double sigma_ph, double *a2f, cudaStream_t st) {
+  if (ngrid <= 0) return;
+  k_eliashberg<<<ngrid, 256, 0, st>>>(nq, nm, omega, lam, wq, grid, sigma_ph, a2f);
   epw_count_launch();
 }
 

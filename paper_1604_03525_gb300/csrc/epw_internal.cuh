@@ -391,6 +391,8 @@ void launch_ph_finalize(int nq, int nm, int nchunk, const double *partial, const
                         const double *dos, double *pi_im, double *lam, double *zeta, cudaStream_t st);
 void launch_dos_terms(int nk, int nw, const double *epsk, const double *wk, double EF, double sigma, double *terms,
                       cudaStream_t st);
+void launch_eliashberg(int nq, int nm, const double *omega, const double *lam, const double *wq, int ngrid,
+                       const double *grid, double sigma_ph, double *a2f, cudaStream_t st);
 // warp-per-pair kernel for nw, 3nat up to 18 (modes 0 and 1; a.Cq set: staged
 // contraction in the q-major layout Cq[q*ldc + kl*cpk + 2c + s], FP32 only)
 template <typename R>

@@ -116,3 +116,27 @@ def test_edge_cases(epw, oracle_lib):
     with pytest.raises(epw.EPWError) as e:
         big.phonon_selfenergy(k, k, T=300.0, EF=0.0, sigma=0.1)
     assert e.value.status == 6
+
+
+def test_eliashberg_function_pipeline(epw, oracle_lib):
+    """omega from epw_interp_g, lambda from epw_phonon_selfenergy, alpha^2 F from epw_eliashberg, against the
+    oracle's chain; host and device buffers."""
+    import torch
+    rng = np.random.default_rng(940)
+    wm = W.make_model("fcc", 2, 1, [1.0], 40, 40, rng)
+    k = W.uniform_grid(5) + 0.01
+    q = W.uniform_grid(6)
+    wq = np.full(len(q), 1.0 / len(q))
+    m = epw.Model(wm)
+    _, _, om, _ = m.interp(k[:1], q, precision=epw.FP64)
+    _, lam, _, _ = m.phonon_selfenergy(k, q, T=300.0, EF=0.0, sigma=0.1, precision=epw.FP64)
+    grid = np.linspace(0.0, 0.15, 301)
+    got = epw.eliashberg(om, lam, grid, 0.004, wq)
+    rom = oracle_lib.phonons(wm, q)[0]
+    rlam = oracle_lib.phonon_self(wm, k, q, None, 300.0, 0.0, 0.1)[1]
+    ref = oracle_lib.eliashberg(rom, rlam, grid, 0.004, wq)
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.abs(ref).max()
+    dev = epw.eliashberg(torch.tensor(om, device="cuda"), torch.tensor(lam, device="cuda"),
+                         torch.tensor(grid, device="cuda"), 0.004).cpu().numpy()
+    assert np.max(np.abs(dev - ref)) <= 1e-9 * np.abs(ref).max()
+    assert np.all(ref >= 0) and ref.max() > 0
