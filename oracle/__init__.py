@@ -80,6 +80,7 @@ def _load():
                 ("oracle_linewidth", [P, I, P, I, P, P, P, P]),
                 ("oracle_linewidth_grad", [P, I, P, I, P, P, P, P, P, P, P]),
                 ("oracle_phonon_self", [P, I, P, P, I, P, P, P, P, P, P]),
+                ("oracle_selfenergy", [P, I, P, I, P, P, P, ctypes.c_double, I, P, P, P]),
             ]:
                 getattr(lib, name).argtypes = args
                 getattr(lib, name).restype = I
@@ -238,6 +239,24 @@ def phonon_self(model, k, q, wk=None, T=300.0, EF=0.0, sigma=0.05, omega_min=1e-
     if rc != 0:
         raise RuntimeError("oracle phonon self-energy: eigensolve did not converge")
     return pi, lam, zeta, float(dos[0])
+
+
+def selfenergy(model, k, q, omega, wq=None, T=300.0, EF=0.0, delta=0.01, omega_min=1e-5):
+    """(Sigma_nk(omega) [nk, nw, nomega] complex (Eq. elselfenergy, i delta broadening, omega from E_F),
+    A_nk(omega) [nk, nw, nomega] (Eq. spectral_funct))."""
+    lib = _load()
+    k, q = _pts(k), _pts(q)
+    b = _Bound(model)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    wq_a = None if wq is None else np.ascontiguousarray(wq, dtype=np.float64)
+    sig = np.zeros((len(k), model.nw, len(om)), dtype=np.complex128)
+    spec = np.zeros((len(k), model.nw, len(om)))
+    pr = _Params(T, EF, 1.0, omega_min)
+    rc = lib.oracle_selfenergy(b.ptr, len(k), _p(k), len(q), _p(q), None if wq_a is None else _p(wq_a),
+                               ctypes.byref(pr), float(delta), len(om), _p(om), _p(sig), _p(spec))
+    if rc != 0:
+        raise RuntimeError("oracle self-energy: eigensolve did not converge")
+    return sig, spec
 
 
 def eliashberg(omega, lam, grid, sigma_ph, wq=None):

@@ -34,6 +34,8 @@
  *     coupling strength lambda_qnu of Eq. (lambdaEQ) with N(E_F) from the k
  *     list, and the nesting function of Eq. (nestingfct); the isotropic
  *     Eliashberg function of Eq. (isotropiceliash) from w_qnu and lambda_qnu.
+ *   - The complex electron self-energy of Eq. (elselfenergy) on a frequency grid
+ *     and the spectral function of Eq. (spectral_funct).
  *
  * Every eigensolve is a plain cyclic complex Jacobi iteration on the Hermitian
  * part (X + X^dagger)/2, run to full double precision; eigenvalues ascend.
@@ -497,6 +499,83 @@ int oracle_phonon_self(const oracle_model *m, int nk, const double *k, const dou
     free(gReq); free(gk); free(tmp); free(gmn); free(Hkq); free(Ukq); free(D); free(ev); free(E);
   }
   free(epsk); free(Uk);
+  return bad ? -1 : 0;
+}
+
+/* Complex electron self-energy of Eq. (elselfenergy) on a frequency grid (omega measured from E_F),
+ * with the broadening i delta:
+ *   sig[k][n][i] = sum_q w_q sum_{m,nu} |g_mn,nu(k,q)|^2 [ (n_qnu + f_mk+q) / (w_i - x_m + w_qnu + i delta)
+ *                                                     + (n_qnu + 1 - f_mk+q) / (w_i - x_m - w_qnu + i delta) ],
+ *   x_m = e_mk+q - E_F; sig [nk][nw][nomega] complex (re, im interleaved).  With spec != NULL also the
+ * spectral function of Eq. (spectral_funct), with Sigma'' = -Im Sigma and the real part shifted by
+ * Sigma'(omega = 0) (Eq. realpartselfenergy):
+ *   spec[k][n][i] = (1/pi) |Sigma''| / ((w_i - (e_nk - E_F) - Sigma~'(w_i))^2 + Sigma''^2). */
+int oracle_selfenergy(const oracle_model *m, int nk, const double *k, int nq, const double *q, const double *wq,
+                      const oracle_params *pr, double delta, int nom, const double *omega, double *sig,
+                      double *spec) {
+  int nw = m->nw, nm = 3 * m->nat, nc = nm * nw * nw;
+  const int nw1 = nom + 1;  /* the grid and omega = 0 */
+  double *epsk = malloc(sizeof(double) * (long)nk * nw);
+  double *Uk = malloc(sizeof(cplx) * (long)nk * nw * nw);
+  int bad = oracle_bands(m, nk, k, epsk, Uk);
+  cplx *acc = calloc((size_t)nk * nw * nw1, sizeof(cplx));
+#pragma omp parallel for schedule(dynamic) reduction(+ : bad)
+  for (int ik = 0; ik < nk; ik++) {
+    cplx *gReq = malloc(sizeof(cplx) * (long)m->nRe * nc);
+    cplx *gk = malloc(sizeof(cplx) * nc), *tmp = malloc(sizeof(cplx) * nc), *gmn = malloc(sizeof(cplx) * nc);
+    cplx *Hkq = malloc(sizeof(cplx) * nw * nw), *Ukq = malloc(sizeof(cplx) * nw * nw);
+    cplx *D = malloc(sizeof(cplx) * nm * nm), *ev = malloc(sizeof(cplx) * nm * nm), *E = malloc(sizeof(cplx) * nm * nm);
+    double w2[64], w[64], ekq[64];
+    cplx *my = acc + (long)ik * nw * nw1;
+    for (int iq = 0; iq < nq; iq++) {
+      const double *qq = q + 3 * iq;
+      const double wqi = wq ? wq[iq] : 1.0 / nq;
+      oracle_dynmat(m, qq, D);
+      if (oracle_eigh(nm, D, w2, ev) < 0) bad++;
+      for (int j = 0; j < nm; j++) w[j] = (w2[j] >= 0 ? 1.0 : -1.0) * sqrt(fabs(w2[j]));
+      mode_factors(m, w, ev, pr->omega_min, E);
+      oracle_g_Re_q(m, qq, gReq);
+      double kq[3] = {k[3 * ik] + qq[0], k[3 * ik + 1] + qq[1], k[3 * ik + 2] + qq[2]};
+      oracle_hk(m, kq, Hkq);
+      if (oracle_eigh(nw, Hkq, ekq, Ukq) < 0) bad++;
+      g_k_from_Re_q(m, gReq, k + 3 * ik, gk);
+      bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E, gmn, tmp);
+      for (int nu = 0; nu < nm; nu++) {
+        if (w[nu] < pr->omega_min) continue;
+        const double nb = oracle_bose(w[nu], pr->T);
+        for (int mm = 0; mm < nw; mm++) {
+          const double f = oracle_fermi(ekq[mm], pr->EF, pr->T);
+          const double x = ekq[mm] - pr->EF;
+          for (int n = 0; n < nw; n++) {
+            cplx gv = gmn[(nu * nw + mm) * nw + n];
+            const double g2 = wqi * (creal(gv) * creal(gv) + cimag(gv) * cimag(gv));
+            for (int i = 0; i < nw1; i++) {
+              const double om = i < nom ? omega[i] : 0.0;
+              my[(long)n * nw1 + i] += g2 * ((nb + f) / (om - x + w[nu] + I * delta) +
+                                             (nb + 1.0 - f) / (om - x - w[nu] + I * delta));
+            }
+          }
+        }
+      }
+    }
+    free(gReq); free(gk); free(tmp); free(gmn); free(Hkq); free(Ukq); free(D); free(ev); free(E);
+  }
+  for (int ik = 0; ik < nk; ik++)
+    for (int n = 0; n < nw; n++) {
+      const cplx *a = acc + ((long)ik * nw + n) * nw1;
+      const double re0 = creal(a[nom]);
+      for (int i = 0; i < nom; i++) {
+        const long o = ((long)ik * nw + n) * nom + i;
+        sig[2 * o] = creal(a[i]);
+        sig[2 * o + 1] = cimag(a[i]);
+        if (spec) {
+          const double s2 = -cimag(a[i]);
+          const double den = omega[i] - (epsk[(long)ik * nw + n] - pr->EF) - (creal(a[i]) - re0);
+          spec[o] = fabs(s2) / (M_PI * (den * den + s2 * s2));
+        }
+      }
+    }
+  free(acc); free(epsk); free(Uk);
   return bad ? -1 : 0;
 }
 

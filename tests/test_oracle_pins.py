@@ -445,3 +445,45 @@ def test_eliashberg_function_pins(oracle_lib):
     a2f = oracle_lib.eliashberg(om, lam, grid, s, wq)
     integral = 2 * np.trapezoid(a2f / np.maximum(grid, 1e-12), grid)
     assert abs(integral - (wq[:, None] * lam).sum()) < 1e-5 * (wq[:, None] * lam).sum()
+
+
+# ------------------------------------------- complex self-energy (oracle)
+def test_selfenergy_closed_form_one_band(oracle_lib):
+    """Eq. (elselfenergy) on the one-band model: a sum of analytic terms (no Fourier sum, no eigensolve)."""
+    m = _tb()
+    rng = np.random.default_rng(90)
+    k = rng.random((3, 3))
+    q = W.uniform_grid(4) + 0.01
+    omega = np.linspace(-0.3, 0.3, 13)
+    T, EF, delta = 300.0, 0.05, 0.02
+    sig, _ = oracle_lib.selfenergy(m, k, q, omega, None, T, EF, delta)
+    for ik, kk in enumerate(k):
+        ref = np.zeros(len(omega), dtype=complex)
+        for qq in q:
+            x = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * (kk + qq)).sum() - EF
+            f = _fermi(x + EF, EF, T)
+            for a in range(3):
+                w = 2 * math.sqrt(0.01 / 1.3) * abs(math.sin(math.pi * qq[a]))
+                if w < 1e-5:
+                    continue
+                g2 = 0.05**2 * math.sin(2 * math.pi * qq[a]) ** 2 / (2 * 1.3 * w)
+                n = _bose(w, T)
+                ref += g2 * ((n + f) / (omega - x + w + 1j * delta) + (n + 1 - f) / (omega - x - w + 1j * delta))
+        ref /= len(q)
+        assert np.allclose(sig[ik, 0], ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
+
+
+def test_spectral_function_normalisation(oracle_lib):
+    """int A_nk(w) dw = 1: with Sigma analytic in the upper half plane (positive weights over
+    w - a + i delta) and a real constant shift, -Im G / pi is a normalised density.  Only the
+    squared Sigma'' in the denominator of Eq. (spectral_funct) has this property."""
+    rng = np.random.default_rng(91)
+    # a coupling weak enough that the spectral weight lies well inside the +-40 eV grid
+    m = W.make_model("fcc", 2, 1, [1.0], 20, 20, rng, g_amp=0.01)
+    k = rng.random((2, 3))
+    q = W.uniform_grid(3) + 0.05
+    omega = np.linspace(-40.0, 40.0, 160001)
+    sig, spec = oracle_lib.selfenergy(m, k, q, omega, None, 300.0, 0.0, 0.05)
+    norm = np.trapezoid(spec, omega, axis=-1)
+    assert np.all(np.abs(norm - 1.0) < 1e-5), norm
+    assert np.all(-sig.imag >= 0)
