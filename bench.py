@@ -196,6 +196,8 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "tf32x3", "bf16x3", "fp32", "fp64"])
     ap.add_argument("--other-steps", type=int, default=2, help="timed steps of the other tensor-core/FP32 forms")
     ap.add_argument("--backward-steps", type=int, default=3, help="timed adjoint calls (0: skip)")
+    ap.add_argument("--se-steps", type=int, default=1,
+                    help="timed complex self-energy + spectral function calls (100 k, 64 frequencies; 0: skip)")
     ap.add_argument("--phonon-steps", type=int, default=2,
                     help="timed phonon-side calls (Pi'', lambda, nesting over the same k x q; 0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU form (0: skip)")
@@ -341,6 +343,23 @@ def main():
         pms = e0.elapsed_time(e1) / args.phonon_steps
         phonon = {"value": pairs / (pms / 1e3), "unit": "pairs/s", "ms_per_step": pms, "precision": name,
                   "what": "Pi''_qnu (on shell), lambda_qnu, nesting zeta_q, N(E_F): per-q sums over the 1000 k"}
+    selfen = None
+    if args.se_steps > 0:
+        # Sigma_nk(omega) and A_nk(omega) (Eqs. elselfenergy, spectral_funct) on 64 frequencies, first 100 k
+        om = torch.linspace(-0.3, 0.3, 64, dtype=torch.float64, device=dev)
+        sk = dict(T=wl.T, EF=wl.EF, delta=wl.sigma, precision=prec)
+        m.selfenergy(k[:100], q, om, wq, **sk)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.se_steps):
+            m.selfenergy(k[:100], q, om, wq, **sk)
+        e1.record()
+        torch.cuda.synchronize()
+        sms = e0.elapsed_time(e1) / args.se_steps
+        sp = 100 * len(wl.q)
+        selfen = {"value": sp / (sms / 1e3), "unit": "pairs/s", "ms_per_step": sms, "precision": name,
+                  "what": "Sigma_nk(omega), A_nk(omega) on 64 frequencies: 100 k x the 40^3 q grid"}
     others = {}
     if args.other_steps > 0:
         for oname, op in (("bf16x3", epw.BF16X3), ("tf32x3", epw.TF32X3), ("fp32", epw.FP32)):
@@ -392,7 +411,7 @@ def main():
                                    f"T={T_SWEEP[0]:.0f} K (rank r: T_sweep[r])", "pairs_per_step_per_gpu": pairs,
                        "precision": name, "l2": "flushed between timed steps (256 MB write)"},
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof,
-            "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu_form": fp64, "other_forms": others, "backward": backward, "phonon_side": phonon,
+            "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu_form": fp64, "other_forms": others, "backward": backward, "phonon_side": phonon, "selfenergy": selfen,
         }
         print(json.dumps(line))
     m.close()

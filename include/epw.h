@@ -196,6 +196,23 @@ epw_status epw_phonon_selfenergy(const epw_model *model, int nk, const double *k
                                  const double *q, const epw_params *params, double *pi_imag, double *lambda,
                                  double *nesting, double *dos_ef, void *stream);
 
+/* Complex electron self-energy of Eq. (elselfenergy) on a frequency grid, with
+ * the broadening i delta (delta > 0, eV) and omega measured from E_F:
+ *   sigma[k][n][i] = sum_q w_q sum_{m,nu} |g_mn,nu(k,q)|^2
+ *        [ (n_qnu + f_mk+q) / (omega_i - (e_mk+q - E_F) + w_qnu + i delta)
+ *        + (n_qnu + 1 - f_mk+q) / (omega_i - (e_mk+q - E_F) - w_qnu + i delta) ]
+ * (complex, re/im interleaved, [nk][nw][nomega]), and, when spectral != NULL, the
+ * spectral function of Eq. (spectral_funct)
+ *   spectral[k][n][i] = (1/pi) |Sigma''| / ((omega_i - (e_nk - E_F) - Sigma~'(omega_i))^2 + Sigma''^2),
+ * Sigma'' = -Im Sigma, Sigma~' = Re Sigma(omega) - Re Sigma(0) (Eq. realpartselfenergy).
+ * params: T_K, EF_eV, omega_min_eV and precision as for epw_linewidth (sigma_eV is not
+ * used: the width here is delta).  Host or device pointers.  FP64/FP32 on the CUDA cores,
+ * TF32X3/BF16X3 with the contraction staged on the tensor cores (Re == Rp).  Shapes up to
+ * nw = 8, 3nat = 9.  Sums over q in a fixed order. */
+epw_status epw_selfenergy(const epw_model *model, int nk, const double *k, int nq, const double *q,
+                          const double *wq, const epw_params *params, double delta, int nomega,
+                          const double *omega, double *sigma, double *spectral, void *stream);
+
 /* Isotropic Eliashberg function of Eq. (isotropiceliash) on an omega grid:
  *   a2f[i] = 1/2 sum_q w_q sum_nu omega[q][nu] lambda[q][nu] delta_ph(grid[i] - omega[q][nu])
  * with delta_ph the Gaussian exp(-(x/sigma_ph)^2)/(sigma_ph sqrt(pi)); omega and lambda [nq][nmodes]

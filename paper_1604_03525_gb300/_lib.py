@@ -32,6 +32,7 @@ SIGNATURES = {
     "epw_linewidth_noalloc": (I, [P, I, P, I, P, P, P, P, P]),
     "epw_phonon_selfenergy": (I, [P, I, P, P, I, P, P, P, P, P, P, P]),
     "epw_eliashberg": (I, [I, I, P, P, P, I, P, D, P, P]),
+    "epw_selfenergy": (I, [P, I, P, I, P, P, P, D, I, P, P, P, P]),
     "epw_batch_create": (I, [I, P, P]),
     "epw_batch_run": (I, [P, P]),
     "epw_batch_info": (I, [P, P, P, P]),

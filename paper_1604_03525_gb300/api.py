@@ -176,6 +176,28 @@ class Model:
                                          *[o.ptr for o in outs], _stream_of(ka, qa, wa, *outs)))
         return pi, lam, zeta, (float(dos[0]) if not _is_torch(dos) else dos)
 
+    def selfenergy(self, k, q, omega, wq=None, *, T: float, EF: float, delta: float, omega_min: float = 1e-5,
+                   precision: int = FP64, spectral: bool = True):
+        """(Sigma_nk(omega) [nk, nw, nomega] complex, A_nk(omega) [nk, nw, nomega] or None):
+        Eqs. elselfenergy and spectral_funct on the frequency grid `omega` (eV from E_F)."""
+        lib = _lib.load()
+        ka, qa, wa, oa = _Arg(k, np.float64), _Arg(q, np.float64), _Arg(wq, np.float64), _Arg(omega, np.float64)
+        nk = int(np.prod(ka.keep.shape)) // 3
+        nq = int(np.prod(qa.keep.shape)) // 3
+        nom = int(np.prod(oa.keep.shape))
+        if ka.device:
+            import torch
+            sig = torch.zeros((nk, self.nw, nom), dtype=torch.complex128, device=ka.keep.device)
+            spec = torch.zeros((nk, self.nw, nom), dtype=torch.float64, device=ka.keep.device) if spectral else None
+        else:
+            sig = np.zeros((nk, self.nw, nom), dtype=np.complex128)
+            spec = np.zeros((nk, self.nw, nom)) if spectral else None
+        sa, pa = _Arg(sig, np.complex128), _Arg(spec, np.float64)
+        pr = _lib.Params(float(T), float(EF), 1.0, float(omega_min), int(precision), 0)
+        _check(lib.epw_selfenergy(self._h, nk, ka.ptr, nq, qa.ptr, wa.ptr, ctypes.byref(pr), float(delta), nom,
+                                  oa.ptr, sa.ptr, pa.ptr, _stream_of(ka, qa, wa, oa, sa, pa)))
+        return sig, spec
+
     def linewidth_noalloc(self, k, q, wq=None, *, T: float, EF: float, sigma: float, omega_min: float = 1e-5,
                           precision: int = FP64, out=None):
         """epw_linewidth_noalloc: like linewidth, but the library allocates no device memory.

@@ -1012,6 +1012,124 @@ extern "C" epw_status epw_phonon_selfenergy(const epw_model *mc, int nk, const d
   return EPW_OK;
 }
 
+// ------------------------------------------ complex self-energy, spectral function
+extern "C" epw_status epw_selfenergy(const epw_model *mc, int nk, const double *k, int nq, const double *q,
+                                     const double *wq, const epw_params *par, double delta, int nomega,
+                                     const double *omega, double *sigma, double *spectral, void *stream) {
+  g_err[0] = 0;
+  epw_model *m = const_cast<epw_model *>(mc);
+  CKS(check_common(m, nk, k, nq, q));
+  CKS(check_params(par));
+  if (!(delta > 0.0) || !std::isfinite(delta)) return fail(EPW_ERR_INVALID_ARG, "delta must be > 0");
+  if (nomega < 0 || (nomega > 0 && (!omega || (nk > 0 && !sigma))))
+    return fail(EPW_ERR_INVALID_ARG, "bad frequency grid or null output");
+  if (m->nw > 8 || m->nm > 9)
+    return fail(EPW_ERR_UNSUPPORTED, "the self-energy has no kernel for nw=%d, 3nat=%d (at most 8 and 9)", m->nw,
+                m->nm);
+  const bool tcp = par->precision == EPW_BF16X3 || par->precision == EPW_TF32X3;
+  if (tcp && !m->same_ep) return fail(EPW_ERR_UNSUPPORTED, "the tensor-core forms need Re == Rp");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nw = m->nw;
+  const size_t nout = (size_t)nk * nw * nomega;
+  if (nk == 0 || nomega == 0) return EPW_OK;
+  const int wprec = tcp ? EPW_FP32 : par->precision;
+  const bool sk = !is_device_ptr(k), sq = nq > 0 && !is_device_ptr(q), swq = wq && nq > 0 && !is_device_ptr(wq);
+  const bool som = !is_device_ptr(omega), ssig = !is_device_ptr(sigma), ssp = spectral && !is_device_ptr(spectral);
+  const int nqw = (std::max(nq, 1) + 31) / 32;
+  const size_t per_k = (size_t)nqw * nw * (nomega + 1) * sizeof(double2);
+  int kc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nk, ((size_t)1 << 30) / per_k));
+  struct B {
+    Prep p;
+    TcStaged sg;
+    double *omd, *sigd, *specd;
+    double2 *part;
+  } b;
+  auto plan = [&](Arena &A) -> epw_status {
+    plan_prep(A, m, nk, std::max(nq, 1), wprec, sk, sq, swq, true, b.p);
+    b.sg = TcStaged{};
+    if (tcp) {
+      CKS(tc_staged_plan(A, m, nk, std::max(nq, 1), par->precision == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32,
+                         STAGED_CT_BYTES, b.sg, true));
+      if (!b.sg.ok) return fail(EPW_ERR_UNSUPPORTED, "no staged tensor-core form for this model");
+      kc = std::min(kc, b.sg.kc);
+    }
+    b.omd = som ? A.take<double>((size_t)nomega) : const_cast<double *>(omega);
+    b.sigd = ssig ? (double *)A.take<double2>(nout) : sigma;
+    b.specd = ssp ? A.take<double>(nout) : spectral;
+    b.part = A.take<double2>((size_t)kc * nqw * nw * (nomega + 1));
+    return EPW_OK;
+  };
+  Arena A{nullptr, 0, 0};
+  CKS(plan(A));
+  CKS(ensure_ws(m, A.off));
+  A = Arena{(char *)m->ws, m->ws_bytes, 0};
+  CKS(plan(A));
+  Prep &p = b.p;
+  const double *kd = k, *qd = q, *wqd = wq;
+  if (sk) {
+    CK(cudaMemcpyAsync(p.kd, k, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
+    kd = p.kd;
+  }
+  if (sq) {
+    CK(cudaMemcpyAsync(p.qd, q, sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, st));
+    qd = p.qd;
+  }
+  if (swq) {
+    CK(cudaMemcpyAsync(p.wqd, wq, sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+    wqd = p.wqd;
+  }
+  if (som) CK(cudaMemcpyAsync(b.omd, omega, sizeof(double) * nomega, cudaMemcpyHostToDevice, st));
+  if (nq == 0) {
+    // no q: Sigma = 0, and the spectral function's numerator |Sigma''| is 0 on the grid
+    CK(cudaMemsetAsync(b.sigd, 0, nout * sizeof(double2), st));
+    if (b.specd) CK(cudaMemsetAsync(b.specd, 0, nout * sizeof(double), st));
+  } else {
+    CKS(run_prep(m, nk, kd, nq, qd, wprec, par->omega_min_eV, true, p, nullptr, st));
+    if (tcp) CKS(tc_staged_phases(m, nq, qd, b.sg, st));
+    PairArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nq = nq;
+    a.nw = nw;
+    a.nm = m->nm;
+    a.nRe = m->nRe;
+    a.nRp = m->nRp;
+    a.PqTe = p.PqTe;
+    a.PqTp = p.PqTp;
+    a.BH = p.BH;
+    a.Bg = p.Bg;
+    a.ET = p.ET;
+    a.omegaT = p.omegaT;
+    a.eps_k = p.epsk;
+    a.wq = wqd;
+    a.T = par->T_K;
+    a.EF = par->EF_eV;
+    a.sigma = par->sigma_eV;
+    a.omega_min = par->omega_min_eV;
+    a.dstatus = m->dstatus;
+    for (int k0 = 0; k0 < nk; k0 += kc) {
+      const int n = std::min(kc, nk - k0);
+      a.k0 = k0;
+      a.nk = n;
+      if (tcp) {
+        epw_status s = tc_staged_contract(m, k0, n, nq, (const cx<float> *)p.Bg, (const cx<float> *)p.BH, b.sg, st);
+        if (s != EPW_OK) return fail(s, "staged tensor-core contraction failed");
+        a.Cq = b.sg.Ct;
+        a.ldc = b.sg.pair_ld();
+        a.cpk = b.sg.cpk;
+      }
+      epw_status s = wprec == EPW_FP64 ? launch_pair_se<double>(a, nomega, b.omd, delta, b.part, st)
+                                       : launch_pair_se<float>(a, nomega, b.omd, delta, b.part, st);
+      if (s != EPW_OK) return fail(s, "no self-energy kernel for nw=%d, 3nat=%d", nw, m->nm);
+      launch_se_finalize(n, k0, nw, nqw, nomega, b.part, b.omd, p.epsk, par->EF_eV, (double2 *)b.sigd, b.specd, st);
+    }
+  }
+  CK(cudaGetLastError());
+  if (ssig) CK(cudaMemcpyAsync(sigma, b.sigd, nout * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  if (ssp) CK(cudaMemcpyAsync(spectral, b.specd, nout * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (sk || sq || swq || som || ssig || ssp) return read_status(m, st);
+  return EPW_OK;
+}
+
 // ---------------------------------------------------- Eliashberg function
 extern "C" epw_status epw_eliashberg(int nq, int nmodes, const double *omega, const double *lambda,
                                      const double *wq, int ngrid, const double *grid, double sigma_ph, double *a2f,

@@ -590,6 +590,111 @@ __global__ void k_dos_terms(int nk, int nw, const double *__restrict__ epsk, con
   terms[k] = (wk ? wk[k] : 1.0 / nk) * s;
 }
 
+// Complex self-energy of Eq. (elselfenergy) on a frequency grid (omega from E_F, i delta
+// broadening): one thread per (k, q) pair, a block holds 128 consecutive q of one k.  For
+// each band n and grid point i (the grid, then omega = 0 for the shift of Eq. (realpartselfenergy)),
+// the thread sums over (m, nu), each warp sums its 32 q (shuffles), and lane 0 writes
+//   out[(kl * nqw + q / 32) * nw + n][i]   (complex, re/im),  nqw = ceil(nq / 32).
+template <typename R, int MW, int MM, bool FROMC>
+__global__ void __launch_bounds__(128) k_pair_se(PairArgs a, int nom, const double *__restrict__ omega,
+                                                 double delta, double2 *out) {
+  constexpr int UW = MW <= 4 ? MW : 1;
+  constexpr int UM = MM <= 4 ? MM : 1;
+  const int q = blockIdx.x * 128 + threadIdx.x;
+  const int kl = blockIdx.y, k = a.k0 + kl;
+  const bool valid = q < a.nq;
+  const int qq = valid ? q : 0;
+  const int nw = a.nw, nm = a.nm, nq = a.nq;
+  R ekq[MW];
+  cx<R> U[MW][MW];
+  cx<R> G[MM][MW][MW];
+  const bool conv = pair_vertex<R, MW, MM, FROMC>(a, kl, k, qq, ekq, U, G);
+  if (!conv && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
+  const R wqi = valid ? (R)(a.wq ? a.wq[q] : 1.0 / nq) : R(0);
+  R w[MM], cp[MM][MW], cm[MM][MW];
+#pragma unroll UM
+  for (int v = 0; v < MM; v++) {
+    w[v] = v < nm ? (R)a.omegaT[(size_t)v * nq + qq] : R(0);
+    const bool keep = v < nm && (w[v] >= (R)a.omega_min) && (w[v] > R(0));
+    const R nb = keep ? occ_bose<R>(w[v], a.T) : R(0);
+#pragma unroll UW
+    for (int m = 0; m < MW; m++) {
+      const R f = m < nw ? occ_fermi<R>(ekq[m], a.EF, a.T) : R(0);
+      cp[v][m] = keep ? wqi * (nb + f) : R(0);
+      cm[v][m] = keep ? wqi * (nb + R(1) - f) : R(0);
+    }
+  }
+  const R dl = (R)delta, d2 = dl * dl;
+  const int nqw = (nq + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i <= nom; i++) {
+    const R om = i < nom ? (R)omega[i] : R(0);
+    for (int n = 0; n < nw; n++) {
+      R sr = R(0), si = R(0);
+#pragma unroll UM
+      for (int v = 0; v < MM; v++) {
+        if (v >= nm) continue;
+#pragma unroll UW
+        for (int m = 0; m < MW; m++) {
+          if (m >= nw) continue;
+          const R g2 = cabs2(G[v][m][n]);
+          const R x = om - (ekq[m] - (R)a.EF);
+          const R xp = x + w[v], xm = x - w[v];
+          const R rp = R(1) / (xp * xp + d2), rm = R(1) / (xm * xm + d2);
+          // 1/(x + i delta) = (x - i delta) / (x^2 + delta^2)
+          const R tp = g2 * cp[v][m] * rp, tm = g2 * cm[v][m] * rm;
+          sr += tp * xp + tm * xm;
+          si -= (tp + tm) * dl;
+        }
+      }
+      double dr = (double)sr, di = (double)si;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dr += __shfl_down_sync(0xffffffffu, dr, o);
+        di += __shfl_down_sync(0xffffffffu, di, o);
+      }
+      if (lane == 0 && q - lane < nq)
+        out[(((size_t)kl * nqw + (q >> 5)) * nw + n) * (nom + 1) + i] = make_double2(dr, di);
+    }
+  }
+}
+
+// Sum over the per-warp partials (fixed order, compensated) into Sigma_nk(omega_i) and, with
+// spec, the spectral function of Eq. (spectral_funct) (Sigma'' = -Im Sigma, real part shifted
+// by its value at omega = 0): one thread per (k, n).
+__global__ void k_se_finalize(int nkc, int k0, int nw, int nqw, int nom, const double2 *__restrict__ part,
+                              const double *__restrict__ omega, const double *__restrict__ epsk, double EF,
+                              double2 *sig, double *spec) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nkc * nw) return;
+  const int kl = t / nw, n = t % nw, k = k0 + kl;
+  auto total = [&](int i) {
+    double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+    for (int j = 0; j < nqw; j++) {
+      const double2 x = part[(((size_t)kl * nqw + j) * nw + n) * (nom + 1) + i];
+      double u = sr + x.x;
+      cr += fabs(sr) >= fabs(x.x) ? (sr - u) + x.x : (x.x - u) + sr;
+      sr = u;
+      u = si + x.y;
+      ci += fabs(si) >= fabs(x.y) ? (si - u) + x.y : (x.y - u) + si;
+      si = u;
+    }
+    return make_double2(sr + cr, si + ci);
+  };
+  const double re0 = total(nom).x;
+  const double e = epsk[(size_t)k * nw + n] - EF;
+  for (int i = 0; i < nom; i++) {
+    const double2 s = total(i);
+    const size_t o = ((size_t)k * nw + n) * nom + i;
+    sig[o] = s;
+    if (spec) {
+      const double s2 = -s.y;
+      const double den = omega[i] - e - (s.x - re0);
+      spec[o] = fabs(s2) / (EPW_PI * (den * den + s2 * s2));
+    }
+  }
+}
+
 // alpha^2 F on a grid (Eq. (isotropiceliash)): one block per grid point, each
 // thread a fixed stride of the (q, nu) terms (compensated), then a fixed tree.
 __global__ void k_eliashberg(int nq, int nm, const double *__restrict__ omega, const double *__restrict__ lam,
@@ -892,6 +997,43 @@ void launch_dos_terms(int nk, int nw, const double *epsk, const double *wk, doub
                       cudaStream_t st) {
   if (nk <= 0) return;
   k_dos_terms<<<(nk + 127) / 128, 128, 0, st>>>(nk, nw, epsk, wk, EF, sigma, terms);
+  epw_count_launch();
+}
+
+template <typename R, bool FROMC>
+static epw_status se_dispatch(const PairArgs &a, dim3 grid, int nom, const double *omega, double delta, double2 *out,
+                              cudaStream_t st) {
+  if (a.nw <= 1 && a.nm <= 3)
+    k_pair_se<R, 1, 3, FROMC><<<grid, 128, 0, st>>>(a, nom, omega, delta, out);
+  else if (a.nw <= 4 && a.nm <= 3)
+    k_pair_se<R, 4, 3, FROMC><<<grid, 128, 0, st>>>(a, nom, omega, delta, out);
+  else if (a.nw <= 8 && a.nm <= 9)
+    k_pair_se<R, 8, 9, FROMC><<<grid, 128, 0, st>>>(a, nom, omega, delta, out);
+  else
+    return EPW_ERR_UNSUPPORTED;
+  epw_count_launch();
+  return EPW_OK;
+}
+
+template <typename R>
+epw_status launch_pair_se(const PairArgs &a, int nom, const double *omega, double delta, double2 *out,
+                          cudaStream_t st) {
+  if (a.nk <= 0 || a.nq <= 0) return EPW_OK;
+  dim3 grid((a.nq + 127) / 128, a.nk);
+  if (a.Cq) {
+    if constexpr (sizeof(R) == sizeof(float)) return se_dispatch<float, true>(a, grid, nom, omega, delta, out, st);
+    return EPW_ERR_UNSUPPORTED;
+  }
+  return se_dispatch<R, false>(a, grid, nom, omega, delta, out, st);
+}
+template epw_status launch_pair_se<double>(const PairArgs &, int, const double *, double, double2 *, cudaStream_t);
+template epw_status launch_pair_se<float>(const PairArgs &, int, const double *, double, double2 *, cudaStream_t);
+
+void launch_se_finalize(int nkc, int k0, int nw, int nqw, int nom, const double2 *part, const double *omega,
+                        const double *epsk, double EF, double2 *sig, double *spec, cudaStream_t st) {
+  const int n = nkc * nw;
+  if (n <= 0) return;
+  k_se_finalize<<<(n + 127) / 128, 128, 0, st>>>(nkc, k0, nw, nqw, nom, part, omega, epsk, EF, sig, spec);
   epw_count_launch();
 }
 

@@ -393,6 +393,13 @@ void launch_dos_terms(int nk, int nw, const double *epsk, const double *wk, doub
                       cudaStream_t st);
 void launch_eliashberg(int nq, int nm, const double *omega, const double *lam, const double *wq, int ngrid,
                        const double *grid, double sigma_ph, double *a2f, cudaStream_t st);
+// complex self-energy on a frequency grid (nw <= 8, 3nat <= 9): per-warp partials
+// out[(kl * ceil(nq/32) + warp) * nw + n][nom + 1] (the last point is omega = 0), then the sum
+template <typename R>
+epw_status launch_pair_se(const PairArgs &a, int nom, const double *omega, double delta, double2 *out,
+                          cudaStream_t st);
+void launch_se_finalize(int nkc, int k0, int nw, int nqw, int nom, const double2 *part, const double *omega,
+                        const double *epsk, double EF, double2 *sig, double *spec, cudaStream_t st);
 // warp-per-pair kernel for nw, 3nat up to 18 (modes 0 and 1; a.Cq set: staged
 // contraction in the q-major layout Cq[q*ldc + kl*cpk + 2c + s], FP32 only)
 template <typename R>
