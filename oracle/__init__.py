@@ -56,6 +56,8 @@ class _Model(ctypes.Structure):
         ("nRe", ctypes.c_int), ("Re", ctypes.c_void_p), ("wRe", ctypes.c_void_p), ("H", ctypes.c_void_p),
         ("nRph", ctypes.c_int), ("Rph", ctypes.c_void_p), ("wRph", ctypes.c_void_p), ("Phi", ctypes.c_void_p),
         ("nRp", ctypes.c_int), ("Rp", ctypes.c_void_p), ("wRp", ctypes.c_void_p), ("g", ctypes.c_void_p),
+        ("polar", ctypes.c_int), ("pA", ctypes.c_void_p), ("peps", ctypes.c_void_p), ("pZ", ctypes.c_void_p),
+        ("palpha", ctypes.c_double), ("ppref", ctypes.c_double), ("pgmax", ctypes.c_int),
     ]
 
 
@@ -119,10 +121,17 @@ class _Bound:
             c(m.Rp, np.int32), c(m.wRp, np.float64), c(m.g, np.complex128),
         ]
         k = self.keep
+        pol = getattr(m, "polar", None)
+        if pol is not None:
+            self.keep += [c(pol.A, np.float64), c(pol.eps_inf, np.float64), c(pol.Zstar, np.float64)]
+            pargs = (1, _p(k[10]).value, _p(k[11]).value, _p(k[12]).value, float(pol.alpha), float(pol.prefactor),
+                     int(pol.gmax))
+        else:
+            pargs = (0, None, None, None, 0.0, 0.0, 0)
         self.s = _Model(m.nw, m.nat, _p(k[0]).value,
                         len(m.Re), _p(k[1]).value, _p(k[2]).value, _p(k[3]).value,
                         len(m.Rph), _p(k[4]).value, _p(k[5]).value, _p(k[6]).value,
-                        len(m.Rp), _p(k[7]).value, _p(k[8]).value, _p(k[9]).value)
+                        len(m.Rp), _p(k[7]).value, _p(k[8]).value, _p(k[9]).value, *pargs)
 
     @property
     def ptr(self):

@@ -61,6 +61,12 @@ typedef struct {
   int nRe; const int *Re; const double *wRe; const double *H;  /* H [nRe][nw][nw] complex */
   int nRph; const int *Rph; const double *wRph; const double *Phi; /* [nRph][3nat][3nat] */
   int nRp; const int *Rp; const double *wRp; const double *g;  /* [nRe][nRp][3nat][nw][nw] */
+  /* long-range (polar) part, used when polar != 0: lattice vectors A (rows), eps_inf [3][3],
+     Born charges Z* [nat][3][3] (Z*_{kappa, b alpha}), damping alpha, prefactor, |n_i| <= gmax */
+  int polar;
+  const double *pA, *peps, *pZ;
+  double palpha, ppref;
+  int pgmax;
 } oracle_model;
 
 typedef struct {
@@ -290,10 +296,67 @@ static void g_k_from_Re_q(const oracle_model *m, const cplx *gReq, const double 
   }
 }
 
-/* Mode-basis Bloch vertex: gmn[nu][m][n] = sum_{ka} [Ukq^dag g_ka Uk]_mn E[ka][nu],
- * E[ka][nu] = e_{ka,nu} / sqrt(2 M_k w_nu), or 0 for modes below omega_min. */
+/* Long-range part of the vertex (Sec. "Electron-phonon coupling in polar materials", Eq. (long-range),
+ * with the overlap in its small-(q+G) form [U_k U_k+q^dagger]_nm of that section):
+ *   g^L_mn,nu(k,q) = i C_nu(q) [U_k+q^dagger U_k]_mn   (our columns-are-eigenvectors convention),
+ *   C_nu(q) = pref sum_{kappa, a} E[kappa a][nu] sum_{G, q+G != 0} damp(q+G) ((q+G) . Z*_kappa)_a / ((q+G) . eps . (q+G)),
+ * with E = e / sqrt(2 M w) (the (hbar / 2 M w)^{1/2} e of the equation), (x . Z*_kappa)_a = sum_b x_b Z*_{kappa,b a},
+ * damp(x) = exp(-x . eps . x / (4 alpha)) and G = sum_i n_i b_i (|n_i| <= gmax, b_i . a_j = 2 pi delta_ij),
+ * q + G Cartesian.  The printed equation has neither the prefactor nor a convergence factor; both are
+ * inputs here.  C is zero when the model has no polar part. */
+static void polar_factors(const oracle_model *m, const double q[3], const cplx *E, cplx *C) {
+  const int nm = 3 * m->nat;
+  for (int nu = 0; nu < nm; nu++) C[nu] = 0.0;
+  if (!m->polar) return;
+  const double *A = m->pA;
+  /* b = 2 pi (A^{-1})^T, by cofactors */
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  double inv[9];
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  double b[3][3]; /* b[i][c] = 2 pi inv[c][i] */
+  for (int i = 0; i < 3; i++)
+    for (int c = 0; c < 3; c++) b[i][c] = TWO_PI * inv[c * 3 + i];
+  double *F = calloc((size_t)nm, sizeof(double));
+  const int G = m->pgmax;
+  for (int n1 = -G; n1 <= G; n1++)
+    for (int n2 = -G; n2 <= G; n2++)
+      for (int n3 = -G; n3 <= G; n3++) {
+        double x[3];
+        for (int c = 0; c < 3; c++)
+          x[c] = (q[0] + n1) * b[0][c] + (q[1] + n2) * b[1][c] + (q[2] + n3) * b[2][c];
+        double xex = 0.0;
+        for (int c = 0; c < 3; c++)
+          for (int d = 0; d < 3; d++) xex += x[c] * m->peps[c * 3 + d] * x[d];
+        if (x[0] * x[0] + x[1] * x[1] + x[2] * x[2] == 0.0) continue; /* G = -q */
+        const double w = exp(-xex / (4.0 * m->palpha)) / xex;
+        for (int kap = 0; kap < m->nat; kap++)
+          for (int a = 0; a < 3; a++) {
+            double xz = 0.0;
+            for (int c = 0; c < 3; c++) xz += x[c] * m->pZ[(kap * 3 + c) * 3 + a];
+            F[kap * 3 + a] += w * xz;
+          }
+      }
+  for (int nu = 0; nu < nm; nu++) {
+    cplx s = 0.0;
+    for (int ka = 0; ka < nm; ka++) s += E[ka * nm + nu] * F[ka];
+    C[nu] = m->ppref * s;
+  }
+  free(F);
+}
+
+/* Mode-basis Bloch vertex: gmn[nu][m][n] = sum_{ka} [Ukq^dag g_ka Uk]_mn E[ka][nu] (+ i C_nu [Ukq^dag Uk]_mn
+ * when C != NULL), E[ka][nu] = e_{ka,nu} / sqrt(2 M_k w_nu), or 0 for modes below omega_min. */
 static void bloch_mode_vertex(int nw, int nm, const cplx *gk, const cplx *Uk, const cplx *Ukq,
-                              const cplx *E, cplx *gmn, cplx *tmp) {
+                              const cplx *E, cplx *gmn, cplx *tmp, const cplx *C) {
   /* tmp[ka][m][n] = (Ukq^dag g_ka Uk)_mn */
   for (int ka = 0; ka < nm; ka++)
     for (int a = 0; a < nw; a++)
@@ -310,6 +373,13 @@ static void bloch_mode_vertex(int nw, int nm, const cplx *gk, const cplx *Uk, co
       for (int ka = 0; ka < nm; ka++) s += tmp[ka * nw * nw + i] * E[ka * nm + nu];
       gmn[nu * nw * nw + i] = s;
     }
+  if (C)
+    for (int a = 0; a < nw; a++)
+      for (int b = 0; b < nw; b++) {
+        cplx o = 0.0; /* [Ukq^dag Uk]_ab */
+        for (int i = 0; i < nw; i++) o += conj(Ukq[i * nw + a]) * Uk[i * nw + b];
+        for (int nu = 0; nu < nm; nu++) gmn[(nu * nw + a) * nw + b] += I * C[nu] * o;
+      }
 }
 
 static void mode_factors(const oracle_model *m, const double *w, const cplx *ev, double omega_min, cplx *E) {
@@ -337,6 +407,8 @@ int oracle_interp(const oracle_model *m, int nk, const double *k, int nq, const 
     double ekq[64];
     oracle_g_Re_q(m, q + 3 * iq, gReq);
     mode_factors(m, omega + (long)iq * nm, (cplx *)ev + (long)iq * nm * nm, omega_min, E);
+    cplx Cp[64];
+    polar_factors(m, q + 3 * iq, E, Cp);
     for (int ik = 0; ik < nk; ik++) {
       double kq[3] = {k[3 * ik] + q[3 * iq], k[3 * ik + 1] + q[3 * iq + 1], k[3 * ik + 2] + q[3 * iq + 2]};
       oracle_hk(m, kq, Hkq);
@@ -344,7 +416,7 @@ int oracle_interp(const oracle_model *m, int nk, const double *k, int nq, const 
       memcpy(eps_kq + ((long)ik * nq + iq) * nw, ekq, sizeof(double) * nw);
       g_k_from_Re_q(m, gReq, k + 3 * ik, gk);
       bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E,
-                        (cplx *)g + ((long)ik * nq + iq) * nc, tmp);
+                        (cplx *)g + ((long)ik * nq + iq) * nc, tmp, m->polar ? Cp : NULL);
     }
     free(gReq); free(gk); free(tmp); free(Hkq); free(Ukq); free(E);
   }
@@ -386,13 +458,15 @@ int oracle_linewidth(const oracle_model *m, int nk, const double *k, int nq, con
       if (oracle_eigh(nm, D, w2, ev) < 0) bad++;
       for (int j = 0; j < nm; j++) w[j] = (w2[j] >= 0 ? 1.0 : -1.0) * sqrt(fabs(w2[j]));
       mode_factors(m, w, ev, pr->omega_min, E);
+      cplx Cp[64];
+      polar_factors(m, qq, E, Cp);
       oracle_g_Re_q(m, qq, gReq);
       for (int ik = 0; ik < nk; ik++) {
         double kq[3] = {k[3 * ik] + qq[0], k[3 * ik + 1] + qq[1], k[3 * ik + 2] + qq[2]};
         oracle_hk(m, kq, Hkq);
         if (oracle_eigh(nw, Hkq, ekq, Ukq) < 0) bad++;
         g_k_from_Re_q(m, gReq, k + 3 * ik, gk);
-        bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E, gmn, tmp);
+        bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E, gmn, tmp, m->polar ? Cp : NULL);
         for (int n = 0; n < nw; n++) {
           double en = epsk[(long)ik * nw + n];
           for (int nu = 0; nu < nm; nu++) {
@@ -462,6 +536,8 @@ int oracle_phonon_self(const oracle_model *m, int nk, const double *k, const dou
       if (oracle_eigh(nm, D, w2, ev) < 0) bad++;
       for (int j = 0; j < nm; j++) w[j] = (w2[j] >= 0 ? 1.0 : -1.0) * sqrt(fabs(w2[j]));
       mode_factors(m, w, ev, pr->omega_min, E);
+      cplx Cp[64];
+      polar_factors(m, qq, E, Cp);
       oracle_g_Re_q(m, qq, gReq);
       for (int nu = 0; nu < nm; nu++) sp[nu] = sl[nu] = (nsum){0.0, 0.0};
       sz = (nsum){0.0, 0.0};
@@ -471,7 +547,7 @@ int oracle_phonon_self(const oracle_model *m, int nk, const double *k, const dou
         oracle_hk(m, kq, Hkq);
         if (oracle_eigh(nw, Hkq, ekq, Ukq) < 0) bad++;
         g_k_from_Re_q(m, gReq, k + 3 * ik, gk);
-        bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E, gmn, tmp);
+        bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E, gmn, tmp, m->polar ? Cp : NULL);
         for (int n = 0; n < nw; n++) {
           const double en = epsk[(long)ik * nw + n];
           const double dn = oracle_gauss(en - pr->EF, pr->sigma);
@@ -534,12 +610,14 @@ int oracle_selfenergy(const oracle_model *m, int nk, const double *k, int nq, co
       if (oracle_eigh(nm, D, w2, ev) < 0) bad++;
       for (int j = 0; j < nm; j++) w[j] = (w2[j] >= 0 ? 1.0 : -1.0) * sqrt(fabs(w2[j]));
       mode_factors(m, w, ev, pr->omega_min, E);
+      cplx Cp[64];
+      polar_factors(m, qq, E, Cp);
       oracle_g_Re_q(m, qq, gReq);
       double kq[3] = {k[3 * ik] + qq[0], k[3 * ik + 1] + qq[1], k[3 * ik + 2] + qq[2]};
       oracle_hk(m, kq, Hkq);
       if (oracle_eigh(nw, Hkq, ekq, Ukq) < 0) bad++;
       g_k_from_Re_q(m, gReq, k + 3 * ik, gk);
-      bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E, gmn, tmp);
+      bloch_mode_vertex(nw, nm, gk, (cplx *)Uk + (long)ik * nw * nw, Ukq, E, gmn, tmp, m->polar ? Cp : NULL);
       for (int nu = 0; nu < nm; nu++) {
         if (w[nu] < pr->omega_min) continue;
         const double nb = oracle_bose(w[nu], pr->T);
@@ -637,6 +715,8 @@ int oracle_linewidth_grad(const oracle_model *m, int nk, const double *k, int nq
       if (oracle_eigh(nm, D, w2, ev) < 0) bad++;
       for (int j = 0; j < nm; j++) w[j] = (w2[j] >= 0 ? 1.0 : -1.0) * sqrt(fabs(w2[j]));
       mode_factors(m, w, ev, pr->omega_min, E);
+      cplx Cp[64];
+      polar_factors(m, qq, E, Cp);
       oracle_g_Re_q(m, qq, gReq);
       for (long i = 0; i < (long)m->nRe * nc; i++) barReq[i] = 0.0;
       for (int ik = 0; ik < nk; ik++) {
@@ -645,7 +725,7 @@ int oracle_linewidth_grad(const oracle_model *m, int nk, const double *k, int nq
         oracle_hk(m, kq, Hkq);
         if (oracle_eigh(nw, Hkq, ekq, Ukq) < 0) bad++;
         g_k_from_Re_q(m, gReq, k + 3 * ik, gk);
-        bloch_mode_vertex(nw, nm, gk, U, Ukq, E, gmn, tmp);
+        bloch_mode_vertex(nw, nm, gk, U, Ukq, E, gmn, tmp, m->polar ? Cp : NULL);
         /* W_{nu,mn} g_{nu,mn}, and the temperature / Fermi-level partials */
         for (int nu = 0; nu < nm; nu++)
           for (int mm = 0; mm < nw; mm++)

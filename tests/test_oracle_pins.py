@@ -487,3 +487,60 @@ def test_spectral_function_normalisation(oracle_lib):
     norm = np.trapezoid(spec, omega, axis=-1)
     assert np.all(np.abs(norm - 1.0) < 1e-5), norm
     assert np.all(-sig.imag >= 0)
+
+
+# ------------------------------------------------------ polar vertex (oracle)
+def test_polar_vertex_closed_form_one_band(oracle_lib):
+    """One band, one atom, simple cubic (a = 1), Z* = z I, eps_inf = e I and the G = 0 term alone:
+    g^L_a = i pref z q_a damp / (2 pi e |q|^2 sqrt(2 M w_a)) with damp = exp(-e (2 pi |q|)^2 / (4 alpha)),
+    imaginary against the real short-range g0 sin(2 pi q_a) / sqrt(2 M w_a): |g|^2 is the sum of squares."""
+    m = _tb()
+    z, e, alpha, pref = 1.7, 5.0, 0.8, 0.03
+    m = dataclasses.replace(m, polar=W.models.PolarTerms(A=np.eye(3), eps_inf=e * np.eye(3), Zstar=z * np.eye(3)[None],
+                                                         alpha=alpha, prefactor=pref, gmax=0))
+    k = W.uniform_grid(3) + 0.05
+    q = W.uniform_grid(6) + 0.013  # no q on a reciprocal lattice vector
+    T, EF, sigma, M = 300.0, 0.1, 0.05, 1.3
+    got = oracle_lib.linewidth(m, k, q, None, T, EF, sigma)[:, 0]
+    ref = np.zeros(len(k))
+    for ik, kk in enumerate(k):
+        ek = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * kk).sum()
+        s = 0.0
+        for qq in q:
+            ekq = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * (kk + qq)).sum()
+            f = _fermi(ekq, EF, T)
+            q2 = float((qq**2).sum())
+            damp = math.exp(-e * (2 * math.pi) ** 2 * q2 / (4 * alpha))
+            for a in range(3):
+                w = 2 * math.sqrt(0.01 / M) * abs(math.sin(math.pi * qq[a]))
+                gs = 0.05 * math.sin(2 * math.pi * qq[a]) / math.sqrt(2 * M * w)
+                gl = pref * z * qq[a] * damp / (2 * math.pi * e * q2 * math.sqrt(2 * M * w))
+                g2 = gs * gs + gl * gl
+                n = _bose(w, T)
+                s += g2 * ((n + f) * _gauss(ek - ekq + w, sigma) + (n + 1 - f) * _gauss(ek - ekq - w, sigma))
+        ref[ik] = math.pi * s / len(q)
+    assert np.allclose(got, ref, rtol=1e-11, atol=1e-14 * np.abs(ref).max())
+    # and the long-range part is not negligible here
+    base = oracle_lib.linewidth(dataclasses.replace(m, polar=None), k, q, None, T, EF, sigma)[:, 0]
+    assert np.abs(got - base).max() > 0.1 * np.abs(base).max()
+
+
+def test_polar_vertex_diverges_as_one_over_q(oracle_lib):
+    """|g^L| |q| tends to a constant as q -> 0 along a direction (the G = 0 term of Eq. long-range),
+    for an optical mode of a two-atom model with neutral Born charges."""
+    rng = np.random.default_rng(95)
+    m = W.make_model("diamond", 1, 2, [1.0, 1.2], 20, 20, rng)
+    m = dataclasses.replace(m, polar=W.models.polar_terms("diamond", 2, rng, prefactor=0.05, gmax=2))
+    short = dataclasses.replace(m, polar=None)
+    qhat = np.array([0.3, -0.2, 0.5])
+    k = np.array([[0.1, 0.2, 0.3]])
+    vals = []
+    for t in (1e-3, 1e-4, 1e-5):
+        q = (t * qhat)[None]
+        _, _, om, g = oracle_lib.interp(m, k, q)
+        _, _, _, gs = oracle_lib.interp(short, k, q)
+        gl = np.abs(g[0, 0, -1, 0, 0] - gs[0, 0, -1, 0, 0])  # highest (optical) mode, one band
+        vals.append(gl * t)
+    assert vals[0] > 0
+    assert abs(vals[1] - vals[2]) < 1e-3 * vals[2]
+    assert abs(vals[0] - vals[2]) < 1e-1 * vals[2]

@@ -44,6 +44,34 @@ LATTICES = {
 }
 
 
+@dataclasses.dataclass
+class PolarTerms:
+    """Inputs of the long-range vertex: lattice vectors A (rows, units of a), the high-frequency
+    dielectric tensor, Born effective charges Z*[kappa][b][alpha], the damping alpha of the G sum
+    (1/a^2), the overall prefactor (eV) and the G box |n_i| <= gmax."""
+
+    A: np.ndarray
+    eps_inf: np.ndarray
+    Zstar: np.ndarray
+    alpha: float
+    prefactor: float
+    gmax: int
+
+
+def polar_terms(lattice: str, nat: int, rng: np.random.Generator, prefactor: float = 0.05, alpha: float = 1.0,
+                gmax: int = 2) -> PolarTerms:
+    """Seeded synthetic polar inputs: eps_inf symmetric positive definite (eigenvalues 4..10), Z* random
+    3x3 per atom with the charge-neutrality sum rule sum_kappa Z*_kappa = 0 (a single atom gets
+    Z* = 0 unless given explicitly)."""
+    A, _ = LATTICES[lattice]
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    eps = Q @ np.diag(4.0 + 6.0 * rng.random(3)) @ Q.T
+    Z = rng.standard_normal((nat, 3, 3))
+    Z -= Z.mean(axis=0, keepdims=True)
+    return PolarTerms(A=np.array(A, dtype=np.float64), eps_inf=0.5 * (eps + eps.T), Zstar=Z, alpha=alpha,
+                      prefactor=prefactor, gmax=gmax)
+
+
 def _canonical_order(R: np.ndarray, A: np.ndarray) -> np.ndarray:
     """Sort integer vectors by Cartesian length, then lexicographically."""
     lengths = np.round(np.linalg.norm(R @ A, axis=1), 9)
@@ -124,6 +152,7 @@ class WannierModel:
     Rp: np.ndarray  # [nRp,3] int32
     wRp: np.ndarray  # [nRp]
     g: np.ndarray  # [nRe,nRp,3nat,nw,nw] complex128
+    polar: Optional["PolarTerms"] = None  # long-range part of the vertex (polar materials)
 
     @property
     def nmodes(self) -> int:
