@@ -288,6 +288,28 @@ void epw_batch_free(epw_batch *batch);
  * status, free. */
 epw_status epw_linewidth_batched(int njobs, const epw_linewidth_job *jobs, void *stream);
 
+/* Long-range (polar) part of the vertex, Sec. "Electron-phonon coupling in
+ * polar materials", Eq. (long-range), with the overlap in its small-(q+G) form
+ * [U_k U_k+q^dagger]_nm of that section.  Once set, every interpolated vertex of
+ * the model is g = g^S + g^L with g^S the Wannier-interpolated g(Re,Rp) and
+ *   g^L_mn,nu(k,q) = i C_nu(q) [U_k+q^dagger U_k]_mn,
+ *   C_nu(q) = prefactor sum_{kappa,a} e_{kappa a,nu}(q) / sqrt(2 M_kappa w_qnu)
+ *             sum_{G, q+G != 0} exp(-(q+G).eps.(q+G) / (4 alpha)) ((q+G).Z*_kappa)_a / ((q+G).eps.(q+G)),
+ * (x.Z*)_a = sum_b x_b Z*_{kappa, b a}, q + G Cartesian from the lattice vectors A
+ * (rows, any length unit L; b_i . a_j = 2 pi delta_ij), G = sum n_i b_i with
+ * |n_i| <= gmax.  The printed equation has no prefactor and no convergence factor
+ * for the G sum: prefactor (eV L^-1 scale of the model's vertex) and alpha (L^-2)
+ * are inputs.  Zstar [nat][3][3] host memory, copied.  NULL removes the term. */
+typedef struct {
+  double A[3][3];
+  double eps_inf[3][3];
+  const double *Zstar;
+  double alpha;
+  double prefactor;
+  int gmax;
+} epw_polar_desc;
+epw_status epw_set_polar(epw_model *model, const epw_polar_desc *polar);
+
 /* Wait for the model's work on `stream` and report device-side failures
  * (EPW_ERR_NOT_CONVERGED) raised since the previous epw_sync; clears them. */
 epw_status epw_sync(const epw_model *model, void *stream);

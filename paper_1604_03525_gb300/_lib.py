@@ -38,6 +38,7 @@ SIGNATURES = {
     "epw_batch_info": (I, [P, P, P, P]),
     "epw_batch_free": (None, [P]),
     "epw_linewidth_batched": (I, [I, P, P]),
+    "epw_set_polar": (I, [P, P]),
     "epw_sync": (I, [P, P]),
     "epw_model_info": (I, [P, P, P, P, P, P]),
     "epw_launch_count": (ctypes.c_uint64, []),
@@ -60,6 +61,10 @@ class WannierDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("T_K", D), ("EF_eV", D), ("sigma_eV", D), ("omega_min_eV", D),
                 ("precision", I), ("reserved", I)]
+
+
+class PolarDesc(ctypes.Structure):
+    _fields_ = [("A", D * 9), ("eps_inf", D * 9), ("Zstar", P), ("alpha", D), ("prefactor", D), ("gmax", I)]
 
 
 class LinewidthJob(ctypes.Structure):

@@ -94,6 +94,23 @@ class Model:
         _check(lib.epw_load_wannier(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
         self._keep = None
+        if getattr(wm, "polar", None) is not None:
+            self.set_polar(wm.polar)
+
+    def set_polar(self, polar):
+        """Long-range vertex of polar materials (epw_set_polar); polar has A, eps_inf, Zstar [nat,3,3],
+        alpha, prefactor, gmax (None removes it)."""
+        lib = _lib.load()
+        if polar is None:
+            _check(lib.epw_set_polar(self._h, None))
+            return
+        Z = np.ascontiguousarray(polar.Zstar, dtype=np.float64)
+        if Z.shape != (self.nat, 3, 3):
+            raise ValueError(f"Zstar shape {Z.shape} != {(self.nat, 3, 3)}")
+        d = _lib.PolarDesc((ctypes.c_double * 9)(*np.asarray(polar.A, dtype=np.float64).ravel()),
+                           (ctypes.c_double * 9)(*np.asarray(polar.eps_inf, dtype=np.float64).ravel()),
+                           Z.ctypes.data, float(polar.alpha), float(polar.prefactor), int(polar.gmax))
+        _check(lib.epw_set_polar(self._h, ctypes.byref(d)))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

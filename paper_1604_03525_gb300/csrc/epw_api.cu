@@ -75,7 +75,7 @@ static epw_status upload(T **dst, const T *src, size_t n) {
 }
 
 static void free_model_arrays(epw_model *m) {
-  void *ptrs[] = {m->Re, m->Rp, m->Rph, m->wRe, m->wRp, m->Hw, m->Phiw, m->gw, m->mass, m->dstatus, m->ws};
+  void *ptrs[] = {m->Re, m->Rp, m->Rph, m->wRe, m->wRp, m->Hw, m->Phiw, m->gw, m->mass, m->dstatus, m->ws, m->pZ};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->ev) {
@@ -207,6 +207,46 @@ extern "C" epw_status epw_set_vertex(epw_model *m, const void *g, int g_is_c64, 
   return EPW_OK;
 }
 
+extern "C" epw_status epw_set_polar(epw_model *m, const epw_polar_desc *d) {
+  g_err[0] = 0;
+  if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
+  if (!d) {
+    m->polar = 0;
+    return EPW_OK;
+  }
+  if (!d->Zstar) return fail(EPW_ERR_INVALID_ARG, "null Born charges");
+  if (!(d->alpha > 0.0) || !std::isfinite(d->alpha)) return fail(EPW_ERR_INVALID_ARG, "alpha must be > 0");
+  if (d->gmax < 0 || d->gmax > 16) return fail(EPW_ERR_INVALID_ARG, "gmax must be in [0, 16]");
+  if (!std::isfinite(d->prefactor)) return fail(EPW_ERR_INVALID_ARG, "prefactor must be finite");
+  const double *A = &d->A[0][0];
+  const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                     A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return fail(EPW_ERR_INVALID_ARG, "singular lattice vectors");
+  double inv[9];
+  inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  for (int i = 0; i < 3; i++)
+    for (int c = 0; c < 3; c++) m->pb[i * 3 + c] = 2.0 * EPW_PI * inv[c * 3 + i];
+  for (int i = 0; i < 9; i++) m->peps[i] = (&d->eps_inf[0][0])[i];
+  int cur = -1;
+  CK(cudaGetDevice(&cur));
+  if (cur != m->device) return fail(EPW_ERR_INVALID_ARG, "model lives on device %d, current device is %d", m->device, cur);
+  if (!m->pZ) CK(cudaMalloc((void **)&m->pZ, sizeof(double) * 9 * m->nat));
+  CK(cudaMemcpy(m->pZ, d->Zstar, sizeof(double) * 9 * m->nat, cudaMemcpyHostToDevice));
+  m->palpha = d->alpha;
+  m->ppref = d->prefactor;
+  m->pgmax = d->gmax;
+  m->polar = 1;
+  return EPW_OK;
+}
+
 extern "C" epw_status epw_model_info(const epw_model *m, int *nw, int *nat, int *nRe, int *nRp, int *nRph) {
   if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
   if (nw) *nw = m->nw;
@@ -295,6 +335,7 @@ static void plan_prep(Arena &A, const epw_model *m, int nk, int nq, int prec, bo
   p.ev = A.take<cx<double>>((size_t)nq * nm2);
   p.omegaT = A.take<double>((size_t)nq * m->nm);
   p.ET = A.take<char>(sR * nm2 * (size_t)nq);
+  p.Cpol = m->polar ? A.take<char>(sR * (size_t)m->nm * nq) : nullptr;
   if (need_B) {
     size_t nbg = (size_t)nk * m->nRp * m->nm * nw2;
     p.G1 = A.take<char>(sR * nbg);
@@ -338,6 +379,12 @@ static epw_status run_prep(const epw_model *m, int nk, const double *k, int nq, 
   launch_phonon_post(nq, nm, p.w2, p.ev, m->mass, omega_min, p.omegaT,
                      prec == EPW_FP64 ? (cx<double> *)p.ET : nullptr, prec == EPW_FP64 ? nullptr : (cx<float> *)p.ET,
                      omega_out, st);
+  if (m->polar) {
+    if (prec == EPW_FP64)
+      launch_polar_factors<double>(m, nq, q, (const cx<double> *)p.ET, (cx<double> *)p.Cpol, st);
+    else
+      launch_polar_factors<float>(m, nq, q, (const cx<float> *)p.ET, (cx<float> *)p.Cpol, st);
+  }
   if (need_B && nk > 0) {
     const int ncol = m->nRp * nm * (int)nw2;
     if (prec == EPW_FP64) {
@@ -499,6 +546,8 @@ epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, c
     return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
   if (tcp && L.tc.ok) {
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
+    L.tc.Cpol = m->polar ? (const float2 *)p.Cpol : nullptr;
+    L.tc.Uk64 = p.Uk;
     epw_status s = tc_linewidth(m, nk, kd, nq, qd, wqd, par, p.PkRM, p.epsk, p.Uk, p.omegaT, (const cx<float> *)p.ET,
                                 (const cx<float> *)p.Bg, (const cx<float> *)p.BH, L.tc, out, st);
     if (s != EPW_OK) return fail(s, "tensor-core path: %s", g_err[0] ? g_err : "unsupported shape");
@@ -530,6 +579,8 @@ epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, c
       a.omega_min = par->omega_min_eV;
       a.partial = L.partial;
       a.dstatus = m->dstatus;
+      a.Cpol = m->polar ? p.Cpol : nullptr;
+      a.Uk = p.Uk;
       a.Cq = L.sg.Ct;
       a.ldc = L.sg.pair_ld();
       a.cpk = L.sg.cpk;
@@ -563,6 +614,8 @@ epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, c
     a.omega_min = par->omega_min_eV;
     a.partial = L.partial;
     a.dstatus = m->dstatus;
+    a.Cpol = m->polar ? p.Cpol : nullptr;
+    a.Uk = p.Uk;
     epw_timing_begin(m, st);
     epw_status s = prec == EPW_FP64 ? launch_pair<double>(a, 0, st) : launch_pair<float>(a, 0, st);
     epw_timing_end(m, st);
@@ -625,6 +678,8 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
   CKS(run_prep(m, nk, kd, nq, qd, wprec, omega_min, nk > 0, p, omd, st));
   if (ekd && nk > 0) CK(cudaMemcpyAsync(ekd, p.epsk, sizeof(double) * nk * nw, cudaMemcpyDeviceToDevice, st));
   if (tc && nk > 0 && nq > 0 && (ekqd || gd)) {
+    tcb.Cpol = m->polar ? (const float2 *)p.Cpol : nullptr;
+    tcb.Uk64 = p.Uk;
     epw_status s = tc_interp(m, nk, nq, qd, omega_min, p.epsk, p.omegaT, (const cx<float> *)p.ET,
                              (const cx<float> *)p.Bg, (const cx<float> *)p.BH, tcb, ekqd, gd, st);
     if (s != EPW_OK) return fail(s, "tensor-core interpolation failed");
@@ -651,6 +706,8 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
       a.eps_kq = ekqd;
       a.gout = (cx<double> *)gd;
       a.dstatus = m->dstatus;
+      a.Cpol = m->polar ? p.Cpol : nullptr;
+      a.Uk = p.Uk;
       a.Cq = sg.Ct;
       a.ldc = sg.pair_ld();
       a.cpk = sg.cpk;
@@ -678,6 +735,8 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
     a.eps_kq = ekqd;
     a.gout = (cx<double> *)gd;
     a.dstatus = m->dstatus;
+    a.Cpol = m->polar ? p.Cpol : nullptr;
+    a.Uk = p.Uk;
     epw_status s = precision == EPW_FP64 ? launch_pair<double>(a, 1, st) : launch_pair<float>(a, 1, st);
     if (s != EPW_OK) return fail(s, "no per-pair kernel for nw=%d, 3nat=%d", m->nw, m->nm);
   }
@@ -776,6 +835,8 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   CK(cudaMemsetAsync(b.gwbar, 0, sR * ng, st));
   if (nk > 0 && nq > 0 && tcb) {
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
+    b.tc.Cpol = m->polar ? (const float2 *)p.Cpol : nullptr;
+    b.tc.Uk64 = p.Uk;
     epw_status s = tc_linewidth_backward(m, nk, nq, qd, wqd, par, p.epsk, p.Uk, p.Pk32, p.omegaT,
                                          (const cx<float> *)p.ET, (const cx<float> *)p.Bg, (const cx<float> *)p.BH,
                                          b.cotd, b.tc, b.tw, (cx<float> *)b.gwbar, b.sc, st);
@@ -816,6 +877,8 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
       a.partialE = b.pE;
       a.nkc = kc;
       a.dstatus = m->dstatus;
+      a.Cpol = m->polar ? p.Cpol : nullptr;
+      a.Uk = p.Uk;
       if (staged) {
         a.Cq = b.sg.Ct;
         a.ldc = b.sg.pair_ld();
@@ -975,6 +1038,8 @@ extern "C" epw_status epw_phonon_selfenergy(const epw_model *mc, int nk, const d
     a.sigma = par->sigma_eV;
     a.omega_min = par->omega_min_eV;
     a.dstatus = m->dstatus;
+    a.Cpol = m->polar ? p.Cpol : nullptr;
+    a.Uk = p.Uk;
     a.nkc = kper;
     if (tcp) {
       CKS(tc_staged_phases(m, nq, qd, b.sg, st));
@@ -1106,6 +1171,8 @@ extern "C" epw_status epw_selfenergy(const epw_model *mc, int nk, const double *
     a.sigma = par->sigma_eV;
     a.omega_min = par->omega_min_eV;
     a.dstatus = m->dstatus;
+    a.Cpol = m->polar ? p.Cpol : nullptr;
+    a.Uk = p.Uk;
     for (int k0 = 0; k0 < nk; k0 += kc) {
       const int n = std::min(kc, nk - k0);
       a.k0 = k0;
@@ -1246,6 +1313,8 @@ extern "C" epw_status epw_linewidth_noalloc(const epw_model *mc, int nk, const d
   a.omega_min = par->omega_min_eV;
   a.partial = L.partial;  // every entry is written before it is read
   a.dstatus = m->dstatus;
+  a.Cpol = m->polar ? p.Cpol : nullptr;
+  a.Uk = p.Uk;
   epw_status s = prec == EPW_FP64 ? launch_pair<double>(a, 0, st) : launch_pair<float>(a, 0, st);
   if (s != EPW_OK) return fail(s, "no per-pair kernel for nw=%d, 3nat=%d in this precision", m->nw, m->nm);
   launch_finalize(nk, (nq + 127) / 128, m->nw, L.partial, imsigma, st);

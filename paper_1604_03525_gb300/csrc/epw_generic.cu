@@ -314,6 +314,27 @@ __device__ __forceinline__ bool pair_vertex(const PairArgs &a, int kl, int k, in
       }
     }
   }
+  if (a.Cpol) {
+    // long-range part: G_nu += i C_nu(q) [U_k+q^dagger U_k]
+    const cx<double> *Uk = a.Uk + (size_t)k * nw2;
+    const cx<R> *Cp = (const cx<R> *)a.Cpol;
+#pragma unroll UW
+    for (int m = 0; m < MW; m++)
+#pragma unroll UW
+      for (int n = 0; n < MW; n++) {
+        if (m >= nw || n >= nw) continue;
+        cx<R> o = mkc<R>(0, 0);
+#pragma unroll UW
+        for (int i = 0; i < MW; i++)
+          if (i < nw) cfma(o, conjc(U[i][m]), ccast<R>(Uk[i * nw + n]));
+#pragma unroll UM
+        for (int v = 0; v < MM; v++) {
+          if (v >= nm) continue;
+          const cx<R> c = Cp[(size_t)v * nq + qq];
+          cfma(G[v][m][n], mkc<R>(-c.y, c.x), o);  // i c o
+        }
+      }
+  }
   return !nc;
 }
 
@@ -695,6 +716,47 @@ __global__ void k_se_finalize(int nkc, int k0, int nw, int nqw, int nom, const d
   }
 }
 
+// C_nu(q) = pref sum_{kappa,a} E[kappa a][nu] F_{kappa a}(q), F = sum_{G, q+G != 0} damp(q+G)
+// ((q+G).Z*_kappa)_a / ((q+G).eps.(q+G)), damp(x) = exp(-x.eps.x / (4 alpha)), G = sum n_i b_i,
+// |n_i| <= gmax (Eq. (long-range) with the readings of its prefactor and convergence factor).
+// One thread per q; F accumulated in FP64.
+template <typename R>
+__global__ void k_polar_factors(int nq, int nm, int nat, const double *__restrict__ q, PolarK pk,
+                                const double *__restrict__ Z, const cx<R> *__restrict__ ET, cx<R> *C) {
+  const int iq = blockIdx.x * blockDim.x + threadIdx.x;
+  if (iq >= nq) return;
+  double F[18];
+  for (int i = 0; i < 18; i++) F[i] = 0.0;
+  const double q0 = q[3 * iq], q1 = q[3 * iq + 1], q2 = q[3 * iq + 2];
+  const int G = pk.gmax;
+  for (int n1 = -G; n1 <= G; n1++)
+    for (int n2 = -G; n2 <= G; n2++)
+      for (int n3 = -G; n3 <= G; n3++) {
+        double x[3];
+        for (int c = 0; c < 3; c++)
+          x[c] = (q0 + n1) * pk.b[c] + (q1 + n2) * pk.b[3 + c] + (q2 + n3) * pk.b[6 + c];
+        if (x[0] * x[0] + x[1] * x[1] + x[2] * x[2] == 0.0) continue;
+        double xex = 0.0;
+        for (int c = 0; c < 3; c++)
+          for (int d = 0; d < 3; d++) xex += x[c] * pk.eps[c * 3 + d] * x[d];
+        const double w = exp(-xex / (4.0 * pk.alpha)) / xex;
+        for (int kap = 0; kap < nat; kap++)
+          for (int a = 0; a < 3; a++) {
+            const double *Zk = Z + kap * 9;
+            F[kap * 3 + a] += w * (x[0] * Zk[a] + x[1] * Zk[3 + a] + x[2] * Zk[6 + a]);
+          }
+      }
+  for (int v = 0; v < nm; v++) {
+    double cr = 0.0, ci = 0.0;
+    for (int ka = 0; ka < nm; ka++) {
+      const cx<R> e = ET[((size_t)ka * nm + v) * nq + iq];
+      cr += (double)e.x * F[ka];
+      ci += (double)e.y * F[ka];
+    }
+    C[(size_t)v * nq + iq] = mkc<R>((R)(pk.pref * cr), (R)(pk.pref * ci));
+  }
+}
+
 // alpha^2 F on a grid (Eq. (isotropiceliash)): one block per grid point, each
 // thread a fixed stride of the (q, nu) terms (compensated), then a fixed tree.
 __global__ void k_eliashberg(int nq, int nm, const double *__restrict__ omega, const double *__restrict__ lam,
@@ -1036,6 +1098,25 @@ void launch_se_finalize(int nkc, int k0, int nw, int nqw, int nom, const double2
   k_se_finalize<<<(n + 127) / 128, 128, 0, st>>>(nkc, k0, nw, nqw, nom, part, omega, epsk, EF, sig, spec);
   epw_count_launch();
 }
+
+template <typename R>
+void launch_polar_factors(const epw_model *m, int nq, const double *q, const cx<R> *ET, cx<R> *C, cudaStream_t st) {
+  if (nq <= 0 || !m->polar) return;
+  PolarK pk;
+  for (int i = 0; i < 9; i++) {
+    pk.b[i] = m->pb[i];
+    pk.eps[i] = m->peps[i];
+  }
+  pk.alpha = m->palpha;
+  pk.pref = m->ppref;
+  pk.gmax = m->pgmax;
+  k_polar_factors<R><<<(nq + 127) / 128, 128, 0, st>>>(nq, m->nm, m->nat, q, pk, m->pZ, ET, C);
+  epw_count_launch();
+}
+template void launch_polar_factors<double>(const epw_model *, int, const double *, const cx<double> *, cx<double> *,
+                                           cudaStream_t);
+template void launch_polar_factors<float>(const epw_model *, int, const double *, const cx<float> *, cx<float> *,
+                                          cudaStream_t);
 
 void launch_eliashberg(int nq, int nm, const double *omega, const double *lam, const double *wq, int ngrid,
                        const double *grid, double sigma_ph, double *a2f, cudaStream_t st) {

@@ -34,6 +34,7 @@ struct Prep {
   void *ET;                // [nm*nm][nq] working precision
   void *G1, *Bg, *BH;      // working precision
   cx<float> *Pk32, *gw32;  // FP32 copies for the k-side contraction
+  void *Cpol;              // [nm][nq] long-range factors C_nu(q), working precision (polar models)
 };
 
 // Buffers of one linewidth job.

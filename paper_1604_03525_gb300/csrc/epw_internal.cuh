@@ -309,6 +309,13 @@ struct epw_model {
   int timing;
   int nev;
   cudaEvent_t *ev;        // [2 * EPW_MAX_TIMED]
+  // long-range (polar) part of the vertex (epw_set_polar); polar == 0: none
+  int polar;
+  double pb[9];           // reciprocal vectors b_i (rows), 2 pi (A^{-1})^T
+  double peps[9];         // eps_inf
+  double *pZ;             // device [nat][3][3]
+  double palpha, ppref;
+  int pgmax;
 };
 
 #define EPW_MAX_TIMED 4096
@@ -376,6 +383,9 @@ struct PairArgs {
   size_t ldc;
   int cpk;
   int nk_total;  // phonon side: all k-points of the call (the 1/nk weight when wq (= w_k) is null)
+  // long-range vertex: g_nu += i C_nu(q) (U_k+q^dagger U_k), C [nm][nq] (R precision), U_k FP64 [nk][nw][nw]
+  const void *Cpol;
+  const cx<double> *Uk;
 };
 // mode: 0 linewidth, 1 interp, 2 backward
 template <typename R>
@@ -391,6 +401,15 @@ void launch_ph_finalize(int nq, int nm, int nchunk, const double *partial, const
                         const double *dos, double *pi_im, double *lam, double *zeta, cudaStream_t st);
 void launch_dos_terms(int nk, int nw, const double *epsk, const double *wk, double EF, double sigma, double *terms,
                       cudaStream_t st);
+// Lattice / dielectric inputs of the long-range vertex, by value for the kernel.
+struct PolarK {
+  double b[9], eps[9];
+  double alpha, pref;
+  int gmax;
+};
+// C_nu(q) of the long-range vertex (Eq. (long-range)) into C [nm][nq] from the mode factors E [nm*nm][nq]
+template <typename R>
+void launch_polar_factors(const epw_model *m, int nq, const double *q, const cx<R> *ET, cx<R> *C, cudaStream_t st);
 void launch_eliashberg(int nq, int nm, const double *omega, const double *lam, const double *wq, int ngrid,
                        const double *grid, double sigma_ph, double *a2f, cudaStream_t st);
 // complex self-energy on a frequency grid (nw <= 8, 3nat <= 9): per-warp partials

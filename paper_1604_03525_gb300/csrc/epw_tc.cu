@@ -604,6 +604,9 @@ struct TcArgs {
   double *partT, *partE;  // [nk][4*nqt] per-warp sums of dL/dT and dL/dE_F
   float T;
   unsigned *dstatus;
+  // long-range vertex (polar models; null otherwise): C_nu(q) [nm][nq], U_k [nk][nw][nw]
+  const float2 *Cpol;
+  const float2 *UkF;
 };
 
 // tf32 term: an fp32 with its 13 low mantissa bits cleared after rounding to nearest
@@ -770,6 +773,19 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
       }
     }
 
+    if (a.Cpol) {
+      // long-range part: G_nu += i C_nu(q) U_k, so that U_k+q^dagger G picks up i C [U_k+q^dagger U_k]
+      const float2 c = __ldg(a.Cpol + (size_t)nu * a.nq + qq);
+      const float2 *Uk = a.UkF + (size_t)kk * NW * NW;
+#pragma unroll
+      for (int i = 0; i < NW; i++)
+#pragma unroll
+        for (int j = 0; j < NW; j++) {
+          const float2 u = __ldg(Uk + i * NW + j);
+          G[i][j].x = fmaf(-c.y, u.x, fmaf(-c.x, u.y, G[i][j].x));
+          G[i][j].y = fmaf(c.x, u.x, fmaf(-c.y, u.y, G[i][j].y));
+        }
+    }
     if constexpr (MODE == 2) {
       const float kf = keep ? 1.0f : 0.0f;
       const float dn = kf * nbnu * (nbnu + 1.0f) * wnu * a.invkT / a.T;
@@ -1227,6 +1243,7 @@ epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffe
   b.wqF = A.take<float>((size_t)nq);
   b.ekF = A.take<float>((size_t)nk * m->nw);
   b.partial = A.take<double>((size_t)nk * 4 * b.nqt * m->nw);
+  b.UkF = m->polar ? A.take<float2>((size_t)nk * m->nw * m->nw) : nullptr;
   return EPW_OK;
 }
 
@@ -1258,6 +1275,7 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
     k_tc_tables<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nm, nk, m->nw, omegaT, par->T_K, wq, epsk, b.nbT, b.omF,
                                                    b.wqF, b.ekF);
     epw_count_launch();
+    if (b.Cpol) launch_cast_c64_to_c32((size_t)nk * m->nw * m->nw, b.Uk64, (cx<float> *)b.UkF, st);
   }
   CUtensorMap ah, al, bh, bl;
   std::memset(&ah, 0, sizeof(ah));
@@ -1294,6 +1312,8 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
   a.eps_kq = eps_kq;
   a.gout = (double2 *)gout;
   a.dstatus = m->dstatus;
+  a.Cpol = b.Cpol;
+  a.UkF = b.Cpol ? b.UkF : nullptr;
   cudaError_t e;
   if (mode == 0) {
     epw_timing_begin(const_cast<epw_model *>(m), st);
@@ -1683,6 +1703,7 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
     n = (size_t)nk * nw;
     k_cot_table<<<grid_for(n, 256), 256, 0, st>>>(n, cot, w.cotF);
     epw_count_launch();
+    if (b.Cpol) launch_cast_c64_to_c32((size_t)nk * nw * nw, b.Uk64, (cx<float> *)b.UkF, st);
   }
   CUtensorMap ah, al, ph, pl;
   if (!make_map(&ah, b.Ahi, TC_OP_TF32, b.kpad, nq, BM) || !make_map(&al, b.Alo, TC_OP_TF32, b.kpad, nq, BM) ||
@@ -1740,6 +1761,8 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
     a.partE = w.partE;
     a.T = (float)par->T_K;
     a.dstatus = m->dstatus;
+    a.Cpol = b.Cpol;
+    a.UkF = b.Cpol ? b.UkF + (size_t)k0 * nw * nw : nullptr;
     cudaError_t e = launch_tc_shape<TC_OP_TF32, 2>(nw, m->nm, ah, al, bh, bl, a, st);
     epw_count_launch();
     if (e != cudaSuccess) return EPW_ERR_CUDA;

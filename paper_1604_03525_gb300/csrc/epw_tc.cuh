@@ -17,6 +17,10 @@ struct TcBuffers {
   int op, kpad, cpk, nk_pad, nqt, kpt;
   bool ok;           // shape has a tensor-core kernel
   size_t a_block_bytes;  // q-block of the A operand visited by all k groups (0: default)
+  // long-range vertex (polar models): set by the caller before a call; UkF is laid out by tc_plan
+  const float2 *Cpol;        // [nm][nq]
+  const cx<double> *Uk64;    // [nk][nw][nw]
+  float2 *UkF;               // FP32 copy of Uk64
 };
 
 // True when the model's shape has a tensor-core kernel (Re == Rp sets and a

@@ -210,6 +210,21 @@ __global__ void __launch_bounds__(WARPS * 32) k_pair_wide(PairArgs a) {
           }
         }
       }
+      if (a.Cpol) {
+        // long-range part in the Wannier gauge: G'_nu += i C_nu(q) U_k
+        const cx<R> *Cp = (const cx<R> *)a.Cpol;
+        const cx<double> *Uk = a.Uk + (size_t)k * nw2;
+#pragma unroll
+        for (int b = 0; b < NB; b++) {
+          if (b >= nb) break;
+          const cx<R> c = Cp[(size_t)(v0 + b) * nq + q];
+#pragma unroll
+          for (int t = 0; t < TMAX; t++) {
+            const int e = lane + 32 * t;
+            if (e < nw2) cfma(Gp[b][t], mkc<R>(-c.y, c.x), ccast<R>(Uk[e]));
+          }
+        }
+      }
 #pragma unroll
       for (int b = 0; b < NB; b++) {
         if (b >= nb) break;

@@ -64,16 +64,17 @@ def test_struct_layouts_match_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     src = tmp_path / "sz.c"
-    src.write_text('#include <stdio.h>\n#include "epw.h"\nint main(void){printf("%zu %zu %zu %zu %zu\\n",'
+    src.write_text('#include <stdio.h>\n#include "epw.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
                    ' sizeof(epw_wannier_desc), sizeof(epw_params), sizeof(epw_linewidth_job),'
-                   ' offsetof(epw_linewidth_job, params), offsetof(epw_linewidth_job, imsigma));return 0;}\n')
+                   ' offsetof(epw_linewidth_job, params), offsetof(epw_linewidth_job, imsigma),'
+                   ' sizeof(epw_polar_desc), offsetof(epw_polar_desc, gmax));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run([cc, "-include", "stddef.h", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
     sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     J = _lib.LinewidthJob
     assert sizes == [ctypes.sizeof(_lib.WannierDesc), ctypes.sizeof(_lib.Params), ctypes.sizeof(J),
-                     J.params.offset, J.imsigma.offset]
+                     J.params.offset, J.imsigma.offset, ctypes.sizeof(_lib.PolarDesc), _lib.PolarDesc.gmax.offset]
 
 
 def test_batch_arguments_rejected_without_gpu_work(lib):
