@@ -310,6 +310,14 @@ typedef struct {
 } epw_polar_desc;
 epw_status epw_set_polar(epw_model *model, const epw_polar_desc *polar);
 
+/* Self-test of the device failure path on the current GPU: a kernel waits,
+ * with the same bounded mbarrier wait the tensor-core kernels use, on a barrier
+ * that nothing arrives at, for `cycles` clock cycles (1..4e9; 2e6 is about 1 ms).
+ * The wait gives up, raises the device timeout flag and the kernel returns; the
+ * call then returns EPW_ERR_TIMEOUT (the expected outcome) with *waited_out = 1.
+ * No fault, trap or hang is involved and the context stays usable. */
+epw_status epw_selftest_wait_timeout(long long cycles, int *waited_out);
+
 /* Wait for the model's work on `stream` and report device-side failures
  * (EPW_ERR_NOT_CONVERGED) raised since the previous epw_sync; clears them. */
 epw_status epw_sync(const epw_model *model, void *stream);

@@ -39,6 +39,7 @@ SIGNATURES = {
     "epw_batch_free": (None, [P]),
     "epw_linewidth_batched": (I, [I, P, P]),
     "epw_set_polar": (I, [P, P]),
+    "epw_selftest_wait_timeout": (I, [ctypes.c_longlong, P]),
     "epw_sync": (I, [P, P]),
     "epw_model_info": (I, [P, P, P, P, P, P]),
     "epw_launch_count": (ctypes.c_uint64, []),

@@ -78,6 +78,11 @@ static void free_model_arrays(epw_model *m) {
   void *ptrs[] = {m->Re, m->Rp, m->Rph, m->wRe, m->wRp, m->Hw, m->Phiw, m->gw, m->mass, m->dstatus, m->ws, m->pZ};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (m->aux) cudaStreamDestroy(m->aux);
+  if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+  if (m->ev_join) cudaEventDestroy(m->ev_join);
+  m->aux = nullptr;
+  m->ev_fork = m->ev_join = nullptr;
   if (m->ev) {
     for (int i = 0; i < 2 * EPW_MAX_TIMED; i++)
       if (m->ev[i]) cudaEventDestroy(m->ev[i]);
@@ -151,6 +156,12 @@ extern "C" epw_status epw_load_wannier(const epw_wannier_desc *d, epw_model **ou
   m->nRph = d->nRph;
   m->same_ep = same_set(d->nRe, d->Re, d->nRp, d->Rp);
   m->same_eph = same_set(d->nRe, d->Re, d->nRph, d->Rph);
+  m->rmax = 0;
+  for (int t = 0; t < 3; t++) {
+    const int n = t == 0 ? d->nRe : t == 1 ? d->nRp : d->nRph;
+    const int32_t *R = t == 0 ? d->Re : t == 1 ? d->Rp : d->Rph;
+    for (long i = 0; i < 3L * n; i++) m->rmax = std::max(m->rmax, std::abs((int)R[i]));
+  }
   epw_status s = EPW_OK;
   if ((s = upload(&m->Re, (const int *)d->Re, 3 * (size_t)d->nRe)) != EPW_OK ||
       (s = upload(&m->Rp, (const int *)d->Rp, 3 * (size_t)d->nRp)) != EPW_OK ||
@@ -355,36 +366,56 @@ static void plan_prep(Arena &A, const epw_model *m, int nk, int nq, int prec, bo
 }
 
 // Phases, k-side bands, phonons and the k-side vertex (Bg, BH).
-static epw_status run_prep(const epw_model *m, int nk, const double *k, int nq, const double *q, int prec,
-                           double omega_min, bool need_B, Prep &p, double *omega_out, cudaStream_t st) {
+// The k side (bands at k, k-side vertex) and the q side (phases, phonons, long-range factors) are
+// independent: the q side runs on the model's second stream, forked from and joined back into st.
+static epw_status prep_streams(epw_model *m) {
+  if (m->aux) return EPW_OK;
+  CK(cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
+  return EPW_OK;
+}
+
+static epw_status run_prep(const epw_model *mc, int nk, const double *k, int nq, const double *q, int prec,
+                           double omega_min, bool need_B, Prep &p, double *omega_out, cudaStream_t st,
+                           bool fork = true) {
+  epw_model *m = const_cast<epw_model *>(mc);
   const int nw = m->nw, nm = m->nm;
   const size_t nw2 = (size_t)nw * nw;
-  // k side (FP64): phases, H(k), eigensolve
-  launch_phases(nk, k, m->nRe, m->Re, p.PkRM, p.PkT, nullptr, st);
-  launch_fourier_d(nk, m->nRe, p.PkT, m->Hw, (int)nw2, p.Hk, st);
-  launch_eigh_d(nk, nw, p.Hk, p.epsk, p.Uk, m->dstatus, st);
+  cudaStream_t sq = st;
+  fork = fork && nq > 0 && nk > 0;
+  if (fork) {
+    CKS(prep_streams(m));
+    CK(cudaEventRecord(m->ev_fork, st));
+    CK(cudaStreamWaitEvent(m->aux, m->ev_fork, 0));
+    sq = m->aux;
+  }
   // q side: phases in working precision (+ FP64 for phonons)
   if (prec == EPW_FP64) {
-    launch_phases(nq, q, m->nRe, m->Re, nullptr, (cx<double> *)p.PqTe, nullptr, st);
-    if (!m->same_ep) launch_phases(nq, q, m->nRp, m->Rp, nullptr, (cx<double> *)p.PqTp, nullptr, st);
-    if (!m->same_eph) launch_phases(nq, q, m->nRph, m->Rph, nullptr, p.PqTph, nullptr, st);
+    launch_phases(nq, q, m->nRe, m->Re, m->rmax, nullptr, (cx<double> *)p.PqTe, nullptr, sq);
+    if (!m->same_ep) launch_phases(nq, q, m->nRp, m->Rp, m->rmax, nullptr, (cx<double> *)p.PqTp, nullptr, sq);
+    if (!m->same_eph) launch_phases(nq, q, m->nRph, m->Rph, m->rmax, nullptr, p.PqTph, nullptr, sq);
   } else {
-    launch_phases(nq, q, m->nRe, m->Re, nullptr, m->same_eph ? p.PqTph : nullptr, (cx<float> *)p.PqTe, st);
-    if (!m->same_ep) launch_phases(nq, q, m->nRp, m->Rp, nullptr, nullptr, (cx<float> *)p.PqTp, st);
-    if (!m->same_eph) launch_phases(nq, q, m->nRph, m->Rph, nullptr, p.PqTph, nullptr, st);
+    launch_phases(nq, q, m->nRe, m->Re, m->rmax, nullptr, m->same_eph ? p.PqTph : nullptr, (cx<float> *)p.PqTe, sq);
+    if (!m->same_ep) launch_phases(nq, q, m->nRp, m->Rp, m->rmax, nullptr, nullptr, (cx<float> *)p.PqTp, sq);
+    if (!m->same_eph) launch_phases(nq, q, m->nRph, m->Rph, m->rmax, nullptr, p.PqTph, nullptr, sq);
   }
   // phonons (FP64)
-  launch_fourier_d(nq, m->nRph, p.PqTph, m->Phiw, nm * nm, p.D, st);
-  launch_eigh_d(nq, nm, p.D, p.w2, p.ev, m->dstatus, st);
+  launch_fourier_d(nq, m->nRph, p.PqTph, m->Phiw, nm * nm, p.D, sq);
+  launch_eigh_d(nq, nm, p.D, p.w2, p.ev, m->dstatus, sq);
   launch_phonon_post(nq, nm, p.w2, p.ev, m->mass, omega_min, p.omegaT,
                      prec == EPW_FP64 ? (cx<double> *)p.ET : nullptr, prec == EPW_FP64 ? nullptr : (cx<float> *)p.ET,
-                     omega_out, st);
+                     omega_out, sq);
   if (m->polar) {
     if (prec == EPW_FP64)
-      launch_polar_factors<double>(m, nq, q, (const cx<double> *)p.ET, (cx<double> *)p.Cpol, st);
+      launch_polar_factors<double>(m, nq, q, (const cx<double> *)p.ET, (cx<double> *)p.Cpol, sq);
     else
-      launch_polar_factors<float>(m, nq, q, (const cx<float> *)p.ET, (cx<float> *)p.Cpol, st);
+      launch_polar_factors<float>(m, nq, q, (const cx<float> *)p.ET, (cx<float> *)p.Cpol, sq);
   }
+  // k side (FP64): phases, H(k), eigensolve, then the k-side vertex
+  launch_phases(nk, k, m->nRe, m->Re, m->rmax, p.PkRM, p.PkT, nullptr, st);
+  launch_fourier_d(nk, m->nRe, p.PkT, m->Hw, (int)nw2, p.Hk, st);
+  launch_eigh_d(nk, nw, p.Hk, p.epsk, p.Uk, m->dstatus, st);
   if (need_B && nk > 0) {
     const int ncol = m->nRp * nm * (int)nw2;
     if (prec == EPW_FP64) {
@@ -399,6 +430,10 @@ static epw_status run_prep(const epw_model *m, int nk, const double *k, int nq, 
                           false, st);
       launch_build_B<float>(m, nk, p.PkRM, (const cx<float> *)p.G1, p.Uk, (cx<float> *)p.Bg, (cx<float> *)p.BH, st);
     }
+  }
+  if (fork) {
+    CK(cudaEventRecord(m->ev_join, sq));
+    CK(cudaStreamWaitEvent(st, m->ev_join, 0));
   }
   CK(cudaGetLastError());
   return EPW_OK;
@@ -548,12 +583,14 @@ epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, c
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
     L.tc.Cpol = m->polar ? (const float2 *)p.Cpol : nullptr;
     L.tc.Uk64 = p.Uk;
+    L.tc.Pq64 = m->same_eph ? p.PqTph : nullptr;
     epw_status s = tc_linewidth(m, nk, kd, nq, qd, wqd, par, p.PkRM, p.epsk, p.Uk, p.omegaT, (const cx<float> *)p.ET,
                                 (const cx<float> *)p.Bg, (const cx<float> *)p.BH, L.tc, out, st);
     if (s != EPW_OK) return fail(s, "tensor-core path: %s", g_err[0] ? g_err : "unsupported shape");
   } else if (tcp) {
     // staged tensor-core form: contraction per chunk of k on the tensor cores, per-pair work from HBM
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
+    L.sg.Pq64 = m->same_eph ? p.PqTph : nullptr;
     CKS(tc_staged_phases(m, nq, qd, L.sg, st));
     epw_timing_begin(m, st);
     for (int k0 = 0; k0 < nk; k0 += L.sg.kc) {
@@ -680,10 +717,12 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
   if (tc && nk > 0 && nq > 0 && (ekqd || gd)) {
     tcb.Cpol = m->polar ? (const float2 *)p.Cpol : nullptr;
     tcb.Uk64 = p.Uk;
+    tcb.Pq64 = m->same_eph ? p.PqTph : nullptr;
     epw_status s = tc_interp(m, nk, nq, qd, omega_min, p.epsk, p.omegaT, (const cx<float> *)p.ET,
                              (const cx<float> *)p.Bg, (const cx<float> *)p.BH, tcb, ekqd, gd, st);
     if (s != EPW_OK) return fail(s, "tensor-core interpolation failed");
   } else if (staged && nk > 0 && nq > 0 && (ekqd || gd)) {
+    sg.Pq64 = m->same_eph ? p.PqTph : nullptr;
     CKS(tc_staged_phases(m, nq, qd, sg, st));
     for (int k0 = 0; k0 < nk; k0 += sg.kc) {
       const int kc = std::min(sg.kc, nk - k0);
@@ -837,12 +876,14 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
     b.tc.Cpol = m->polar ? (const float2 *)p.Cpol : nullptr;
     b.tc.Uk64 = p.Uk;
+    b.tc.Pq64 = m->same_eph ? p.PqTph : nullptr;
     epw_status s = tc_linewidth_backward(m, nk, nq, qd, wqd, par, p.epsk, p.Uk, p.Pk32, p.omegaT,
                                          (const cx<float> *)p.ET, (const cx<float> *)p.Bg, (const cx<float> *)p.BH,
                                          b.cotd, b.tc, b.tw, (cx<float> *)b.gwbar, b.sc, st);
     if (s != EPW_OK) return fail(s, "tensor-core adjoint failed");
   } else if (nk > 0 && nq > 0) {
     CKS(run_prep(m, nk, kd, nq, qd, prec, par->omega_min_eV, true, p, nullptr, st));
+    b.sg.Pq64 = m->same_eph ? p.PqTph : nullptr;
     if (staged) CKS(tc_staged_phases(m, nq, qd, b.sg, st));
     for (int k0 = 0; k0 < nk; k0 += nkc) {
       const int kc = std::min(nkc, nk - k0);
@@ -1008,7 +1049,7 @@ extern "C" epw_status epw_phonon_selfenergy(const epw_model *mc, int nk, const d
     CKS(run_prep(m, nk, kd, nq, qd, wprec, par->omega_min_eV, true, p, nullptr, st));
   } else if (nk > 0) {
     // bands at k only (N(E_F))
-    launch_phases(nk, kd, m->nRe, m->Re, p.PkRM, p.PkT, nullptr, st);
+    launch_phases(nk, kd, m->nRe, m->Re, m->rmax, p.PkRM, p.PkT, nullptr, st);
     launch_fourier_d(nk, m->nRe, p.PkT, m->Hw, m->nw * m->nw, p.Hk, st);
     launch_eigh_d(nk, m->nw, p.Hk, p.epsk, p.Uk, m->dstatus, st);
   }
@@ -1042,6 +1083,7 @@ extern "C" epw_status epw_phonon_selfenergy(const epw_model *mc, int nk, const d
     a.Uk = p.Uk;
     a.nkc = kper;
     if (tcp) {
+      b.sg.Pq64 = m->same_eph ? p.PqTph : nullptr;
       CKS(tc_staged_phases(m, nq, qd, b.sg, st));
       int chunk0 = 0;
       for (int k0 = 0; k0 < nk; k0 += b.sg.kc) {
@@ -1150,6 +1192,7 @@ extern "C" epw_status epw_selfenergy(const epw_model *mc, int nk, const double *
     if (b.specd) CK(cudaMemsetAsync(b.specd, 0, nout * sizeof(double), st));
   } else {
     CKS(run_prep(m, nk, kd, nq, qd, wprec, par->omega_min_eV, true, p, nullptr, st));
+    b.sg.Pq64 = m->same_eph ? p.PqTph : nullptr;
     if (tcp) CKS(tc_staged_phases(m, nq, qd, b.sg, st));
     PairArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -1194,6 +1237,33 @@ extern "C" epw_status epw_selfenergy(const epw_model *mc, int nk, const double *
   if (ssig) CK(cudaMemcpyAsync(sigma, b.sigd, nout * sizeof(double2), cudaMemcpyDeviceToHost, st));
   if (ssp) CK(cudaMemcpyAsync(spectral, b.specd, nout * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (sk || sq || swq || som || ssig || ssp) return read_status(m, st);
+  return EPW_OK;
+}
+
+// ---------------------------------------------------- failure-path self-test
+extern "C" epw_status epw_selftest_wait_timeout(long long cycles, int *waited_out) {
+  g_err[0] = 0;
+  if (cycles < 1 || cycles > 4000000000LL) return fail(EPW_ERR_INVALID_ARG, "cycles must be in [1, 4e9]");
+  struct D {
+    unsigned st[4];
+    int w;
+  };
+  D *d = nullptr;
+  CK(cudaMalloc((void **)&d, sizeof(D)));
+  epw_status s = EPW_OK;
+  cudaError_t e = cudaMemset(d, 0, sizeof(D));
+  if (e == cudaSuccess) {
+    s = tc_wait_selftest(cycles, d->st, &d->w, 0);
+    e = cudaDeviceSynchronize();
+  }
+  D h;
+  std::memset(&h, 0, sizeof(h));
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(D), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(EPW_ERR_CUDA, "self-test: %s", cudaGetErrorString(e));
+  if (s != EPW_OK) return fail(s, "self-test launch failed");
+  if (waited_out) *waited_out = h.w;
+  if (h.st[0] & EPW_DEV_TIMEOUT) return fail(EPW_ERR_TIMEOUT, "the bounded wait ran out (expected)");
   return EPW_OK;
 }
 
@@ -1290,7 +1360,7 @@ extern "C" epw_status epw_linewidth_noalloc(const epw_model *mc, int nk, const d
   A = Arena{scratch, (size_t)EPW_NOALLOC_SCRATCH_BYTES, 0};
   CKS(plan_linewidth(A, m, nk, nq, prec, false, false, false, false, L));
   Prep &p = L.p;
-  CKS(run_prep(m, nk, k, nq, q, prec, par->omega_min_eV, true, p, nullptr, st));
+  CKS(run_prep(m, nk, k, nq, q, prec, par->omega_min_eV, true, p, nullptr, st, /*fork=*/false));
   PairArgs a;
   std::memset(&a, 0, sizeof(a));
   a.nk = nk;

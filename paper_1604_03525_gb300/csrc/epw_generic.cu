@@ -36,6 +36,36 @@ __global__ void k_phases(int npt, const double *__restrict__ x, int nR, const in
   }
 }
 
+// The same phases from one-axis factors: e^{2 pi i x.R} = prod_j e^{2 pi i (x_j R_j mod 1)},
+// the factors for R_j in [-PH_RMAX, PH_RMAX] formed once per point (FP64 argument
+// reduction, sincospi), then two complex products per R.  One thread per point.
+constexpr int PH_RMAX = 8;
+__global__ void k_phases_fact(int npt, const double *__restrict__ x, int nR, const int *__restrict__ R,
+                              cx<double> *rowmajor, cx<double> *T64, cx<float> *T32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npt) return;
+  cx<double> F[3][2 * PH_RMAX + 1];
+  for (int j = 0; j < 3; j++) {
+    const double xj = x[3 * i + j];
+    for (int n = -PH_RMAX; n <= PH_RMAX; n++) {
+      double a = xj * n;
+      a -= rint(a);
+      double s, c;
+      sincospi(2.0 * a, &s, &c);
+      F[j][n + PH_RMAX] = mkc(c, s);
+    }
+  }
+  for (int r = 0; r < nR; r++) {
+    const cx<double> f0 = F[0][R[3 * r] + PH_RMAX], f1 = F[1][R[3 * r + 1] + PH_RMAX], f2 = F[2][R[3 * r + 2] + PH_RMAX];
+    const cx<double> f01 = mkc(f0.x * f1.x - f0.y * f1.y, f0.x * f1.y + f0.y * f1.x);
+    const cx<double> p = mkc(f01.x * f2.x - f01.y * f2.y, f01.x * f2.y + f01.y * f2.x);
+    if (rowmajor) rowmajor[(size_t)i * nR + r] = p;
+    const size_t idx = (size_t)r * npt + i;
+    if (T64) T64[idx] = p;
+    if (T32) T32[idx] = mkc((float)p.x, (float)p.y);
+  }
+}
+
 // out[i][e] = sum_r PT[r][i] X[r][e]   (PT transposed phases [nR][npt])
 __global__ void k_fourier_d(int npt, int nR, const cx<double> *__restrict__ PT, const cx<double> *__restrict__ X,
                             int msize, cx<double> *out) {
@@ -900,11 +930,14 @@ __global__ void k_dg_scale(int nRe, int nRp, size_t per, const double *__restric
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-void launch_phases(int npt, const double *x, int nR, const int *R, cx<double> *rm, cx<double> *T64, cx<float> *T32,
-                   cudaStream_t st) {
+void launch_phases(int npt, const double *x, int nR, const int *R, int rmax, cx<double> *rm, cx<double> *T64,
+                   cx<float> *T32, cudaStream_t st) {
   size_t n = (size_t)npt * nR;
   if (!n) return;
-  k_phases<<<nblocks(n, 256), 256, 0, st>>>(npt, x, nR, R, rm, T64, T32);
+  if (rmax <= PH_RMAX && nR >= 2 * (2 * PH_RMAX + 1))
+    k_phases_fact<<<(npt + 127) / 128, 128, 0, st>>>(npt, x, nR, R, rm, T64, T32);
+  else
+    k_phases<<<nblocks(n, 256), 256, 0, st>>>(npt, x, nR, R, rm, T64, T32);
   epw_count_launch();
 }
 

@@ -296,6 +296,7 @@ struct epw_model {
   int nw, nat, nm;
   int nRe, nRp, nRph;
   int same_ep, same_eph;  // R sets identical (Re==Rp, Re==Rph)
+  int rmax;               // largest |R component| over the three sets
   int *Re, *Rp, *Rph;     // [n][3]
   double *wRe, *wRp;      // [n]
   cx<double> *Hw;         // [nRe][nw][nw], wRe folded
@@ -309,6 +310,9 @@ struct epw_model {
   int timing;
   int nev;
   cudaEvent_t *ev;        // [2 * EPW_MAX_TIMED]
+  // second stream for the q side of the preparation, and its fork / join events
+  cudaStream_t aux;
+  cudaEvent_t ev_fork, ev_join;
   // long-range (polar) part of the vertex (epw_set_polar); polar == 0: none
   int polar;
   double pb[9];           // reciprocal vectors b_i (rows), 2 pi (A^{-1})^T
@@ -342,8 +346,9 @@ void epw_count_launch();
 
 // ------------------------------------------------------------- kernels
 // Generic SIMT path (epw_generic.cu)
-void launch_phases(int npt, const double *x, int nR, const int *R, cx<double> *out_rowmajor, cx<double> *out_T,
-                   cx<float> *out_T32, cudaStream_t st);
+// rmax: the largest |R component| of the set (one-axis factors when small)
+void launch_phases(int npt, const double *x, int nR, const int *R, int rmax, cx<double> *out_rowmajor,
+                   cx<double> *out_T, cx<float> *out_T32, cudaStream_t st);
 void launch_fourier_d(int npt, int nR, const cx<double> *P, const cx<double> *X, int msize, cx<double> *out,
                       cudaStream_t st);
 void launch_eigh_d(int nmat, int n, cx<double> *A, double *w, cx<double> *V, unsigned *dstatus, cudaStream_t st);

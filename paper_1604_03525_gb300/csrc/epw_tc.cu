@@ -209,14 +209,15 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 }
 
 // Bounded wait on an mbarrier phase.  Returns false on abort or timeout.
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag, unsigned *dstatus) {
+__device__ __forceinline__ bool wait_bar_limit(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                               unsigned *dstatus, long long limit) {
   if (mbar_try(bar, parity)) return true;
   long long t0 = clock64();
   uint32_t it = 0;
   while (!mbar_try(bar, parity)) {
     if ((++it & 127u) == 0) {
       if (*abort_flag) return false;
-      if (clock64() - t0 > WAIT_CYCLES) {
+      if (clock64() - t0 > limit) {
         *abort_flag = 1;
         atomicOr(dstatus, EPW_DEV_TIMEOUT);
         return false;
@@ -224,6 +225,24 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
     }
   }
   return true;
+}
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag, unsigned *dstatus) {
+  return wait_bar_limit(bar, parity, abort_flag, dstatus, WAIT_CYCLES);
+}
+
+// Self-test of the failure path: one thread waits, with the kernels' bounded
+// wait, on an mbarrier that nothing arrives at; after `limit` cycles the wait
+// raises EPW_DEV_TIMEOUT in dstatus and returns, and the kernel exits.
+__global__ void k_wait_selftest(long long limit, unsigned *dstatus, int *waited_out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_sh;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    volatile int *ab = &abort_sh;
+    *waited_out = wait_bar_limit(smem_u32(&bar), 0, ab, dstatus, limit) ? 0 : 1;
+  }
 }
 // Bounded wait that ignores the abort flag (used to drain in-flight work).
 __device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity) {
@@ -1096,6 +1115,37 @@ __global__ void k_build_a(int nq, int nR, int kpad, const double *__restrict__ q
   }
 }
 
+// The same A operand from the FP64 q phases P [nR][nq] already formed for the
+// phonons (same R set): a 32 x 32 tile transpose, no trigonometry.  Columns
+// kk >= 2 nR (padding) are written by k_a_pad.
+template <typename T>
+__global__ void k_build_a_from(int nq, int nR, int kpad, const cx<double> *__restrict__ P, T *hi, T *lo) {
+  __shared__ cx<double> tile[32][33];
+  const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int r = r0 + j, q = q0 + threadIdx.x;
+    tile[j][threadIdx.x] = (r < nR && q < nq) ? P[(size_t)r * nq + q] : mkc(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int q = q0 + j;
+    if (q >= nq) continue;
+    for (int u = threadIdx.x; u < 64; u += 32) {
+      const int rl = u >> 1, t = u & 1, r = r0 + rl;
+      if (r >= nR) continue;
+      const cx<double> v = tile[rl][j];
+      split_store<T>(t ? v.y : v.x, hi, lo, (size_t)q * kpad + 2 * (nR - 1 - r) + t);
+    }
+  }
+}
+template <typename T>
+__global__ void k_a_pad(int nq, int k0, int kpad, T *hi, T *lo) {
+  const int w = kpad - k0;
+  const size_t n = (size_t)nq * w;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    split_store<T>(0.0, hi, lo, (i / w) * kpad + k0 + i % w);
+}
+
 // B[k][col][kk] (K-major hi/lo) of the real GEMM:
 //   col = 2c + s (s: re/im of output column c), kk = 2r + t (t: re/im of P_q(R_r)),
 //   (s,t) = (0,0): Re b, (0,1): -Im b, (1,0): Im b, (1,1): Re b,  b = B_k[r][c].
@@ -1146,6 +1196,26 @@ __global__ void k_tc_tables(int nq, int nm, int nk, int nw, const double *__rest
 inline int grid_for(size_t n, int bs) {
   size_t b = (n + bs - 1) / bs;
   return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+// A operand (q phases, split): from the FP64 phases when they exist, else computed here.
+template <typename T>
+void build_a(int nq, int nR, int kpad, const double *q, const int *R, const cx<double> *P64, T *hi, T *lo,
+             cudaStream_t st) {
+  if (P64) {
+    dim3 grid((nq + 31) / 32, (nR + 31) / 32);
+    k_build_a_from<T><<<grid, dim3(32, 8), 0, st>>>(nq, nR, kpad, P64, hi, lo);
+    epw_count_launch();
+    if (kpad > 2 * nR) {
+      const size_t n = (size_t)nq * (kpad - 2 * nR);
+      k_a_pad<T><<<grid_for(n, 256), 256, 0, st>>>(nq, 2 * nR, kpad, hi, lo);
+      epw_count_launch();
+    }
+  } else {
+    const size_t n = (size_t)nq * kpad;
+    k_build_a<T><<<grid_for(n, 256), 256, 0, st>>>(nq, nR, kpad, q, R, hi, lo);
+    epw_count_launch();
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1256,14 +1326,11 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
   const int op = b.op;
   const int esz = op == TC_OP_BF16 ? 2 : 4;
   {
-    size_t n = (size_t)nq * b.kpad;
     if (op == TC_OP_BF16)
-      k_build_a<__nv_bfloat16><<<grid_for(n, 256), 256, 0, st>>>(nq, nR, b.kpad, q, m->Re, (__nv_bfloat16 *)b.Ahi,
-                                                                  (__nv_bfloat16 *)b.Alo);
+      build_a<__nv_bfloat16>(nq, nR, b.kpad, q, m->Re, b.Pq64, (__nv_bfloat16 *)b.Ahi, (__nv_bfloat16 *)b.Alo, st);
     else
-      k_build_a<float><<<grid_for(n, 256), 256, 0, st>>>(nq, nR, b.kpad, q, m->Re, (float *)b.Ahi, (float *)b.Alo);
-    epw_count_launch();
-    n = (size_t)b.nk_pad * b.cpk * b.kpad;
+      build_a<float>(nq, nR, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
+    size_t n = (size_t)b.nk_pad * b.cpk * b.kpad;
     if (op == TC_OP_BF16)
       k_build_b<__nv_bfloat16><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, BH32,
                                                                   Bg32, (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo);
@@ -1686,10 +1753,8 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
   const int nR = m->nRe, nw = m->nw, nc = w.nc;
   // forward operands (tf32 split), epilogue tables, conj-phase operand, cotangent table
   {
-    size_t n = (size_t)nq * b.kpad;
-    k_build_a<float><<<grid_for(n, 256), 256, 0, st>>>(nq, nR, b.kpad, q, m->Re, (float *)b.Ahi, (float *)b.Alo);
-    epw_count_launch();
-    n = (size_t)b.nk_pad * b.cpk * b.kpad;
+    build_a<float>(nq, nR, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
+    size_t n = (size_t)b.nk_pad * b.cpk * b.kpad;
     k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, nw, m->nm, b.cpk, b.kpad, BH32, Bg32,
                                                         (float *)b.Bhi, (float *)b.Blo);
     epw_count_launch();
@@ -1839,13 +1904,10 @@ epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, 
 
 epw_status tc_staged_phases(const epw_model *m, int nq, const double *q, TcStaged &s, cudaStream_t st) {
   if (!s.ok) return EPW_ERR_UNSUPPORTED;
-  const size_t n = (size_t)nq * s.kpad;
   if (s.op == TC_OP_BF16)
-    k_build_a<__nv_bfloat16><<<grid_for(n, 256), 256, 0, st>>>(nq, m->nRe, s.kpad, q, m->Re,
-                                                                (__nv_bfloat16 *)s.Ahi, (__nv_bfloat16 *)s.Alo);
+    build_a<__nv_bfloat16>(nq, m->nRe, s.kpad, q, m->Re, s.Pq64, (__nv_bfloat16 *)s.Ahi, (__nv_bfloat16 *)s.Alo, st);
   else
-    k_build_a<float><<<grid_for(n, 256), 256, 0, st>>>(nq, m->nRe, s.kpad, q, m->Re, (float *)s.Ahi, (float *)s.Alo);
-  epw_count_launch();
+    build_a<float>(nq, m->nRe, s.kpad, q, m->Re, s.Pq64, (float *)s.Ahi, (float *)s.Alo, st);
   return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
 }
 
@@ -1902,6 +1964,13 @@ epw_status tc_staged_contract(const epw_model *m, int k0, int kc, int nq, const 
     }
     k_tc_gemm_nt<TC_OP_TF32><<<std::min(items, sms), G_THREADS, G_SMEM, st>>>(ah, al, bh_m, bl_m, g);
   }
+  epw_count_launch();
+  return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
+}
+
+epw_status tc_wait_selftest(long long cycles, unsigned *dstatus, int *waited_out, cudaStream_t st) {
+  if (cycles < 1 || cycles > 4000000000LL) return EPW_ERR_INVALID_ARG;
+  k_wait_selftest<<<1, 32, 0, st>>>(cycles, dstatus, waited_out);
   epw_count_launch();
   return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
 }

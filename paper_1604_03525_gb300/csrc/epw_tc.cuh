@@ -21,6 +21,7 @@ struct TcBuffers {
   const float2 *Cpol;        // [nm][nq]
   const cx<double> *Uk64;    // [nk][nw][nw]
   float2 *UkF;               // FP32 copy of Uk64
+  const cx<double> *Pq64;    // FP64 q phases of the Re set [nR][nq] when already formed (else null)
 };
 
 // True when the model's shape has a tensor-core kernel (Re == Rp sets and a
@@ -80,6 +81,7 @@ struct TcStaged {
   bool ok;
   bool qmajor;      // layout read by the warp-per-pair kernel (nw > 8 or 3nat > 9)
   size_t ldn;
+  const cx<double> *Pq64;  // FP64 q phases of the Re set [nR][nq] when already formed (else null)
   // leading dimension for the per-pair kernel's reads
   size_t pair_ld() const { return qmajor ? ldn : (size_t)ldc; }
 };
@@ -93,3 +95,7 @@ epw_status tc_staged_phases(const epw_model *m, int nq, const double *q, TcStage
 // Contraction of k-points [k0, k0 + kc) into s.Ct.
 epw_status tc_staged_contract(const epw_model *m, int k0, int kc, int nq, const cx<float> *Bg32,
                               const cx<float> *BH32, TcStaged &s, cudaStream_t st);
+
+// One bounded mbarrier wait, on a barrier nothing arrives at, for `cycles` clock cycles
+// (the kernels' wait with a short limit): sets EPW_DEV_TIMEOUT in dstatus and *waited_out = 1.
+epw_status tc_wait_selftest(long long cycles, unsigned *dstatus, int *waited_out, cudaStream_t st);

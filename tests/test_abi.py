@@ -77,6 +77,11 @@ def test_struct_layouts_match_header(tmp_path):
                      J.params.offset, J.imsigma.offset, ctypes.sizeof(_lib.PolarDesc), _lib.PolarDesc.gmax.offset]
 
 
+def test_selftest_arguments_rejected_without_gpu_work(lib):
+    assert lib.epw_selftest_wait_timeout(0, None) == 1
+    assert lib.epw_selftest_wait_timeout(5000000000, None) == 1
+
+
 def test_batch_arguments_rejected_without_gpu_work(lib):
     h = ctypes.c_void_p()
     assert lib.epw_batch_create(-1, None, ctypes.byref(h)) == 1
