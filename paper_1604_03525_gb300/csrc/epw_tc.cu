@@ -186,6 +186,16 @@ __device__ __forceinline__ void tmem_load(uint32_t taddr, float (&r)[NCOL]) {
   }
 }
 
+// Asynchronous global -> shared copies (no register round trip); wait_all
+// completes every copy this thread has issued.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(__cvta_generic_to_global(src)) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(__cvta_generic_to_global(src)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // K-major, 128-byte-swizzled smem operand: rows of 128 B, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
@@ -354,27 +364,27 @@ struct RotR {
   float c, s, tb;
 };
 
-// Rotation of the (p,q) plane of a real symmetric matrix zeroing a_pq:
-// t = 2 a_pq sgn(d) / (|d| + sqrt(d^2 + 4 a_pq^2)), d = a_qq - a_pp, c = 1/sqrt(1+t^2), s = t c;
-// a_pp -= t a_pq, a_qq += t a_pq (the real case of the complex rotation above).
+// Rotation of the (p,q) plane of a real symmetric matrix zeroing a_pq, from the
+// half-angle formulas: d = a_qq - a_pp, r = sqrt(d^2 + 4 a_pq^2), cos 2t = |d|/r
+// (1 when r = 0), c^2 = (1 + cos 2t)/2, s = sgn(d) a_pq/(r c) (= sin 2t/(2c)), and
+// the diagonal moves by t a_pq = sgn(d) a_pq^2/(r c^2): a_pp -= t a_pq, a_qq += t a_pq.
+// (The same rotation as t = 2 a_pq sgn(d)/(|d| + r), c = 1/sqrt(1+t^2), s = t c,
+// with two reciprocal square roots and no division.)
 __device__ __forceinline__ RotR rotr_params(float app, float aqq, float apq) {
   const float d = aqq - app;
   const float x = fmaf(d, d, 4.0f * apq * apq);
   const float xs = fmaxf(x, 1e-37f);
   float ri = rsqrt_approx(xs);
-  ri = ri * fmaf(-0.5f * xs * ri, ri, 1.5f);
-  const float sq = x * ri;
-  const float den = fmaxf(fabsf(d) + sq, 1e-30f);
-  float rden = rcp_approx(den);
-  rden = rden * fmaf(-den, rden, 2.0f);
-  const float t = (d >= 0.0f ? 2.0f : -2.0f) * apq * rden;
-  const float u = fmaf(t, t, 1.0f);
-  float c = rsqrt_approx(u);
-  c = c * fmaf(-0.5f * u * c, c, 1.5f);
+  ri = ri * fmaf(-0.5f * xs * ri, ri, 1.5f);  // 1/r
+  const float cos2 = x > 0.0f ? fabsf(d) * ri : 1.0f;
+  const float u = fmaf(0.5f, cos2, 0.5f);      // c^2, in [1/2, 1]
+  float ru = rsqrt_approx(u);
+  ru = ru * fmaf(-0.5f * u * ru, ru, 1.5f);    // 1/c
+  const float sa = (d >= 0.0f ? apq : -apq) * ri;  // sin 2t / 2
   RotR r;
-  r.c = c;
-  r.s = t * c;
-  r.tb = t * apq;
+  r.c = u * ru;
+  r.s = sa * ru;
+  r.tb = sa * apq * (ru * ru);
   return r;
 }
 
@@ -393,11 +403,14 @@ __device__ __forceinline__ void rotr_apply(float (&S)[4][4], cx<float> (&V)[4][4
     skp = r.c * a - r.s * b;
     skq = fmaf(r.s, a, r.c * b);
   }
+  // eigenvector columns: (re, im) of each entry as one packed pair
+  const float2 c2 = make_float2(r.c, r.c), s2 = make_float2(r.s, r.s), ns2 = make_float2(-r.s, -r.s);
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    const cx<float> vp = V[k][P], vq = V[k][Q];
-    V[k][P] = mkc(r.c * vp.x - r.s * vq.x, r.c * vp.y - r.s * vq.y);
-    V[k][Q] = mkc(fmaf(r.s, vp.x, r.c * vq.x), fmaf(r.s, vp.y, r.c * vq.y));
+    const float2 vp = make_float2(V[k][P].x, V[k][P].y), vq = make_float2(V[k][Q].x, V[k][Q].y);
+    const float2 np = __ffma2_rn(ns2, vq, __fmul2_rn(c2, vp)), nq = __ffma2_rn(s2, vp, __fmul2_rn(c2, vq));
+    V[k][P] = mkc(np.x, np.y);
+    V[k][Q] = mkc(nq.x, nq.y);
   }
 }
 
@@ -643,9 +656,21 @@ struct Shape {
   static constexpr int KPS = 128 / CPK;  // k per slot (per epilogue warp)
   static constexpr int KPT = 2 * KPS;    // k per tile
   static constexpr int H2 = 2 * NW * NW; // real columns of one NW x NW complex block
+  // planar column pairs (k_build_b): shapes that fill the 128-column slot with an even NW
+  static constexpr bool PLANAR = (NW % 2 == 0) && (CPK == 128);
   static_assert(CPK_RAW <= 128, "one k must fit in a 128-column slot");
   static_assert(CPK <= 32 || H2 == 32, "wide shapes read 32-column blocks");
 };
+
+// Shared memory after the operand stages holding the per-q tables of the packed
+// linewidth epilogue, one column per epilogue thread: E [nm*nm][256] float2,
+// w [nm][256], n [nm][256] floats.  Copied in with cp.async when a pair starts,
+// read after its eigensolve.
+constexpr int NEPI_THREADS = NEPI_WARPS * 32;
+template <int NW, int NM, int MODE>
+constexpr int tab_bytes() {
+  return (MODE == 0 && Shape<NW, NM>::PLANAR) ? NEPI_THREADS * (NM * NM * 8 + 2 * NM * 4) : 0;
+}
 
 // Tile -> (k group, q tile) in q-blocks of `qblock` tiles, k-group-major inside a block.
 __device__ __forceinline__ void item_coords(const TcArgs &a, int item, int &kg, int &qt) {
@@ -659,6 +684,143 @@ __device__ __forceinline__ void item_coords(const TcArgs &a, int item, int &kg, 
   qt = b * a.qblock + r % qbs;
 }
 
+// Real column of the re (s = 0) or im (s = 1) part of complex column c of one
+// NW x NW block of the accumulator (planar pairs: see k_build_b).
+template <bool PLANAR>
+__device__ __forceinline__ int ccol(int c, int s) {
+  return PLANAR ? 4 * (c >> 1) + 2 * s + (c & 1) : 2 * c + s;
+}
+
+// packed FP32 (two lanes per instruction)
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Linewidth terms of Eq. (linewidthel) for one pair from planar accumulator
+// columns (NW even).  Entries (i, j) and (i, j+1) of a block travel as one
+// float2 of real parts and one of imaginary parts, so the mode projection
+// G_nu = sum_a E[a][nu] X_a, the rotation y_nu = U_k+q^dagger G_nu, |y|^2 and
+// the Gaussian arguments each handle two n columns per packed instruction.
+// The Gaussian argument is formed as -(x s)^2 with s = sqrt(log2 e)/sigma, so
+// that exp(-(x/sigma)^2) = 2^(-(x s)^2).
+template <int NW, int NM>
+__device__ __forceinline__ void tables_prefetch(const TcArgs &a, int qq, float *tab) {
+  const int te = threadIdx.x - 32 * EPI_WARP0;
+  const uint32_t t0 = smem_u32(tab);
+#pragma unroll
+  for (int j = 0; j < NM * NM; j++) cp_async8(t0 + 8u * (j * NEPI_THREADS + te), a.ET + (size_t)j * a.nq + qq);
+  const uint32_t t1 = t0 + 8u * NM * NM * NEPI_THREADS;
+#pragma unroll
+  for (int nu = 0; nu < NM; nu++) {
+    cp_async4(t1 + 4u * (nu * NEPI_THREADS + te), a.omegaT + (size_t)nu * a.nq + qq);
+    cp_async4(t1 + 4u * ((NM + nu) * NEPI_THREADS + te), a.nbT + (size_t)nu * a.nq + qq);
+  }
+}
+
+template <int NW, int NM>
+__device__ __forceinline__ void modes_linewidth_packed(const TcArgs &a, uint32_t tcol, int qq, int kk,
+                                                       const float *tab, const cx<float> (&V)[NW][NW],
+                                                       const float (&em)[NW], const float (&fm)[NW],
+                                                       const float (&ek)[NW], float (&acc)[NW]) {
+  const int te = threadIdx.x - 32 * EPI_WARP0;
+  const float2 *tE = reinterpret_cast<const float2 *>(tab) + te;
+  const float *tW = tab + 2 * NM * NM * NEPI_THREADS + te;
+  cp_async_wait_all();
+  constexpr int NP = NW / 2;
+  constexpr int H2 = 2 * NW * NW;
+  const float sc = a.inv_sigma * 1.2011224087864498f;  // sqrt(log2 e) / sigma
+  float2 eks[NP], accp[NP];
+#pragma unroll
+  for (int p = 0; p < NP; p++) {
+    eks[p] = make_float2(ek[2 * p] * sc, ek[2 * p + 1] * sc);
+    accp[p] = make_float2(0.0f, 0.0f);
+  }
+#pragma unroll 1
+  for (int nu = 0; nu < NM; nu++) {
+    const float wnu = tW[nu * NEPI_THREADS];
+    const float nbnu = tW[(NM + nu) * NEPI_THREADS];
+    float2 E[NM];
+#pragma unroll
+    for (int al = 0; al < NM; al++) E[al] = tE[(al * NM + nu) * NEPI_THREADS];
+    const bool keep = (wnu >= a.omega_min) && (wnu > 0.0f);
+    // G_nu, planar: Gr[i][p] = Re (G_i,2p, G_i,2p+1), Gi[i][p] = Im (...)
+    float2 Gr[NW][NP], Gi[NW][NP];
+#pragma unroll
+    for (int al = 0; al < NM; al++) {
+      float x[H2];
+      tmem_load<H2>(tcol + H2 * (1 + al), x);
+      const float2 er = bc2(E[al].x), ei = bc2(E[al].y), nei = bc2(-E[al].y);
+#pragma unroll
+      for (int i = 0; i < NW; i++)
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          const int o = 4 * (i * NP + p);
+          const float2 xr = make_float2(x[o], x[o + 1]), xi = make_float2(x[o + 2], x[o + 3]);
+          if (al == 0) {
+            Gr[i][p] = ffma2(nei, xi, fmul2(er, xr));
+            Gi[i][p] = ffma2(ei, xr, fmul2(er, xi));
+          } else {
+            Gr[i][p] = ffma2(nei, xi, ffma2(er, xr, Gr[i][p]));
+            Gi[i][p] = ffma2(ei, xr, ffma2(er, xi, Gi[i][p]));
+          }
+        }
+    }
+    if (a.Cpol) {
+      // long-range part: G_nu += i C_nu(q) U_k
+      const float2 c = __ldg(a.Cpol + (size_t)nu * a.nq + qq);
+      const float2 *Uk = a.UkF + (size_t)kk * NW * NW;
+      const float2 ncy = bc2(-c.y), ncx = bc2(-c.x), cx2 = bc2(c.x);
+#pragma unroll
+      for (int i = 0; i < NW; i++)
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          const float2 u0 = __ldg(Uk + i * NW + 2 * p), u1 = __ldg(Uk + i * NW + 2 * p + 1);
+          const float2 ur = make_float2(u0.x, u1.x), ui = make_float2(u0.y, u1.y);
+          Gr[i][p] = ffma2(ncy, ur, ffma2(ncx, ui, Gr[i][p]));
+          Gi[i][p] = ffma2(cx2, ur, ffma2(ncy, ui, Gi[i][p]));
+        }
+    }
+    const float ws = wnu * sc;
+#pragma unroll
+    for (int m = 0; m < NW; m++) {
+      // y = (U^dagger G)_m,(2p, 2p+1)
+      float2 yr[NP], yi[NP];
+#pragma unroll
+      for (int i = 0; i < NW; i++) {
+        const float2 vr = bc2(V[i][m].x), vi = bc2(V[i][m].y), nvi = bc2(-V[i][m].y);
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          if (i == 0) {
+            yr[p] = ffma2(vi, Gi[i][p], fmul2(vr, Gr[i][p]));
+            yi[p] = ffma2(nvi, Gr[i][p], fmul2(vr, Gi[i][p]));
+          } else {
+            yr[p] = ffma2(vi, Gi[i][p], ffma2(vr, Gr[i][p], yr[p]));
+            yi[p] = ffma2(nvi, Gr[i][p], ffma2(vr, Gi[i][p], yi[p]));
+          }
+        }
+      }
+      const float2 cp = bc2(keep ? nbnu + fm[m] : 0.0f), cm = bc2(keep ? nbnu + 1.0f - fm[m] : 0.0f);
+      const float ems = em[m] * sc;
+      const float2 op = bc2(ws - ems), om = bc2(-ws - ems);  // x+- = e_nk - e_mk+q +- w, scaled
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        const float2 g2 = ffma2(yi[p], yi[p], fmul2(yr[p], yr[p]));
+        const float2 xp = fadd2(eks[p], op), xm = fadd2(eks[p], om);
+        const float2 tp = fmul2(xp, xp), tm = fmul2(xm, xm);
+        const float2 dp = make_float2(ex2_approx(-tp.x), ex2_approx(-tp.y));
+        const float2 dm = make_float2(ex2_approx(-tm.x), ex2_approx(-tm.y));
+        accp[p] = ffma2(g2, ffma2(cm, dm, fmul2(cp, dp)), accp[p]);
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; p++) {
+    acc[2 * p] = accp[p].x;
+    acc[2 * p + 1] = accp[p].y;
+  }
+}
+
 // ------------------------------------------------------------------ epilogue
 // One (k,q) pair per thread; the accumulator holds [H(k+q) | (g_a U_k)_a=0..NM-1].
 // MODE 0: linewidth terms summed over the warp's q rows; MODE 1: write e_k+q
@@ -668,11 +830,12 @@ __device__ __forceinline__ void item_coords(const TcArgs &a, int item, int &kg, 
 //   dL/dT, dL/dE_F through n(w, T) and f(e, T, E_F) (deltas hold neither).
 template <int NW, int NM, int MODE>
 __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, int q, int k, bool valid, int quad,
-                                              int qt) {
+                                              int qt, float *tab) {
   using S = Shape<NW, NM>;
   constexpr int H2 = S::H2;
   const int qq = q < a.nq ? q : 0;
   const int kk = k < a.nk ? k : 0;
+  if constexpr (MODE == 0 && S::PLANAR) tables_prefetch<NW, NM>(a, qq, tab);
   // per-q and per-k data first, so their latency overlaps the eigensolve
   float ek[NW];
 #pragma unroll
@@ -689,20 +852,21 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   } else {
     tmem_load<H2>(tcol, hb);
   }
+  constexpr bool PL = S::PLANAR;
   Herm<NW> H;
 #pragma unroll
   for (int i = 0; i < NW; i++)
 #pragma unroll
     for (int j = i; j < NW; j++) {
-      const int o = 2 * (i * NW + j);
-      const int o2 = 2 * (j * NW + i);
+      const int o = ccol<PL>(i * NW + j, 0), oi = ccol<PL>(i * NW + j, 1);
+      const int o2 = ccol<PL>(j * NW + i, 0), o2i = ccol<PL>(j * NW + i, 1);
       float re, im;
       if constexpr (ONE_LOAD) {
         re = 0.5f * (all[o] + all[o2]);
-        im = 0.5f * (all[o + 1] - all[o2 + 1]);
+        im = 0.5f * (all[oi] - all[o2i]);
       } else {
         re = 0.5f * (hb[o] + hb[o2]);
-        im = 0.5f * (hb[o + 1] - hb[o2 + 1]);
+        im = 0.5f * (hb[oi] - hb[o2i]);
       }
       H.a[i][j] = mkc(re, i == j ? 0.0f : im);
     }
@@ -755,6 +919,9 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
 #pragma unroll
         for (int j = 0; j < NW; j++) Xb[al][i][j] = mkc(0.0f, 0.0f);
   }
+  if constexpr (MODE == 0 && PL) {
+    modes_linewidth_packed<NW, NM>(a, tcol, qq, kk, tab, V, em, fm, ek, acc);
+  } else {
   // one mode per iteration (not unrolled: keeps the code within the instruction cache)
 #pragma unroll 1
   for (int nu = 0; nu < NM; nu++) {
@@ -788,7 +955,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
 #pragma unroll
         for (int i = 0; i < NW; i++)
 #pragma unroll
-          for (int j = 0; j < NW; j++) cfma(G[i][j], E[al], mkc(x[2 * (i * NW + j)], x[2 * (i * NW + j) + 1]));
+          for (int j = 0; j < NW; j++) cfma(G[i][j], E[al], mkc(x[ccol<PL>(i * NW + j, 0)], x[ccol<PL>(i * NW + j, 1)]));
       }
     }
 
@@ -869,6 +1036,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
         }
       }
     }
+  }
   }
   if constexpr (MODE == 2) {
     // Xbar rows (k, a, j, n), K index 2q + (re, im), split into two tf32 terms
@@ -1037,6 +1205,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // -------------------------------------------------------------- epilogue
     const int quad = warp & 3;
     const int slot = (warp - EPI_WARP0) >> 2;
+    float *tab = reinterpret_cast<float *>(smem_raw + (smem0 - smem_u32(smem_raw)) + STAGES * STAGE_BYTES);
     int titer = 0;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x, titer++) {
       const int ts = titer & 1;
@@ -1051,7 +1220,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll 1
       for (int j = 0; j < S::KPS; j++) {
         const int k = kg * S::KPT + slot * S::KPS + j;
-        epilogue_pair<NW, NM, MODE>(a, tbase + j * S::CPK, q, k, q < a.nq && k < a.nk, quad, qt);
+        epilogue_pair<NW, NM, MODE>(a, tbase + j * S::CPK, q, k, q < a.nq && k < a.nk, quad, qt, tab);
       }
       tc_fence_before();
       __syncwarp();
@@ -1150,8 +1319,11 @@ __global__ void k_a_pad(int nq, int k0, int kpad, T *hi, T *lo) {
 //   col = 2c + s (s: re/im of output column c), kk = 2r + t (t: re/im of P_q(R_r)),
 //   (s,t) = (0,0): Re b, (0,1): -Im b, (1,0): Im b, (1,1): Re b,  b = B_k[r][c].
 // Output columns c: [0, nw^2) H(k+q)_ij, then (a, j, n) of g_a(k,q) U_k.
+// planar != 0: columns in pairs, col = 4 (c/2) + 2s + c%2 (two real parts, then
+// the two imaginary parts of the neighbouring output columns c, c+1), so that
+// the epilogue reads one float2 of real parts and one of imaginary parts.
 template <typename T>
-__global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad,
+__global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad, int planar,
                           const cx<float> *__restrict__ BH, const cx<float> *__restrict__ Bg, T *hi, T *lo) {
   const int nw2 = nw * nw;
   const int nc = nw2 * (nm + 1);
@@ -1163,7 +1335,9 @@ __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, i
     int k = (int)(rest / cpk);
     float v = 0.0f;
     if (k < nk && col < 2 * nc && kk < 2 * nR) {
-      int c = col >> 1, s = col & 1, r = nR - 1 - (kk >> 1), t = kk & 1;
+      const int c = planar ? 2 * (col >> 2) + (col & 1) : col >> 1;
+      const int s = planar ? (col >> 1) & 1 : col & 1;
+      const int r = nR - 1 - (kk >> 1), t = kk & 1;
       cx<float> b = c < nw2 ? BH[((size_t)k * nR + r) * nw2 + c] : Bg[((size_t)k * nR + r) * nm * nw2 + (c - nw2)];
       v = s == 0 ? (t == 0 ? b.x : -b.y) : (t == 0 ? b.y : b.x);
     }
@@ -1245,12 +1419,13 @@ bool make_map(CUtensorMap *map, const void *base, int op, uint64_t inner, uint64
   return r == CUDA_SUCCESS;
 }
 
-bool shape_info(int nw, int nm, int &cpk, int &kpt) {
-#define EPW_TC_SHAPE(W, M)  \
-  if (nw == W && nm == M) { \
-    cpk = Shape<W, M>::CPK; \
-    kpt = Shape<W, M>::KPT; \
-    return true;            \
+bool shape_info(int nw, int nm, int &cpk, int &kpt, int &planar) {
+#define EPW_TC_SHAPE(W, M)                 \
+  if (nw == W && nm == M) {                \
+    cpk = Shape<W, M>::CPK;                \
+    kpt = Shape<W, M>::KPT;                \
+    planar = Shape<W, M>::PLANAR ? 1 : 0;  \
+    return true;                           \
   }
   EPW_TC_SHAPE(4, 3)
   EPW_TC_SHAPE(1, 3)
@@ -1265,7 +1440,8 @@ cudaError_t launch_tc(const CUtensorMap &ah, const CUtensorMap &al, const CUtens
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_linewidth<OP, NW, NM, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES + tab_bytes<NW, NM, MODE>());
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -1274,7 +1450,7 @@ cudaError_t launch_tc(const CUtensorMap &ah, const CUtensorMap &al, const CUtens
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int items = a.nkg * a.nqt;
   int grid = items < sms ? items : sms;
-  k_tc_linewidth<OP, NW, NM, MODE><<<grid, NTHREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
+  k_tc_linewidth<OP, NW, NM, MODE><<<grid, NTHREADS, SMEM_BYTES + tab_bytes<NW, NM, MODE>(), st>>>(ah, al, bh, bl, a);
   return cudaGetLastError();
 }
 
@@ -1290,14 +1466,14 @@ cudaError_t launch_tc_shape(int nw, int nm, const CUtensorMap &ah, const CUtenso
 }  // namespace
 
 bool tc_supported(const epw_model *m) {
-  int cpk, kpt;
-  return m->same_ep && shape_info(m->nw, m->nm, cpk, kpt);
+  int cpk, kpt, planar;
+  return m->same_ep && shape_info(m->nw, m->nm, cpk, kpt, planar);
 }
 
 epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffers &b) {
   b = TcBuffers{};
   b.op = op;
-  b.ok = m->same_ep && shape_info(m->nw, m->nm, b.cpk, b.kpt);
+  b.ok = m->same_ep && shape_info(m->nw, m->nm, b.cpk, b.kpt, b.planar);
   if (!b.ok) return EPW_OK;
   const int esz = op == TC_OP_BF16 ? 2 : 4;
   const int kal = op == TC_OP_BF16 ? 16 : 8;  // K per MMA
@@ -1332,10 +1508,12 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
       build_a<float>(nq, nR, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
     size_t n = (size_t)b.nk_pad * b.cpk * b.kpad;
     if (op == TC_OP_BF16)
-      k_build_b<__nv_bfloat16><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, BH32,
+      k_build_b<__nv_bfloat16><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad,
+                                                                  b.planar, BH32,
                                                                   Bg32, (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo);
     else
-      k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, BH32, Bg32,
+      k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, b.planar,
+                                                          BH32, Bg32,
                                                           (float *)b.Bhi, (float *)b.Blo);
     epw_count_launch();
     n = (size_t)nq * m->nm + nq + (size_t)nk * m->nw;
@@ -1755,7 +1933,8 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
   {
     build_a<float>(nq, nR, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
     size_t n = (size_t)b.nk_pad * b.cpk * b.kpad;
-    k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, nw, m->nm, b.cpk, b.kpad, BH32, Bg32,
+    k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, nw, m->nm, b.cpk, b.kpad, b.planar,
+                                                        BH32, Bg32,
                                                         (float *)b.Bhi, (float *)b.Blo);
     epw_count_launch();
     n = (size_t)nq * m->nm + nq + (size_t)nk * nw;
@@ -1918,10 +2097,10 @@ epw_status tc_staged_contract(const epw_model *m, int k0, int kc, int nq, const 
   const size_t nb = (size_t)kc * s.cpk * s.kpad;
   const cx<float> *bh = BH32 + (size_t)k0 * nR * nw2, *bg = Bg32 + (size_t)k0 * nR * m->nm * nw2;
   if (s.op == TC_OP_BF16)
-    k_build_b<__nv_bfloat16><<<grid_for(nb, 256), 256, 0, st>>>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, bh, bg,
+    k_build_b<__nv_bfloat16><<<grid_for(nb, 256), 256, 0, st>>>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, 0, bh, bg,
                                                                  (__nv_bfloat16 *)s.Bhi, (__nv_bfloat16 *)s.Blo);
   else
-    k_build_b<float><<<grid_for(nb, 256), 256, 0, st>>>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, bh, bg,
+    k_build_b<float><<<grid_for(nb, 256), 256, 0, st>>>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, 0, bh, bg,
                                                          (float *)s.Bhi, (float *)s.Blo);
   epw_count_launch();
   const int rows = kc * s.cpk;

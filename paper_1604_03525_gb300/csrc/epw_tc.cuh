@@ -15,6 +15,7 @@ struct TcBuffers {
   float *ekF;        // band energies at k [nk][nw]
   double *partial;   // [nk][4*nqt][nw]
   int op, kpad, cpk, nk_pad, nqt, kpt;
+  int planar;        // B columns in re/im pairs (see k_build_b)
   bool ok;           // shape has a tensor-core kernel
   size_t a_block_bytes;  // q-block of the A operand visited by all k groups (0: default)
   // long-range vertex (polar models): set by the caller before a call; UkF is laid out by tc_plan
