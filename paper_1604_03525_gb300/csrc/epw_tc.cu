@@ -16,10 +16,12 @@
 // projection with e_q / sqrt(2 M w), the U_k+q^dagger rotation, |g|^2, the
 // Gaussian deltas and occupations, summed over each warp's 32 q rows.
 //
-// CTA layout (persistent, one CTA per SM, 10 warps):
+// CTA layout (persistent, one CTA per SM):
 //   warp 0      TMA producer (A = q-phase tile, B = k-vertex tile, 2 stages)
 //   warp 1      TMEM allocator and MMA issuer (one elected thread)
-//   warps 2..9  epilogue: warp w reads TMEM lanes 32*(w%4).., k-slot (w-2)/4
+//   warps 2..   epilogue: warp w reads TMEM lanes 32*(w%4)..; the (tile, k slot)
+//               items of its lane quadrant are shared round-robin by the
+//               quadrant's warps (three in the linewidth form, two otherwise)
 // Tensor memory holds two accumulator stages of 256 columns (512 in total),
 // so the MMA of the next tile overlaps the epilogue of the current one.
 // Tiles are visited in q-blocks (so that a block of A stays in L2) and, inside
@@ -45,9 +47,15 @@ constexpr int A_BYTES = BM * ROWB;    // 16 KiB
 constexpr int B_BYTES = BN * ROWB;    // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr int NTHREADS = 320;
 constexpr int EPI_WARP0 = 2;
-constexpr int NEPI_WARPS = 8;
+constexpr int ITEMS_PER_TILE = 8;     // (lane quadrant, k slot) items per tile
+// Epilogue warps: the linewidth form runs three per lane quadrant (items taken
+// round-robin, so more warps hide each other's latency); the other forms two.
+constexpr int EPI_WARPS_LW = 12;
+template <int MODE>
+constexpr int epi_warps() { return MODE == 0 ? EPI_WARPS_LW : 8; }
+template <int MODE>
+constexpr int nthreads() { return 32 * (EPI_WARP0 + epi_warps<MODE>()); }
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 constexpr size_t A_BLOCK_BYTES = 48u << 20;      // q-block size target (A operand bytes)
@@ -191,10 +199,10 @@ __device__ __forceinline__ void tmem_load(uint32_t taddr, float (&r)[NCOL]) {
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(__cvta_generic_to_global(src)) : "memory");
 }
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(__cvta_generic_to_global(src)) : "memory");
-}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));
+}
 
 // K-major, 128-byte-swizzled smem operand: rows of 128 B, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
@@ -662,14 +670,14 @@ struct Shape {
   static_assert(CPK <= 32 || H2 == 32, "wide shapes read 32-column blocks");
 };
 
-// Shared memory after the operand stages holding the per-q tables of the packed
-// linewidth epilogue, one column per epilogue thread: E [nm*nm][256] float2,
-// w [nm][256], n [nm][256] floats.  Copied in with cp.async when a pair starts,
-// read after its eigensolve.
-constexpr int NEPI_THREADS = NEPI_WARPS * 32;
+// Per-q tables of the packed linewidth epilogue, fetched when a pair starts and
+// read after its eigensolve: the mode factors E are copied with cp.async into
+// shared memory after the operand stages, one column per epilogue thread
+// (E [nm*nm][NT] float2); w and n are prefetched into L1.
+constexpr int NEPI_THREADS = 32 * EPI_WARPS_LW;
 template <int NW, int NM, int MODE>
 constexpr int tab_bytes() {
-  return (MODE == 0 && Shape<NW, NM>::PLANAR) ? NEPI_THREADS * (NM * NM * 8 + 2 * NM * 4) : 0;
+  return (MODE == 0 && Shape<NW, NM>::PLANAR) ? NEPI_THREADS * NM * NM * 8 : 0;
 }
 
 // Tile -> (k group, q tile) in q-blocks of `qblock` tiles, k-group-major inside a block.
@@ -710,11 +718,10 @@ __device__ __forceinline__ void tables_prefetch(const TcArgs &a, int qq, float *
   const uint32_t t0 = smem_u32(tab);
 #pragma unroll
   for (int j = 0; j < NM * NM; j++) cp_async8(t0 + 8u * (j * NEPI_THREADS + te), a.ET + (size_t)j * a.nq + qq);
-  const uint32_t t1 = t0 + 8u * NM * NM * NEPI_THREADS;
 #pragma unroll
   for (int nu = 0; nu < NM; nu++) {
-    cp_async4(t1 + 4u * (nu * NEPI_THREADS + te), a.omegaT + (size_t)nu * a.nq + qq);
-    cp_async4(t1 + 4u * ((NM + nu) * NEPI_THREADS + te), a.nbT + (size_t)nu * a.nq + qq);
+    prefetch_l1(a.omegaT + (size_t)nu * a.nq + qq);
+    prefetch_l1(a.nbT + (size_t)nu * a.nq + qq);
   }
 }
 
@@ -725,7 +732,6 @@ __device__ __forceinline__ void modes_linewidth_packed(const TcArgs &a, uint32_t
                                                        const float (&ek)[NW], float (&acc)[NW]) {
   const int te = threadIdx.x - 32 * EPI_WARP0;
   const float2 *tE = reinterpret_cast<const float2 *>(tab) + te;
-  const float *tW = tab + 2 * NM * NM * NEPI_THREADS + te;
   cp_async_wait_all();
   constexpr int NP = NW / 2;
   constexpr int H2 = 2 * NW * NW;
@@ -738,8 +744,8 @@ __device__ __forceinline__ void modes_linewidth_packed(const TcArgs &a, uint32_t
   }
 #pragma unroll 1
   for (int nu = 0; nu < NM; nu++) {
-    const float wnu = tW[nu * NEPI_THREADS];
-    const float nbnu = tW[(NM + nu) * NEPI_THREADS];
+    const float wnu = __ldg(a.omegaT + (size_t)nu * a.nq + qq);
+    const float nbnu = __ldg(a.nbT + (size_t)nu * a.nq + qq);
     float2 E[NM];
 #pragma unroll
     for (int al = 0; al < NM; al++) E[al] = tE[(al * NM + nu) * NEPI_THREADS];
@@ -1079,7 +1085,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
 }
 
 template <int OP, int NW, int NM, int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(nthreads<MODE>(), 1)
     k_tc_linewidth(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                    const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcArgs a) {
   using S = Shape<NW, NM>;
@@ -1100,7 +1106,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int s = 0; s < 2; s++) {
       mbar_init(smem_u32(&bar_tfull[s]), 1);
-      mbar_init(smem_u32(&bar_tempty[s]), NEPI_WARPS);
+      mbar_init(smem_u32(&bar_tempty[s]), ITEMS_PER_TILE);
     }
     mbar_init(smem_u32(&bar_final), 1);
     abort_sh = 0;
@@ -1203,11 +1209,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
   } else {
     // -------------------------------------------------------------- epilogue
+    // Items of a lane quadrant: (tile titer, k slot) in order it = 2 titer + slot;
+    // the quadrant's NG warps take them round-robin.  A tile's accumulator is
+    // released once all ITEMS_PER_TILE items are done, so no warp can fall two
+    // phases behind a tensor-memory stage.
+    constexpr int NG = epi_warps<MODE>() / 4;
     const int quad = warp & 3;
-    const int slot = (warp - EPI_WARP0) >> 2;
+    const int widx = (warp - EPI_WARP0) >> 2;
     float *tab = reinterpret_cast<float *>(smem_raw + (smem0 - smem_u32(smem_raw)) + STAGES * STAGE_BYTES);
-    int titer = 0;
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x, titer++) {
+    for (int it = widx;; it += NG) {
+      const int titer = it >> 1, slot = it & 1;
+      const int item = blockIdx.x + titer * gridDim.x;
+      if (item >= nitems) break;
       const int ts = titer & 1;
       const uint32_t tpar = (titer >> 1) & 1;
       const bool ok = wait_bar(smem_u32(&bar_tfull[ts]), tpar, abort_flag, a.dstatus);
@@ -1450,7 +1463,8 @@ cudaError_t launch_tc(const CUtensorMap &ah, const CUtensorMap &al, const CUtens
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int items = a.nkg * a.nqt;
   int grid = items < sms ? items : sms;
-  k_tc_linewidth<OP, NW, NM, MODE><<<grid, NTHREADS, SMEM_BYTES + tab_bytes<NW, NM, MODE>(), st>>>(ah, al, bh, bl, a);
+  k_tc_linewidth<OP, NW, NM, MODE><<<grid, nthreads<MODE>(), SMEM_BYTES + tab_bytes<NW, NM, MODE>(), st>>>(ah, al, bh,
+                                                                                                   bl, a);
   return cudaGetLastError();
 }
 
