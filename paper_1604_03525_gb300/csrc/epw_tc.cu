@@ -439,6 +439,16 @@ __device__ __forceinline__ float rcp_nr(float x) {
   return r * fmaf(-x, r, 2.0f);
 }
 
+// Fermi-Dirac occupation as fermi_f, with the reciprocal from rcp.approx and one
+// Newton step instead of an IEEE division.
+__device__ __forceinline__ float fermi_fast(float d, float invkT) {
+  if (invkT <= 0.0f) return d < 0.0f ? 1.0f : (d > 0.0f ? 0.0f : 0.5f);
+  const float x = d * invkT;
+  const float t = __expf(-fabsf(x));
+  const float r = rcp_nr(1.0f + t);
+  return x > 0.0f ? t * r : r;
+}
+
 __device__ __forceinline__ Hh householder(cx<float> x0, float srest) {
   const float n0sq = cabs2(x0);
   const float tot = n0sq + srest;
@@ -905,7 +915,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
     }
   }
 #pragma unroll
-  for (int m = 0; m < NW; m++) fm[m] = fermi_f(em[m] - a.EF, a.invkT);
+  for (int m = 0; m < NW; m++) fm[m] = fermi_fast(em[m] - a.EF, a.invkT);
   float acc[NW];
 #pragma unroll
   for (int n = 0; n < NW; n++) acc[n] = 0.0f;
