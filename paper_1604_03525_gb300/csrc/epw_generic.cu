@@ -37,17 +37,18 @@ __global__ void k_phases(int npt, const double *__restrict__ x, int nR, const in
 }
 
 // The same phases from one-axis factors: e^{2 pi i x.R} = prod_j e^{2 pi i (x_j R_j mod 1)},
-// the factors for R_j in [-PH_RMAX, PH_RMAX] formed once per point (FP64 argument
-// reduction, sincospi), then two complex products per R.  One thread per point.
+// the factors for R_j in [-rmax, rmax] (rmax <= PH_RMAX, the largest |R_j| of the set)
+// formed once per point (FP64 argument reduction, sincospi), then two complex
+// products per R.  One thread per point.
 constexpr int PH_RMAX = 8;
-__global__ void k_phases_fact(int npt, const double *__restrict__ x, int nR, const int *__restrict__ R,
+__global__ void k_phases_fact(int npt, const double *__restrict__ x, int nR, const int *__restrict__ R, int rmax,
                               cx<double> *rowmajor, cx<double> *T64, cx<float> *T32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npt) return;
   cx<double> F[3][2 * PH_RMAX + 1];
   for (int j = 0; j < 3; j++) {
     const double xj = x[3 * i + j];
-    for (int n = -PH_RMAX; n <= PH_RMAX; n++) {
+    for (int n = -rmax; n <= rmax; n++) {
       double a = xj * n;
       a -= rint(a);
       double s, c;
@@ -935,7 +936,7 @@ void launch_phases(int npt, const double *x, int nR, const int *R, int rmax, cx<
   size_t n = (size_t)npt * nR;
   if (!n) return;
   if (rmax <= PH_RMAX && nR >= 2 * (2 * PH_RMAX + 1))
-    k_phases_fact<<<(npt + 127) / 128, 128, 0, st>>>(npt, x, nR, R, rm, T64, T32);
+    k_phases_fact<<<(npt + 127) / 128, 128, 0, st>>>(npt, x, nR, R, rmax < 0 ? 0 : rmax, rm, T64, T32);
   else
     k_phases<<<nblocks(n, 256), 256, 0, st>>>(npt, x, nR, R, rm, T64, T32);
   epw_count_launch();

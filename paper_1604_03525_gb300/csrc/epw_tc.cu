@@ -1345,27 +1345,53 @@ __global__ void k_a_pad(int nq, int k0, int kpad, T *hi, T *lo) {
 // planar != 0: columns in pairs, col = 4 (c/2) + 2s + c%2 (two real parts, then
 // the two imaginary parts of the neighbouring output columns c, c+1), so that
 // the epilogue reads one float2 of real parts and one of imaginary parts.
+// Built through a shared-memory tile: a block reads 32 output columns c x 32 R
+// vectors of B_k along c (coalesced) and writes the matching 64 real columns x 64
+// K entries along K (coalesced).  Rows k >= nk, columns c >= nc and K >= 2 nR are 0.
 template <typename T>
 __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad, int planar,
                           const cx<float> *__restrict__ BH, const cx<float> *__restrict__ Bg, T *hi, T *lo) {
+  __shared__ cx<float> tile[32][33];  // [R index from the K tile][c - c0]
   const int nw2 = nw * nw;
   const int nc = nw2 * (nm + 1);
-  size_t n = (size_t)nk_pad * cpk * kpad;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    int kk = (int)(idx % kpad);
-    size_t rest = idx / kpad;
-    int col = (int)(rest % cpk);
-    int k = (int)(rest / cpk);
-    float v = 0.0f;
-    if (k < nk && col < 2 * nc && kk < 2 * nR) {
-      const int c = planar ? 2 * (col >> 2) + (col & 1) : col >> 1;
-      const int s = planar ? (col >> 1) & 1 : col & 1;
-      const int r = nR - 1 - (kk >> 1), t = kk & 1;
-      cx<float> b = c < nw2 ? BH[((size_t)k * nR + r) * nw2 + c] : Bg[((size_t)k * nR + r) * nm * nw2 + (c - nw2)];
-      v = s == 0 ? (t == 0 ? b.x : -b.y) : (t == 0 ? b.y : b.x);
+  const int c0 = blockIdx.y * 32;
+  const int kk0 = blockIdx.x * 64, rr0 = kk0 >> 1;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int k = blockIdx.z; k < nk_pad; k += gridDim.z) {
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+      const int rr = rr0 + j, c = c0 + threadIdx.x;
+      cx<float> b = mkc(0.0f, 0.0f);
+      if (k < nk && rr < nR && c < nc) {
+        const int r = nR - 1 - rr;
+        b = c < nw2 ? BH[((size_t)k * nR + r) * nw2 + c] : Bg[((size_t)k * nR + r) * nm * nw2 + (c - nw2)];
+      }
+      tile[j][threadIdx.x] = b;
     }
-    split_store<T>((double)v, hi, lo, idx);
+    __syncthreads();
+    for (int e = tid; e < 64 * 64; e += blockDim.x * blockDim.y) {
+      const int kl = e & 63, cl = e >> 6;
+      const int col = 2 * c0 + cl, kk = kk0 + kl;
+      if (col >= cpk || kk >= kpad) continue;
+      const int c = planar ? 2 * (col >> 2) + (col & 1) : col >> 1;
+      const int sr = planar ? (col >> 1) & 1 : col & 1;
+      float v = 0.0f;
+      if (kk < 2 * nR) {
+        const cx<float> b = tile[(kk >> 1) - rr0][c - c0];
+        const int t = kk & 1;
+        v = sr == 0 ? (t == 0 ? b.x : -b.y) : (t == 0 ? b.y : b.x);
+      }
+      split_store<T>((double)v, hi, lo, ((size_t)k * cpk + col) * kpad + kk);
+    }
+    __syncthreads();
   }
+}
+
+template <typename T>
+void launch_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad, int planar, const cx<float> *BH,
+                    const cx<float> *Bg, T *hi, T *lo, cudaStream_t st) {
+  const dim3 grid((kpad + 63) / 64, (cpk + 63) / 64, std::min(nk_pad, 65535));
+  k_build_b<T><<<grid, dim3(32, 8), 0, st>>>(nk, nk_pad, nR, nw, nm, cpk, kpad, planar, BH, Bg, hi, lo);
+  epw_count_launch();
 }
 
 // FP32 tables of the epilogue, evaluated once per call: Bose factors n(w_qnu, T)
@@ -1530,17 +1556,13 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
       build_a<__nv_bfloat16>(nq, nR, b.kpad, q, m->Re, b.Pq64, (__nv_bfloat16 *)b.Ahi, (__nv_bfloat16 *)b.Alo, st);
     else
       build_a<float>(nq, nR, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
-    size_t n = (size_t)b.nk_pad * b.cpk * b.kpad;
     if (op == TC_OP_BF16)
-      k_build_b<__nv_bfloat16><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad,
-                                                                  b.planar, BH32,
-                                                                  Bg32, (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo);
+      launch_build_b<__nv_bfloat16>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, b.planar, BH32, Bg32,
+                                    (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo, st);
     else
-      k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, b.planar,
-                                                          BH32, Bg32,
-                                                          (float *)b.Bhi, (float *)b.Blo);
-    epw_count_launch();
-    n = (size_t)nq * m->nm + nq + (size_t)nk * m->nw;
+      launch_build_b<float>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, b.planar, BH32, Bg32, (float *)b.Bhi,
+                            (float *)b.Blo, st);
+    size_t n = (size_t)nq * m->nm + nq + (size_t)nk * m->nw;
     k_tc_tables<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nm, nk, m->nw, omegaT, par->T_K, wq, epsk, b.nbT, b.omF,
                                                    b.wqF, b.ekF);
     epw_count_launch();
@@ -1956,12 +1978,9 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
   // forward operands (tf32 split), epilogue tables, conj-phase operand, cotangent table
   {
     build_a<float>(nq, nR, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
-    size_t n = (size_t)b.nk_pad * b.cpk * b.kpad;
-    k_build_b<float><<<grid_for(n, 256), 256, 0, st>>>(nk, b.nk_pad, nR, nw, m->nm, b.cpk, b.kpad, b.planar,
-                                                        BH32, Bg32,
-                                                        (float *)b.Bhi, (float *)b.Blo);
-    epw_count_launch();
-    n = (size_t)nq * m->nm + nq + (size_t)nk * nw;
+    launch_build_b<float>(nk, b.nk_pad, nR, nw, m->nm, b.cpk, b.kpad, b.planar, BH32, Bg32, (float *)b.Bhi,
+                          (float *)b.Blo, st);
+    size_t n = (size_t)nq * m->nm + nq + (size_t)nk * nw;
     k_tc_tables<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nm, nk, nw, omegaT, par->T_K, wq, epsk, b.nbT, b.omF,
                                                    b.wqF, b.ekF);
     epw_count_launch();
@@ -2118,15 +2137,12 @@ epw_status tc_staged_contract(const epw_model *m, int k0, int kc, int nq, const 
                               const cx<float> *BH32, TcStaged &s, cudaStream_t st) {
   if (!s.ok || kc > s.kc) return EPW_ERR_UNSUPPORTED;
   const int nR = m->nRe, nw2 = m->nw * m->nw;
-  const size_t nb = (size_t)kc * s.cpk * s.kpad;
   const cx<float> *bh = BH32 + (size_t)k0 * nR * nw2, *bg = Bg32 + (size_t)k0 * nR * m->nm * nw2;
   if (s.op == TC_OP_BF16)
-    k_build_b<__nv_bfloat16><<<grid_for(nb, 256), 256, 0, st>>>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, 0, bh, bg,
-                                                                 (__nv_bfloat16 *)s.Bhi, (__nv_bfloat16 *)s.Blo);
+    launch_build_b<__nv_bfloat16>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, 0, bh, bg, (__nv_bfloat16 *)s.Bhi,
+                                  (__nv_bfloat16 *)s.Blo, st);
   else
-    k_build_b<float><<<grid_for(nb, 256), 256, 0, st>>>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, 0, bh, bg,
-                                                         (float *)s.Bhi, (float *)s.Blo);
-  epw_count_launch();
+    launch_build_b<float>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, 0, bh, bg, (float *)s.Bhi, (float *)s.Blo, st);
   const int rows = kc * s.cpk;
   CUtensorMap ah, al, bh_m, bl_m;
   if (!make_map(&ah, s.Ahi, s.op, s.kpad, nq, 128) || !make_map(&al, s.Alo, s.op, s.kpad, nq, 128) ||
