@@ -49,11 +49,15 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr int EPI_WARP0 = 2;
 constexpr int ITEMS_PER_TILE = 8;     // (lane quadrant, k slot) items per tile
-// Epilogue warps: the linewidth form runs three per lane quadrant (items taken
-// round-robin, so more warps hide each other's latency); the other forms two.
+// Epilogue warps per form, a multiple of 4 (one group per TMEM lane quadrant; a
+// quadrant's (tile, k slot) items are taken round-robin by its warps): the
+// linewidth form runs three per quadrant so that more warps hide each other's
+// latency; the adjoint one, with the registers of a whole sub-partition for its
+// conjugate-gradient accumulators; interpolation two.
 constexpr int EPI_WARPS_LW = 12;
+constexpr int EPI_WARPS_ADJ = 4;
 template <int MODE>
-constexpr int epi_warps() { return MODE == 0 ? EPI_WARPS_LW : 8; }
+constexpr int epi_warps() { return MODE == 0 ? EPI_WARPS_LW : MODE == 2 ? EPI_WARPS_ADJ : 8; }
 template <int MODE>
 constexpr int nthreads() { return 32 * (EPI_WARP0 + epi_warps<MODE>()); }
 constexpr uint32_t TMEM_COLS = 512;
@@ -837,6 +841,181 @@ __device__ __forceinline__ void modes_linewidth_packed(const TcArgs &a, uint32_t
   }
 }
 
+// Adjoint terms (MODE 2) of one pair from planar accumulator columns (NW even),
+// the packed counterpart of the generic MODE 2 loop in epilogue_pair: per mode
+// W_nu,mn = c_nk pi w_q [(n+f) d+ + (n+1-f) d-], Z_nu = U (2 W_nu o y_nu) with
+// y_nu = U^dagger G_nu, and Xbar_a = sum_nu conj(E[a][nu]) Z_nu, written as the
+// tf32-split rows (k, a, j, n); the dL/dT and dL/dE_F terms go to sT and sE.
+// Two n columns per packed FP32 instruction, as in modes_linewidth_packed.
+template <int NW, int NM>
+__device__ __forceinline__ void modes_adjoint_packed(const TcArgs &a, uint32_t tcol, int q, int qq, int k, int kk,
+                                                     bool valid, const cx<float> (&V)[NW][NW],
+                                                     const float (&em)[NW], const float (&fm)[NW],
+                                                     const float (&ek)[NW], const float (&cw)[NW], float &sT,
+                                                     float &sE) {
+  constexpr int NP = NW / 2;
+  constexpr int H2 = 2 * NW * NW;
+  const float sc = a.inv_sigma * 1.2011224087864498f;  // sqrt(log2 e) / sigma
+  float2 eks[NP], cw2[NP], sT2 = make_float2(0.0f, 0.0f), sE2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int p = 0; p < NP; p++) {
+    eks[p] = make_float2(ek[2 * p] * sc, ek[2 * p + 1] * sc);
+    cw2[p] = make_float2(cw[2 * p], cw[2 * p + 1]);
+  }
+  // per band m at k+q: df/dT and df/dE_F (mode independent)
+  float dfT[NW], dfE[NW];
+#pragma unroll
+  for (int m = 0; m < NW; m++) {
+    const float ff = fermi_ff_f(em[m] - a.EF, a.invkT);
+    dfT[m] = ff * (em[m] - a.EF) * a.invkT / a.T;
+    dfE[m] = ff * a.invkT;
+  }
+  float2 Xr[NM][NW][NP], Xi[NM][NW][NP];
+#pragma unroll
+  for (int al = 0; al < NM; al++)
+#pragma unroll
+    for (int j = 0; j < NW; j++)
+#pragma unroll
+      for (int p = 0; p < NP; p++) Xr[al][j][p] = Xi[al][j][p] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+  for (int nu = 0; nu < NM; nu++) {
+    const float wnu = __ldg(a.omegaT + (size_t)nu * a.nq + qq);
+    const float nbnu = __ldg(a.nbT + (size_t)nu * a.nq + qq);
+    float2 E[NM];
+#pragma unroll
+    for (int al = 0; al < NM; al++) E[al] = __ldg(a.ET + ((size_t)al * NM + nu) * a.nq + qq);
+    const bool keep = (wnu >= a.omega_min) && (wnu > 0.0f);
+    const float kf = keep ? 1.0f : 0.0f;
+    const float dn = kf * nbnu * (nbnu + 1.0f) * wnu * a.invkT / a.T;
+    float2 Gr[NW][NP], Gi[NW][NP];
+#pragma unroll
+    for (int al = 0; al < NM; al++) {
+      float x[H2];
+      tmem_load<H2>(tcol + H2 * (1 + al), x);
+      const float2 er = bc2(E[al].x), ei = bc2(E[al].y), nei = bc2(-E[al].y);
+#pragma unroll
+      for (int i = 0; i < NW; i++)
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          const int o = 4 * (i * NP + p);
+          const float2 xr = make_float2(x[o], x[o + 1]), xi = make_float2(x[o + 2], x[o + 3]);
+          if (al == 0) {
+            Gr[i][p] = ffma2(nei, xi, fmul2(er, xr));
+            Gi[i][p] = ffma2(ei, xr, fmul2(er, xi));
+          } else {
+            Gr[i][p] = ffma2(nei, xi, ffma2(er, xr, Gr[i][p]));
+            Gi[i][p] = ffma2(ei, xr, ffma2(er, xi, Gi[i][p]));
+          }
+        }
+    }
+    if (a.Cpol) {
+      // long-range part: G_nu += i C_nu(q) U_k
+      const float2 c = __ldg(a.Cpol + (size_t)nu * a.nq + qq);
+      const float2 *Uk = a.UkF + (size_t)kk * NW * NW;
+      const float2 ncy = bc2(-c.y), ncx = bc2(-c.x), cx2 = bc2(c.x);
+#pragma unroll
+      for (int i = 0; i < NW; i++)
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          const float2 u0 = __ldg(Uk + i * NW + 2 * p), u1 = __ldg(Uk + i * NW + 2 * p + 1);
+          const float2 ur = make_float2(u0.x, u1.x), ui = make_float2(u0.y, u1.y);
+          Gr[i][p] = ffma2(ncy, ur, ffma2(ncx, ui, Gr[i][p]));
+          Gi[i][p] = ffma2(cx2, ur, ffma2(ncy, ui, Gi[i][p]));
+        }
+    }
+    float2 Zr[NW][NP], Zi[NW][NP];
+#pragma unroll
+    for (int j = 0; j < NW; j++)
+#pragma unroll
+      for (int p = 0; p < NP; p++) Zr[j][p] = Zi[j][p] = make_float2(0.0f, 0.0f);
+    const float ws = wnu * sc;
+    float2 kcw[NP], cw2x[NP];
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      kcw[p] = fmul2(bc2(kf), cw2[p]);
+      cw2x[p] = fmul2(bc2(2.0f), cw2[p]);
+    }
+#pragma unroll
+    for (int m = 0; m < NW; m++) {
+      float2 yr[NP], yi[NP];
+#pragma unroll
+      for (int i = 0; i < NW; i++) {
+        const float2 vr = bc2(V[i][m].x), vi = bc2(V[i][m].y), nvi = bc2(-V[i][m].y);
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          if (i == 0) {
+            yr[p] = ffma2(vi, Gi[i][p], fmul2(vr, Gr[i][p]));
+            yi[p] = ffma2(nvi, Gr[i][p], fmul2(vr, Gi[i][p]));
+          } else {
+            yr[p] = ffma2(vi, Gi[i][p], ffma2(vr, Gr[i][p], yr[p]));
+            yi[p] = ffma2(nvi, Gr[i][p], ffma2(vr, Gi[i][p], yi[p]));
+          }
+        }
+      }
+      const float2 cp = bc2(kf * (nbnu + fm[m])), cm = bc2(kf * (nbnu + 1.0f - fm[m]));
+      const float2 dpT = bc2(dn + dfT[m]), dmT = bc2(dn - dfT[m]), dE = bc2(dfE[m]);
+      const float ems = em[m] * sc;
+      const float2 op = bc2(ws - ems), om = bc2(-ws - ems);
+      float2 ybr[NP], ybi[NP];
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        const float2 g2 = ffma2(yi[p], yi[p], fmul2(yr[p], yr[p]));
+        const float2 xp = fadd2(eks[p], op), xm = fadd2(eks[p], om);
+        const float2 tp = fmul2(xp, xp), tm = fmul2(xm, xm);
+        const float2 ep = make_float2(ex2_approx(-tp.x), ex2_approx(-tp.y));
+        const float2 en = make_float2(ex2_approx(-tm.x), ex2_approx(-tm.y));
+        const float2 wv = fmul2(cw2x[p], ffma2(cm, en, fmul2(cp, ep)));
+        const float2 kg = fmul2(kcw[p], g2);
+        sT2 = ffma2(kg, ffma2(dmT, en, fmul2(dpT, ep)), sT2);
+        sE2 = ffma2(fmul2(kg, dE), fadd2(ep, make_float2(-en.x, -en.y)), sE2);
+        ybr[p] = fmul2(wv, yr[p]);
+        ybi[p] = fmul2(wv, yi[p]);
+      }
+      // Z[j][n] += U[j][m] yb[n]
+#pragma unroll
+      for (int j = 0; j < NW; j++) {
+        const float2 vr = bc2(V[j][m].x), vi = bc2(V[j][m].y), nvi = bc2(-V[j][m].y);
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          Zr[j][p] = ffma2(nvi, ybi[p], ffma2(vr, ybr[p], Zr[j][p]));
+          Zi[j][p] = ffma2(vi, ybr[p], ffma2(vr, ybi[p], Zi[j][p]));
+        }
+      }
+    }
+    // Xbar_a += conj(E[a][nu]) Z_nu
+#pragma unroll
+    for (int al = 0; al < NM; al++) {
+      const float2 er = bc2(E[al].x), ei = bc2(E[al].y), nei = bc2(-E[al].y);
+#pragma unroll
+      for (int j = 0; j < NW; j++)
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          Xr[al][j][p] = ffma2(ei, Zi[j][p], ffma2(er, Zr[j][p], Xr[al][j][p]));
+          Xi[al][j][p] = ffma2(nei, Zr[j][p], ffma2(er, Zi[j][p], Xi[al][j][p]));
+        }
+    }
+  }
+  sT = sT2.x + sT2.y;
+  sE = sE2.x + sE2.y;
+  if (valid) {
+    // Xbar rows (k, a, j, n), K index 2q + (re, im), split into two tf32 terms
+#pragma unroll
+    for (int al = 0; al < NM; al++)
+#pragma unroll
+      for (int j = 0; j < NW; j++)
+#pragma unroll
+        for (int n = 0; n < NW; n++) {
+          const size_t row = (size_t)k * (NM * NW * NW) + (al * NW + j) * NW + n;
+          const float re = (n & 1) ? Xr[al][j][n >> 1].y : Xr[al][j][n >> 1].x;
+          const float im = (n & 1) ? Xi[al][j][n >> 1].y : Xi[al][j][n >> 1].x;
+          const float hr = tf32_rn(re), hi = tf32_rn(im);
+          *reinterpret_cast<float2 *>(a.xhi + row * a.ldx + 2 * (size_t)q) = make_float2(hr, hi);
+          *reinterpret_cast<float2 *>(a.xlo + row * a.ldx + 2 * (size_t)q) =
+              make_float2(tf32_rn(re - hr), tf32_rn(im - hi));
+        }
+  }
+}
+
 // ------------------------------------------------------------------ epilogue
 // One (k,q) pair per thread; the accumulator holds [H(k+q) | (g_a U_k)_a=0..NM-1].
 // MODE 0: linewidth terms summed over the warp's q rows; MODE 1: write e_k+q
@@ -852,6 +1031,15 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   const int qq = q < a.nq ? q : 0;
   const int kk = k < a.nk ? k : 0;
   if constexpr (MODE == 0 && S::PLANAR) tables_prefetch<NW, NM>(a, qq, tab);
+  if constexpr (MODE == 2 && S::PLANAR) {
+#pragma unroll
+    for (int j = 0; j < NM * NM; j++) prefetch_l1(a.ET + (size_t)j * a.nq + qq);
+#pragma unroll
+    for (int nu = 0; nu < NM; nu++) {
+      prefetch_l1(a.omegaT + (size_t)nu * a.nq + qq);
+      prefetch_l1(a.nbT + (size_t)nu * a.nq + qq);
+    }
+  }
   // per-q and per-k data first, so their latency overlaps the eigensolve
   float ek[NW];
 #pragma unroll
@@ -937,6 +1125,8 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   }
   if constexpr (MODE == 0 && PL) {
     modes_linewidth_packed<NW, NM>(a, tcol, qq, kk, tab, V, em, fm, ek, acc);
+  } else if constexpr (MODE == 2 && PL) {
+    modes_adjoint_packed<NW, NM>(a, tcol, q, qq, k, kk, valid, V, em, fm, ek, cw, sT, sE);
   } else {
   // one mode per iteration (not unrolled: keeps the code within the instruction cache)
 #pragma unroll 1
@@ -1056,7 +1246,7 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   }
   if constexpr (MODE == 2) {
     // Xbar rows (k, a, j, n), K index 2q + (re, im), split into two tf32 terms
-    if (valid) {
+    if (valid && !PL) {
 #pragma unroll
       for (int al = 0; al < NM; al++)
 #pragma unroll
