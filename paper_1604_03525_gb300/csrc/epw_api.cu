@@ -81,8 +81,9 @@ static void free_model_arrays(epw_model *m) {
   if (m->aux) cudaStreamDestroy(m->aux);
   if (m->ev_fork) cudaEventDestroy(m->ev_fork);
   if (m->ev_join) cudaEventDestroy(m->ev_join);
+  if (m->ev_phase) cudaEventDestroy(m->ev_phase);
   m->aux = nullptr;
-  m->ev_fork = m->ev_join = nullptr;
+  m->ev_fork = m->ev_join = m->ev_phase = nullptr;
   if (m->ev) {
     for (int i = 0; i < 2 * EPW_MAX_TIMED; i++)
       if (m->ev[i]) cudaEventDestroy(m->ev[i]);
@@ -373,12 +374,16 @@ static epw_status prep_streams(epw_model *m) {
   CK(cudaStreamCreateWithFlags(&m->aux, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&m->ev_phase, cudaEventDisableTiming));
   return EPW_OK;
 }
 
+// tcb (optional): the fused tensor-core kernel's operands are built here, B on the
+// main stream after the k side and A after the q phases, both while the q-side
+// phonon work (FP64) still runs on the second stream.
 static epw_status run_prep(const epw_model *mc, int nk, const double *k, int nq, const double *q, int prec,
                            double omega_min, bool need_B, Prep &p, double *omega_out, cudaStream_t st,
-                           bool fork = true) {
+                           bool fork = true, TcBuffers *tcb = nullptr) {
   epw_model *m = const_cast<epw_model *>(mc);
   const int nw = m->nw, nm = m->nm;
   const size_t nw2 = (size_t)nw * nw;
@@ -400,6 +405,7 @@ static epw_status run_prep(const epw_model *mc, int nk, const double *k, int nq,
     if (!m->same_ep) launch_phases(nq, q, m->nRp, m->Rp, m->rmax, nullptr, nullptr, (cx<float> *)p.PqTp, sq);
     if (!m->same_eph) launch_phases(nq, q, m->nRph, m->Rph, m->rmax, nullptr, p.PqTph, nullptr, sq);
   }
+  if (tcb && fork) CK(cudaEventRecord(m->ev_phase, sq));
   // phonons (FP64)
   launch_fourier_d(nq, m->nRph, p.PqTph, m->Phiw, nm * nm, p.D, sq);
   launch_eigh_d(nq, nm, p.D, p.w2, p.ev, m->dstatus, sq);
@@ -430,6 +436,13 @@ static epw_status run_prep(const epw_model *mc, int nk, const double *k, int nq,
                           false, st);
       launch_build_B<float>(m, nk, p.PkRM, (const cx<float> *)p.G1, p.Uk, (cx<float> *)p.Bg, (cx<float> *)p.BH, st);
     }
+  }
+  if (tcb && nk > 0 && nq > 0) {
+    tcb->Pq64 = m->same_eph ? p.PqTph : nullptr;
+    tc_build_b(m, nk, (const cx<float> *)p.Bg, (const cx<float> *)p.BH, *tcb, st);
+    if (fork) CK(cudaStreamWaitEvent(st, m->ev_phase, 0));
+    tc_build_a(m, nq, q, *tcb, st);
+    tcb->prebuilt = true;
   }
   if (fork) {
     CK(cudaEventRecord(m->ev_join, sq));
@@ -580,7 +593,7 @@ epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, c
   if (tcp && !L.tc.ok && !L.sg.ok)
     return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
   if (tcp && L.tc.ok) {
-    CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
+    CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st, true, &L.tc));
     L.tc.Cpol = m->polar ? (const float2 *)p.Cpol : nullptr;
     L.tc.Uk64 = p.Uk;
     L.tc.Pq64 = m->same_eph ? p.PqTph : nullptr;

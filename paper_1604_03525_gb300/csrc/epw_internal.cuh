@@ -312,7 +312,7 @@ struct epw_model {
   cudaEvent_t *ev;        // [2 * EPW_MAX_TIMED]
   // second stream for the q side of the preparation, and its fork / join events
   cudaStream_t aux;
-  cudaEvent_t ev_fork, ev_join;
+  cudaEvent_t ev_fork, ev_join, ev_phase;
   // long-range (polar) part of the vertex (epw_set_polar); polar == 0: none
   int polar;
   double pb[9];           // reciprocal vectors b_i (rows), 2 pi (A^{-1})^T

@@ -1705,6 +1705,23 @@ cudaError_t launch_tc_shape(int nw, int nm, const CUtensorMap &ah, const CUtenso
 
 }  // namespace
 
+void tc_build_b(const epw_model *m, int nk, const cx<float> *Bg32, const cx<float> *BH32, TcBuffers &b,
+                cudaStream_t st) {
+  if (b.op == TC_OP_BF16)
+    launch_build_b<__nv_bfloat16>(nk, b.nk_pad, m->nRe, m->nw, m->nm, b.cpk, b.kpad, b.planar, BH32, Bg32,
+                                  (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo, st);
+  else
+    launch_build_b<float>(nk, b.nk_pad, m->nRe, m->nw, m->nm, b.cpk, b.kpad, b.planar, BH32, Bg32, (float *)b.Bhi,
+                          (float *)b.Blo, st);
+}
+
+void tc_build_a(const epw_model *m, int nq, const double *q, TcBuffers &b, cudaStream_t st) {
+  if (b.op == TC_OP_BF16)
+    build_a<__nv_bfloat16>(nq, m->nRe, b.kpad, q, m->Re, b.Pq64, (__nv_bfloat16 *)b.Ahi, (__nv_bfloat16 *)b.Alo, st);
+  else
+    build_a<float>(nq, m->nRe, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
+}
+
 bool tc_supported(const epw_model *m) {
   int cpk, kpt, planar;
   return m->same_ep && shape_info(m->nw, m->nm, cpk, kpt, planar);
@@ -1742,16 +1759,11 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
   const int op = b.op;
   const int esz = op == TC_OP_BF16 ? 2 : 4;
   {
-    if (op == TC_OP_BF16)
-      build_a<__nv_bfloat16>(nq, nR, b.kpad, q, m->Re, b.Pq64, (__nv_bfloat16 *)b.Ahi, (__nv_bfloat16 *)b.Alo, st);
-    else
-      build_a<float>(nq, nR, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
-    if (op == TC_OP_BF16)
-      launch_build_b<__nv_bfloat16>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, b.planar, BH32, Bg32,
-                                    (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo, st);
-    else
-      launch_build_b<float>(nk, b.nk_pad, nR, m->nw, m->nm, b.cpk, b.kpad, b.planar, BH32, Bg32, (float *)b.Bhi,
-                            (float *)b.Blo, st);
+    if (!b.prebuilt) {
+      tc_build_a(m, nq, q, b, st);
+      tc_build_b(m, nk, Bg32, BH32, b, st);
+    }
+    b.prebuilt = false;
     size_t n = (size_t)nq * m->nm + nq + (size_t)nk * m->nw;
     k_tc_tables<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nm, nk, m->nw, omegaT, par->T_K, wq, epsk, b.nbT, b.omF,
                                                    b.wqF, b.ekF);

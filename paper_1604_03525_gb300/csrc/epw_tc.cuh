@@ -17,6 +17,7 @@ struct TcBuffers {
   int op, kpad, cpk, nk_pad, nqt, kpt;
   int planar;        // B columns in re/im pairs (see k_build_b)
   bool ok;           // shape has a tensor-core kernel
+  bool prebuilt;     // A and B already built for the next tc_linewidth/tc_interp call
   size_t a_block_bytes;  // q-block of the A operand visited by all k groups (0: default)
   // long-range vertex (polar models): set by the caller before a call; UkF is laid out by tc_plan
   const float2 *Cpol;        // [nm][nq]
@@ -30,6 +31,11 @@ struct TcBuffers {
 bool tc_supported(const epw_model *m);
 // Lay out (or measure, with a null arena base) the buffers of the tensor-core path.
 epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffers &b);
+// Builds of the fused kernel's operands on stream st: B from the k-side vertex,
+// A from the q phases (b.Pq64 when set, else from q).
+void tc_build_b(const epw_model *m, int nk, const cx<float> *Bg32, const cx<float> *BH32, TcBuffers &b,
+                cudaStream_t st);
+void tc_build_a(const epw_model *m, int nq, const double *q, TcBuffers &b, cudaStream_t st);
 // Im Sigma [nk][nw] into `out` (device) from the shared preparation outputs.
 epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, const double *q, const double *wq,
                         const epw_params *par, const cx<double> *PkRM, const double *epsk, const cx<double> *Uk,
