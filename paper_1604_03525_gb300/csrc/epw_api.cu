@@ -75,7 +75,8 @@ static epw_status upload(T **dst, const T *src, size_t n) {
 }
 
 static void free_model_arrays(epw_model *m) {
-  void *ptrs[] = {m->Re, m->Rp, m->Rph, m->wRe, m->wRp, m->Hw, m->Phiw, m->gw, m->mass, m->dstatus, m->ws, m->pZ};
+  void *ptrs[] = {m->Re, m->Rp, m->Rph, m->wRe, m->wRp, m->Hw, m->Phiw, m->Phidf, m->gw, m->mass, m->dstatus, m->ws,
+                  m->pZ};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->aux) cudaStreamDestroy(m->aux);
@@ -124,6 +125,12 @@ extern "C" epw_status epw_load_wannier(const epw_wannier_desc *d, epw_model **ou
         Phiw[e] = mkc(s * d->Phi[2 * e], s * d->Phi[2 * e + 1]);
       }
   }
+  // the same force constants as double-float pairs (hi = fl32(x), lo = fl32(x - hi))
+  std::vector<float4> Phidf(Phiw.size());
+  for (size_t e = 0; e < Phiw.size(); e++) {
+    const float rh = (float)Phiw[e].x, ih = (float)Phiw[e].y;
+    Phidf[e] = make_float4(rh, (float)(Phiw[e].x - (double)rh), ih, (float)(Phiw[e].y - (double)ih));
+  }
   const size_t per = nm * nw2;
   std::vector<cx<double>> gw((size_t)d->nRe * d->nRp * per);
   std::vector<double> wRe(d->nRe, 1.0), wRp(d->nRp, 1.0);
@@ -169,6 +176,7 @@ extern "C" epw_status epw_load_wannier(const epw_wannier_desc *d, epw_model **ou
       (s = upload(&m->Rph, (const int *)d->Rph, 3 * (size_t)d->nRph)) != EPW_OK ||
       (s = upload(&m->wRe, wRe.data(), wRe.size())) != EPW_OK || (s = upload(&m->wRp, wRp.data(), wRp.size())) != EPW_OK ||
       (s = upload(&m->Hw, Hw.data(), Hw.size())) != EPW_OK || (s = upload(&m->Phiw, Phiw.data(), Phiw.size())) != EPW_OK ||
+      (s = upload(&m->Phidf, Phidf.data(), Phidf.size())) != EPW_OK ||
       (s = upload(&m->gw, gw.data(), gw.size())) != EPW_OK ||
       (s = upload(&m->mass, d->mass, (size_t)nat)) != EPW_OK) {
     free_model_arrays(m);
@@ -395,8 +403,12 @@ static epw_status run_prep(const epw_model *mc, int nk, const double *k, int nq,
     CK(cudaStreamWaitEvent(m->aux, m->ev_fork, 0));
     sq = m->aux;
   }
-  // q side: phases in working precision (+ FP64 for phonons)
-  if (prec == EPW_FP64) {
+  // q side: phases in working precision (+ FP64 for phonons); the fused tensor-core
+  // form takes phases, A operand and D(q) from one double-float kernel instead
+  const bool qs = tcb && prec != EPW_FP64 && tc_qside(m, nq, q, *tcb, p.D, sq);
+  if (qs) {
+    tcb->prebuilt_a = true;
+  } else if (prec == EPW_FP64) {
     launch_phases(nq, q, m->nRe, m->Re, m->rmax, nullptr, (cx<double> *)p.PqTe, nullptr, sq);
     if (!m->same_ep) launch_phases(nq, q, m->nRp, m->Rp, m->rmax, nullptr, (cx<double> *)p.PqTp, nullptr, sq);
     if (!m->same_eph) launch_phases(nq, q, m->nRph, m->Rph, m->rmax, nullptr, p.PqTph, nullptr, sq);
@@ -405,9 +417,9 @@ static epw_status run_prep(const epw_model *mc, int nk, const double *k, int nq,
     if (!m->same_ep) launch_phases(nq, q, m->nRp, m->Rp, m->rmax, nullptr, nullptr, (cx<float> *)p.PqTp, sq);
     if (!m->same_eph) launch_phases(nq, q, m->nRph, m->Rph, m->rmax, nullptr, p.PqTph, nullptr, sq);
   }
-  if (tcb && fork) CK(cudaEventRecord(m->ev_phase, sq));
-  // phonons (FP64)
-  launch_fourier_d(nq, m->nRph, p.PqTph, m->Phiw, nm * nm, p.D, sq);
+  if (tcb && fork && !qs) CK(cudaEventRecord(m->ev_phase, sq));
+  // phonons (FP64 eigensolve)
+  if (!qs) launch_fourier_d(nq, m->nRph, p.PqTph, m->Phiw, nm * nm, p.D, sq);
   launch_eigh_d(nq, nm, p.D, p.w2, p.ev, m->dstatus, sq);
   launch_phonon_post(nq, nm, p.w2, p.ev, m->mass, omega_min, p.omegaT,
                      prec == EPW_FP64 ? (cx<double> *)p.ET : nullptr, prec == EPW_FP64 ? nullptr : (cx<float> *)p.ET,
@@ -438,11 +450,14 @@ static epw_status run_prep(const epw_model *mc, int nk, const double *k, int nq,
     }
   }
   if (tcb && nk > 0 && nq > 0) {
-    tcb->Pq64 = m->same_eph ? p.PqTph : nullptr;
     tc_build_b(m, nk, (const cx<float> *)p.Bg, (const cx<float> *)p.BH, *tcb, st);
-    if (fork) CK(cudaStreamWaitEvent(st, m->ev_phase, 0));
-    tc_build_a(m, nq, q, *tcb, st);
-    tcb->prebuilt = true;
+    tcb->prebuilt_b = true;
+    if (!qs) {
+      tcb->Pq64 = m->same_eph ? p.PqTph : nullptr;
+      if (fork) CK(cudaStreamWaitEvent(st, m->ev_phase, 0));
+      tc_build_a(m, nq, q, *tcb, st);
+      tcb->prebuilt_a = true;
+    }
   }
   if (fork) {
     CK(cudaEventRecord(m->ev_join, sq));

@@ -301,6 +301,7 @@ struct epw_model {
   double *wRe, *wRp;      // [n]
   cx<double> *Hw;         // [nRe][nw][nw], wRe folded
   cx<double> *Phiw;       // [nRph][nm][nm], wRph and 1/sqrt(M M') folded
+  float4 *Phidf;          // Phiw in double-float: (Re hi, Re lo, Im hi, Im lo) per entry
   cx<double> *gw;         // [nRe][nRp][nm][nw][nw], wRe wRp folded
   double *mass;           // [nat]
   unsigned int *dstatus;  // device status word

@@ -1631,6 +1631,141 @@ void build_a(int nq, int nR, int kpad, const double *q, const int *R, const cx<d
   }
 }
 
+// ----------------------------------------------- q side in double-float
+// An FP64 value carried as hi + lo (two FP32, |lo| <= ulp(hi)/2): products by the
+// error-free FMA product of the high parts plus the cross terms (Dekker), sums by
+// Knuth's TwoSum of the high parts; about 2^-47 relative per operation.  The
+// *_rn intrinsics keep the compiler from contracting the error terms into FMAs.
+struct dflt {
+  float h, l;
+};
+__device__ __forceinline__ dflt df_make(double x) {
+  const float h = (float)x;
+  dflt r;
+  r.h = h;
+  r.l = (float)(x - (double)h);
+  return r;
+}
+__device__ __forceinline__ dflt df_norm(float s, float e) {
+  dflt r;
+  r.h = __fadd_rn(s, e);
+  r.l = __fsub_rn(e, __fsub_rn(r.h, s));
+  return r;
+}
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  return df_norm(p, e);
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float v = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.h, __fsub_rn(s, v)), __fsub_rn(b.h, v)), __fadd_rn(a.l, b.l));
+  return df_norm(s, e);
+}
+__device__ __forceinline__ dflt df_neg(dflt a) {
+  a.h = -a.h;
+  a.l = -a.l;
+  return a;
+}
+struct dfcx {
+  dflt x, y;
+};
+__device__ __forceinline__ dfcx dfc_mul(dfcx a, dfcx b) {
+  dfcx r;
+  r.x = df_add(df_mul(a.x, b.x), df_neg(df_mul(a.y, b.y)));
+  r.y = df_add(df_mul(a.x, b.y), df_mul(a.y, b.x));
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void split_df(dflt v, T &hi, T &lo);
+template <>
+__device__ __forceinline__ void split_df<__nv_bfloat16>(dflt v, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+  hi = __float2bfloat16_rn(v.h);
+  lo = __float2bfloat16_rn(__fadd_rn(__fsub_rn(v.h, __bfloat162float(hi)), v.l));
+}
+template <>
+__device__ __forceinline__ void split_df<float>(dflt v, float &hi, float &lo) {
+  hi = tf32_round(v.h);
+  lo = tf32_round(__fadd_rn(__fsub_rn(v.h, hi), v.l));
+}
+
+// The q side of the fused tensor-core form in one pass, one thread per q
+// (R = Rph = Re): the one-axis factors e^{2 pi i (q_j n mod 1)}, |n| <= rmax, in
+// FP64 (argument reduced mod 1, sincospi); the phases P_q(R) = prod_j factor_j in
+// double-float; the A operand row of q written directly (K index 2 (nR-1-r) + re/im,
+// split hi/lo, zero up to kpad) in 16-byte chunks; and the mass-scaled dynamical
+// matrix D(q) = sum_R P_q(R) Phi(R) accumulated in double-float and written in FP64
+// for the eigensolve.
+constexpr int QS_RMAX = 8;
+template <typename T, int NM2>
+__global__ void __launch_bounds__(128) k_qside_df(int nq, const double *__restrict__ q, int nR,
+                                                  const int *__restrict__ R, int rmax,
+                                                  const float4 *__restrict__ Phidf, int kpad, T *Ahi, T *Alo,
+                                                  cx<double> *D) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nq) return;
+  dfcx F[3][2 * QS_RMAX + 1];
+  for (int j = 0; j < 3; j++) {
+    const double xj = q[3 * i + j];
+    for (int n = -rmax; n <= rmax; n++) {
+      double a = xj * n;
+      a -= rint(a);
+      double sn, cs;
+      sincospi(2.0 * a, &sn, &cs);
+      F[j][n + QS_RMAX].x = df_make(cs);
+      F[j][n + QS_RMAX].y = df_make(sn);
+    }
+  }
+  dfcx acc[NM2];
+#pragma unroll
+  for (int e = 0; e < NM2; e++) acc[e].x.h = acc[e].x.l = acc[e].y.h = acc[e].y.l = 0.0f;
+  constexpr int PER = 16 / (int)sizeof(T);  // elements per 16-byte chunk
+  constexpr int RB = PER / 2;               // R vectors per chunk
+  T *hrow = Ahi + (size_t)i * kpad, *lrow = Alo + (size_t)i * kpad;
+  for (int rr0 = 0; rr0 < kpad / 2; rr0 += RB) {
+    __align__(16) T hb[PER];
+    __align__(16) T lb[PER];
+#pragma unroll
+    for (int u = 0; u < RB; u++) {
+      const int rr = rr0 + u;  // K order: R index r = nR - 1 - rr
+      T h0 = T(0.0f), l0 = T(0.0f), h1 = T(0.0f), l1 = T(0.0f);
+      if (rr < nR) {
+        const int r = nR - 1 - rr;
+        const dfcx p = dfc_mul(dfc_mul(F[0][R[3 * r] + QS_RMAX], F[1][R[3 * r + 1] + QS_RMAX]),
+                               F[2][R[3 * r + 2] + QS_RMAX]);
+        split_df<T>(p.x, h0, l0);
+        split_df<T>(p.y, h1, l1);
+        const float4 *ph = Phidf + (size_t)r * NM2;
+#pragma unroll
+        for (int e = 0; e < NM2; e++) {
+          const float4 f = __ldg(ph + e);
+          dfcx b;
+          b.x.h = f.x;
+          b.x.l = f.y;
+          b.y.h = f.z;
+          b.y.l = f.w;
+          const dfcx t = dfc_mul(p, b);
+          acc[e].x = df_add(acc[e].x, t.x);
+          acc[e].y = df_add(acc[e].y, t.y);
+        }
+      }
+      hb[2 * u] = h0;
+      hb[2 * u + 1] = h1;
+      lb[2 * u] = l0;
+      lb[2 * u + 1] = l1;
+    }
+    *reinterpret_cast<uint4 *>(hrow + 2 * rr0) = *reinterpret_cast<const uint4 *>(hb);
+    *reinterpret_cast<uint4 *>(lrow + 2 * rr0) = *reinterpret_cast<const uint4 *>(lb);
+  }
+  cx<double> *d = D + (size_t)i * NM2;
+#pragma unroll
+  for (int e = 0; e < NM2; e++)
+    d[e] = mkc((double)acc[e].x.h + (double)acc[e].x.l, (double)acc[e].y.h + (double)acc[e].y.l);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -1722,6 +1857,19 @@ void tc_build_a(const epw_model *m, int nq, const double *q, TcBuffers &b, cudaS
     build_a<float>(nq, m->nRe, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
 }
 
+bool tc_qside(const epw_model *m, int nq, const double *q, TcBuffers &b, cx<double> *D, cudaStream_t st) {
+  if (!b.ok || !m->same_eph || m->nm != 3 || m->rmax > QS_RMAX || nq <= 0) return false;
+  const int grid = (nq + 127) / 128;
+  if (b.op == TC_OP_BF16)
+    k_qside_df<__nv_bfloat16, 9><<<grid, 128, 0, st>>>(nq, q, m->nRe, m->Re, m->rmax, m->Phidf, b.kpad,
+                                                        (__nv_bfloat16 *)b.Ahi, (__nv_bfloat16 *)b.Alo, D);
+  else
+    k_qside_df<float, 9><<<grid, 128, 0, st>>>(nq, q, m->nRe, m->Re, m->rmax, m->Phidf, b.kpad, (float *)b.Ahi,
+                                                (float *)b.Alo, D);
+  epw_count_launch();
+  return true;
+}
+
 bool tc_supported(const epw_model *m) {
   int cpk, kpt, planar;
   return m->same_ep && shape_info(m->nw, m->nm, cpk, kpt, planar);
@@ -1759,11 +1907,9 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
   const int op = b.op;
   const int esz = op == TC_OP_BF16 ? 2 : 4;
   {
-    if (!b.prebuilt) {
-      tc_build_a(m, nq, q, b, st);
-      tc_build_b(m, nk, Bg32, BH32, b, st);
-    }
-    b.prebuilt = false;
+    if (!b.prebuilt_a) tc_build_a(m, nq, q, b, st);
+    if (!b.prebuilt_b) tc_build_b(m, nk, Bg32, BH32, b, st);
+    b.prebuilt_a = b.prebuilt_b = false;
     size_t n = (size_t)nq * m->nm + nq + (size_t)nk * m->nw;
     k_tc_tables<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nm, nk, m->nw, omegaT, par->T_K, wq, epsk, b.nbT, b.omF,
                                                    b.wqF, b.ekF);

@@ -17,7 +17,7 @@ struct TcBuffers {
   int op, kpad, cpk, nk_pad, nqt, kpt;
   int planar;        // B columns in re/im pairs (see k_build_b)
   bool ok;           // shape has a tensor-core kernel
-  bool prebuilt;     // A and B already built for the next tc_linewidth/tc_interp call
+  bool prebuilt_a, prebuilt_b;  // A / B already built for the next tc_linewidth/tc_interp call
   size_t a_block_bytes;  // q-block of the A operand visited by all k groups (0: default)
   // long-range vertex (polar models): set by the caller before a call; UkF is laid out by tc_plan
   const float2 *Cpol;        // [nm][nq]
@@ -36,6 +36,10 @@ epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffe
 void tc_build_b(const epw_model *m, int nk, const cx<float> *Bg32, const cx<float> *BH32, TcBuffers &b,
                 cudaStream_t st);
 void tc_build_a(const epw_model *m, int nq, const double *q, TcBuffers &b, cudaStream_t st);
+// The q side of the fused form in one kernel (double-float phases and D(q), A
+// operand written directly); false (nothing launched) when the model has no such
+// form (R sets differ, 3nat != 3 or |R_j| beyond the factor table).
+bool tc_qside(const epw_model *m, int nq, const double *q, TcBuffers &b, cx<double> *D, cudaStream_t st);
 // Im Sigma [nk][nw] into `out` (device) from the shared preparation outputs.
 epw_status tc_linewidth(const epw_model *m, int nk, const double *k, int nq, const double *q, const double *wq,
                         const epw_params *par, const cx<double> *PkRM, const double *epsk, const cx<double> *Uk,
