@@ -83,8 +83,11 @@ static void free_model_arrays(epw_model *m) {
   if (m->ev_fork) cudaEventDestroy(m->ev_fork);
   if (m->ev_join) cudaEventDestroy(m->ev_join);
   if (m->ev_phase) cudaEventDestroy(m->ev_phase);
-  m->aux = nullptr;
-  m->ev_fork = m->ev_join = m->ev_phase = nullptr;
+  if (m->aux2) cudaStreamDestroy(m->aux2);
+  if (m->ev_fork2) cudaEventDestroy(m->ev_fork2);
+  if (m->ev_join2) cudaEventDestroy(m->ev_join2);
+  m->aux = m->aux2 = nullptr;
+  m->ev_fork = m->ev_join = m->ev_phase = m->ev_fork2 = m->ev_join2 = nullptr;
   if (m->ev) {
     for (int i = 0; i < 2 * EPW_MAX_TIMED; i++)
       if (m->ev[i]) cudaEventDestroy(m->ev[i]);
@@ -383,6 +386,9 @@ static epw_status prep_streams(epw_model *m) {
   CK(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&m->ev_phase, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&m->aux2, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&m->ev_fork2, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&m->ev_join2, cudaEventDisableTiming));
   return EPW_OK;
 }
 
@@ -430,10 +436,20 @@ static epw_status run_prep(const epw_model *mc, int nk, const double *k, int nq,
     else
       launch_polar_factors<float>(m, nq, q, (const cx<float> *)p.ET, (cx<float> *)p.Cpol, sq);
   }
-  // k side (FP64): phases, H(k), eigensolve, then the k-side vertex
+  // k side (FP64): phases, H(k), eigensolve, then the k-side vertex; with a fork the
+  // bands (H(k), eigensolve) run on a third stream beside the vertex GEMM, which
+  // needs only the phases, and are joined before the U_k rotation
   launch_phases(nk, k, m->nRe, m->Re, m->rmax, p.PkRM, p.PkT, nullptr, st);
-  launch_fourier_d(nk, m->nRe, p.PkT, m->Hw, (int)nw2, p.Hk, st);
-  launch_eigh_d(nk, nw, p.Hk, p.epsk, p.Uk, m->dstatus, st);
+  const bool fork2 = fork && need_B && prec != EPW_FP64;
+  cudaStream_t sk = st;
+  if (fork2) {
+    CK(cudaEventRecord(m->ev_fork2, st));
+    CK(cudaStreamWaitEvent(m->aux2, m->ev_fork2, 0));
+    sk = m->aux2;
+  }
+  launch_fourier_d(nk, m->nRe, p.PkT, m->Hw, (int)nw2, p.Hk, sk);
+  launch_eigh_d(nk, nw, p.Hk, p.epsk, p.Uk, m->dstatus, sk);
+  if (fork2) CK(cudaEventRecord(m->ev_join2, sk));
   if (need_B && nk > 0) {
     const int ncol = m->nRp * nm * (int)nw2;
     if (prec == EPW_FP64) {
@@ -446,6 +462,7 @@ static epw_status run_prep(const epw_model *mc, int nk, const double *k, int nq,
       launch_cast_c64_to_c32((size_t)m->nRe * ncol, m->gw, p.gw32, st);
       launch_cgemm<float>(nk, ncol, m->nRe, p.Pk32, m->nRe, false, false, p.gw32, ncol, (cx<float> *)p.G1, ncol,
                           false, st);
+      if (fork2) CK(cudaStreamWaitEvent(st, m->ev_join2, 0));
       launch_build_B<float>(m, nk, p.PkRM, (const cx<float> *)p.G1, p.Uk, (cx<float> *)p.Bg, (cx<float> *)p.BH, st);
     }
   }

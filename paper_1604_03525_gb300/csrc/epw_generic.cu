@@ -861,6 +861,48 @@ __global__ void k_finalize(int nk, int nqb, int nw, const double *__restrict__ p
   if (lane == 0) out[w] = EPW_PI * (s + c);
 }
 
+// The same sums with one block of four warps per k when nw divides 32: the
+// partial row of k is read contiguously, warp w taking the w-th quarter; lane l
+// owns band n = l % nw, lanes with the same n are combined by a fixed shuffle tree
+// (offsets 16 .. nw) and the four warps' sums in warp order.
+__global__ void __launch_bounds__(128) k_finalize_k(int nk, int nqb, int nw, const double *__restrict__ partial,
+                                                    double *out) {
+  __shared__ double sh_s[4][32], sh_c[4][32];
+  const int k = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double *row = partial + (size_t)k * nqb * nw;
+  const int n = nqb * nw;
+  const int per = ((n + 127) / 128) * 32;  // elements per warp, a multiple of 32
+  const int j0 = warp * per, j1 = min(n, j0 + per);
+  double s = 0.0, c = 0.0;
+  int j = j0 + lane;
+  for (; j + 96 < j1; j += 128) {
+    const double x0 = row[j], x1 = row[j + 32], x2 = row[j + 64], x3 = row[j + 96];
+    neumaier_add(s, c, x0);
+    neumaier_add(s, c, x1);
+    neumaier_add(s, c, x2);
+    neumaier_add(s, c, x3);
+  }
+  for (; j < j1; j += 32) neumaier_add(s, c, row[j]);
+  for (int o = 16; o >= nw; o >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, s, o);
+    const double c2 = __shfl_down_sync(0xffffffffu, c, o);
+    neumaier_add(s, c, s2);
+    c += c2;
+  }
+  sh_s[warp][lane] = s;
+  sh_c[warp][lane] = c;
+  __syncthreads();
+  if (warp == 0 && lane < nw) {
+    double S = 0.0, C = 0.0;
+    for (int w = 0; w < 4; w++) {
+      neumaier_add(S, C, sh_s[w][lane]);
+      C += sh_c[w][lane];
+    }
+    out[(size_t)k * nw + lane] = EPW_PI * (S + C);
+  }
+}
+
 // out[0] (+)= scale * sum_i partial[i], one block, fixed order, compensated.
 __global__ void k_sum_scalar(int n, const double *__restrict__ partial, double scale, double *out) {
   __shared__ double ss[256], cc[256];
@@ -952,15 +994,16 @@ void launch_fourier_d(int npt, int nR, const cx<double> *PT, const cx<double> *X
 
 void launch_eigh_d(int nmat, int n, cx<double> *A, double *w, cx<double> *V, unsigned *dstatus, cudaStream_t st) {
   if (!nmat) return;
-  int b = (nmat + 63) / 64;
+  // one warp per block: the FP64 pipe is per SM, so small batches spread over more SMs
+  int b = (nmat + 31) / 32;
   if (n <= 3)
-    k_eigh_d<3><<<b, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
+    k_eigh_d<3><<<b, 32, 0, st>>>(nmat, n, A, w, V, dstatus);
   else if (n <= 4)
-    k_eigh_d<4><<<b, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
+    k_eigh_d<4><<<b, 32, 0, st>>>(nmat, n, A, w, V, dstatus);
   else if (n <= 9)
-    k_eigh_d<9><<<b, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
+    k_eigh_d<9><<<(nmat + 63) / 64, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
   else
-    k_eigh_d<18><<<b, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
+    k_eigh_d<18><<<(nmat + 63) / 64, 64, 0, st>>>(nmat, n, A, w, V, dstatus);
   epw_count_launch();
 }
 
@@ -1170,7 +1213,10 @@ void launch_set_vertex(const epw_model *m, const void *g, int is_c64, cudaStream
 void launch_finalize(int nk, int nqb, int nw, const double *partial, double *out, cudaStream_t st) {
   int n = nk * nw;  // one warp each
   if (!n) return;
-  k_finalize<<<(n + 3) / 4, 128, 0, st>>>(nk, nqb, nw, partial, out);
+  if (32 % nw == 0)
+    k_finalize_k<<<nk, 128, 0, st>>>(nk, nqb, nw, partial, out);
+  else
+    k_finalize<<<(n + 3) / 4, 128, 0, st>>>(nk, nqb, nw, partial, out);
   epw_count_launch();
 }
 

@@ -314,6 +314,9 @@ struct epw_model {
   // second stream for the q side of the preparation, and its fork / join events
   cudaStream_t aux;
   cudaEvent_t ev_fork, ev_join, ev_phase;
+  // third stream: the k-side bands (H(k) and its eigensolve) beside the k-side vertex GEMM
+  cudaStream_t aux2;
+  cudaEvent_t ev_fork2, ev_join2;
   // long-range (polar) part of the vertex (epw_set_polar); polar == 0: none
   int polar;
   double pb[9];           // reciprocal vectors b_i (rows), 2 pi (A^{-1})^T

@@ -1528,6 +1528,23 @@ __global__ void k_a_pad(int nq, int k0, int kpad, T *hi, T *lo) {
     split_store<T>(0.0, hi, lo, (i / w) * kpad + k0 + i % w);
 }
 
+// hi/lo split of an FP32 value, in FP32: v - hi is exact (hi is v rounded to
+// fewer mantissa bits), so this equals split_store of (double)v.
+template <typename T>
+__device__ __forceinline__ void split_store_f(float v, T *hi, T *lo, size_t i);
+template <>
+__device__ __forceinline__ void split_store_f<__nv_bfloat16>(float v, __nv_bfloat16 *hi, __nv_bfloat16 *lo, size_t i) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[i] = h;
+  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+template <>
+__device__ __forceinline__ void split_store_f<float>(float v, float *hi, float *lo, size_t i) {
+  const float h = tf32_round(v);
+  hi[i] = h;
+  lo[i] = tf32_round(v - h);
+}
+
 // B[k][col][kk] (K-major hi/lo) of the real GEMM:
 //   col = 2c + s (s: re/im of output column c), kk = 2r + t (t: re/im of P_q(R_r)),
 //   (s,t) = (0,0): Re b, (0,1): -Im b, (1,0): Im b, (1,1): Re b,  b = B_k[r][c].
@@ -1570,7 +1587,7 @@ __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, i
         const int t = kk & 1;
         v = sr == 0 ? (t == 0 ? b.x : -b.y) : (t == 0 ? b.y : b.x);
       }
-      split_store<T>((double)v, hi, lo, ((size_t)k * cpk + col) * kpad + kk);
+      split_store_f<T>(v, hi, lo, ((size_t)k * cpk + col) * kpad + kk);
     }
     __syncthreads();
   }
