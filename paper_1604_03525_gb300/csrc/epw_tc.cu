@@ -1709,39 +1709,71 @@ __device__ __forceinline__ void split_df<float>(dflt v, float &hi, float &lo) {
   lo = tf32_round(__fadd_rn(__fsub_rn(v.h, hi), v.l));
 }
 
+// Accumulator of a double-float sum: the high parts are added exactly by TwoSum
+// and every rounding error (of the sums and of the products) gathers in lo,
+// which is folded in once at the end.
+struct dfacc {
+  float h, l;
+};
+// acc += a * b (a, b double-float; the error-free product of the high parts)
+__device__ __forceinline__ void dfa_fma(dfacc &acc, dflt a, dflt b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  const float s = __fadd_rn(acc.h, p);
+  const float v = __fsub_rn(s, acc.h);
+  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, v)), __fsub_rn(p, v));
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
+}
+
 // The q side of the fused tensor-core form in one pass, one thread per q
-// (R = Rph = Re): the one-axis factors e^{2 pi i (q_j n mod 1)}, |n| <= rmax, in
-// FP64 (argument reduced mod 1, sincospi); the phases P_q(R) = prod_j factor_j in
-// double-float; the A operand row of q written directly (K index 2 (nR-1-r) + re/im,
-// split hi/lo, zero up to kpad) in 16-byte chunks; and the mass-scaled dynamical
-// matrix D(q) = sum_R P_q(R) Phi(R) accumulated in double-float and written in FP64
-// for the eigensolve.
+// (R = Rph = Re): the one-axis factors e^{2 pi i q_j n}, |n| <= rmax, from
+// e^{2 pi i (q_j mod 1)} (FP64 argument reduction, sincospi) by double-float
+// powers (negative n as conjugates), kept in shared memory; the phases
+// P_q(R) = prod_j factor_j in double-float; the A operand row of q written
+// directly (K index 2 (nR-1-r) + re/im, split hi/lo, zero up to kpad) in 16-byte
+// chunks; and the mass-scaled dynamical matrix D(q) = sum_R P_q(R) Phi(R)
+// accumulated in double-float and written in FP64 for the eigensolve.
 constexpr int QS_RMAX = 8;
+constexpr int QS_THREADS = 64;
 template <typename T, int NM2>
-__global__ void __launch_bounds__(128) k_qside_df(int nq, const double *__restrict__ q, int nR,
-                                                  const int *__restrict__ R, int rmax,
-                                                  const float4 *__restrict__ Phidf, int kpad, T *Ahi, T *Alo,
-                                                  cx<double> *D) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nq) return;
-  dfcx F[3][2 * QS_RMAX + 1];
+__global__ void __launch_bounds__(QS_THREADS) k_qside_df(int nq, const double *__restrict__ q, int nR,
+                                                         const int *__restrict__ R, int rmax,
+                                                         const float4 *__restrict__ Phidf, int kpad, T *Ahi, T *Alo,
+                                                         cx<double> *D) {
+  extern __shared__ float4 fsh[];  // [3][2 rmax + 1][QS_THREADS]: (Re hi, Re lo, Im hi, Im lo)
+  const int i = blockIdx.x * QS_THREADS + threadIdx.x;
+  const int nf = 2 * rmax + 1;
+  const int ii = i < nq ? i : nq - 1;
   for (int j = 0; j < 3; j++) {
-    const double xj = q[3 * i + j];
-    for (int n = -rmax; n <= rmax; n++) {
-      double a = xj * n;
-      a -= rint(a);
-      double sn, cs;
-      sincospi(2.0 * a, &sn, &cs);
-      F[j][n + QS_RMAX].x = df_make(cs);
-      F[j][n + QS_RMAX].y = df_make(sn);
+    double a = q[3 * ii + j];
+    a -= rint(a);
+    double sn, cs;
+    sincospi(2.0 * a, &sn, &cs);
+    dfcx f1, f;
+    f1.x = df_make(cs);
+    f1.y = df_make(sn);
+    f.x = df_make(1.0);
+    f.y = df_make(0.0);
+    float4 *col = fsh + (size_t)j * nf * QS_THREADS + threadIdx.x;
+    col[rmax * QS_THREADS] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    for (int n = 1; n <= rmax; n++) {
+      f = dfc_mul(f, f1);
+      col[(rmax + n) * QS_THREADS] = make_float4(f.x.h, f.x.l, f.y.h, f.y.l);
+      col[(rmax - n) * QS_THREADS] = make_float4(f.x.h, f.x.l, -f.y.h, -f.y.l);
     }
   }
-  dfcx acc[NM2];
+  // each thread reads only its own column: no barrier needed
+  if (i >= nq) return;
+  dfacc ax[NM2], ay[NM2];
 #pragma unroll
-  for (int e = 0; e < NM2; e++) acc[e].x.h = acc[e].x.l = acc[e].y.h = acc[e].y.l = 0.0f;
+  for (int e = 0; e < NM2; e++) ax[e].h = ax[e].l = ay[e].h = ay[e].l = 0.0f;
   constexpr int PER = 16 / (int)sizeof(T);  // elements per 16-byte chunk
   constexpr int RB = PER / 2;               // R vectors per chunk
   T *hrow = Ahi + (size_t)i * kpad, *lrow = Alo + (size_t)i * kpad;
+  const float4 *F0 = fsh + threadIdx.x + rmax * QS_THREADS;
+  const float4 *F1 = F0 + nf * QS_THREADS, *F2 = F1 + nf * QS_THREADS;
   for (int rr0 = 0; rr0 < kpad / 2; rr0 += RB) {
     __align__(16) T hb[PER];
     __align__(16) T lb[PER];
@@ -1751,22 +1783,28 @@ __global__ void __launch_bounds__(128) k_qside_df(int nq, const double *__restri
       T h0 = T(0.0f), l0 = T(0.0f), h1 = T(0.0f), l1 = T(0.0f);
       if (rr < nR) {
         const int r = nR - 1 - rr;
-        const dfcx p = dfc_mul(dfc_mul(F[0][R[3 * r] + QS_RMAX], F[1][R[3 * r + 1] + QS_RMAX]),
-                               F[2][R[3 * r + 2] + QS_RMAX]);
+        const float4 g0 = F0[R[3 * r] * QS_THREADS], g1 = F1[R[3 * r + 1] * QS_THREADS],
+                     g2 = F2[R[3 * r + 2] * QS_THREADS];
+        dfcx a, b, c;
+        a.x = {g0.x, g0.y};
+        a.y = {g0.z, g0.w};
+        b.x = {g1.x, g1.y};
+        b.y = {g1.z, g1.w};
+        c.x = {g2.x, g2.y};
+        c.y = {g2.z, g2.w};
+        const dfcx p = dfc_mul(dfc_mul(a, b), c);
         split_df<T>(p.x, h0, l0);
         split_df<T>(p.y, h1, l1);
+        const dflt npy = df_neg(p.y);
         const float4 *ph = Phidf + (size_t)r * NM2;
 #pragma unroll
         for (int e = 0; e < NM2; e++) {
           const float4 f = __ldg(ph + e);
-          dfcx b;
-          b.x.h = f.x;
-          b.x.l = f.y;
-          b.y.h = f.z;
-          b.y.l = f.w;
-          const dfcx t = dfc_mul(p, b);
-          acc[e].x = df_add(acc[e].x, t.x);
-          acc[e].y = df_add(acc[e].y, t.y);
+          const dflt fx = {f.x, f.y}, fy = {f.z, f.w};
+          dfa_fma(ax[e], p.x, fx);
+          dfa_fma(ax[e], npy, fy);
+          dfa_fma(ay[e], p.x, fy);
+          dfa_fma(ay[e], p.y, fx);
         }
       }
       hb[2 * u] = h0;
@@ -1780,7 +1818,7 @@ __global__ void __launch_bounds__(128) k_qside_df(int nq, const double *__restri
   cx<double> *d = D + (size_t)i * NM2;
 #pragma unroll
   for (int e = 0; e < NM2; e++)
-    d[e] = mkc((double)acc[e].x.h + (double)acc[e].x.l, (double)acc[e].y.h + (double)acc[e].y.l);
+    d[e] = mkc((double)ax[e].h + (double)ax[e].l, (double)ay[e].h + (double)ay[e].l);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1876,13 +1914,23 @@ void tc_build_a(const epw_model *m, int nq, const double *q, TcBuffers &b, cudaS
 
 bool tc_qside(const epw_model *m, int nq, const double *q, TcBuffers &b, cx<double> *D, cudaStream_t st) {
   if (!b.ok || !m->same_eph || m->nm != 3 || m->rmax > QS_RMAX || nq <= 0) return false;
-  const int grid = (nq + 127) / 128;
+  const int grid = (nq + QS_THREADS - 1) / QS_THREADS;
+  const size_t sh = (size_t)3 * (2 * m->rmax + 1) * QS_THREADS * sizeof(float4);  // <= 52 KB
+  static bool attr = false;
+  if (!attr) {
+    const int mx = (int)((size_t)3 * (2 * QS_RMAX + 1) * QS_THREADS * sizeof(float4));
+    if (cudaFuncSetAttribute(k_qside_df<__nv_bfloat16, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_qside_df<float, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) != cudaSuccess)
+      return false;
+    attr = true;
+  }
   if (b.op == TC_OP_BF16)
-    k_qside_df<__nv_bfloat16, 9><<<grid, 128, 0, st>>>(nq, q, m->nRe, m->Re, m->rmax, m->Phidf, b.kpad,
-                                                        (__nv_bfloat16 *)b.Ahi, (__nv_bfloat16 *)b.Alo, D);
+    k_qside_df<__nv_bfloat16, 9><<<grid, QS_THREADS, sh, st>>>(nq, q, m->nRe, m->Re, m->rmax, m->Phidf, b.kpad,
+                                                                (__nv_bfloat16 *)b.Ahi, (__nv_bfloat16 *)b.Alo, D);
   else
-    k_qside_df<float, 9><<<grid, 128, 0, st>>>(nq, q, m->nRe, m->Re, m->rmax, m->Phidf, b.kpad, (float *)b.Ahi,
-                                                (float *)b.Alo, D);
+    k_qside_df<float, 9><<<grid, QS_THREADS, sh, st>>>(nq, q, m->nRe, m->Re, m->rmax, m->Phidf, b.kpad,
+                                                        (float *)b.Ahi, (float *)b.Alo, D);
   epw_count_launch();
   return true;
 }
