@@ -757,7 +757,7 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
     CK(cudaMemcpyAsync(p.qd, q, sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, st));
     qd = p.qd;
   }
-  CKS(run_prep(m, nk, kd, nq, qd, wprec, omega_min, nk > 0, p, omd, st));
+  CKS(run_prep(m, nk, kd, nq, qd, wprec, omega_min, nk > 0, p, omd, st, true, tc ? &tcb : nullptr));
   if (ekd && nk > 0) CK(cudaMemcpyAsync(ekd, p.epsk, sizeof(double) * nk * nw, cudaMemcpyDeviceToDevice, st));
   if (tc && nk > 0 && nq > 0 && (ekqd || gd)) {
     tcb.Cpol = m->polar ? (const float2 *)p.Cpol : nullptr;

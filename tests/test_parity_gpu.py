@@ -231,3 +231,22 @@ def test_tc_benchmark_model_per_quantity(epw, oracle_lib, prec, tol_e, tol_g):
           f"degenerate |g|^2 max rel {worst:.2e}")
     assert de.max() < tol_e
     assert worst < tol_g
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tc_phonons_wide_r_set(epw, oracle_lib, prec):
+    """Phonons of the tensor-core forms (phases by one-axis factor powers and D(q) in double-float)
+    on a 429-vector fcc set (|R_j| up to 5), at Gamma, near Gamma and at random q: w^2 within
+    1e-14 eV^2 of the FP64 oracle, and the bands at k+q within the split-contraction error."""
+    wm = W.make_model("fcc", 4, 1, [1.0], 400, 400, np.random.default_rng(620))
+    rng = np.random.default_rng(621)
+    k = rng.random((2, 3))
+    q = np.concatenate([np.zeros((1, 3)), 1e-3 * rng.standard_normal((8, 3)), rng.random((120, 3))])
+    m = epw.Model(wm)
+    ek, ekq, om, g = m.interp(k, q, precision=epw.PRECISIONS[prec])
+    rk, rkq, rom, rg = oracle_lib.interp(wm, k, q)
+    assert np.abs(ek - rk).max() < 1e-10
+    w2err = np.abs(om * np.abs(om) - rom * np.abs(rom)).max()
+    print(prec, "wide R set: w^2 max abs err", w2err, "eps_k+q max abs err", np.abs(ekq - rkq).max())
+    assert w2err < 1e-14
+    assert np.abs(ekq - rkq).max() < (2e-4 if prec == "bf16x3" else 1e-4)
