@@ -642,6 +642,20 @@ __global__ void k_dos_terms(int nk, int nw, const double *__restrict__ epsk, con
   terms[k] = (wk ? wk[k] : 1.0 / nk) * s;
 }
 
+// 1/x for x > 0: FP32 from rcp.approx with one Newton step (about an ulp), FP64 exact.
+template <typename R>
+__device__ __forceinline__ R rcp_pos(R x);
+template <>
+__device__ __forceinline__ float rcp_pos<float>(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r * fmaf(-x, r, 2.0f);
+}
+template <>
+__device__ __forceinline__ double rcp_pos<double>(double x) {
+  return 1.0 / x;
+}
+
 // Complex self-energy of Eq. (elselfenergy) on a frequency grid (omega from E_F, i delta
 // broadening): one thread per (k, q) pair, a block holds 128 consecutive q of one k.  For
 // each band n and grid point i (the grid, then omega = 0 for the shift of Eq. (realpartselfenergy)),
@@ -679,27 +693,42 @@ __global__ void __launch_bounds__(128) k_pair_se(PairArgs a, int nom, const doub
   const R dl = (R)delta, d2 = dl * dl;
   const int nqw = (nq + 31) / 32;
   const int lane = threadIdx.x & 31;
+  // |g_mn,nu|^2 once; the Lorentzian factors depend on (omega_i, nu, m) only and
+  // serve every band n
+  R g2[MM][MW][MW];
+#pragma unroll UM
+  for (int v = 0; v < MM; v++)
+#pragma unroll UW
+    for (int m = 0; m < MW; m++)
+#pragma unroll UW
+      for (int n = 0; n < MW; n++) g2[v][m][n] = (v < nm && m < nw && n < nw) ? cabs2(G[v][m][n]) : R(0);
   for (int i = 0; i <= nom; i++) {
     const R om = i < nom ? (R)omega[i] : R(0);
-    for (int n = 0; n < nw; n++) {
-      R sr = R(0), si = R(0);
-#pragma unroll UM
-      for (int v = 0; v < MM; v++) {
-        if (v >= nm) continue;
+    R sr[MW], si[MW];
 #pragma unroll UW
-        for (int m = 0; m < MW; m++) {
-          if (m >= nw) continue;
-          const R g2 = cabs2(G[v][m][n]);
-          const R x = om - (ekq[m] - (R)a.EF);
-          const R xp = x + w[v], xm = x - w[v];
-          const R rp = R(1) / (xp * xp + d2), rm = R(1) / (xm * xm + d2);
-          // 1/(x + i delta) = (x - i delta) / (x^2 + delta^2)
-          const R tp = g2 * cp[v][m] * rp, tm = g2 * cm[v][m] * rm;
-          sr += tp * xp + tm * xm;
-          si -= (tp + tm) * dl;
+    for (int n = 0; n < MW; n++) sr[n] = si[n] = R(0);
+#pragma unroll UM
+    for (int v = 0; v < MM; v++) {
+      if (v >= nm) continue;
+#pragma unroll UW
+      for (int m = 0; m < MW; m++) {
+        if (m >= nw) continue;
+        const R x = om - (ekq[m] - (R)a.EF);
+        const R xp = x + w[v], xm = x - w[v];
+        // 1/(x + i delta) = (x - i delta) / (x^2 + delta^2)
+        const R ap = cp[v][m] * rcp_pos<R>(xp * xp + d2), am = cm[v][m] * rcp_pos<R>(xm * xm + d2);
+        const R tr = ap * xp + am * xm, ti = ap + am;
+#pragma unroll UW
+        for (int n = 0; n < MW; n++) {
+          sr[n] += g2[v][m][n] * tr;
+          si[n] += g2[v][m][n] * ti;
         }
       }
-      double dr = (double)sr, di = (double)si;
+    }
+#pragma unroll UW
+    for (int n = 0; n < MW; n++) {
+      if (n >= nw) continue;
+      double dr = (double)sr[n], di = -(double)dl * (double)si[n];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         dr += __shfl_down_sync(0xffffffffu, dr, o);
