@@ -742,17 +742,19 @@ __global__ void __launch_bounds__(128) k_pair_se(PairArgs a, int nom, const doub
 
 // Sum over the per-warp partials (fixed order, compensated) into Sigma_nk(omega_i) and, with
 // spec, the spectral function of Eq. (spectral_funct) (Sigma'' = -Im Sigma, real part shifted
-// by its value at omega = 0): one thread per (k, n).
+// by its value at omega = 0): one block per (k, n), one thread per grid point (the q-warp rows
+// of a (k, n) are read along omega, contiguously), then the spectral function from the sums.
 __global__ void k_se_finalize(int nkc, int k0, int nw, int nqw, int nom, const double2 *__restrict__ part,
                               const double *__restrict__ omega, const double *__restrict__ epsk, double EF,
                               double2 *sig, double *spec) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nkc * nw) return;
-  const int kl = t / nw, n = t % nw, k = k0 + kl;
-  auto total = [&](int i) {
+  __shared__ double re0s;
+  const int kl = blockIdx.x / nw, n = blockIdx.x % nw, k = k0 + kl;
+  const size_t stride = (size_t)nw * (nom + 1);
+  const double2 *base = part + ((size_t)kl * nqw * nw + n) * (nom + 1);
+  for (int i = threadIdx.x; i <= nom; i += blockDim.x) {
     double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
     for (int j = 0; j < nqw; j++) {
-      const double2 x = part[(((size_t)kl * nqw + j) * nw + n) * (nom + 1) + i];
+      const double2 x = base[(size_t)j * stride + i];
       double u = sr + x.x;
       cr += fabs(sr) >= fabs(x.x) ? (sr - u) + x.x : (x.x - u) + sr;
       sr = u;
@@ -760,19 +762,22 @@ __global__ void k_se_finalize(int nkc, int k0, int nw, int nqw, int nom, const d
       ci += fabs(si) >= fabs(x.y) ? (si - u) + x.y : (x.y - u) + si;
       si = u;
     }
-    return make_double2(sr + cr, si + ci);
-  };
-  const double re0 = total(nom).x;
+    const double2 t = make_double2(sr + cr, si + ci);
+    if (i < nom)
+      sig[((size_t)k * nw + n) * nom + i] = t;
+    else
+      re0s = t.x;
+  }
+  __syncthreads();
+  if (!spec) return;
+  const double re0 = re0s;
   const double e = epsk[(size_t)k * nw + n] - EF;
-  for (int i = 0; i < nom; i++) {
-    const double2 s = total(i);
+  for (int i = threadIdx.x; i < nom; i += blockDim.x) {
     const size_t o = ((size_t)k * nw + n) * nom + i;
-    sig[o] = s;
-    if (spec) {
-      const double s2 = -s.y;
-      const double den = omega[i] - e - (s.x - re0);
-      spec[o] = fabs(s2) / (EPW_PI * (den * den + s2 * s2));
-    }
+    const double2 t = sig[o];
+    const double s2 = -t.y;
+    const double den = omega[i] - e - (t.x - re0);
+    spec[o] = fabs(s2) / (EPW_PI * (den * den + s2 * s2));
   }
 }
 
@@ -1201,7 +1206,8 @@ void launch_se_finalize(int nkc, int k0, int nw, int nqw, int nom, const double2
                         const double *epsk, double EF, double2 *sig, double *spec, cudaStream_t st) {
   const int n = nkc * nw;
   if (n <= 0) return;
-  k_se_finalize<<<(n + 127) / 128, 128, 0, st>>>(nkc, k0, nw, nqw, nom, part, omega, epsk, EF, sig, spec);
+  const int bs = nom + 1 <= 64 ? 64 : nom + 1 <= 128 ? 128 : 256;
+  k_se_finalize<<<n, bs, 0, st>>>(nkc, k0, nw, nqw, nom, part, omega, epsk, EF, sig, spec);
   epw_count_launch();
 }
 
