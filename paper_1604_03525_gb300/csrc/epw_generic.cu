@@ -4,9 +4,11 @@
 // Method: EPW (Ponce et al. 2016), Eq. (linewidthel) for the reduction and the
 // Wannier interpolation of Sec. "Electron-phonon coupling in polar materials"
 // (step iii) with the U rotations of the overlap equation there.
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "epw_internal.cuh"
+#include "epw_eig4.cuh"
 
 namespace {
 
@@ -293,7 +295,28 @@ __device__ __forceinline__ bool pair_vertex(const PairArgs &a, int kl, int k, in
     }
   }
   bool nc = false;
-  jacobi_herm<R, MW>(A, U, nw, jacobi_tol<R>::tol2, jacobi_tol<R>::maxsweep, nc);
+  if constexpr (std::is_same<R, float>::value && MW == 4) {
+    if (nw == 4) {
+      // FP32 4 x 4: Householder reduction to a real tridiagonal matrix, real Jacobi
+      // (the same eigensolve as the fused kernel; every lane of the warp calls it)
+      Herm<4> Hm;
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = i; j < 4; j++)
+          Hm.a[i][j] = i == j ? mkc(A[i][i].x, 0.0f)
+                              : mkc(0.5f * (A[i][j].x + A[j][i].x), 0.5f * (A[i][j].y - A[j][i].y));
+      nc = !eig_herm4(Hm, U);
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) A[i][j] = i == j ? mkc(Hm.a[i][i].x, 0.0f) : mkc(0.0f, 0.0f);
+    } else {
+      jacobi_herm<R, MW>(A, U, nw, jacobi_tol<R>::tol2, jacobi_tol<R>::maxsweep, nc);
+    }
+  } else {
+    jacobi_herm<R, MW>(A, U, nw, jacobi_tol<R>::tol2, jacobi_tol<R>::maxsweep, nc);
+  }
   sort_eig<R, MW>(A, U, ekq, nw);
 #pragma unroll UM
   for (int v = 0; v < MM; v++)
@@ -527,7 +550,9 @@ __global__ void __launch_bounds__(128) k_pair_ph(PairArgs a) {
   constexpr int UW = MW <= 4 ? MW : 1;
   constexpr int UM = MM <= 4 ? MM : 1;
   const int q = blockIdx.x * 128 + threadIdx.x;
-  if (q >= a.nq) return;
+  // lanes past the last q run on q = 0 (the eigensolve exits on a warp vote) and write nothing
+  const bool valid = q < a.nq;
+  const int qq = valid ? q : 0;
   const int nw = a.nw, nm = a.nm, nq = a.nq;
   const int kc0 = blockIdx.y * a.nkc;
   const int kc1 = min(a.nk, kc0 + a.nkc);
@@ -537,7 +562,7 @@ __global__ void __launch_bounds__(128) k_pair_ph(PairArgs a) {
   bool keep[MM];
 #pragma unroll UM
   for (int v = 0; v < MM; v++) {
-    w[v] = v < nm ? (R)a.omegaT[(size_t)v * nq + q] : R(0);
+    w[v] = v < nm ? (R)a.omegaT[(size_t)v * nq + qq] : R(0);
     keep[v] = v < nm && (w[v] >= (R)a.omega_min) && (w[v] > R(0));
   }
   double sp[MM], sl[MM], sz = 0.0;
@@ -548,8 +573,8 @@ __global__ void __launch_bounds__(128) k_pair_ph(PairArgs a) {
     R ekq[MW];
     cx<R> U[MW][MW];
     cx<R> G[MM][MW][MW];
-    const bool conv = pair_vertex<R, MW, MM, FROMC>(a, kl, k, q, ekq, U, G);
-    if (!conv) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
+    const bool conv = pair_vertex<R, MW, MM, FROMC>(a, kl, k, qq, ekq, U, G);
+    if (!conv && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
     const double wk = a.wq ? a.wq[k] : 1.0 / a.nk_total;
     R en[MW], dn[MW], dm[MW];
 #pragma unroll UW
@@ -591,6 +616,7 @@ __global__ void __launch_bounds__(128) k_pair_ph(PairArgs a) {
       sl[v] += wk * (double)l;
     }
   }
+  if (!valid) return;
   double *o = a.partial + ((size_t)blockIdx.y * nq + q) * (2 * nm + 1);
   for (int v = 0; v < nm; v++) {
     o[v] = sp[v < MM ? v : 0];
