@@ -754,14 +754,16 @@ __global__ void __launch_bounds__(128) k_pair_se(PairArgs a, int nom, const doub
 #pragma unroll UW
     for (int n = 0; n < MW; n++) {
       if (n >= nw) continue;
-      double dr = (double)sr[n], di = -(double)dl * (double)si[n];
+      // warp sum in the working precision (FP32 forms: 32 terms, a few ulp; the FP64
+      // pipe is a small fraction of FP32 here), then FP64 for the cross-warp sum
+      R dr = sr[n], di = -dl * si[n];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         dr += __shfl_down_sync(0xffffffffu, dr, o);
         di += __shfl_down_sync(0xffffffffu, di, o);
       }
       if (lane == 0 && q - lane < nq)
-        out[(((size_t)kl * nqw + (q >> 5)) * nw + n) * (nom + 1) + i] = make_double2(dr, di);
+        out[(((size_t)kl * nqw + (q >> 5)) * nw + n) * (nom + 1) + i] = make_double2((double)dr, (double)di);
     }
   }
 }
