@@ -251,6 +251,29 @@ __device__ __forceinline__ double block_sum128(double v, double *sh /*[4]*/) {
   return s;
 }
 
+// 1/x for x > 0: FP32 from rcp.approx with one Newton step (about an ulp), FP64 exact.
+template <typename R>
+__device__ __forceinline__ R rcp_pos(R x);
+template <>
+__device__ __forceinline__ float rcp_pos<float>(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r * fmaf(-x, r, 2.0f);
+}
+template <>
+__device__ __forceinline__ double rcp_pos<double>(double x) {
+  return 1.0 / x;
+}
+
+// f(a) - f(b) for scaled arguments a, b = (e - E_F)/kT (T > 0), given ia = 1/(1 + e^{-|a|})
+// and ib = 1/(1 + e^{-|b|}): 2 sinh(d/2) e^{-S/2} ia ib with d = b - a, S = |a| + |b|, the sinh
+// through expm1 of d or -d so that no exponent is positive (the identity of fermi_diff_f).
+__device__ __forceinline__ float fermi_diff_scaled(float a, float b, float ia, float ib) {
+  const float d = b - a, S = fabsf(a) + fabsf(b);
+  const float num = d >= 0.0f ? -__expf(0.5f * (d - S)) * expm1f(-d) : __expf(-0.5f * (d + S)) * expm1f(d);
+  return num * ia * ib;
+}
+
 // The vertex of one pair (k, q) (kl = k - a.k0; qq a valid q):
 //   H(k+q)   = sum_Re P_q(Re) BH_k(Re)  (or the staged contraction)  -> Jacobi -> e_m (ascending), U
 //   X_a      = sum_Rp P_q(Rp) Bg_k(Rp, a)   (= g_a(k,q) U_k)
@@ -568,6 +591,7 @@ __global__ void __launch_bounds__(128) k_pair_ph(PairArgs a) {
   double sp[MM], sl[MM], sz = 0.0;
 #pragma unroll UM
   for (int v = 0; v < MM; v++) sp[v] = sl[v] = 0.0;
+  const float efF = (float)a.EF, iktF = a.T > 0.0 ? (float)(1.0 / (EPW_KB * a.T)) : 0.0f;
   for (int kl = kc0; kl < kc1; kl++) {
     const int k = a.k0 + kl;
     R ekq[MW];
@@ -585,6 +609,17 @@ __global__ void __launch_bounds__(128) k_pair_ph(PairArgs a) {
     }
     R z = R(0);
     R fd[MW][MW];  // f_nk - f_mk+q
+    // FP32 form: the scaled arguments (e - E_F)/kT and 1/(1 + e^{-|a|}) once per band
+    float ga[MW], ia[MW], gb[MW], ib[MW];
+    if constexpr (sizeof(R) == sizeof(float)) {
+#pragma unroll UW
+      for (int n = 0; n < MW; n++) {
+        ga[n] = (en[n] - efF) * iktF;
+        ia[n] = rcp_pos<float>(1.0f + __expf(-fabsf(ga[n])));
+        gb[n] = (ekq[n] - efF) * iktF;
+        ib[n] = rcp_pos<float>(1.0f + __expf(-fabsf(gb[n])));
+      }
+    }
 #pragma unroll UW
     for (int m = 0; m < MW; m++)
 #pragma unroll UW
@@ -595,7 +630,8 @@ __global__ void __launch_bounds__(128) k_pair_ph(PairArgs a) {
           if constexpr (sizeof(R) == sizeof(double))
             fd[m][n] = (R)fermi_diff_d((double)en[n], (double)ekq[m], a.EF, a.T);
           else
-            fd[m][n] = (R)fermi_diff_f((float)en[n], (float)ekq[m], a.EF, a.T);
+            fd[m][n] = a.T > 0.0 ? fermi_diff_scaled(ga[n], gb[m], ia[n], ib[m])
+                                 : fermi_diff_f((float)en[n], (float)ekq[m], a.EF, a.T);
         }
       }
     sz += wk * (double)z;
@@ -666,20 +702,6 @@ __global__ void k_dos_terms(int nk, int nw, const double *__restrict__ epsk, con
   double s = 0.0;
   for (int n = 0; n < nw; n++) s += gauss_r<double>(epsk[(size_t)k * nw + n] - EF, inv, norm);
   terms[k] = (wk ? wk[k] : 1.0 / nk) * s;
-}
-
-// 1/x for x > 0: FP32 from rcp.approx with one Newton step (about an ulp), FP64 exact.
-template <typename R>
-__device__ __forceinline__ R rcp_pos(R x);
-template <>
-__device__ __forceinline__ float rcp_pos<float>(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r * fmaf(-x, r, 2.0f);
-}
-template <>
-__device__ __forceinline__ double rcp_pos<double>(double x) {
-  return 1.0 / x;
 }
 
 // Complex self-energy of Eq. (elselfenergy) on a frequency grid (omega from E_F, i delta
