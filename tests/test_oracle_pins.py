@@ -10,6 +10,8 @@ sign or index, transposed operand):
                    two-step order, with Wigner-Seitz weights for even grids;
 * two-step order   vs the direct double sum, rotated with LAPACK eigenvectors
                    (also a gauge-invariance check: different eigensolvers);
+* gauge            random unitaries inside exactly degenerate subspaces of U_k,
+                   U_k+q and e_q leave the degenerate-block sums of |g|^2 unchanged;
 * linewidth        vs the closed-form one-band model (no Fourier sum and no
                    eigensolve on the checking side);
 * symmetries       time reversal with real inputs, acoustic sum rule,
@@ -544,3 +546,59 @@ def test_polar_vertex_diverges_as_one_over_q(oracle_lib):
     assert vals[0] > 0
     assert abs(vals[1] - vals[2]) < 1e-3 * vals[2]
     assert abs(vals[0] - vals[2]) < 1e-1 * vals[2]
+
+
+def _random_unitary_in_blocks(vals, tol, rng):
+    """A unitary that mixes only eigenvectors whose (ascending) values lie within tol."""
+    from tests._util import group_labels
+    lab = group_labels(vals, tol)
+    n = len(vals)
+    W = np.zeros((n, n), dtype=complex)
+    for b in range(lab.max() + 1):
+        idx = np.where(lab == b)[0]
+        z = rng.standard_normal((len(idx), len(idx))) + 1j * rng.standard_normal((len(idx), len(idx)))
+        Q, R = np.linalg.qr(z)
+        W[np.ix_(idx, idx)] = Q * (np.diag(R) / np.abs(np.diag(R)))
+    return W
+
+
+def test_gauge_invariance_in_degenerate_subspaces(oracle_lib):
+    """Random unitaries inside degenerate subspaces of U_k, U_k+q and e_q leave |g|^2 summed
+    over the degenerate blocks unchanged (the gauge-invariant quantity compared throughout).
+    Every band is doubly degenerate (H(R) = h(R) x I_2) and the sc spring model has degenerate
+    transverse modes on the q axes, so the gauge freedom is exercised."""
+    rng = np.random.default_rng(910)
+    m1 = W.make_model("sc", 1, 1, [1.0], None, None, rng, box=1)
+    H2 = np.stack([np.kron(h, np.eye(2)) for h in m1.H])
+    nR = len(m1.Re)
+    g2 = (rng.standard_normal((nR, nR, 3, 2, 2)) + 1j * rng.standard_normal((nR, nR, 3, 2, 2))) * 0.05
+    m = dataclasses.replace(m1, nw=2, H=H2, g=g2)
+    k = rng.random((2, 3))
+    q = np.array([[0.25, 0.0, 0.0], [0.0, 0.375, 0.0], [0.13, 0.41, 0.77]])
+    eps_k, eps_kq, omega, g = oracle_lib.interp(m, k, q)
+    msq = np.repeat(np.sqrt(m.mass), 3)
+    mrep = np.repeat(m.mass, 3)
+    changed = 0.0
+    for ik in range(len(k)):
+        for iq in range(len(q)):
+            G = oracle_lib.g_wannier_direct(m, k[ik], q[iq])
+            Hk = sum(np.exp(2j * np.pi * k[ik] @ R) * Hr for R, Hr in zip(m.Re, m.H))
+            Hkq = sum(np.exp(2j * np.pi * (k[ik] + q[iq]) @ R) * Hr for R, Hr in zip(m.Re, m.H))
+            D = sum(np.exp(2j * np.pi * q[iq] @ R) * P for R, P in zip(m.Rph, m.Phi)) / np.outer(msq, msq)
+            ek, Uk = np.linalg.eigh(Hk)
+            ekq, Ukq = np.linalg.eigh(Hkq)
+            w2, e = np.linalg.eigh(D)
+            w = np.sqrt(np.abs(w2)) * np.sign(w2)
+            Uk = Uk @ _random_unitary_in_blocks(ek, 1e-9, rng)
+            Ukq = Ukq @ _random_unitary_in_blocks(ekq, 1e-9, rng)
+            e = e @ _random_unitary_in_blocks(w2, 1e-12, rng)
+            keep = w >= 1e-5
+            E = np.where(keep[None, :], e / np.sqrt(2 * np.outer(mrep, np.where(keep, w, 1.0))), 0)
+            gB = np.einsum("im,aij,jn->amn", Ukq.conj(), G, Uk)
+            ref = np.einsum("amn,av->vmn", gB, E)
+            a = degenerate_sums(np.abs(g[ik, iq]) ** 2, ekq, ek, w, 1e-9)
+            b = degenerate_sums(np.abs(ref) ** 2, ekq, ek, w, 1e-9)
+            assert np.allclose(a, b, rtol=1e-10, atol=1e-14 * b.max())
+            changed = max(changed, np.abs(np.abs(g[ik, iq]) ** 2 - np.abs(ref) ** 2).max() / b.max())
+    # the rotated gauge really differs element by element
+    assert changed > 1e-3
