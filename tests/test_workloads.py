@@ -8,6 +8,7 @@ import numpy as np
 
 import workloads as W
 
+
 def test_fcc_window_kpoints_follow_their_rule(oracle_lib):
     wl = W.make_workload("fcc_nw4", nq_sub=1)
     eps_grid, _ = oracle_lib.bands(wl.model, W.uniform_grid(20))
