@@ -10,12 +10,20 @@ itself is listed in the tests named):
 * ``eigh``            -- pinned to LAPACK (numpy.linalg.eigh) and residuals
                          (tests/test_oracle_pins.py).
 * ``bands``/``phonons`` -- closed-form tight-binding bands and spring-model
-                         phonons; time reversal; acoustic sum rule.
+                         phonons; a two-atom chain with unequal masses (both
+                         branches); time reversal; acoustic sum rule.
 * ``g_wannier``       -- two-step (Rp then Re) order against the direct double
                          sum; round trip through a coarse grid; closed form.
 * ``linewidth``       -- closed-form one-band model (no Fourier sum, no
-                         eigensolve on the check side); constant-vertex
-                         (Einstein) reduction; gauge invariance; non-negativity.
+                         eigensolve on the check side); the two-atom chain with
+                         the vertex on either atom (per-atom masses in the mode
+                         factors); constant-vertex (Einstein) reduction; gauge
+                         invariance; non-negativity.
+* ``selfenergy``      -- closed-form one-band Sigma(omega); the spectral function
+                         point by point with its Re Sigma(0) shift; unit norm.
+* polar vertex        -- one-band closed form at G = 0; the G sum (|n_i| <= 2,
+                         anisotropic eps, full Born charges) against an integral
+                         representation of the lattice sum; 1/|q| divergence.
 * ``interp``          -- gauge-invariant degenerate-subspace sums against the
                          closed form and the symmetries above.
 * ``linewidth_grad``  -- central finite differences of ``linewidth``.

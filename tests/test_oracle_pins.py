@@ -17,7 +17,16 @@ sign or index, transposed operand):
 * symmetries       time reversal with real inputs, acoustic sum rule,
                    non-negativity;
 * occupations      closed forms, limits, n(-w) = -1 - n(w), unit-norm delta;
-* adjoint          central finite differences of the forward oracle.
+* adjoint          central finite differences of the forward oracle;
+* masses           a two-atom chain with unequal masses: both phonon branches and
+                   the linewidth with the vertex on either atom (1/sqrt(M_k M_k')
+                   in D(q), 1/sqrt(2 M_k w) per atom in the mode factors);
+* constant vertex  Einstein phonons with g_a(k,q) = c_a: Im Sigma from the band
+                   energies alone (degenerate modes summed);
+* spectral fn      A_nk(w) point by point from the closed-form Sigma of the
+                   one-band model with its Re Sigma(0) shift;
+* polar G sum      |n_i| <= 2, diagonal anisotropic eps, full Born charges,
+                   against an integral representation of the lattice sum.
 """
 import dataclasses
 import itertools
@@ -602,3 +611,176 @@ def test_gauge_invariance_in_degenerate_subspaces(oracle_lib):
             changed = max(changed, np.abs(np.abs(g[ik, iq]) ** 2 - np.abs(ref) ** 2).max() / b.max())
     # the rotated gauge really differs element by element
     assert changed > 1e-3
+
+
+# ------------------------------------------------ unequal masses (two-atom chain)
+def _chain_closed_form(q, M, Kx):
+    """Branches of the x-polarised chain: eigenvalues lam_+- of
+    [[2K/M0, b], [conj b, 2K/M1]], b = -K (1 + e^{-2 pi i q_x}) / sqrt(M0 M1), and the
+    weights |e_0|^2, |e_1|^2 of each eigenvector on the two atoms."""
+    M0, M1 = M
+    s = Kx * (1.0 / M0 + 1.0 / M1)
+    root = np.sqrt(s * s - 4.0 * Kx * Kx * np.sin(np.pi * q[:, 0]) ** 2 / (M0 * M1))
+    lam = np.stack([s - root, s + root], axis=1)  # acoustic, optical
+    b2 = Kx * Kx * np.abs(1.0 + np.exp(-2j * np.pi * q[:, 0])) ** 2 / (M0 * M1)
+    d = lam - 2.0 * Kx / M0
+    e0 = b2[:, None] / (b2[:, None] + d * d)
+    return np.sqrt(lam), e0, 1.0 - e0
+
+
+def test_two_atom_chain_phonons_closed_form(oracle_lib):
+    M, K = (1.0, 2.5), (0.010, 0.017, 0.029)
+    m = W.diatomic_chain_model(M=M, Kdiag=K)
+    rng = np.random.default_rng(140)
+    q = rng.random((40, 3))
+    w, _ = oracle_lib.phonons(m, q)
+    ref = np.concatenate([_chain_closed_form(q, M, Kc)[0] for Kc in K], axis=1)
+    assert np.allclose(np.sort(w, axis=1), np.sort(ref, axis=1), rtol=1e-10, atol=1e-13)
+
+
+@pytest.mark.parametrize("couple,comp", [(0, 0), (1, 0), (0, 1), (1, 2)])
+def test_two_atom_chain_linewidth_per_atom_mass(oracle_lib, couple, comp):
+    """The vertex on one displacement component of one atom: |g_nu|^2 = g0^2 sin^2(2 pi q_x)
+    |e_couple|^2 / (2 M_couple w_nu) on the two branches of that polarisation, 0 on the others
+    (no Fourier sum, no eigensolve here)."""
+    M, K, g0 = (1.0, 2.5), (0.010, 0.017, 0.029), 0.05
+    m = W.diatomic_chain_model(M=M, Kdiag=K, couple=couple, comp=comp, g0=g0)
+    k = W.uniform_grid(2) + 0.07
+    q = W.uniform_grid(6) + 0.031
+    T, EF, sigma = 300.0, 0.05, 0.05
+    got = oracle_lib.linewidth(m, k, q, None, T, EF, sigma)[:, 0]
+    w, e0, e1 = _chain_closed_form(q, M, K[comp])
+    wt = e0 if couple == 0 else e1
+    ref = np.zeros(len(k))
+    for ik, kk in enumerate(k):
+        ek = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * kk).sum()
+        s = 0.0
+        for iq, qq in enumerate(q):
+            ekq = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * (kk + qq)).sum()
+            f = _fermi(ekq, EF, T)
+            for br in range(2):
+                wv = w[iq, br]
+                g2 = g0 ** 2 * math.sin(2 * math.pi * qq[0]) ** 2 * wt[iq, br] / (2 * M[couple] * wv)
+                n = _bose(wv, T)
+                s += g2 * ((n + f) * _gauss(ek - ekq + wv, sigma) + (n + 1 - f) * _gauss(ek - ekq - wv, sigma))
+        ref[ik] = math.pi * s / len(q)
+    assert np.all(ref > 0)
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-14 * ref.max())
+
+
+# --------------------------------------------- constant vertex (Einstein phonons)
+@pytest.mark.parametrize("T,EF", [(300.0, 0.1), (0.0, -0.2)])
+def test_constant_vertex_einstein_reduction(oracle_lib, T, EF):
+    """g_a(k,q) = c_a and w_qnu = w0 for all three (degenerate) modes: sum_nu |g_nu|^2 =
+    |c|^2 / (2 M w0) whatever the eigenvectors, so Im Sigma_k = pi |c|^2/(2 M w0) sum_q w_q
+    [(n + f) d(e_k - e_k+q + w0) + (n + 1 - f) d(e_k - e_k+q - w0)] from band energies alone."""
+    M, w0, c = 1.4, 0.06, np.array([0.03, -0.02j, 0.05])
+    m = W.einstein_model(M=M, w0=w0, c=c)
+    k = W.uniform_grid(3) + 0.05
+    q = W.uniform_grid(7)
+    sigma = 0.04
+    got = oracle_lib.linewidth(m, k, q, None, T, EF, sigma)[:, 0]
+    c2 = float(np.sum(np.abs(c) ** 2)) / (2 * M * w0)
+    n = _bose(w0, T)
+    ref = np.zeros(len(k))
+    for ik, kk in enumerate(k):
+        ek = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * kk).sum()
+        s = 0.0
+        for qq in q:
+            ekq = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * (kk + qq)).sum()
+            f = _fermi(ekq, EF, T)
+            s += (n + f) * _gauss(ek - ekq + w0, sigma) + (n + 1 - f) * _gauss(ek - ekq - w0, sigma)
+        ref[ik] = math.pi * c2 * s / len(q)
+    assert np.all(ref > 0)
+    assert np.allclose(got, ref, rtol=1e-11, atol=1e-14 * ref.max())
+
+
+# ------------------------------------- spectral function point by point (one band)
+def test_spectral_function_pointwise_with_shift(oracle_lib):
+    """Eq. (spectral_funct) with Sigma~' = Sigma'(w) - Sigma'(0) (Eq. realpartselfenergy, w from E_F),
+    from the closed-form Sigma(w) of the one-band model on the grid and at w = 0."""
+    m = _tb()
+    rng = np.random.default_rng(92)
+    k = rng.random((3, 3))
+    q = W.uniform_grid(4) + 0.01
+    omega = np.linspace(-0.4, 0.4, 41)
+    T, EF, delta = 300.0, 0.05, 0.02
+
+    def sigma_cf(kk, om):
+        out = np.zeros(len(om), dtype=complex)
+        for qq in q:
+            x = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * (kk + qq)).sum() - EF
+            f = _fermi(x + EF, EF, T)
+            for a in range(3):
+                w = 2 * math.sqrt(0.01 / 1.3) * abs(math.sin(math.pi * qq[a]))
+                if w < 1e-5:
+                    continue
+                g2 = 0.05 ** 2 * math.sin(2 * math.pi * qq[a]) ** 2 / (2 * 1.3 * w)
+                nb = _bose(w, T)
+                out += g2 * ((nb + f) / (om - x + w + 1j * delta) + (nb + 1 - f) / (om - x - w + 1j * delta))
+        return out / len(q)
+
+    _, spec = oracle_lib.selfenergy(m, k, q, omega, None, T, EF, delta)
+    for ik, kk in enumerate(k):
+        s = sigma_cf(kk, omega)
+        s0 = sigma_cf(kk, np.zeros(1))[0]
+        xn = 0.2 - 2 * 0.5 * np.cos(2 * np.pi * kk).sum() - EF
+        s2 = -s.imag
+        ref = np.abs(s2) / (math.pi * ((omega - xn - (s.real - s0.real)) ** 2 + s2 ** 2))
+        assert np.allclose(spec[ik, 0], ref, rtol=1e-10, atol=1e-14 * ref.max())
+        # the shift matters: without it the spectral function differs
+        unshifted = np.abs(s2) / (math.pi * ((omega - xn - s.real) ** 2 + s2 ** 2))
+        assert np.abs(unshifted - ref).max() > 1e-3 * ref.max()
+
+
+# ------------------------------------------ polar G sum beyond G = 0 (one atom)
+def _polar_F_integral(q, eps_d, Z, alpha, gmax):
+    """F_a = sum_{|n_i| <= gmax} (x Z)_a e^{-x.eps.x/(4 alpha)} / (x.eps.x), x = 2 pi (q + n) (sc, a = 1),
+    for diagonal eps, through e^{-s/(4 alpha)}/s = int_{1/(4 alpha)}^inf e^{-s t} dt: the sum over the
+    G box becomes a product of one-axis sums under a one-dimensional integral,
+      sum_G x_c e^{-s t} = S1_c(t) prod_{d != c} S0_d(t),
+      S0_d(t) = sum_n e^{-eps_d x_d^2 t},  S1_c(t) = sum_n x_c e^{-eps_c x_c^2 t}."""
+    from scipy.integrate import quad
+    ns = np.arange(-gmax, gmax + 1)
+    xs = [2 * np.pi * (q[c] + ns) for c in range(3)]
+
+    def S0(d, t):
+        return float(np.sum(np.exp(-eps_d[d] * xs[d] ** 2 * t)))
+
+    def S1(c, t):
+        return float(np.sum(xs[c] * np.exp(-eps_d[c] * xs[c] ** 2 * t)))
+
+    I = np.zeros(3)
+    for c in range(3):
+        others = [d for d in range(3) if d != c]
+        f = lambda t, c=c, o=others: S1(c, t) * S0(o[0], t) * S0(o[1], t)  # noqa: E731
+        I[c] = quad(f, 1.0 / (4 * alpha), np.inf, epsabs=0.0, epsrel=1e-13, limit=400)[0]
+    return I @ Z  # F_a = sum_c I_c Z[c][a]
+
+
+def test_polar_g_sum_anisotropic_beyond_gamma(oracle_lib):
+    """One band, one atom (the tight-binding model, Cartesian modes), diagonal anisotropic eps_inf,
+    a full Born-charge tensor, G box |n_i| <= 2: the long-range vertex of each mode,
+    |g^L_a| = pref |F_a| / sqrt(2 M w_a), against the integral representation of the G sum."""
+    m = _tb()
+    eps_d = np.array([4.0, 6.5, 9.0])
+    Z = np.array([[1.3, 0.4, -0.2], [0.1, 0.8, 0.5], [-0.6, 0.3, 1.7]])
+    alpha, pref, gmax, M = 40.0, 0.04, 2, 1.3
+    mp = dataclasses.replace(m, polar=W.models.PolarTerms(A=np.eye(3), eps_inf=np.diag(eps_d), Zstar=Z[None],
+                                                          alpha=alpha, prefactor=pref, gmax=gmax))
+    rng = np.random.default_rng(96)
+    k = rng.random((1, 3))
+    q = rng.random((6, 3)) - 0.5
+    _, _, om, g = oracle_lib.interp(mp, k, q)
+    _, _, _, gs = oracle_lib.interp(m, k, q)
+    for iq, qq in enumerate(q):
+        F = _polar_F_integral(qq, eps_d, Z, alpha, gmax)
+        gl = np.abs(g[0, iq, :, 0, 0] - gs[0, iq, :, 0, 0])  # modes in ascending w
+        wa = 2 * math.sqrt(0.01 / M) * np.abs(np.sin(np.pi * qq))
+        order = np.argsort(wa)
+        ref = pref * np.abs(F[order]) / np.sqrt(2 * M * wa[order])
+        assert np.allclose(om[iq], wa[order], rtol=1e-12)
+        assert np.allclose(gl, ref, rtol=1e-9, atol=1e-15), (gl, ref)
+        # terms beyond G = 0 matter at this alpha
+        F0 = _polar_F_integral(qq, eps_d, Z, alpha, 0)
+        assert np.abs(F - F0).max() > 1e-3 * np.abs(F).max()

@@ -19,4 +19,6 @@ from .models import (  # noqa: F401
     WORKLOADS,
     load_kpoint_file,
     tight_binding_model,
+    diatomic_chain_model,
+    einstein_model,
 )

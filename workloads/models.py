@@ -316,6 +316,70 @@ def tight_binding_model(eps0=0.2, t=0.5, K=0.01, g0=0.05, mass=1.0) -> WannierMo
     )
 
 
+def diatomic_chain_model(M=(1.0, 2.5), Kdiag=(0.010, 0.017, 0.029), couple=0, comp=0, g0=0.05, eps0=0.2, t=0.5):
+    """One band; a simple cubic cell (a = 1) with two atoms, kappa = 0 at the origin and
+    kappa = 1 at (1/2, 0, 0), masses M; chains along x: each atom bonded to its two x
+    neighbours of the other kind by the spring tensor diag(Kdiag) (one chain per Cartesian
+    polarisation).  Electrons as in tight_binding_model.  The vertex couples only the
+    displacement component `comp` of atom `couple`: g_{couple,comp}(Re=0, Rp=+-e_x) = -+ i g0/2.
+
+    Force constants Phi(R)_{kappa alpha, kappa' beta}: atom kappa in cell 0 with atom kappa'
+    in cell R.  Every interpolated quantity has a closed form (used by the tests).
+    """
+    Re = box_vectors(1)
+    idx = _index_of(Re)
+    H = np.zeros((len(Re), 1, 1), dtype=np.complex128)
+    H[idx[(0, 0, 0)], 0, 0] = eps0
+    for a in range(3):
+        for sgn in (+1, -1):
+            e = [0, 0, 0]
+            e[a] = sgn
+            H[idx[tuple(e)], 0, 0] = -t
+    Kt = np.diag(np.asarray(Kdiag, dtype=np.float64))
+    Phi = np.zeros((len(Re), 6, 6), dtype=np.complex128)
+    i0, ip, im = idx[(0, 0, 0)], idx[(1, 0, 0)], idx[(-1, 0, 0)]
+    Phi[i0, 0:3, 0:3] = 2.0 * Kt
+    Phi[i0, 3:6, 3:6] = 2.0 * Kt
+    Phi[i0, 0:3, 3:6] = -Kt  # atom 0 with atom 1 of the same cell
+    Phi[i0, 3:6, 0:3] = -Kt
+    Phi[im, 0:3, 3:6] = -Kt  # atom 0 with atom 1 of the cell at -e_x
+    Phi[ip, 3:6, 0:3] = -Kt  # atom 1 with atom 0 of the cell at +e_x
+    g = np.zeros((len(Re), len(Re), 6, 1, 1), dtype=np.complex128)
+    for sgn in (+1, -1):
+        g[i0, idx[(sgn, 0, 0)], 3 * couple + comp, 0, 0] = -sgn * 0.5j * g0
+    return WannierModel(
+        lattice="sc", nw=1, nat=2, mass=np.asarray(M, dtype=np.float64),
+        Re=Re, wRe=np.ones(len(Re)), H=H,
+        Rph=Re.copy(), wRph=np.ones(len(Re)), Phi=Phi,
+        Rp=Re.copy(), wRp=np.ones(len(Re)), g=g,
+    )
+
+
+def einstein_model(M=1.4, w0=0.06, c=(0.03, -0.02j, 0.05), eps0=0.2, t=0.5):
+    """One band, one atom, simple cubic: tight-binding electrons, dispersionless (Einstein)
+    phonons Phi(0) = M w0^2 I (three modes of frequency w0) and a constant vertex
+    g_a(Re=0, Rp=0) = c_a, so that g_a(k,q) = c_a for every k and q."""
+    Re = box_vectors(1)
+    idx = _index_of(Re)
+    H = np.zeros((len(Re), 1, 1), dtype=np.complex128)
+    H[idx[(0, 0, 0)], 0, 0] = eps0
+    for a in range(3):
+        for sgn in (+1, -1):
+            e = [0, 0, 0]
+            e[a] = sgn
+            H[idx[tuple(e)], 0, 0] = -t
+    Phi = np.zeros((len(Re), 3, 3), dtype=np.complex128)
+    Phi[idx[(0, 0, 0)]] = M * w0 * w0 * np.eye(3)
+    g = np.zeros((len(Re), len(Re), 3, 1, 1), dtype=np.complex128)
+    g[idx[(0, 0, 0)], idx[(0, 0, 0)], :, 0, 0] = np.asarray(c, dtype=np.complex128)
+    return WannierModel(
+        lattice="sc", nw=1, nat=1, mass=np.array([M]),
+        Re=Re, wRe=np.ones(len(Re)), H=H,
+        Rph=Re.copy(), wRph=np.ones(len(Re)), Phi=Phi,
+        Rp=Re.copy(), wRp=np.ones(len(Re)), g=g,
+    )
+
+
 @dataclasses.dataclass
 class Workload:
     """One run of the linewidth path: a model, k and q lists, and parameters."""
