@@ -330,11 +330,15 @@ uint64_t epw_launch_count(void);
 
 /* Measurement hook.  While enabled, each launch of the dominant (per-pair)
  * kernel is bracketed by CUDA events recorded on its launch stream (at most
- * 4096 launches are kept).  epw_timing_read synchronizes those events and
- * returns the summed device time (ms) and the number of launches, then
- * clears them. */
+ * 4096 launches are kept); the wide-shape tensor-core form also brackets its
+ * per-pair eigensolve kernel, as a second tag.  epw_timing_read synchronizes
+ * those events and returns the summed device time (ms) and the number of
+ * launches of the dominant kernel, then clears them all.
+ * epw_timing_read_tags returns both tags: ms2[0], n2[0] the dominant kernel,
+ * ms2[1], n2[1] the secondary one (either pointer may be NULL), then clears. */
 epw_status epw_timing_enable(epw_model *model, int enable);
 epw_status epw_timing_read(epw_model *model, double *total_ms, int *launches);
+epw_status epw_timing_read_tags(epw_model *model, double *ms2, int *n2);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *epw_last_error(void);

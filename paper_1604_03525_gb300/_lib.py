@@ -45,6 +45,7 @@ SIGNATURES = {
     "epw_launch_count": (ctypes.c_uint64, []),
     "epw_timing_enable": (I, [P, I]),
     "epw_timing_read": (I, [P, P, P]),
+    "epw_timing_read_tags": (I, [P, P, P]),
     "epw_last_error": (ctypes.c_char_p, []),
     "epw_abi_version": (I, []),
 }

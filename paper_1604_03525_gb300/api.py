@@ -151,6 +151,15 @@ class Model:
         _check(_lib.load().epw_timing_read(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
+    def timing_read_tags(self):
+        """((ms, launches) of the dominant kernel, (ms, launches) of the secondary one) since
+        the last read; the secondary one is the per-pair eigensolve kernel of the wide-shape
+        tensor-core form."""
+        ms = (ctypes.c_double * 2)()
+        n = (ctypes.c_int * 2)()
+        _check(_lib.load().epw_timing_read_tags(self._h, ms, n))
+        return (ms[0], n[0]), (ms[1], n[1])
+
     # ------------------------------------------------------------- linewidth
     def linewidth(self, k, q, wq=None, *, T: float, EF: float, sigma: float, omega_min: float = 1e-5,
                   precision: int = FP64, out=None):

@@ -94,6 +94,8 @@ static void free_model_arrays(epw_model *m) {
     free(m->ev);
     m->ev = nullptr;
   }
+  free(m->ev_tag);
+  m->ev_tag = nullptr;
   tc_free(m);
 }
 
@@ -283,10 +285,14 @@ extern "C" epw_status epw_model_info(const epw_model *m, int *nw, int *nat, int 
 extern "C" uint64_t epw_launch_count(void) { return g_launches.load(); }
 
 // ------------------------------------------------------ measurement hook
-void epw_timing_begin(epw_model *m, cudaStream_t st) {
+// Timed launches carry a tag: 0 the dominant kernel, 1 a secondary one (the
+// per-pair eigensolve kernel of the wide-shape form).
+void epw_timing_begin_tag(epw_model *m, cudaStream_t st, int tag) {
   if (!m->timing || !m->ev || m->nev >= EPW_MAX_TIMED) return;
   cudaEventRecord(m->ev[2 * m->nev], st);
+  m->ev_tag[m->nev] = (unsigned char)(tag & 1);
 }
+void epw_timing_begin(epw_model *m, cudaStream_t st) { epw_timing_begin_tag(m, st, 0); }
 void epw_timing_end(epw_model *m, cudaStream_t st) {
   if (!m->timing || !m->ev || m->nev >= EPW_MAX_TIMED) return;
   cudaEventRecord(m->ev[2 * m->nev + 1], st);
@@ -297,7 +303,8 @@ extern "C" epw_status epw_timing_enable(epw_model *m, int enable) {
   if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
   if (enable && !m->ev) {
     m->ev = (cudaEvent_t *)calloc(2 * EPW_MAX_TIMED, sizeof(cudaEvent_t));
-    if (!m->ev) return fail(EPW_ERR_OOM, "host allocation failed");
+    m->ev_tag = (unsigned char *)calloc(EPW_MAX_TIMED, 1);
+    if (!m->ev || !m->ev_tag) return fail(EPW_ERR_OOM, "host allocation failed");
     for (int i = 0; i < 2 * EPW_MAX_TIMED; i++) CK(cudaEventCreate(&m->ev[i]));
   }
   m->timing = enable ? 1 : 0;
@@ -305,18 +312,31 @@ extern "C" epw_status epw_timing_enable(epw_model *m, int enable) {
   return EPW_OK;
 }
 
-extern "C" epw_status epw_timing_read(epw_model *m, double *total_ms, int *launches) {
+extern "C" epw_status epw_timing_read_tags(epw_model *m, double *ms2, int *n2) {
   if (!m) return fail(EPW_ERR_INVALID_ARG, "null model");
-  double tot = 0.0;
+  double tot[2] = {0.0, 0.0};
+  int cnt[2] = {0, 0};
   for (int i = 0; i < m->nev; i++) {
     float ms = 0.0f;
     CK(cudaEventSynchronize(m->ev[2 * i + 1]));
     CK(cudaEventElapsedTime(&ms, m->ev[2 * i], m->ev[2 * i + 1]));
-    tot += ms;
+    tot[m->ev_tag[i]] += ms;
+    cnt[m->ev_tag[i]]++;
   }
-  if (total_ms) *total_ms = tot;
-  if (launches) *launches = m->nev;
+  for (int t = 0; t < 2; t++) {
+    if (ms2) ms2[t] = tot[t];
+    if (n2) n2[t] = cnt[t];
+  }
   m->nev = 0;
+  return EPW_OK;
+}
+
+extern "C" epw_status epw_timing_read(epw_model *m, double *total_ms, int *launches) {
+  double ms2[2];
+  int n2[2];
+  CKS(epw_timing_read_tags(m, ms2, n2));
+  if (total_ms) *total_ms = ms2[0];
+  if (launches) *launches = n2[0];
   return EPW_OK;
 }
 extern "C" const char *epw_last_error(void) { return g_err; }
@@ -541,9 +561,13 @@ epw_status epwi_plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int
   plan_prep(A, m, nk, nq, tc ? EPW_FP32 : prec, sk, sq, swq, true, L.p);
   L.sg = TcStaged{};
   L.tc = TcBuffers{};
+  L.w = TcwBuffers{};
   if (tc && tc_supported(m)) {
     CKS(tc_plan(A, m, nk, nq, op, L.tc));
     L.tc.a_block_bytes = tune.a_block_bytes;
+    L.partial = nullptr;
+  } else if (tc && tcw_supported(m)) {
+    CKS(tcw_plan(A, m, nk, nq, op, 0, L.w));
     L.partial = nullptr;
   } else {
     if (tc) CKS(tc_staged_plan(A, m, nk, nq, op, tune.staged_ct_bytes ? tune.staged_ct_bytes : STAGED_CT_BYTES, L.sg));
@@ -622,7 +646,7 @@ epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, c
   const int prec = par->precision;
   Prep &p = L.p;
   const bool tcp = prec == EPW_BF16X3 || prec == EPW_TF32X3;
-  if (tcp && !L.tc.ok && !L.sg.ok)
+  if (tcp && !L.tc.ok && !L.sg.ok && !L.w.ok)
     return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
   if (tcp && L.tc.ok) {
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st, true, &L.tc));
@@ -632,6 +656,13 @@ epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, c
     epw_status s = tc_linewidth(m, nk, kd, nq, qd, wqd, par, p.PkRM, p.epsk, p.Uk, p.omegaT, (const cx<float> *)p.ET,
                                 (const cx<float> *)p.Bg, (const cx<float> *)p.BH, L.tc, out, st);
     if (s != EPW_OK) return fail(s, "tensor-core path: %s", g_err[0] ? g_err : "unsupported shape");
+  } else if (tcp && L.w.ok) {
+    // wide-shape fused form: per chunk of k, the H(k+q) eigensolve kernel and the vertex kernel
+    CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));
+    epw_status s = tcw_linewidth(m, nk, nq, qd, wqd, par, p.epsk, p.omegaT, (const cx<float> *)p.ET,
+                                 (const cx<float> *)p.Bg, (const cx<float> *)p.BH, m->same_eph ? p.PqTph : nullptr,
+                                 p.Uk, m->polar ? (const float2 *)p.Cpol : nullptr, L.w, out, st);
+    if (s != EPW_OK) return fail(s, "wide tensor-core path: %s", g_err[0] ? g_err : "launch failed");
   } else if (tcp) {
     // staged tensor-core form: contraction per chunk of k on the tensor cores, per-pair work from HBM
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st));

@@ -33,13 +33,15 @@
 namespace {
 
 // ----------------------------------------------------------------- autotuner
-// A job's path: the fused tensor-core kernel, the staged tensor-core form, or
-// the SIMT per-pair kernel (no tile knob).
-enum Path { PATH_SIMT = 0, PATH_FUSED = 1, PATH_STAGED = 2 };
+// A job's path: the fused tensor-core kernel, the wide-shape fused form (no
+// tile knob), the staged tensor-core form, or the SIMT per-pair kernel (no tile
+// knob).
+enum Path { PATH_SIMT = 0, PATH_FUSED = 1, PATH_STAGED = 2, PATH_WIDE = 3 };
 
 int job_path(const epw_model *m, int prec) {
   if (prec != EPW_BF16X3 && prec != EPW_TF32X3) return PATH_SIMT;
   if (tc_supported(m)) return PATH_FUSED;
+  if (tcw_supported(m)) return PATH_WIDE;
   if (tc_staged_supported(m)) return PATH_STAGED;
   return -1;
 }

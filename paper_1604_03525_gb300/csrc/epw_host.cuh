@@ -44,6 +44,7 @@ struct LwPlan {
   double *out_d;
   TcBuffers tc;
   TcStaged sg;
+  TcwBuffers w;  // wide-shape fused form
 };
 
 // Lays out (or, with a null arena base, measures) the buffers of one job.

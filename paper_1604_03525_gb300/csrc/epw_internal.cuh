@@ -311,6 +311,7 @@ struct epw_model {
   int timing;
   int nev;
   cudaEvent_t *ev;        // [2 * EPW_MAX_TIMED]
+  unsigned char *ev_tag;  // [EPW_MAX_TIMED] tag of each timed launch
   // second stream for the q side of the preparation, and its fork / join events
   cudaStream_t aux;
   cudaEvent_t ev_fork, ev_join, ev_phase;
@@ -330,6 +331,7 @@ struct epw_model {
 
 // Record the start / stop event of a timed launch (no-op unless timing is on).
 void epw_timing_begin(epw_model *m, cudaStream_t st);
+void epw_timing_begin_tag(epw_model *m, cudaStream_t st, int tag);
 void epw_timing_end(epw_model *m, cudaStream_t st);
 
 // Bump allocator over the model's workspace arena.

@@ -37,12 +37,12 @@
 
 #include "epw_eig4.cuh"
 #include "epw_tc.cuh"
+#include "epw_tcgen05.cuh"
 
 namespace {
 
 constexpr int BM = 128;               // q rows per tile
 constexpr int BN = 256;               // real accumulator columns per tile
-constexpr int ROWB = 128;             // bytes per smem operand row (one 128-byte swizzle row)
 constexpr int STAGES = 2;
 constexpr int A_BYTES = BM * ROWB;    // 16 KiB
 constexpr int B_BYTES = BN * ROWB;    // 32 KiB
@@ -62,7 +62,6 @@ constexpr int epi_warps() { return MODE == 0 ? EPI_WARPS_LW : MODE == 2 ? EPI_WA
 template <int MODE>
 constexpr int nthreads() { return 32 * (EPI_WARP0 + epi_warps<MODE>()); }
 constexpr uint32_t TMEM_COLS = 512;
-constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 constexpr size_t A_BLOCK_BYTES = 48u << 20;      // q-block size target (A operand bytes)
 
 template <int OP>
@@ -88,44 +87,6 @@ struct OpT<TC_OP_TF32> {
       (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 
-// ------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(map), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
 template <int OP>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
   if constexpr (OP == TC_OP_BF16) {
@@ -142,106 +103,6 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t b
         : "memory");
   }
 }
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 lanes x 32 bit, 8 consecutive columns per thread; waits for completion.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&r)[8]) {
-  uint32_t u0, u1, u2, u3, u4, u5, u6, u7;
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(u0), "=r"(u1), "=r"(u2), "=r"(u3), "=r"(u4), "=r"(u5), "=r"(u6), "=r"(u7)
-      : "r"(taddr)
-      : "memory");
-  r[0] = __uint_as_float(u0);
-  r[1] = __uint_as_float(u1);
-  r[2] = __uint_as_float(u2);
-  r[3] = __uint_as_float(u3);
-  r[4] = __uint_as_float(u4);
-  r[5] = __uint_as_float(u5);
-  r[6] = __uint_as_float(u6);
-  r[7] = __uint_as_float(u7);
-}
-// 32 consecutive columns per thread; waits for completion.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32]) {
-  uint32_t u[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
-        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]),
-        "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
-        "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; i++) r[i] = __uint_as_float(u[i]);
-}
-// NCOL (multiple of 8, at most 32) consecutive columns into a register array.
-template <int NCOL>
-__device__ __forceinline__ void tmem_load(uint32_t taddr, float (&r)[NCOL]) {
-  static_assert(NCOL % 8 == 0 && NCOL <= 32, "8..32 columns in groups of 8");
-  if constexpr (NCOL == 32) {
-    tmem_ld32(taddr, r);
-  } else {
-#pragma unroll
-    for (int c = 0; c < NCOL; c += 8) {
-      float t[8];
-      tmem_ld8(taddr + c, t);
-#pragma unroll
-      for (int i = 0; i < 8; i++) r[c + i] = t[i];
-    }
-  }
-}
-
-// Asynchronous global -> shared copies (no register round trip); wait_all
-// completes every copy this thread has issued.
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(__cvta_generic_to_global(src)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(__cvta_generic_to_global(p)));
-}
-
-// K-major, 128-byte-swizzled smem operand: rows of 128 B, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// Bounded wait on an mbarrier phase.  Returns false on abort or timeout.
-__device__ __forceinline__ bool wait_bar_limit(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                               unsigned *dstatus, long long limit) {
-  if (mbar_try(bar, parity)) return true;
-  long long t0 = clock64();
-  uint32_t it = 0;
-  while (!mbar_try(bar, parity)) {
-    if ((++it & 127u) == 0) {
-      if (*abort_flag) return false;
-      if (clock64() - t0 > limit) {
-        *abort_flag = 1;
-        atomicOr(dstatus, EPW_DEV_TIMEOUT);
-        return false;
-      }
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag, unsigned *dstatus) {
-  return wait_bar_limit(bar, parity, abort_flag, dstatus, WAIT_CYCLES);
-}
 
 // Self-test of the failure path: one thread waits, with the kernels' bounded
 // wait, on an mbarrier that nothing arrives at; after `limit` cycles the wait
@@ -257,13 +118,6 @@ __global__ void k_wait_selftest(long long limit, unsigned *dstatus, int *waited_
     *waited_out = wait_bar_limit(smem_u32(&bar), 0, ab, dstatus, limit) ? 0 : 1;
   }
 }
-// Bounded wait that ignores the abort flag (used to drain in-flight work).
-__device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity) {
-  long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > WAIT_CYCLES) break;
-}
-
 
 struct TcArgs {
   int nk, nq, nqt, nkg, kpad, nkb, qblock;
@@ -287,13 +141,6 @@ struct TcArgs {
   const float2 *Cpol;
   const float2 *UkF;
 };
-
-// tf32 term: an fp32 with its 13 low mantissa bits cleared after rounding to nearest
-__device__ __forceinline__ float tf32_rn(float x) {
-  uint32_t u = __float_as_uint(x);
-  if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
-  return __uint_as_float(u);
-}
 
 template <int NW, int NM>
 struct Shape {
@@ -338,11 +185,6 @@ __device__ __forceinline__ int ccol(int c, int s) {
   return PLANAR ? 4 * (c >> 1) + 2 * s + (c & 1) : 2 * c + s;
 }
 
-// packed FP32 (two lanes per instruction)
-__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 // Linewidth terms of Eq. (linewidthel) for one pair from planar accumulator
 // columns (NW even).  Entries (i, j) and (i, j+1) of a block travel as one
@@ -1519,6 +1361,47 @@ cudaError_t launch_tc_shape(int nw, int nm, const CUtensorMap &ah, const CUtenso
 }
 
 }  // namespace
+
+// Operand builders, tensor maps and FP32 tables for the other tensor-core kernels.
+void tc_build_b_raw(int op, int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad, const cx<float> *BH,
+                    const cx<float> *Bg, void *hi, void *lo, cudaStream_t st) {
+  if (op == TC_OP_BF16)
+    launch_build_b<__nv_bfloat16>(nk, nk_pad, nR, nw, nm, cpk, kpad, 0, BH, Bg, (__nv_bfloat16 *)hi,
+                                  (__nv_bfloat16 *)lo, st);
+  else
+    launch_build_b<float>(nk, nk_pad, nR, nw, nm, cpk, kpad, 0, BH, Bg, (float *)hi, (float *)lo, st);
+}
+void tc_build_a_raw(int op, int nq, int nR, int kpad, const double *q, const int *R, const cx<double> *P64, void *hi,
+                    void *lo, cudaStream_t st) {
+  if (op == TC_OP_BF16)
+    build_a<__nv_bfloat16>(nq, nR, kpad, q, R, P64, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo, st);
+  else
+    build_a<float>(nq, nR, kpad, q, R, P64, (float *)hi, (float *)lo, st);
+}
+bool tc_make_map(CUtensorMap *map, const void *base, int op, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  return make_map(map, base, op, inner, rows, box_rows);
+}
+bool tc_make_map_rb(CUtensorMap *map, const void *base, int op, uint64_t inner, uint64_t rows, uint32_t box_rows,
+                    int row_bytes) {
+  auto fn = encode_fn();
+  if (!fn || (row_bytes != 128 && row_bytes != 64)) return false;
+  const int esz = op == TC_OP_BF16 ? 2 : 4;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(row_bytes / esz), box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, op == TC_OP_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+void tc_tables(int nq, int nm, int nk, int nw, const double *omegaT, double T, const double *wq, const double *epsk,
+               float *nbT, float *omF, float *wqF, float *ekF, cudaStream_t st) {
+  const size_t n = (size_t)nq * nm + nq + (size_t)nk * nw;
+  k_tc_tables<<<grid_for(n, 256), 256, 0, st>>>(nq, nm, nk, nw, omegaT, T, wq, epsk, nbT, omF, wqF, ekF);
+  epw_count_launch();
+}
 
 void tc_build_b(const epw_model *m, int nk, const cx<float> *Bg32, const cx<float> *BH32, TcBuffers &b,
                 cudaStream_t st) {

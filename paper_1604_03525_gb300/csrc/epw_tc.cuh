@@ -1,5 +1,7 @@
 // Tensor-core (tcgen05) form of the fused linewidth kernel.
 #pragma once
+#include <cuda.h>
+
 #include "epw_internal.cuh"
 
 // Operand split of the tensor-core contraction.
@@ -51,6 +53,50 @@ epw_status tc_interp(const epw_model *m, int nk, int nq, const double *q, double
                      const double *omegaT, const cx<float> *ET32, const cx<float> *Bg32, const cx<float> *BH32,
                      TcBuffers &b, double *eps_kq, double *g, cudaStream_t st);
 void tc_free(epw_model *m);
+
+// Raw operand builders and maps shared with the wide-shape kernels (epw_tcw.cu):
+// B rows [nk_pad][cpk][kpad] from BH [nk][nR][nw][nw] and Bg [nk][nR][nm][nw][nw]
+// (nm = 0: the H(k+q) block only); A [nq][kpad] from P64 [nR][nq] or from q.
+void tc_build_b_raw(int op, int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad, const cx<float> *BH,
+                    const cx<float> *Bg, void *hi, void *lo, cudaStream_t st);
+void tc_build_a_raw(int op, int nq, int nR, int kpad, const double *q, const int *R, const cx<double> *P64, void *hi,
+                    void *lo, cudaStream_t st);
+// 2D K-major map [rows][inner], box [box_rows][128 bytes], 128-byte swizzle.
+bool tc_make_map(CUtensorMap *map, const void *base, int op, uint64_t inner, uint64_t rows, uint32_t box_rows);
+// The same with rows of row_bytes (128: 128-byte swizzle; 64: 64-byte swizzle).
+bool tc_make_map_rb(CUtensorMap *map, const void *base, int op, uint64_t inner, uint64_t rows, uint32_t box_rows,
+                    int row_bytes);
+// FP32 tables: Bose factors and frequencies [nm][nq], q weights [nq], band energies [nk][nw].
+void tc_tables(int nq, int nm, int nk, int nw, const double *omegaT, double T, const double *wq, const double *epsk,
+               float *nbT, float *omF, float *wqF, float *ekF, cudaStream_t st);
+
+// Wide-shape fused form (epw_tcw.cu) for shapes whose per-k columns exceed the
+// fused kernel's slot: per chunk of k, kernel E contracts H(k+q) on the tensor
+// cores and diagonalises it per pair (eigenvalues and the eigenvectors some
+// band at k can reach within the Gaussian cutoff go to HBM), then kernel G
+// contracts (g_a(k,q) U_k) and evaluates only the (m, n) terms whose Gaussians
+// do not underflow.
+struct TcwBuffers {
+  void *Ahi, *Alo;     // q phases [nq][kpad]
+  void *BEhi, *BElo;   // H(k+q) operand of one chunk [kc_pad][cpk][kpad]
+  void *BGhi, *BGlo;   // vertex operand of one chunk [nchunk][bng][kpad]
+  float *epsq;         // [kc][nw][ldq] eigenvalues of H(k+q)
+  float2 *Uq;          // [kc][nw(m)][nw(i)][ldq] eigenvector m (reachable m only)
+  float *nbT, *omF, *wqF, *ekF, *thr;
+  double *partial;     // [nk][4 nqt][nw]
+  float2 *UkF;         // polar models: FP32 U_k [nk][nw][nw]
+  int op, kpad, kc, ldq, nqt, cpk, kpt, entp, cn, bng;
+  bool ok;
+};
+bool tcw_supported(const epw_model *m);
+// bytes: budget of the per-chunk eigen buffers (0: default)
+epw_status tcw_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t bytes, TcwBuffers &b);
+// Im Sigma [nk][nw] into `out` (device) from the preparation outputs (P64: FP64 q phases of
+// the Re set [nR][nq] or null; Cpol [nm][nq] and Uk for polar models, else null).
+epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, const double *wq,
+                         const epw_params *par, const double *epsk, const double *omegaT, const cx<float> *ET32,
+                         const cx<float> *Bg32, const cx<float> *BH32, const cx<double> *P64,
+                         const cx<double> *Uk, const float2 *Cpol, TcwBuffers &b, double *out, cudaStream_t st);
 
 // Buffers of the tensor-core adjoint (per chunk of kc k-points).
 struct TcBwdBuffers {

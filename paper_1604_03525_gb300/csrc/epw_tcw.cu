@@ -1,0 +1,733 @@
+// Wide-shape fused linewidth path on the 5th-generation tensor cores (sm_103a),
+// for models whose per-k accumulator columns 2 nw^2 (3nat + 1) exceed the fused
+// kernel's 128-column slot (diamond nw = 8 with 6 modes, hexagonal nw = 5 with 9).
+//
+// The per-pair work of Eq. (linewidthel) splits into two tcgen05 kernels per
+// chunk of k-points, both over the same A operand of q phases P_q(R) (real GEMM,
+// K = 2 nR with re/im interleaved, split into two bf16 or tf32 terms, three
+// MMAs per K step, FP32 accumulation in tensor memory):
+//
+//  E  C[q][(k, i, j)] = sum_R P_q(R) P_k(R) H(R) = H(k+q)_ij; the epilogue takes
+//     the Hermitian part and diagonalises it per pair in FP32 (Householder +
+//     implicit QR, epw_eigqr.cuh), writes the eigenvalues e_m,k+q and, for the
+//     bands m that some band n at k can reach within the Gaussian cutoff
+//     (|e_nk - e_m,k+q| <= max_nu w_q,nu + X sigma), the eigenvectors u_m.
+//  G  C[q][((k, n), a, j)] = sum_R P_q(R) (g_a(k,R) U_k)_jn = (g_a(k,q) U_k)_jn,
+//     the columns of one band n of k contiguous; the epilogue forms, for the
+//     reachable (m, n) only, t_a = u_m^dagger (g_a U_k)_{:,n},
+//     g_mn,nu = sum_a E_q[a][nu] t_a (+ i C_nu(q) u_m^dagger U_k e_n for the
+//     long-range part), the occupations and Gaussians of Eq. (linewidthel),
+//     and sums |g|^2 W over the warp's 32 q rows into per-(k, q tile) partials.
+//
+// The cutoff X = sqrt(130 ln 2) (about 9.49) makes every skipped Gaussian
+// 2^-(x s)^2 with (x s)^2 > 130, which the flush-to-zero ex2 of the dense form
+// returns as exactly 0, so the sum equals the dense one term for term.
+// Both kernels are persistent (one CTA per SM): warp 0 issues TMA copies, warp
+// 1 owns tensor memory and issues the MMAs, warps 2..9 are the epilogue (two
+// per TMEM lane quadrant, taking the quadrant's items round-robin); tensor
+// memory holds two 256-column accumulator stages so the MMAs of the next tile
+// overlap the epilogue of the current one.  Every wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "epw_eigqr.cuh"
+#include "epw_tc.cuh"
+#include "epw_tcgen05.cuh"
+
+namespace {
+
+constexpr int BM = 128;  // q rows per tile
+// Operand stages: kernel E two of 128-byte K rows (128-byte swizzle); kernel G,
+// whose MMAs are the bulk of the work, four of 64-byte K rows (64-byte swizzle),
+// so that three stages are in flight while the MMAs consume the fourth.
+template <int KIND>
+constexpr int w_rowb() {
+  return KIND == 0 ? 128 : 64;
+}
+template <int KIND>
+constexpr int w_stages() {
+  return KIND == 0 ? 2 : 4;
+}
+constexpr int EPI_WARP0 = 2;
+// Epilogue warps: kernel E one per TMEM lane quadrant (six warps in all, so that
+// each thread may hold 255 registers for the eigensolve); kernel G two per quadrant.
+template <int KIND>
+constexpr int epi_warps() {
+  return KIND == 0 ? 8 : 8;
+}
+template <int KIND>
+constexpr int nthreads() {
+  return 32 * (EPI_WARP0 + epi_warps<KIND>());
+}
+constexpr uint32_t TMEM_COLS = 512;
+constexpr size_t A_BLOCK_BYTES = 48u << 20;  // q-block of the A operand kept in L2 across column groups
+// Gaussian cutoff: the dense form's ex2.approx.ftz(-(x s)^2) is exactly 0 for (x s)^2 > 126
+constexpr double CUT_SIGMAS = 9.4921453036541;  // sqrt(130 ln 2)
+
+template <int OP>
+struct WOp;
+template <>
+struct WOp<TC_OP_BF16> {
+  using T = __nv_bfloat16;
+  static constexpr int ESZ = 2, KSTEP = 16;
+  static constexpr bool F16 = true;
+  static constexpr uint32_t FMT = 1;
+};
+template <>
+struct WOp<TC_OP_TF32> {
+  using T = float;
+  static constexpr int ESZ = 4, KSTEP = 8;
+  static constexpr bool F16 = false;
+  static constexpr uint32_t FMT = 2;
+};
+// instruction descriptor: D = F32, A = B = bf16 (kind::f16) or tf32, both K-major, M = 128
+template <int OP, int N>
+constexpr uint32_t w_idesc() {
+  return (1u << 4) | (WOp<OP>::FMT << 7) | (WOp<OP>::FMT << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int NW, int NM>
+struct WShape {
+  static constexpr int H2 = 2 * NW * NW;                            // real columns of H(k+q)
+  static constexpr int CPK = H2 <= 32 ? 32 : H2 <= 64 ? 64 : 128;   // E columns per k
+  static constexpr int KPT = 256 / CPK;                             // k per E tile
+  static constexpr int ENT = 2 * NM * NW;                           // G columns of one band n of one k
+  static constexpr int ENTP = (ENT + 31) / 32 * 32;
+  static constexpr int CN = 256 / ENTP;                             // (k, n) entries per G tile
+  static constexpr int BNG = CN * ENTP;
+  static_assert(H2 <= 128 && ENTP <= 256, "shape beyond the wide tensor-core form");
+};
+template <int NW, int NM, int KIND>
+constexpr int w_bn() {
+  return KIND == 0 ? 256 : WShape<NW, NM>::BNG;
+}
+template <int NW, int NM, int KIND>
+constexpr int w_units() {
+  return KIND == 0 ? WShape<NW, NM>::KPT : WShape<NW, NM>::CN;
+}
+template <int NW, int NM, int KIND>
+constexpr int w_smem() {
+  return w_stages<KIND>() * (2 * BM + 2 * w_bn<NW, NM, KIND>()) * w_rowb<KIND>() + 1024;
+}
+
+struct TcwArgs {
+  int nq, nqt, ngrp, kpad, nkb, qblock;
+  int k0, kc;             // chunk: global k = k0 + kl, kl < kc
+  int ldq;                // q stride of the per-pair buffers (nqt * 128)
+  const float *epsk;      // [nk][nw]
+  const float *thr;       // [nq] max kept w_q,nu + cutoff (negative: no kept mode)
+  const float *omegaT;    // [nm][nq]
+  const float *nbT;       // [nm][nq]
+  const float2 *ET;       // [nm*nm][nq] mode factors e/sqrt(2 M w)
+  const float *wq;        // [nq]
+  float EF, invkT, sc, gnorm, omega_min;
+  float *epsq;            // [kc][nw][ldq]
+  float2 *Uq;             // [kc][nw][nw][ldq]
+  double *partial;        // [nk][4 nqt][nw]
+  unsigned *dstatus;
+  const float2 *Cpol;     // [nm][nq] or null
+  const float2 *UkF;      // [nk][nw][nw]
+};
+
+// Tile -> (column group, q tile): q-blocks of `qblock` tiles, group-major inside a block.
+__device__ __forceinline__ void w_coords(const TcwArgs &a, int item, int &grp, int &qt) {
+  const int per = a.qblock * a.ngrp;
+  const int nb = (a.nqt + a.qblock - 1) / a.qblock;
+  int b = item / per;
+  if (b > nb - 1) b = nb - 1;
+  const int r = item - b * per;
+  const int qbs = min(a.qblock, a.nqt - b * a.qblock);
+  grp = r / qbs;
+  qt = b * a.qblock + r % qbs;
+}
+
+// The one relevance test both kernels evaluate (same FP32 operands, same result).
+__device__ __forceinline__ bool reachable(float ek, float em, float thr) { return fabsf(ek - em) <= thr; }
+
+// ------------------------------------------------------------ epilogue E
+template <int NW>
+__device__ __forceinline__ void eig_pair(const TcwArgs &a, uint32_t tcol, int q, int kl, bool valid) {
+  constexpr int H2 = 2 * NW * NW;
+  constexpr int LD = (H2 + 31) / 32 * 32;
+  Herm<NW> H;
+  {
+    float hb[LD];
+#pragma unroll
+    for (int c = 0; c < LD; c += 32) {
+      float t[32];
+      tmem_ld32(tcol + c, t);
+#pragma unroll
+      for (int i = 0; i < 32; i++) hb[c + i] = t[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NW; i++)
+#pragma unroll
+      for (int j = i; j < NW; j++) {
+        const int o = 2 * (i * NW + j), o2 = 2 * (j * NW + i);
+        H.a[i][j] = mkc(0.5f * (hb[o] + hb[o2]), i == j ? 0.0f : 0.5f * (hb[o + 1] - hb[o2 + 1]));
+      }
+  }
+  HhQR<NW> S;
+  hh_tridiag<NW>(H, S);
+  const bool conv = tri_qr<NW>(S);
+  if (!conv && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
+  const int kg = valid ? a.k0 + kl : 0;
+  const float thr = valid ? __ldg(a.thr + q) : -1.0f;
+  float ek[NW];
+#pragma unroll
+  for (int n = 0; n < NW; n++) ek[n] = __ldg(a.epsk + (size_t)kg * NW + n);
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < NW; m++) a.epsq[((size_t)kl * NW + m) * a.ldq + q] = S.d[m];
+  }
+  // one loop body over m (instruction cache); unreachable bands are skipped by the warp
+#pragma unroll 1
+  for (int m = 0; m < NW; m++) {
+    const float dm = pick<NW>(S.d, m);
+    bool rel = false;
+#pragma unroll
+    for (int n = 0; n < NW; n++) rel = rel || reachable(ek[n], dm, thr);
+    rel = rel && valid;
+    if (!__any_sync(0xffffffffu, rel)) continue;
+    cx<float> u[NW];
+    hh_vector<NW>(S, m, u);
+    if (rel) {
+      float2 *dst = a.Uq + ((size_t)kl * NW + m) * NW * a.ldq + q;
+#pragma unroll
+      for (int i = 0; i < NW; i++) dst[(size_t)i * a.ldq] = make_float2(u[i].x, u[i].y);
+    }
+  }
+}
+
+// ------------------------------------------------------------ epilogue G
+// Linewidth terms of one pair (k, q) and one band n at k from the accumulator
+// columns (a, j) of (g_a(k,q) U_k)_{jn}: only the bands m with a reachable
+// delta are evaluated (the warp runs the union over its lanes).
+template <int NW, int NM>
+__device__ __forceinline__ float g_entry(const TcwArgs &a, uint32_t tcol, int q, int kl, int n, bool valid) {
+  constexpr int ENT = 2 * NM * NW;
+  constexpr int LD = (ENT + 31) / 32 * 32;
+  const int qq = valid ? q : 0;
+  const int kg = valid ? a.k0 + kl : 0;
+  const float thr = valid ? __ldg(a.thr + q) : -1.0f;
+  const float ek = __ldg(a.epsk + (size_t)kg * NW + n);
+  // bands m at k+q with a Gaussian above the cutoff, as a bit mask
+  uint32_t relm = 0;
+#pragma unroll
+  for (int m = 0; m < NW; m++) {
+    const float em = valid ? a.epsq[((size_t)kl * NW + m) * a.ldq + q] : 0.0f;
+    if (valid && reachable(ek, em, thr)) relm |= 1u << m;
+  }
+  if (!__any_sync(0xffffffffu, relm != 0)) return 0.0f;
+  float om[NM], nb[NM];
+#pragma unroll
+  for (int nu = 0; nu < NM; nu++) {
+    om[nu] = __ldg(a.omegaT + (size_t)nu * a.nq + qq);
+    nb[nu] = __ldg(a.nbT + (size_t)nu * a.nq + qq);
+  }
+  const float eks = ek * a.sc;
+  float acc = 0.0f;
+  // one loop body over m (instruction cache); the warp runs the union of its lanes' bands
+#pragma unroll 1
+  for (int m = 0; m < NW; m++) {
+    const bool rel = (relm >> m) & 1u;
+    if (!__any_sync(0xffffffffu, rel)) continue;
+    cx<float> u[NW];
+    float em = 0.0f;
+    if (rel) {
+      em = a.epsq[((size_t)kl * NW + m) * a.ldq + q];
+      const float2 *src = a.Uq + ((size_t)kl * NW + m) * NW * a.ldq + q;
+#pragma unroll
+      for (int i = 0; i < NW; i++) {
+        const float2 v = src[(size_t)i * a.ldq];
+        u[i] = mkc(v.x, v.y);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NW; i++) u[i] = mkc(0.0f, 0.0f);
+    }
+    // t_a = u_m^dagger (g_a U_k)_{:, n}; the entry's columns 2 (a nw + j) + (re, im)
+    // stream from tensor memory 32 at a time (every lane of the warp loads)
+    cx<float> t[NM];
+#pragma unroll
+    for (int al = 0; al < NM; al++) t[al] = mkc(0.0f, 0.0f);
+#pragma unroll
+    for (int c0 = 0; c0 < LD; c0 += 32) {
+      float xc[32];
+      tmem_ld32(tcol + c0, xc);
+#pragma unroll
+      for (int cc = 0; cc < 32; cc += 2) {
+        const int col = c0 + cc;
+        if (col < ENT) {
+          const int al = col / (2 * NW), j = (col >> 1) % NW;
+          const float br = xc[cc], bi = xc[cc + 1];
+          t[al] = mkc(fmaf(u[j].x, br, fmaf(u[j].y, bi, t[al].x)), fmaf(u[j].x, bi, fmaf(-u[j].y, br, t[al].y)));
+        }
+      }
+    }
+    if (!rel) continue;
+    cx<float> tp = mkc(0.0f, 0.0f);
+    if (a.Cpol) {
+      const float2 *Uk = a.UkF + (size_t)kg * NW * NW;
+#pragma unroll
+      for (int j = 0; j < NW; j++) {
+        const float2 w = __ldg(Uk + j * NW + n);
+        tp = mkc(fmaf(u[j].x, w.x, fmaf(u[j].y, w.y, tp.x)), fmaf(u[j].x, w.y, fmaf(-u[j].y, w.x, tp.y)));
+      }
+    }
+    const float fm = fermi_fast(em - a.EF, a.invkT);
+    const float ems = em * a.sc;
+#pragma unroll
+    for (int nu = 0; nu < NM; nu++) {
+      cx<float> g = mkc(0.0f, 0.0f);
+#pragma unroll
+      for (int al = 0; al < NM; al++) {
+        const float2 e = __ldg(a.ET + ((size_t)al * NM + nu) * a.nq + qq);
+        g = mkc(fmaf(e.x, t[al].x, fmaf(-e.y, t[al].y, g.x)), fmaf(e.x, t[al].y, fmaf(e.y, t[al].x, g.y)));
+      }
+      if (a.Cpol) {
+        const float2 c = __ldg(a.Cpol + (size_t)nu * a.nq + qq);
+        g = mkc(g.x - fmaf(c.x, tp.y, c.y * tp.x), g.y + fmaf(c.x, tp.x, -c.y * tp.y));
+      }
+      const bool keep = (om[nu] >= a.omega_min) && (om[nu] > 0.0f);
+      const float ws = om[nu] * a.sc;
+      const float xp = eks - ems + ws, xm = eks - ems - ws;
+      const float cp = keep ? nb[nu] + fm : 0.0f, cm = keep ? nb[nu] + 1.0f - fm : 0.0f;
+      const float d = cp * ex2_approx(-xp * xp) + cm * ex2_approx(-xm * xm);
+      acc = fmaf(fmaf(g.x, g.x, g.y * g.y), d, acc);
+    }
+  }
+  return acc;
+}
+
+// --------------------------------------------------------------- kernel
+// KIND 0: kernel E (H(k+q), eigensolve); KIND 1: kernel G (vertex, linewidth terms).
+template <int OP, int NW, int NM, int KIND>
+__global__ void __launch_bounds__(nthreads<KIND>(), 1)
+    k_tcw(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+          const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcwArgs a) {
+  using O = WOp<OP>;
+  using S = WShape<NW, NM>;
+  constexpr int BN = w_bn<NW, NM, KIND>();
+  constexpr int UNITS = w_units<NW, NM, KIND>();
+  constexpr int UCOLS = KIND == 0 ? S::CPK : S::ENTP;
+  constexpr int RB = w_rowb<KIND>();
+  constexpr int STAGES = w_stages<KIND>();
+  constexpr int BK = RB / O::ESZ;  // K elements per stage
+  constexpr int A_BYTES = BM * RB;
+  constexpr int B_BYTES = BN * RB;
+  constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr uint32_t IDESC = w_idesc<OP, BN>();
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_tfull[2], bar_tempty[2], bar_final;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t smem0 = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int *abort_flag = &abort_sh;
+  const int nitems = a.ngrp * a.nqt;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int s = 0; s < 2; s++) {
+      mbar_init(smem_u32(&bar_tfull[s]), 1);
+      mbar_init(smem_u32(&bar_tempty[s]), 4 * UNITS);
+    }
+    mbar_init(smem_u32(&bar_final), 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    int issued[STAGES];
+#pragma unroll
+    for (int s = 0; s < STAGES; s++) issued[s] = 0;
+    uint32_t it = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+      int grp, qt;
+      w_coords(a, item, grp, qt);
+      for (int kb = 0; kb < a.nkb; kb++, it++) {
+        const int s = it % STAGES;
+        const uint32_t par = ((it / STAGES) & 1u) ^ 1u;
+        if (lane == 0) {
+          ok = wait_bar(smem_u32(&bar_empty[s]), par, abort_flag, a.dstatus);
+          if (ok) {
+            const uint32_t base = smem0 + s * STAGE;
+            const uint32_t fb = smem_u32(&bar_full[s]);
+            mbar_expect_tx(fb, STAGE);
+            tma_load_2d(base, &mAhi, kb * BK, qt * BM, fb);
+            tma_load_2d(base + A_BYTES, &mAlo, kb * BK, qt * BM, fb);
+            tma_load_2d(base + 2 * A_BYTES, &mBhi, kb * BK, grp * BN, fb);
+            tma_load_2d(base + 2 * A_BYTES + B_BYTES, &mBlo, kb * BK, grp * BN, fb);
+            issued[s] = (int)(it / STAGES) + 1;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int s = 0; s < STAGES; s++)
+        if (issued[s] > 0) drain_bar(smem_u32(&bar_full[s]), (uint32_t)((issued[s] - 1) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA
+    uint32_t it = 0;
+    int titer = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, titer++) {
+      const int ts = titer & 1;
+      const uint32_t tpar = ((titer >> 1) & 1) ^ 1;
+      if (lane == 0) ok = wait_bar(smem_u32(&bar_tempty[ts]), tpar, abort_flag, a.dstatus);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t dcol = tmem + ts * 256;
+      for (int kb = 0; kb < a.nkb; kb++, it++) {
+        const int s = it % STAGES;
+        const uint32_t par = (it / STAGES) & 1u;
+        if (lane == 0) {
+          ok = wait_bar(smem_u32(&bar_full[s]), par, abort_flag, a.dstatus);
+          if (ok) {
+            tc_fence_after();
+            const uint32_t base = smem0 + s * STAGE;
+            const uint64_t dAh = sdesc_sw<RB>(base), dAl = sdesc_sw<RB>(base + A_BYTES);
+            const uint64_t dBh = sdesc_sw<RB>(base + 2 * A_BYTES), dBl = sdesc_sw<RB>(base + 2 * A_BYTES + B_BYTES);
+            const int ksteps = min(BK, a.kpad - kb * BK) / O::KSTEP;
+            for (int ks = 0; ks < ksteps; ks++) {
+              const uint64_t off = (uint64_t)((ks * 32) >> 4);  // 32 bytes of K per MMA
+              const uint32_t acc = (kb == 0 && ks == 0) ? 0u : 1u;
+              umma_id<O::F16>(dcol, dAl + off, dBh + off, IDESC, acc);
+              umma_id<O::F16>(dcol, dAh + off, dBl + off, IDESC, 1u);
+              umma_id<O::F16>(dcol, dAh + off, dBh + off, IDESC, 1u);
+            }
+            umma_commit(smem_u32(&bar_empty[s]));
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+      }
+      if (!ok) break;
+      if (lane == 0) umma_commit(smem_u32(&bar_tfull[ts]));
+      __syncwarp();
+    }
+    if (lane == 0) {
+      umma_commit(smem_u32(&bar_final));
+      drain_bar(smem_u32(&bar_final), 0);
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------------------- epilogue
+    // Items of a lane quadrant: (tile titer, unit u) in order it = UNITS titer + u,
+    // taken round-robin by the quadrant's warps; a tile's accumulator stage is
+    // released after all 4 UNITS items.
+    constexpr int NG = epi_warps<KIND>() / 4;
+    const int quad = warp & 3;
+    const int widx = (warp - EPI_WARP0) >> 2;
+    for (int it = widx;; it += NG) {
+      const int titer = it / UNITS, u = it % UNITS;
+      const int item = blockIdx.x + titer * gridDim.x;
+      if (item >= nitems) break;
+      const int ts = titer & 1;
+      const uint32_t tpar = (titer >> 1) & 1;
+      const bool ok = wait_bar(smem_u32(&bar_tfull[ts]), tpar, abort_flag, a.dstatus);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      int grp, qt;
+      w_coords(a, item, grp, qt);
+      const int q = qt * BM + quad * 32 + lane;
+      const uint32_t tcol = tmem + ((uint32_t)(quad * 32) << 16) + ts * 256 + u * UCOLS;
+      if constexpr (KIND == 0) {
+        const int kl = grp * S::KPT + u;
+        eig_pair<NW>(a, tcol, q, kl, q < a.nq && kl < a.kc);
+      } else {
+        const int e = grp * S::CN + u;
+        const int kl = e / NW, n = e % NW;
+        const bool kval = kl < a.kc;
+        const bool valid = q < a.nq && kval;
+        float v = g_entry<NW, NM>(a, tcol, q, kl, n, valid);
+        v *= valid ? __ldg(a.wq + q) : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0 && kval)
+          a.partial[((size_t)(a.k0 + kl) * (4 * a.nqt) + qt * 4 + quad) * NW + n] = (double)v * (double)a.gnorm;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[ts]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ------------------------------------------------------- operand builder G
+template <typename T>
+__device__ __forceinline__ void wsplit(float v, T *hi, T *lo, size_t i);
+template <>
+__device__ __forceinline__ void wsplit<__nv_bfloat16>(float v, __nv_bfloat16 *hi, __nv_bfloat16 *lo, size_t i) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[i] = h;
+  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+template <>
+__device__ __forceinline__ void wsplit<float>(float v, float *hi, float *lo, size_t i) {
+  const float h = tf32_rn(v);
+  hi[i] = h;
+  lo[i] = tf32_rn(v - h);
+}
+
+// B rows of kernel G: row = c bng + i entp + 2 (a nw + j) + s for entry e = c cn + i
+// = (kl, n) = (e / nw, e % nw); K index kk = 2 rr + t, R index r = nR - 1 - rr
+// (far shells first, as the A operand); value from b = Bg[kl][r][a][j][n]:
+//   (s,t) = (0,0): Re b, (0,1): -Im b, (1,0): Im b, (1,1): Re b.
+// Rows past 2 nm nw in an entry, entries with kl >= kc and K >= 2 nR are 0.
+template <typename T>
+__global__ void k_build_bg(int kc, int nchunk, int nR, int nw, int nm, int cn, int entp, int bng, int kpad,
+                           const cx<float> *__restrict__ Bg, T *hi, T *lo) {
+  const size_t n = (size_t)nchunk * bng * kpad;
+  const int nw2 = nw * nw, ent = 2 * nm * nw;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(idx % kpad);
+    const int row = (int)(idx / kpad);
+    const int c = row / bng, rc = row % bng;
+    const int i = rc / entp, re = rc % entp;
+    const int e = c * cn + i;
+    const int kl = e / nw, nb = e % nw;
+    float v = 0.0f;
+    if (re < ent && kl < kc && kk < 2 * nR) {
+      const int al = re / (2 * nw), j = (re >> 1) % nw, s = re & 1;
+      const int r = nR - 1 - (kk >> 1), t = kk & 1;
+      const cx<float> b = Bg[((size_t)kl * nR + r) * nm * nw2 + al * nw2 + j * nw + nb];
+      v = s == 0 ? (t == 0 ? b.x : -b.y) : (t == 0 ? b.y : b.x);
+    }
+    wsplit<T>(v, hi, lo, idx);
+  }
+}
+
+// thr[q] = max over kept modes of w_q,nu + CUT_SIGMAS sigma (-1 when no mode is kept)
+__global__ void k_tcw_thr(int nq, int nm, const float *__restrict__ omF, float omega_min, float cut, float *thr) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    float w = -1.0f;
+    for (int nu = 0; nu < nm; nu++) {
+      const float o = omF[(size_t)nu * nq + q];
+      if (o >= omega_min && o > 0.0f) w = fmaxf(w, o);
+    }
+    thr[q] = w >= 0.0f ? w + cut : -1.0f;
+  }
+}
+
+inline int grid_n(size_t n, int bs) {
+  size_t b = (n + bs - 1) / bs;
+  return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+template <int OP, int NW, int NM, int KIND>
+cudaError_t launch_tcw(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
+                       const TcwArgs &a, cudaStream_t st) {
+  constexpr int SMEM = w_smem<NW, NM, KIND>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tcw<OP, NW, NM, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int items = a.ngrp * a.nqt;
+  k_tcw<OP, NW, NM, KIND><<<std::min(items, sms), nthreads<KIND>(), SMEM, st>>>(ah, al, bh, bl, a);
+  epw_count_launch();
+  return cudaGetLastError();
+}
+
+// compiled (nw, 3nat) pairs
+#define EPW_TCW_SHAPES(X) X(8, 6) X(5, 9)
+
+template <int OP, int KIND>
+cudaError_t launch_tcw_shape(int nw, int nm, const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh,
+                             const CUtensorMap &bl, const TcwArgs &a, cudaStream_t st) {
+#define EPW_TCW_CASE(W, M) \
+  if (nw == W && nm == M) return launch_tcw<OP, W, M, KIND>(ah, al, bh, bl, a, st);
+  EPW_TCW_SHAPES(EPW_TCW_CASE)
+#undef EPW_TCW_CASE
+  return cudaErrorInvalidValue;
+}
+
+bool tcw_shape(int nw, int nm, int &cpk, int &kpt, int &entp, int &cn, int &bng) {
+#define EPW_TCW_INFO(W, M)          \
+  if (nw == W && nm == M) {         \
+    cpk = WShape<W, M>::CPK;        \
+    kpt = WShape<W, M>::KPT;        \
+    entp = WShape<W, M>::ENTP;      \
+    cn = WShape<W, M>::CN;          \
+    bng = WShape<W, M>::BNG;        \
+    return true;                    \
+  }
+  EPW_TCW_SHAPES(EPW_TCW_INFO)
+#undef EPW_TCW_INFO
+  return false;
+}
+
+constexpr size_t TCW_EIG_BYTES = (size_t)6 << 30;  // per-chunk eigenvalue + eigenvector buffers
+
+}  // namespace
+
+bool tcw_supported(const epw_model *m) {
+  int cpk, kpt, entp, cn, bng;
+  return m->same_ep && tcw_shape(m->nw, m->nm, cpk, kpt, entp, cn, bng);
+}
+
+epw_status tcw_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t bytes, TcwBuffers &b) {
+  b = TcwBuffers{};
+  b.op = op;
+  b.ok = m->same_ep && tcw_shape(m->nw, m->nm, b.cpk, b.kpt, b.entp, b.cn, b.bng);
+  if (!b.ok) return EPW_OK;
+  nk = std::max(nk, 1);
+  nq = std::max(nq, 1);
+  const int nw = m->nw, nm = m->nm;
+  const int esz = op == TC_OP_BF16 ? 2 : 4;
+  const int kal = op == TC_OP_BF16 ? 16 : 8;
+  b.kpad = (2 * m->nRe + kal - 1) / kal * kal;
+  b.nqt = (nq + BM - 1) / BM;
+  b.ldq = b.nqt * BM;
+  const size_t per_k = (size_t)b.ldq * nw * (4 + 8 * (size_t)nw);
+  const size_t budget = bytes ? bytes : TCW_EIG_BYTES;
+  b.kc = (int)std::min<size_t>((size_t)nk, std::max<size_t>(1, budget / per_k));
+  const int kc_pad = (b.kc + b.kpt - 1) / b.kpt * b.kpt;
+  const int nchunk = (b.kc * nw + b.cn - 1) / b.cn;
+  b.Ahi = A.take<char>((size_t)nq * b.kpad * esz);
+  b.Alo = A.take<char>((size_t)nq * b.kpad * esz);
+  b.BEhi = A.take<char>((size_t)kc_pad * b.cpk * b.kpad * esz);
+  b.BElo = A.take<char>((size_t)kc_pad * b.cpk * b.kpad * esz);
+  b.BGhi = A.take<char>((size_t)nchunk * b.bng * b.kpad * esz);
+  b.BGlo = A.take<char>((size_t)nchunk * b.bng * b.kpad * esz);
+  b.epsq = A.take<float>((size_t)b.kc * nw * b.ldq);
+  b.Uq = A.take<float2>((size_t)b.kc * nw * nw * b.ldq);
+  b.nbT = A.take<float>((size_t)nq * nm);
+  b.omF = A.take<float>((size_t)nq * nm);
+  b.wqF = A.take<float>((size_t)nq);
+  b.ekF = A.take<float>((size_t)nk * nw);
+  b.thr = A.take<float>((size_t)nq);
+  b.partial = A.take<double>((size_t)nk * 4 * b.nqt * nw);
+  b.UkF = m->polar ? A.take<float2>((size_t)nk * nw * nw) : nullptr;
+  return EPW_OK;
+}
+
+epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, const double *wq,
+                         const epw_params *par, const double *epsk, const double *omegaT, const cx<float> *ET32,
+                         const cx<float> *Bg32, const cx<float> *BH32, const cx<double> *P64,
+                         const cx<double> *Uk, const float2 *Cpol, TcwBuffers &b, double *out, cudaStream_t st) {
+  if (!b.ok) return EPW_ERR_UNSUPPORTED;
+  const int nw = m->nw, nm = m->nm, nR = m->nRe, op = b.op;
+  const int esz = op == TC_OP_BF16 ? 2 : 4;
+  tc_build_a_raw(op, nq, nR, b.kpad, q, m->Re, P64, b.Ahi, b.Alo, st);
+  tc_tables(nq, nm, nk, nw, omegaT, par->T_K, wq, epsk, b.nbT, b.omF, b.wqF, b.ekF, st);
+  const float cut = (float)(CUT_SIGMAS * par->sigma_eV);
+  k_tcw_thr<<<grid_n(nq, 256), 256, 0, st>>>(nq, nm, b.omF, (float)par->omega_min_eV, cut, b.thr);
+  epw_count_launch();
+  if (Cpol) launch_cast_c64_to_c32((size_t)nk * nw * nw, Uk, (cx<float> *)b.UkF, st);
+  TcwArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nq = nq;
+  a.nqt = b.nqt;
+  a.kpad = b.kpad;
+  const int nkb_e = (b.kpad * esz + 127) / 128, nkb_g = (b.kpad * esz + 63) / 64;
+  a.ldq = b.ldq;
+  a.epsk = b.ekF;
+  a.thr = b.thr;
+  a.omegaT = b.omF;
+  a.nbT = b.nbT;
+  a.ET = (const float2 *)ET32;
+  a.wq = b.wqF;
+  a.EF = (float)par->EF_eV;
+  a.invkT = par->T_K > 0.0 ? (float)(1.0 / (EPW_KB * par->T_K)) : 0.0f;
+  a.sc = (float)(1.2011224087864498 / par->sigma_eV);  // sqrt(log2 e) / sigma
+  a.gnorm = (float)(1.0 / (par->sigma_eV * 1.7724538509055160273));
+  a.omega_min = (float)par->omega_min_eV;
+  a.epsq = b.epsq;
+  a.Uq = b.Uq;
+  a.partial = b.partial;
+  a.dstatus = m->dstatus;
+  a.Cpol = Cpol;
+  a.UkF = Cpol ? b.UkF : nullptr;
+  {
+    const size_t atile = (size_t)BM * b.kpad * esz * 2;
+    int qb = (int)(A_BLOCK_BYTES / atile);
+    qb = std::max(qb, 152);
+    a.qblock = std::max(1, std::min(qb, b.nqt));
+  }
+  CUtensorMap ah, al, eh, el, gh, gl;
+  CUtensorMap ah64, al64;
+  if (!tc_make_map(&ah, b.Ahi, op, b.kpad, nq, BM) || !tc_make_map(&al, b.Alo, op, b.kpad, nq, BM) ||
+      !tc_make_map_rb(&ah64, b.Ahi, op, b.kpad, nq, BM, 64) || !tc_make_map_rb(&al64, b.Alo, op, b.kpad, nq, BM, 64))
+    return EPW_ERR_CUDA;
+  const int kc_pad = (b.kc + b.kpt - 1) / b.kpt * b.kpt;
+  const int nchunk_max = (b.kc * nw + b.cn - 1) / b.cn;
+  if (!tc_make_map(&eh, b.BEhi, op, b.kpad, (uint64_t)kc_pad * b.cpk, 256) ||
+      !tc_make_map(&el, b.BElo, op, b.kpad, (uint64_t)kc_pad * b.cpk, 256) ||
+      !tc_make_map_rb(&gh, b.BGhi, op, b.kpad, (uint64_t)nchunk_max * b.bng, (uint32_t)b.bng, 64) ||
+      !tc_make_map_rb(&gl, b.BGlo, op, b.kpad, (uint64_t)nchunk_max * b.bng, (uint32_t)b.bng, 64))
+    return EPW_ERR_CUDA;
+  const size_t nw2 = (size_t)nw * nw;
+  epw_model *mm = const_cast<epw_model *>(m);
+  for (int k0 = 0; k0 < nk; k0 += b.kc) {
+    const int kc = std::min(b.kc, nk - k0);
+    const int kcp = (kc + b.kpt - 1) / b.kpt * b.kpt;
+    const int nchunk = (kc * nw + b.cn - 1) / b.cn;
+    tc_build_b_raw(op, kc, kcp, nR, nw, 0, b.cpk, b.kpad, BH32 + (size_t)k0 * nR * nw2, nullptr, b.BEhi, b.BElo, st);
+    {
+      const size_t n = (size_t)nchunk * b.bng * b.kpad;
+      const cx<float> *bg = Bg32 + (size_t)k0 * nR * nm * nw2;
+      if (op == TC_OP_BF16)
+        k_build_bg<__nv_bfloat16><<<grid_n(n, 256), 256, 0, st>>>(kc, nchunk, nR, nw, nm, b.cn, b.entp, b.bng, b.kpad,
+                                                                  bg, (__nv_bfloat16 *)b.BGhi, (__nv_bfloat16 *)b.BGlo);
+      else
+        k_build_bg<float><<<grid_n(n, 256), 256, 0, st>>>(kc, nchunk, nR, nw, nm, b.cn, b.entp, b.bng, b.kpad, bg,
+                                                          (float *)b.BGhi, (float *)b.BGlo);
+      epw_count_launch();
+    }
+    a.k0 = k0;
+    a.kc = kc;
+    cudaError_t e;
+    a.ngrp = kcp / b.kpt;
+    a.nkb = nkb_e;
+    epw_timing_begin_tag(mm, st, 1);
+    e = op == TC_OP_BF16 ? launch_tcw_shape<TC_OP_BF16, 0>(nw, nm, ah, al, eh, el, a, st)
+                         : launch_tcw_shape<TC_OP_TF32, 0>(nw, nm, ah, al, eh, el, a, st);
+    epw_timing_end(mm, st);
+    if (e != cudaSuccess) return EPW_ERR_CUDA;
+    a.ngrp = nchunk;
+    a.nkb = nkb_g;
+    epw_timing_begin_tag(mm, st, 0);
+    e = op == TC_OP_BF16 ? launch_tcw_shape<TC_OP_BF16, 1>(nw, nm, ah64, al64, gh, gl, a, st)
+                         : launch_tcw_shape<TC_OP_TF32, 1>(nw, nm, ah64, al64, gh, gl, a, st);
+    epw_timing_end(mm, st);
+    if (e != cudaSuccess) return EPW_ERR_CUDA;
+  }
+  launch_finalize(nk, 4 * b.nqt, nw, b.partial, out, st);
+  return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
+}
