@@ -101,6 +101,8 @@ def _load():
             for name in ("oracle_bose", "oracle_gauss"):
                 getattr(lib, name).argtypes = [ctypes.c_double, ctypes.c_double]
                 getattr(lib, name).restype = ctypes.c_double
+            lib.oracle_gauss_diff.argtypes = [ctypes.c_double] * 3
+            lib.oracle_gauss_diff.restype = ctypes.c_double
             for name in ("oracle_fermi", "oracle_fermi_slope"):
                 getattr(lib, name).argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
                 getattr(lib, name).restype = ctypes.c_double
@@ -326,3 +328,8 @@ def fermi_diff(ea, eb, EF, T):
 
 def gauss(x, sigma):
     return _load().oracle_gauss(float(x), float(sigma))
+
+
+def gauss_diff(x, w, sigma):
+    """delta(x + w) - delta(x - w) of the Gaussian delta, in the sinh form without cancellation."""
+    return _load().oracle_gauss_diff(float(x), float(w), float(sigma))

@@ -137,6 +137,19 @@ double oracle_gauss(double x, double sigma) {
   return exp(-y * y) / (sigma * sqrt(M_PI));
 }
 
+/* delta(x + w) - delta(x - w) for the Gaussian above.  The two exponents differ
+   by 4 x w / sigma^2, so with a = x/sigma, b = w/sigma
+     delta(x + w) - delta(x - w) = -2 exp(-(a^2 + b^2)) sinh(2 a b) / (sigma sqrt(pi)),
+   which keeps full relative accuracy when w << sigma, where the plain difference
+   subtracts two nearly equal numbers.  For |2ab| > 1 the plain difference is
+   well conditioned (the two values differ by a factor e^2 or more) and the
+   product form could overflow in sinh, so that branch takes the difference. */
+double oracle_gauss_diff(double x, double w, double sigma) {
+  const double a = x / sigma, b = w / sigma;
+  if (fabs(2.0 * a * b) > 1.0) return oracle_gauss(x + w, sigma) - oracle_gauss(x - w, sigma);
+  return -2.0 * exp(-(a * a + b * b)) * sinh(2.0 * a * b) / (sigma * sqrt(M_PI));
+}
+
 /* ------------------------------------------------------------- eigensolver */
 
 /* Cyclic complex Jacobi.  A: n x n row-major (overwritten), w: ascending
@@ -746,8 +759,11 @@ int oracle_linewidth_grad(const oracle_model *m, int nk, const double *k, int nq
               double ff = oracle_fermi_slope(ekq[mm], pr->EF, pr->T);
               double df_dT = ff * (ekq[mm] - pr->EF) / (kT * pr->T);
               double df_dE = ff / kT;
-              nsum_add(&sT[tid], c * M_PI * wqi * g2 * ((dn_dT + df_dT) * dp + (dn_dT - df_dT) * dm));
-              nsum_add(&sE[tid], c * M_PI * wqi * g2 * (df_dE * dp - df_dE * dm));
+              /* d Im Sigma / dT = sum (dn/dT (d+ + d-) + df/dT (d+ - d-)) |g|^2, d / dE_F with
+                 df/dE_F (d+ - d-); d+ - d- in the form without cancellation */
+              double dd = oracle_gauss_diff(en - ekq[mm], w[nu], pr->sigma);
+              nsum_add(&sT[tid], c * M_PI * wqi * g2 * (dn_dT * (dp + dm) + df_dT * dd));
+              nsum_add(&sE[tid], c * M_PI * wqi * g2 * df_dE * dd);
             }
         /* bar_ka[j][i] = 2 sum_nu conj(E[ka][nu]) [Ukq (W g)_nu Uk^dag]_ji */
         for (int ka = 0; ka < nm; ka++)

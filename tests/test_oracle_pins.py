@@ -343,6 +343,51 @@ def test_fermi_difference_without_cancellation(oracle_lib):
     assert oracle_lib.fermi_diff(0.0, 0.1, 0.0, 0.0) == 0.5
 
 
+def test_gauss_difference_without_cancellation(oracle_lib):
+    """delta(x + w) - delta(x - w) of the Gaussian delta against 100-digit arithmetic (the plain
+    difference of the two Gaussians), from w ~ 1e-9 sigma (where two rounded double Gaussians
+    cancel to all but a few digits) through w ~ sigma and across the switch to the plain
+    difference at |2 x w| = sigma^2.  Also the symmetries: odd in x, odd in w."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 100
+    sig = 0.05
+    for a in (-3.0, -1.2, -0.3, -1e-4, 0.0, 2e-6, 0.25, 0.9, 1.7, 4.0):
+        for b in (1e-9, 3e-6, 1e-3, 0.02, 0.3, 0.55, 1.0, 2.5):
+            x, w = a * sig, b * sig
+            X, Wm, S = mpmath.mpf(x), mpmath.mpf(w), mpmath.mpf(sig)
+            ref = float((mpmath.e ** (-((X + Wm) / S) ** 2) - mpmath.e ** (-((X - Wm) / S) ** 2))
+                        / (S * mpmath.sqrt(mpmath.pi)))
+            got = oracle_lib.gauss_diff(x, w, sig)
+            assert abs(got - ref) <= 1e-13 * abs(ref) + 1e-300, (a, b, got, ref)
+            assert oracle_lib.gauss_diff(-x, w, sig) == -got
+            assert oracle_lib.gauss_diff(x, -w, sig) == -got
+    # the plain difference of two double Gaussians loses most digits at w = 1e-9 sigma
+    x, w = 0.5 * sig, 1e-9 * sig
+    plain = oracle_lib.gauss(x + w, sig) - oracle_lib.gauss(x - w, sig)
+    exact = oracle_lib.gauss_diff(x, w, sig)
+    assert abs(plain - exact) > 1e-9 * abs(exact)
+
+
+def test_adjoint_fermi_level_with_soft_modes(oracle_lib):
+    """dL/dE_F weights each term by d+ - d-, which is O(w / sigma) for soft modes: with every
+    phonon below sigma / 50 (a soft spring), the oracle's sinh form of the difference still
+    matches a central finite difference of the linewidth in E_F."""
+    rng = np.random.default_rng(61)
+    m = W.make_model("sc", 2, 1, [1.0], None, None, rng, box=1, omega_max=0.002)
+    k = rng.random((3, 3))
+    q = rng.random((6, 3))
+    T, EF, sig = 300.0, 0.2, 0.2
+    cot = rng.random((3, 2))
+    _, _, dEF = oracle_lib.linewidth_grad(m, k, q, None, T, EF, sig, cot=cot, omega_min=1e-7)
+
+    def L(EF):
+        return float((oracle_lib.linewidth(m, k, q, None, T, EF, sig, omega_min=1e-7) * cot).sum())
+
+    fdE = (L(EF + 1e-5) - L(EF - 1e-5)) / 2e-5
+    assert abs(dEF) > 0
+    assert abs(fdE - dEF) <= 1e-6 * abs(dEF), (fdE, dEF)
+
+
 # ------------------------------------------------- phonon self-energy (oracle)
 def _two_band_tb(eps=(-0.3, 0.4), t=0.5, K=0.01, M=1.3, c=((0.05, 0.03), (0.08, 0.02))):
     """Two bands that never mix (H(k) diagonal, band 0 below band 1 everywhere) with
