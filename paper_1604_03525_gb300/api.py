@@ -132,6 +132,7 @@ class Model:
         ga = _Arg(g, np.complex128)
         if tuple(ga.keep.shape) != self.g_shape:
             raise ValueError(f"vertex shape {tuple(ga.keep.shape)} != {self.g_shape}")
+        self._autograd_vertex = None  # the vertex the autograd interface last loaded is gone
         _check(_lib.load().epw_set_vertex(self._h, ga.ptr, 0, _stream_of(ga)))
 
     def reserve(self, nk: int, nq: int, precision: int = FP64):
