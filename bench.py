@@ -1,28 +1,32 @@
 """Benchmark: k.q pairs/s of the electron linewidth (Eq. linewidthel) on one GB300.
 
-Workload: fcc lattice, nw=4 Wannier functions, 1 atom (3 modes), 135 Re and 135
-Rp vectors (whole shells), 1000 k-points inside a 0.2 eV window of E_F, a
-uniform 40^3 q grid (64,000 q), sigma = 20 meV, T = 300 K: 6.4e7 (k,q) pairs
-per step.  A step is one epw_linewidth call: phases, phonons, k-side bands and
-vertex, the per-pair interpolation/rotation/reduction and the final sum.
+Headline workload (the largest single-GPU configuration): diamond lattice with a
+two-atom basis, nw = 8 Wannier functions, 6 modes (masses 1 and 1.2), 249 Re =
+Rp vectors (whole shells), 2000 k-points near the band edges x (60^3 uniform
+grid + 10^5 random q = 316,000 q), sigma = 10 meV, T = 300 K: 6.32e8 (k,q)
+pairs per step.  A step is one epw_linewidth call: q-side phases and phonons,
+k-side bands and vertex, the per-pair interpolation, eigensolve, rotation and
+reduction (the wide-shape tensor-core kernels E and G), and the final sum.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp32|fp64]
-  python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample
-  python bench.py --workload diamond_nw8|hex_nw5|batch   # the other configurations (not the headline)
+The line also carries the fcc nw=4 configuration (1000 k x 40^3 q, the fused
+single-kernel form) under "c2", the hexagonal nw=5 configuration (20^3 k x 40^3 q)
+with its adjoint under "c5", the other split form and the plain FP64 GPU form.
 
-diamond_nw8: diamond two-atom basis, nw=8, 249 Re = Rp, 2000 k near the band edges x (60^3 grid +
-1e5 random q), sigma = 10 meV.  hex_nw5: hexagonal three-atom cell, nw=5, ~300 R, 20^3 k x 40^3 q,
-sigma = 15 meV, T = 50 K.  batch: uneven systems drawn as for the 64-system configuration, at
-reduced sizes (stated in the line) so that the host can build the models, replayed as one CUDA graph.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision auto|bf16x3|tf32x3|fp32|fp64]
+  python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample of the workload
+  python bench.py --workload fcc_nw4|hex_nw5|batch   # another configuration as the line
 
-Under torchrun each rank runs its own copy of the workload at one temperature
-of the T sweep (300, 100, 50, 10 K): weak scaling, no data-path collective.
+Under torchrun the k list of the one problem is split into contiguous shards,
+one per rank (strong scaling: the total work is fixed); no collective runs in
+the timed region, and the shards' Im Sigma are gathered after it.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -33,10 +37,23 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "fcc_nw4"
+WORKLOAD = "diamond_nw8"
 METRIC = "k·q pairs/s for ImΣ_nk on 1 GB300 (and % roofline) at stated error vs FP64 oracle"
-T_SWEEP = [300.0, 100.0, 50.0, 10.0]
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+# The split form that meets the 1e-4 relative target against the oracle on each workload
+# (tests/test_tcw_gpu.py, tests/test_parity_gpu.py: sampled k at the full q lists).
+AUTO_PRECISION = {"diamond_nw8": "bf16x3", "hex_nw5": "bf16x3", "fcc_nw4": "bf16x3"}
+DESCR = {
+    "diamond_nw8": "diamond nw=8 nat=2 (6 modes, M=1,1.2), 249 Re=Rp, 2000 k (band edges) x (60^3 + 1e5 random) q, "
+                   "sigma=10 meV, T=300 K",
+    "fcc_nw4": "fcc nw=4 nat=1, 135 Re=Rp, 1000 k (0.2 eV window of E_F) x 40^3 q, sigma=20 meV, T=300 K",
+    "hex_nw5": "hexagonal nw=5 nat=3 (9 modes), ~300 Re=Rp, 20^3 k x 40^3 q, sigma=15 meV, T=50 K",
+}
+CPU_SAMPLE = {"diamond_nw8": (32, 8192), "fcc_nw4": (1000, 2560), "hex_nw5": (64, 16384)}
+WIDE_PROFILE = os.path.join(ROOT, "profiles", "k_tcw_diamond_nw8.md")
+WIDE_SOURCE = os.path.join(ROOT, "paper_1604_03525_gb300", "csrc", "epw_tcw.cu")
+TC_PROFILE = os.path.join(ROOT, "profiles", "k_tc_linewidth_fcc_nw4.md")
+TC_SOURCE = os.path.join(ROOT, "paper_1604_03525_gb300", "csrc", "epw_tc.cu")
 
 
 def dist_info():
@@ -46,17 +63,19 @@ def dist_info():
     return rank, world, local
 
 
-def algorithmic_flops_per_pair(m):
-    """Contractions S5+S7 per (k,q) pair (complex MAC = 8 flops).
+def flops_per_pair(m):
+    """Algorithmic contraction flops per (k,q) pair (complex MAC = 8 flops).
 
-    H(k+q): 8 nRe nw^2; g(k,q) U_k: 8 nRp 3nat nw^2; U_k+q^+ rotation: 8 3nat nw^3;
-    mode projection: 8 (3nat)^2 nw^2.  Eigensolve sweeps and the delta/occupation
-    terms are not counted (iterative / transcendental, not a fixed flop count).
+    H(k+q): 8 nRe nw^2 (kernel E of the wide form); g(k,q) U_k: 8 nRp 3nat nw^2 (kernel G);
+    U_k+q^+ rotation and mode projection, dense: 8 3nat nw^3 + 8 (3nat)^2 nw^2 (CUDA cores;
+    the wide form evaluates only the terms whose Gaussians do not underflow).  Eigensolve
+    steps, deltas and occupations are not counted.
     """
     nw, nm = m.nw, 3 * m.nat
-    tensor = 8 * nw * nw * (len(m.Re) + nm * len(m.Rp))
-    simt = 8 * nm * nw**3 + 8 * nm * nm * nw * nw
-    return tensor, simt
+    h = 8 * nw * nw * len(m.Re)
+    g = 8 * nw * nw * nm * len(m.Rp)
+    rot = 8 * nm * nw ** 3 + 8 * nm * nm * nw * nw
+    return h, g, rot
 
 
 class ClockSampler:
@@ -115,25 +134,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-TC_SOURCE = os.path.join(ROOT, "paper_1604_03525_gb300", "csrc", "epw_tc.cu")
-TC_PROFILE = os.path.join(ROOT, "profiles", "k_tc_linewidth_fcc_nw4.md")
+def profiled(path, source, key, form):
+    """A figure recorded in a committed ncu summary for this kernel source.
 
-
-def profiled_traffic(form):
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary.
-
-    The summary records `traffic <form> <bytes> source-sha256 <hash>` lines; a
-    value is used only while the kernel source still has that hash (otherwise
-    the counters describe an older kernel and the traffic is reported as null).
+    The summary holds lines `<key> <form> <value> source-sha256 <hash>`; a value is
+    used only while the kernel source still has that hash (otherwise the counters
+    describe an older kernel and null is reported).
     """
-    import hashlib
     try:
-        sha = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
-        for line in open(TC_PROFILE):
+        sha = hashlib.sha256(open(source, "rb").read()).hexdigest()
+        for line in open(path):
             parts = line.strip().strip("`").split()
-            if len(parts) == 5 and parts[0] == "traffic" and parts[1] == form and parts[3] == "source-sha256":
+            if len(parts) == 5 and parts[0] == key and parts[1] == form and parts[3] == "source-sha256":
                 if parts[4] == sha:
-                    return float(parts[2]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/"
+                    return float(parts[2]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + \
+                        os.path.relpath(path, ROOT)
                 return None, "kernel changed since the ncu capture"
     except OSError:
         pass
@@ -148,18 +163,39 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def cpu_baseline(wl_name, nk_s, nq_s):
-    """The FP64 oracle (as it stands) on a bounded sample of the workload."""
-    import oracle
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        info = {}
+        for ln in out.splitlines():
+            if ":" in ln:
+                a, b = ln.split(":", 1)
+                info[a.strip()] = b.strip()
+        name = info.get("Model name") or info.get("BIOS Model name") or platform.processor()
+        return f"{name} ({info.get('Architecture', platform.machine())}, {os.cpu_count()} logical CPUs)"
+    except (OSError, subprocess.SubprocessError):
+        return f"{platform.machine()}, {os.cpu_count()} logical CPUs"
+
+
+def oracle_sample(wl_name, nk_s, nq_s):
     import workloads as W
     wl = W.make_workload(wl_name, nq_sub=nq_s)
     k = wl.k[::max(1, len(wl.k) // nk_s)][:nk_s]
+    return wl, k
+
+
+def cpu_baseline(wl_name, nk_s, nq_s):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+    wl, k = oracle_sample(wl_name, nk_s, nq_s)
     t0 = time.perf_counter()
     oracle.linewidth(wl.model, k, wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
     dt = time.perf_counter() - t0
     pairs = len(k) * len(wl.q)
     return {"value": pairs / dt, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{len(k)} k x {len(wl.q)} q (seeded subsample of the 40^3 grid), {pairs} pairs, {dt:.2f} s"}
+            "cpu": cpu_model(),
+            "sample": f"{len(k)} of the {wl_name} k x {len(wl.q)} q (seeded subsample of its q list), "
+                      f"{pairs} pairs, {dt:.2f} s"}
 
 
 def run_reference(args):
@@ -167,28 +203,26 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    import workloads as W
     oracle.build()
-    nq_s = 512
-    wl = W.make_workload(WORKLOAD, nq_sub=nq_s)
+    nk_s, nq_s = (16, 2048) if args.workload == "diamond_nw8" else (64, 2048)
+    wl, k = oracle_sample(args.workload, nk_s, nq_s)
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.linewidth(wl.model, wl.k, wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
+        oracle.linewidth(wl.model, k, wl.q, wl.wq, wl.T, wl.EF, wl.sigma)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
-    pairs = len(wl.k) * len(wl.q)
+    pairs = len(k) * len(wl.q)
     ms = 1e3 * float(np.mean(times))
     val = pairs / (ms / 1e3)
-    sample = f"{len(wl.k)} k x {nq_s} q per step (seeded subsample of the 40^3 grid), {pairs} pairs"
+    sample = f"{len(k)} k x {len(wl.q)} q per step (seeded subsample of the {args.workload} lists), {pairs} pairs"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "fcc nw=4 nat=1, 135 Re/Rp, 1000 k (0.2 eV window) x 40^3 q, sigma=20 meV, T=300 K",
-                   "sample_per_step": sample},
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": DESCR[args.workload], "sample_per_step": sample},
         "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": sample},
+                         "cpu": cpu_model(), "sample": sample},
         "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -199,8 +233,8 @@ def run_batch(args):
     The draw is the configuration's (nw, nat, lattice, R-shell target, k count, q grid per
     system) with nR <= 150, nk <= 1000, q grids 16^3..32^3 and nw <= 12 (the host builds every
     model in NumPy); systems outside the limits are dropped whole.  All jobs run
-    split-BF16 (the fused kernel where the shape has one, else the staged tensor-core form).
-    A step is one graph replay; the L2 is flushed between steps.
+    split-BF16 (the fused kernel where the shape has one, else the wide or staged tensor-core
+    form).  A step is one graph replay; the L2 is flushed between steps.
     """
     import torch
     import paper_1604_03525_gb300 as epw
@@ -218,7 +252,8 @@ def run_batch(args):
         jobs.append(dict(model=m, k=torch.tensor(k, device=dev), q=torch.tensor(q, device=dev), wq=None, T=300.0,
                          EF=0.0, sigma=0.05, precision=epw.BF16X3))
         pairs += len(k) * len(q)
-        tfl += algorithmic_flops_per_pair(wm)[0] * len(k) * len(q)
+        h, g, _ = flops_per_pair(wm)
+        tfl += (h + g) * len(k) * len(q)
     b = epw.Batch(jobs)  # autotunes, captures the graph and runs every job once
     for _ in range(args.warmup):
         b.run()
@@ -247,273 +282,280 @@ def run_batch(args):
                    "pairs_per_step": pairs, "precision": "bf16x3",
                    "l2": "flushed between timed steps (256 MB write)"},
         "clocks": clk.summary(), "gpu_launches": int(launches),
-        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                     "frac": ach / peaks["bf16_tflops_sustained"], "traffic": None,
-                     "peak_source": f"{peak_src} bf16_tflops_sustained",
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": ach / peaks["bf16_tflops"], "traffic": None,
+                     "peak_source": f"{peak_src} bf16_tflops (burst)",
                      "work": f"{tfl:.3e} algorithmic contraction flops per replay (all systems)"},
         "e2e": None, "cpu_baseline": None,
     }))
     b.close()
 
 
+class Runner:
+    """One workload on this rank's k shard, device buffers, L2 flushed between timed steps."""
+
+    def __init__(self, epw, torch, name, rank, world, dev):
+        import workloads as W
+        self.epw, self.torch, self.name, self.dev = epw, torch, name, dev
+        self.wl = W.make_workload(name)
+        from paper_1604_03525_gb300.shard import shard_bounds
+        self.lo, self.hi = shard_bounds(len(self.wl.k), rank, world)
+        self.m = epw.Model(self.wl.model)
+        self.k = torch.tensor(self.wl.k[self.lo:self.hi], device=dev)
+        self.q = torch.tensor(self.wl.q, device=dev)
+        self.wq = torch.tensor(self.wl.wq, device=dev)
+        self.out = torch.empty((self.hi - self.lo, self.wl.model.nw), dtype=torch.float64, device=dev)
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.pairs = (self.hi - self.lo) * len(self.wl.q)
+        self.pairs_total = len(self.wl.k) * len(self.wl.q)
+
+    def kw(self, prec):
+        return dict(T=self.wl.T, EF=self.wl.EF, sigma=self.wl.sigma, precision=prec)
+
+    def timed(self, nsteps, nwarm, prec, barrier=None, k=None):
+        torch, m = self.torch, self.m
+        k = self.k if k is None else k
+        for _ in range(nwarm):
+            m.linewidth(k, self.q, self.wq, out=self.out[:len(k)], **self.kw(prec))
+        stream = torch.cuda.current_stream()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        (barrier or torch.cuda.synchronize)()
+        m.timing(True)
+        l0 = self.epw.launch_count()
+        for e0, e1 in evs:
+            self.flush.zero_()  # evict L2 between timed steps (outside the timed events)
+            e0.record(stream)
+            m.linewidth(k, self.q, self.wq, out=self.out[:len(k)], **self.kw(prec))
+            e1.record(stream)
+        (barrier or torch.cuda.synchronize)()
+        launches = self.epw.launch_count() - l0
+        (g_ms, g_n), (e_ms, e_n) = m.timing_read_tags()
+        m.timing(False)
+        m.sync()
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        return {"step_ms": step_ms, "kern": (g_ms / nsteps, g_n // max(nsteps, 1)),
+                "eig": (e_ms / nsteps, e_n // max(nsteps, 1)), "launches": launches}
+
+    def e2e(self, prec, n):
+        torch = self.torch
+        kh = torch.tensor(self.wl.k[self.lo:self.hi]).pin_memory()
+        qh = torch.tensor(self.wl.q).pin_memory()
+        wh = torch.tensor(self.wl.wq).pin_memory()
+        oh = torch.empty((self.hi - self.lo, self.wl.model.nw), dtype=torch.float64).pin_memory()
+        self.m.linewidth(kh, qh, wh, out=oh, **self.kw(prec))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            self.m.linewidth(kh, qh, wh, out=oh, **self.kw(prec))
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / n
+        return {"value": self.pairs / dt, "unit": "pairs/s", "h2d_bytes_per_step": int(kh.nbytes + qh.nbytes + wh.nbytes),
+                "d2h_bytes_per_step": int(oh.nbytes)}
+
+
+def roofline(wl_model, prec_name, r, pairs, peaks, peak_src, fused):
+    """Tensor roofline of the path's contraction kernels against the burst bf16 peak
+    (these kernels run for milliseconds to seconds at the boost clock; tf32 = bf16 x 1.1/2.25)."""
+    h, g, rot = flops_per_pair(wl_model)
+    ratio = 1.0 if prec_name == "bf16x3" else 1.1 / 2.25
+    peak = peaks["bf16_tflops"] * ratio
+    src = f"{peak_src} bf16_tflops (burst)" + ("" if ratio == 1.0 else " x 1.1/2.25 (tf32)")
+    g_ms, g_n = r["kern"]
+    e_ms, e_n = r["eig"]
+    if fused:
+        ach = (h + g) * pairs / (g_ms / 1e3) / 1e12
+        out = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+               "peak_source": src, "kernel": "k_tc_linewidth (fused: contraction, eigensolve, rotation, deltas)",
+               "work": f"{h + g} algorithmic contraction flops/pair x {pairs} pairs per step",
+               "kernel_ms": g_ms, "kernel_launches": g_n}
+    else:
+        tot = e_ms + g_ms
+        ach = (h + g) * pairs / (tot / 1e3) / 1e12
+        out = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+               "peak_source": src,
+               "kernel": "k_tcw E + G (H(k+q) contraction + per-pair eigensolve; vertex contraction + "
+                         "rotation and deltas of the reachable terms)",
+               "work": f"{h + g} algorithmic contraction flops/pair ({h} in E, {g} in G) x {pairs} pairs per step",
+               "kernel_ms": tot,
+               "G": {"ms": g_ms, "launches": g_n, "tflops": g * pairs / (g_ms / 1e3) / 1e12,
+                     "frac": g * pairs / (g_ms / 1e3) / 1e12 / peak},
+               "E": {"ms": e_ms, "launches": e_n, "tflops": h * pairs / (e_ms / 1e3) / 1e12,
+                     "frac": h * pairs / (e_ms / 1e3) / 1e12 / peak,
+                     "note": "bound by the FP32 per-pair eigensolve, not the tensor pipe"}}
+    out["executed_tflops"] = 3.0 * out["achieved"]
+    out["executed_frac"] = 3.0 * out["frac"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "tf32x3", "bf16x3", "fp32", "fp64"])
-    ap.add_argument("--other-steps", type=int, default=2, help="timed steps of the other tensor-core/FP32 forms")
-    ap.add_argument("--backward-steps", type=int, default=3, help="timed adjoint calls (0: skip)")
-    ap.add_argument("--se-steps", type=int, default=1,
-                    help="timed complex self-energy + spectral function calls (100 k, 64 frequencies; 0: skip)")
-    ap.add_argument("--phonon-steps", type=int, default=2,
-                    help="timed phonon-side calls (Pi'', lambda, nesting over the same k x q; 0: skip)")
-    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 GPU form (0: skip)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "fcc_nw4", "hex_nw5", "batch"])
+    ap.add_argument("--other-steps", type=int, default=2, help="timed steps of the other split form (0: skip)")
+    ap.add_argument("--fp64-k", type=int, default=8, help="k of the headline list timed in the plain FP64 form (0: skip)")
+    ap.add_argument("--extras", type=int, default=1, help="also time the other configurations and the adjoint")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--nk", type=int, default=0, help="profiling only: use the first NK k-points of the workload")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "diamond_nw8", "hex_nw5", "batch"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
-    if args.workload != WORKLOAD:
-        # the other single-system configurations: the split forms only (a plain FP64 or FP32
-        # step of these sizes takes minutes), few steps (a step is seconds), no extra rows
-        args.steps, args.warmup = min(args.steps, 2), min(args.warmup, 1)
-        args.fp64_steps = args.backward_steps = args.phonon_steps = args.se_steps = 0
-        args.no_e2e = True
 
     import torch
     import paper_1604_03525_gb300 as epw
-    import workloads as W
 
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.init_process_group("nccl", device_id=dev)
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    headline = args.workload == WORKLOAD
-    wl = W.make_workload(WORKLOAD, T=T_SWEEP[rank % len(T_SWEEP)]) if headline else W.make_workload(args.workload)
-    if args.nk > 0:
-        wl.k = wl.k[:args.nk]
-    m = epw.Model(wl.model)
-    dev = torch.device("cuda", local)
-    k = torch.tensor(wl.k, device=dev)
-    q = torch.tensor(wl.q, device=dev)
-    wq = torch.tensor(wl.wq, device=dev)
-    out = torch.empty((len(wl.k), wl.model.nw), dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    pairs = len(wl.k) * len(wl.q)
-
     precs = {"tf32x3": epw.TF32X3, "bf16x3": epw.BF16X3, "fp32": epw.FP32, "fp64": epw.FP64}
-    if args.precision == "auto":
-        # the fastest form that meets the 1e-4 target on this workload: split-BF16
-        # (max relative error 3.4e-5 against the oracle at this size; TF32x3 1.2e-5)
-        name = "bf16x3"
-        try:
-            m.linewidth(k[:8], q[:256], wq[:256], T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=epw.BF16X3)
-        except epw.EPWError:
-            name = "fp32"
-    else:
-        name = args.precision
+    name = AUTO_PRECISION[args.workload] if args.precision == "auto" else args.precision
     prec = precs[name]
-    kw = dict(T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=prec, out=out)
-
-    def timed_steps(nsteps, nwarm, precision):
-        kw2 = dict(kw, precision=precision)
-        for _ in range(nwarm):
-            m.linewidth(k, q, wq, **kw2)
-        stream = torch.cuda.current_stream()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
-        barrier()
-        m.timing(True)
-        l0 = epw.launch_count()
-        for e0, e1 in evs:
-            flush.zero_()  # evict L2 between timed steps (outside the timed events)
-            e0.record(stream)
-            m.linewidth(k, q, wq, **kw2)
-            e1.record(stream)
-        barrier()
-        launches = epw.launch_count() - l0
-        kms, kn = m.timing_read()
-        m.timing(False)
-        step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-        return step_ms, kms / max(kn, 1), kn, launches
-
+    R = Runner(epw, torch, args.workload, rank, world, dev)
     with ClockSampler(local) as clk:
-        step_ms, kern_ms, kern_n, launches = timed_steps(args.steps, args.warmup, prec)
-    t_local = float(np.sum(step_ms))
+        r = R.timed(args.steps, args.warmup, prec, barrier)
+    t_local = float(np.sum(r["step_ms"]))
     if dist is not None:
         t = torch.tensor([t_local], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
+        # the shards' Im Sigma, gathered after the timed region (padded to the largest shard)
+        from paper_1604_03525_gb300.shard import shard_bounds
+        nmax = max(shard_bounds(len(R.wl.k), i, world)[1] - shard_bounds(len(R.wl.k), i, world)[0]
+                   for i in range(world))
+        pad = torch.zeros((nmax, R.wl.model.nw), dtype=torch.float64, device=dev)
+        pad[:len(R.out)] = R.out
+        parts = [torch.empty_like(pad) for _ in range(world)]
+        dist.all_gather(parts, pad)
+        full = torch.cat([parts[i][:shard_bounds(len(R.wl.k), i, world)[1] - shard_bounds(len(R.wl.k), i, world)[0]]
+                          for i in range(world)])
+        assert full.shape[0] == len(R.wl.k) and bool(torch.all(full >= 0))
     else:
         t_max = t_local
     ms_per_step = t_max / args.steps
-    value = world * pairs / (ms_per_step / 1e3)
-
-    # end to end: host (pinned) buffers through the C ABI, copies inside the timed region
-    e2e = None
-    if not args.no_e2e:
-        kh = torch.tensor(wl.k).pin_memory()
-        qh = torch.tensor(wl.q).pin_memory()
-        wh = torch.tensor(wl.wq).pin_memory()
-        oh = torch.empty((len(wl.k), wl.model.nw), dtype=torch.float64).pin_memory()
-        m.linewidth(kh, qh, wh, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=prec, out=oh)
-        barrier()
-        t0 = time.perf_counter()
-        ne = max(1, min(args.steps, 5))
-        for _ in range(ne):
-            m.linewidth(kh, qh, wh, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=prec, out=oh)
-        barrier()
-        dt = (time.perf_counter() - t0) / ne
-        e2e = {"value": world * pairs / dt, "unit": "pairs/s",
-               "h2d_bytes_per_step": int(kh.nbytes + qh.nbytes + wh.nbytes), "d2h_bytes_per_step": int(oh.nbytes)}
-
-    fp64 = None
-    if args.fp64_steps > 0 and prec != epw.FP64:
-        s64, k64, _, _ = timed_steps(args.fp64_steps, 1, epw.FP64)
-        fp64 = {"value": pairs / (np.mean(s64) / 1e3), "unit": "pairs/s", "ms_per_step": float(np.mean(s64)),
-                "kernel_ms": k64}
-    backward = None
-    if args.backward_steps > 0:
-        # adjoint of sum_{k,n} Im Sigma_nk w.r.t. g(Re,Rp), T and E_F, device buffers, g(k,q)
-        # recomputed: the tensor-core form (TF32x3) timed, the FP32 SIMT form once beside it
-        cot = torch.ones((len(wl.k), wl.model.nw), dtype=torch.float64, device=dev)
-
-        def time_backward(op, n):
-            m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=op)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(n):
-                m.linewidth_backward(k, q, cot, wq, T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=op)
-            e1.record()
-            torch.cuda.synchronize()
-            return e0.elapsed_time(e1) / n
-
-        bms = time_backward(epw.TF32X3, args.backward_steps)
-        backward = {"value": pairs / (bms / 1e3), "unit": "pairs/s", "ms_per_step": bms, "precision": "tf32x3",
-                    "what": "dL/dg(Re,Rp), dL/dT, dL/dE_F of L = sum Im Sigma; g(k,q) recomputed"}
-        fms = time_backward(epw.FP32, 1)
-        backward["fp32_simt"] = {"value": pairs / (fms / 1e3), "unit": "pairs/s", "ms_per_step": fms}
-    phonon = None
-    if args.phonon_steps > 0:
-        # per-(q, nu) sums over the k list on the same workload: Pi''_qnu, lambda_qnu, nesting, N(E_F)
-        pk = dict(T=wl.T, EF=wl.EF, sigma=wl.sigma, precision=prec)
-        m.phonon_selfenergy(k, q, **pk)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.phonon_steps):
-            m.phonon_selfenergy(k, q, **pk)
-        e1.record()
-        torch.cuda.synchronize()
-        pms = e0.elapsed_time(e1) / args.phonon_steps
-        phonon = {"value": pairs / (pms / 1e3), "unit": "pairs/s", "ms_per_step": pms, "precision": name,
-                  "what": "Pi''_qnu (on shell), lambda_qnu, nesting zeta_q, N(E_F): per-q sums over the 1000 k"}
-    selfen = None
-    if args.se_steps > 0:
-        # Sigma_nk(omega) and A_nk(omega) (Eqs. elselfenergy, spectral_funct) on 64 frequencies, first 100 k
-        om = torch.linspace(-0.3, 0.3, 64, dtype=torch.float64, device=dev)
-        sk = dict(T=wl.T, EF=wl.EF, delta=wl.sigma, precision=prec)
-        m.selfenergy(k[:100], q, om, wq, **sk)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.se_steps):
-            m.selfenergy(k[:100], q, om, wq, **sk)
-        e1.record()
-        torch.cuda.synchronize()
-        sms = e0.elapsed_time(e1) / args.se_steps
-        sp = 100 * len(wl.q)
-        selfen = {"value": sp / (sms / 1e3), "unit": "pairs/s", "ms_per_step": sms, "precision": name,
-                  "what": "Sigma_nk(omega), A_nk(omega) on 64 frequencies: 100 k x the 40^3 q grid"}
-    others = {}
-    if args.other_steps > 0:
-        forms = (("bf16x3", epw.BF16X3), ("tf32x3", epw.TF32X3), ("fp32", epw.FP32))
-        for oname, op in (forms if headline else forms[:2]):
-            if op == prec:
-                continue
-            try:
-                so, ko, _, _ = timed_steps(args.other_steps, 1, op)
-            except epw.EPWError:
-                continue
-            others[oname] = {"value": pairs / (np.mean(so) / 1e3), "unit": "pairs/s",
-                             "ms_per_step": float(np.mean(so)), "kernel_ms": ko}
-
+    value = R.pairs_total / (ms_per_step / 1e3)
     peaks, peak_src = measured_peaks()
-    tflops, sflops = algorithmic_flops_per_pair(wl.model)
-    fused = wl.model.nw in (1, 2, 4) and 3 * wl.model.nat == 3
-    if prec in (epw.BF16X3, epw.TF32X3) and not fused:
-        # staged form: tcgen05 contraction per k chunk, then the per-pair eigensolve, rotation and
-        # deltas on the CUDA cores (FP32), which dominate; the eigensolve's sweeps are not counted
-        achieved = sflops * pairs / (kern_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": 73.55, "unit": "TFLOP/s", "frac": achieved / 73.55,
-                "traffic": None, "peak_source": "measured FP32 FMA throughput",
-                "work": f"{sflops} rotation + mode-projection flops/pair x {pairs} pairs (per-pair eigensolve "
-                        f"not counted; the tensor-core contraction, {tflops} flops/pair, is a small share)"}
-    elif prec in (epw.BF16X3, epw.TF32X3):
-        achieved = tflops * pairs / (kern_ms / 1e3) / 1e12
-        # a contraction takes the peak of its own dtype: tf32 = measured bf16 x nominal 1.1/2.25
-        ratio = 1.0 if prec == epw.BF16X3 else 1.1 / 2.25
-        peak = peaks["bf16_tflops_sustained"] * ratio
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
-                "peak_source": f"{peak_src} bf16_tflops_sustained" + ("" if ratio == 1.0 else " x 1.1/2.25 (tf32)"),
-                "work": f"{tflops} algorithmic contraction flops/pair x {pairs} pairs "
-                        "(the 3-term split executes 3x this on the tensor pipe)"}
+    fused = args.workload == "fcc_nw4"
+    roof = None
+    if prec in (epw.BF16X3, epw.TF32X3):
+        roof = roofline(R.wl.model, name, r, R.pairs, peaks, peak_src, fused)
+        if fused:
+            roof["traffic"], roof["traffic_source"] = profiled(TC_PROFILE, TC_SOURCE, "traffic", name)
+        else:
+            tpp, src = profiled(WIDE_PROFILE, WIDE_SOURCE, "traffic_per_pair_G", name)
+            nlaunch = max(r["kern"][1], 1)
+            roof["traffic"] = None if tpp is None else tpp * R.pairs / nlaunch
+            roof["traffic_source"] = src + ("" if tpp is None else
+                                            " (per-pair bytes of a smaller capture x the pairs of one G launch)")
     else:
-        # plain CUDA-core arithmetic: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz, FP64 1.25 TFLOP/s nominal
-        # measured FMA rates of this machine's GB300 (8 independent chains per thread)
+        h, g, rot = flops_per_pair(R.wl.model)
         peak = 73.55 if prec == epw.FP32 else 1.257
-        achieved = (tflops + sflops) * pairs / (kern_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": "measured FMA throughput (FP32 73.55 / FP64 1.257 TFLOP/s)", "work": f"{tflops + sflops} algorithmic flops/pair x {pairs} pairs"}
-    if prec in (epw.BF16X3, epw.TF32X3) and fused:
-        # the 3-term split (lo*hi + hi*lo + hi*hi) runs three MMAs per product on the tensor pipe
-        roof["executed_tflops"] = 3.0 * achieved
-        roof["executed_frac"] = 3.0 * achieved / peak
-    roof["kernel_ms"] = kern_ms
-    roof["kernel_launches"] = kern_n
-    if prec in (epw.BF16X3, epw.TF32X3) and headline:
-        roof["traffic"], roof["traffic_source"] = profiled_traffic("bf16x3" if prec == epw.BF16X3 else "tf32x3")
+        ach = (h + g + rot) * R.pairs / (r["kern"][0] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": "measured FMA throughput (FP32 73.55 / FP64 1.257 TFLOP/s)",
+                "work": f"{h + g + rot} algorithmic flops/pair x {R.pairs} pairs", "kernel_ms": r["kern"][0]}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        nks, nqs = {WORKLOAD: (1000, 2560), "diamond_nw8": (64, 8192), "hex_nw5": (64, 16384)}[args.workload]
-        cpu = cpu_baseline(args.workload, nks, nqs)
-
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None,
+        "dtype": {"tf32x3": "tf32x3+f32+f64", "bf16x3": "bf16x3+f32+f64", "fp32": "f32+f64", "fp64": "f64"}[name],
+        "data": "synthetic",
+        "config": {"workload": DESCR[args.workload], "pairs_per_step": R.pairs_total,
+                   "k_shard": "contiguous k slice per rank (strong scaling)", "precision": name,
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "clocks": clk.summary(), "gpu_launches": int(r["launches"] // max(args.steps, 1) * args.steps),
+        "roofline": roof,
+    }
+    if not args.no_e2e:
+        e = R.e2e(prec, max(1, min(args.steps, 3)))
+        if dist is not None:
+            t = torch.tensor([R.pairs / e["value"]], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e["value"] = R.pairs_total / float(t.item())
+        line["e2e"] = e
+    if rank == 0 and world == 1:
+        if args.other_steps > 0 and prec in (epw.BF16X3, epw.TF32X3):
+            oname = "tf32x3" if name == "bf16x3" else "bf16x3"
+            ro = R.timed(args.other_steps, 1, precs[oname])
+            oms = float(np.mean(ro["step_ms"]))
+            line["other_forms"] = {oname: {"value": R.pairs / (oms / 1e3), "unit": "pairs/s", "ms_per_step": oms,
+                                           "roofline": roofline(R.wl.model, oname, ro, R.pairs, peaks, peak_src,
+                                                                fused)}}
+        if args.fp64_k > 0:
+            # the plain FP64 GPU form (SIMT, FP64 contraction, eigensolve and sums) on the first
+            # fp64_k k of the list x the full q list: seconds per k at this size
+            nk64 = min(args.fp64_k, len(R.k))
+            r64 = R.timed(1, 1, epw.FP64, k=R.k[:nk64])
+            ms64 = float(np.mean(r64["step_ms"]))
+            v64 = nk64 * len(R.wl.q) / (ms64 / 1e3)
+            line["fp64_gpu_form"] = {"value": v64, "unit": "pairs/s", "ms_per_step": ms64,
+                                     "sample": f"first {nk64} k x the full q list",
+                                     "speedup_of_headline_form": value / v64}
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(args.workload, *CPU_SAMPLE[args.workload])
+        if args.extras and args.workload == WORKLOAD:
+            line["c2"] = extra_fused(epw, torch, dev, peaks, peak_src)
+            line["c5"] = extra_hex(epw, torch, dev, peaks, peak_src)
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"tf32x3": "tf32x3+f32+f64", "bf16x3": "bf16x3+f32+f64", "fp32": "f32+f64",
-                                                     "fp64": "f64"}[name],
-            "data": "synthetic",
-            "config": {"workload": ("fcc nw=4 nat=1, 135 Re/Rp, 1000 k (0.2 eV window) x 40^3 q, sigma=20 meV, "
-                                    f"T={T_SWEEP[0]:.0f} K (rank r: T_sweep[r])") if headline else
-                                   f"{wl.name}: nw={wl.model.nw} nat={wl.model.nat}, {len(wl.model.Re)} Re/Rp, "
-                                   f"{len(wl.k)} k x {len(wl.q)} q, sigma={wl.sigma * 1e3:.0f} meV, T={wl.T:.0f} K",
-                       "pairs_per_step_per_gpu": pairs,
-                       "precision": name, "l2": "flushed between timed steps (256 MB write)"},
-            "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof,
-            "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu_form": fp64, "other_forms": others, "backward": backward, "phonon_side": phonon, "selfenergy": selfen,
-        }
         print(json.dumps(line))
-    m.close()
+    R.m.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def extra_fused(epw, torch, dev, peaks, peak_src):
+    """The fcc nw=4 configuration on the fused single-kernel form (BF16x3), 10 steps."""
+    R = Runner(epw, torch, "fcc_nw4", 0, 1, dev)
+    r = R.timed(10, 3, epw.BF16X3)
+    ms = float(np.mean(r["step_ms"]))
+    roof = roofline(R.wl.model, "bf16x3", r, R.pairs, peaks, peak_src, True)
+    roof["traffic"], roof["traffic_source"] = profiled(TC_PROFILE, TC_SOURCE, "traffic", "bf16x3")
+    out = {"workload": DESCR["fcc_nw4"], "value": R.pairs / (ms / 1e3), "unit": "pairs/s", "ms_per_step": ms,
+           "precision": "bf16x3", "roofline": roof}
+    R.m.close()
+    return out
+
+
+def extra_hex(epw, torch, dev, peaks, peak_src):
+    """The hexagonal nw=5 configuration (BF16x3 forward) and its adjoint (TF32x3 and BF16x3)."""
+    R = Runner(epw, torch, "hex_nw5", 0, 1, dev)
+    r = R.timed(2, 1, epw.BF16X3)
+    ms = float(np.mean(r["step_ms"]))
+    out = {"workload": DESCR["hex_nw5"], "value": R.pairs / (ms / 1e3), "unit": "pairs/s", "ms_per_step": ms,
+           "precision": "bf16x3", "roofline": roofline(R.wl.model, "bf16x3", r, R.pairs, peaks, peak_src, False)}
+    cot = torch.ones((len(R.k), R.wl.model.nw), dtype=torch.float64, device=dev)
+    out["backward"] = {}
+    for pname, p in (("tf32x3", epw.TF32X3), ("bf16x3", epw.BF16X3)):
+        kw = dict(T=R.wl.T, EF=R.wl.EF, sigma=R.wl.sigma, precision=p)
+        R.m.linewidth_backward(R.k, R.q, cot, R.wq, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        R.m.linewidth_backward(R.k, R.q, cot, R.wq, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1)
+        out["backward"][pname] = {
+            "value": R.pairs / (bms / 1e3), "unit": "pairs/s", "ms_per_step": bms,
+            "what": "dL/dg(Re,Rp), dL/dT, dL/dE_F of L = sum Im Sigma at the full size; g(k,q) recomputed "
+                    "(forward contraction staged on the tensor cores, adjoint GEMMs in FP32)"}
+    R.m.close()
+    return out
 
 
 if __name__ == "__main__":

@@ -85,9 +85,10 @@ typedef enum {
  *                FP32; phases, phonons, k-side work and the reduction in FP64.
  *   EPW_TF32X3 : as EPW_BF16X3 with tf32 terms (about 16x smaller contraction
  *                error, half the tensor throughput).
- * The two tensor-core forms need Re == Rp (same vectors, same order) and a
- * compiled (nw, 3nat) shape: (1,3), (2,3), (4,3); otherwise the call returns
- * EPW_ERR_UNSUPPORTED and EPW_FP32 / EPW_FP64 serve every shape. */
+ * The split forms serve every shape up to nw = 18, 3nat = 18 with Re and Rp
+ * equal or not (the contraction runs over both sets); the entry points that
+ * have per-pair kernels only up to nw = 8, 3nat = 9 (adjoint, phonon-side sums,
+ * complex self-energy) say so and return EPW_ERR_UNSUPPORTED beyond. */
 typedef enum { EPW_FP64 = 0, EPW_FP32 = 1, EPW_BF16X3 = 2, EPW_TF32X3 = 3 } epw_precision;
 
 typedef struct epw_model epw_model; /* opaque */
@@ -163,7 +164,14 @@ epw_status epw_interp_g(const epw_model *model, int nk, const double *k, int nq,
 
 /* Electron linewidth Im Sigma_nk [nk][nw] (eV) on the k list, summed over the
  * q list with weights wq (NULL: 1/nq each).  Sums of the positive terms are
- * deterministic (fixed order, compensated in FP64). */
+ * deterministic (fixed order, compensated in FP64).
+ * Split precisions run on the tensor cores: models whose per-k columns
+ * 2 nw^2 (3nat + 1) fit 128 take one fused kernel; (nw, 3nat) = (8, 6) and
+ * (5, 9) take the wide-shape form (H(k+q) eigensolve beside the vertex
+ * contraction; only terms whose Gaussians do not underflow in FP32 are
+ * evaluated, which leaves the sums unchanged); the environment variable
+ * EPW_WIDE_FORM=split selects its two-kernel variant instead of the fused one;
+ * other shapes take the staged form. */
 epw_status epw_linewidth(const epw_model *model, int nk, const double *k, int nq, const double *q,
                          const double *wq, const epw_params *params, double *imsigma, void *stream);
 
@@ -190,7 +198,7 @@ epw_status epw_linewidth_backward(const epw_model *model, int nk, const double *
  * (eV for pi_imag; lambda and nesting dimensionless / per eV^2); any output may
  * be NULL; pointers host or device.  precision: EPW_FP64, EPW_FP32 (CUDA
  * cores) or EPW_TF32X3 / EPW_BF16X3 (contraction on the tensor cores, staged
- * per chunk of k; needs Re == Rp).  Shapes up to nw = 8, 3nat = 9; others
+ * per chunk of k).  Shapes up to nw = 8, 3nat = 9; others
  * return EPW_ERR_UNSUPPORTED.  Per-q sums over k are formed in a fixed order. */
 epw_status epw_phonon_selfenergy(const epw_model *model, int nk, const double *k, const double *wk, int nq,
                                  const double *q, const epw_params *params, double *pi_imag, double *lambda,
@@ -207,7 +215,7 @@ epw_status epw_phonon_selfenergy(const epw_model *model, int nk, const double *k
  * Sigma'' = -Im Sigma, Sigma~' = Re Sigma(omega) - Re Sigma(0) (Eq. realpartselfenergy).
  * params: T_K, EF_eV, omega_min_eV and precision as for epw_linewidth (sigma_eV is not
  * used: the width here is delta).  Host or device pointers.  FP64/FP32 on the CUDA cores,
- * TF32X3/BF16X3 with the contraction staged on the tensor cores (Re == Rp).  Shapes up to
+ * TF32X3/BF16X3 with the contraction staged on the tensor cores.  Shapes up to
  * nw = 8, 3nat = 9.  Sums over q in a fixed order. */
 epw_status epw_selfenergy(const epw_model *model, int nk, const double *k, int nq, const double *q,
                           const double *wq, const epw_params *params, double delta, int nomega,

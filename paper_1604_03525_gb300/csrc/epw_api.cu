@@ -552,7 +552,11 @@ extern "C" epw_status epw_sync(const epw_model *m, void *stream) {
 // Contraction buffer of the staged tensor-core form (per chunk of k).
 static const size_t STAGED_CT_BYTES = (size_t)4 << 30;
 
-EpwTune epwi_default_tune() { return EpwTune{0, STAGED_CT_BYTES}; }
+// EPW_WIDE_FORM=split selects the two-kernel wide-shape form (default: the fused kernel).
+EpwTune epwi_default_tune() {
+  const char *w = getenv("EPW_WIDE_FORM");
+  return EpwTune{0, STAGED_CT_BYTES, (w && strcmp(w, "split") == 0) ? 1 : 0};
+}
 
 epw_status epwi_plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,
                                bool sout, const EpwTune &tune, LwPlan &L) {
@@ -567,7 +571,7 @@ epw_status epwi_plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int
     L.tc.a_block_bytes = tune.a_block_bytes;
     L.partial = nullptr;
   } else if (tc && tcw_supported(m)) {
-    CKS(tcw_plan(A, m, nk, nq, op, 0, L.w));
+    CKS(tcw_plan(A, m, nk, nq, op, 0, L.w, tune.wide_split != 0));
     L.partial = nullptr;
   } else {
     if (tc) CKS(tc_staged_plan(A, m, nk, nq, op, tune.staged_ct_bytes ? tune.staged_ct_bytes : STAGED_CT_BYTES, L.sg));
@@ -647,7 +651,7 @@ epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, c
   Prep &p = L.p;
   const bool tcp = prec == EPW_BF16X3 || prec == EPW_TF32X3;
   if (tcp && !L.tc.ok && !L.sg.ok && !L.w.ok)
-    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
+    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d", m->nw, m->nm);
   if (tcp && L.tc.ok) {
     CKS(run_prep(m, nk, kd, nq, qd, EPW_FP32, par->omega_min_eV, true, p, nullptr, st, true, &L.tc));
     L.tc.Cpol = m->polar ? (const float2 *)p.Cpol : nullptr;
@@ -750,7 +754,7 @@ extern "C" epw_status epw_interp_g(const epw_model *mc, int nk, const double *k,
   const bool tcp = precision == EPW_BF16X3 || precision == EPW_TF32X3;
   const bool tc = tcp && tc_supported(m), staged = tcp && tc_staged_supported(m);
   if (tcp && !tc && !staged)
-    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
+    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d", m->nw, m->nm);
   const int wprec = tcp ? EPW_FP32 : precision;  // precision of the shared preparation
   if (!(omega_min >= 0.0)) return fail(EPW_ERR_INVALID_ARG, "omega_min must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
@@ -875,13 +879,15 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   if (!(par->T_K > 0.0)) return fail(EPW_ERR_INVALID_ARG, "the adjoint needs T_K > 0");
   if (nk > 0 && !cot) return fail(EPW_ERR_INVALID_ARG, "null grad_imsigma");
   const int prec = par->precision >= EPW_BF16X3 ? EPW_FP32 : par->precision;
-  // tensor-core adjoint (TF32 split) for shapes the fused kernel serves
+  // tensor-core adjoint (TF32 split) for shapes the fused kernel serves (Re == Rp: its
+  // q-contraction of the adjoint runs over one R set)
   const bool tcp = par->precision == EPW_BF16X3 || par->precision == EPW_TF32X3;
-  const bool tcb = tcp && tc_supported(m);
-  // other shapes: the forward contraction of the recompute staged on the tensor cores
-  const bool staged = tcp && !tcb && tc_staged_supported(m);
+  const bool tcb = tcp && m->same_ep && tc_supported(m);
+  // other shapes, and Re != Rp: the forward contraction of the recompute staged on the
+  // tensor cores (its K layout carries both R sets)
+  const bool staged = tcp && !tcb && m->nw <= 18 && m->nm <= 18;
   if (tcp && !tcb && !staged)
-    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", m->nw, m->nm);
+    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d", m->nw, m->nm);
   if (m->nw > 8 || m->nm > 9)
     return fail(EPW_ERR_UNSUPPORTED, "the adjoint has no kernel for nw=%d, 3nat=%d (at most 8 and 9)", m->nw, m->nm);
   cudaStream_t st = (cudaStream_t)stream;
@@ -912,7 +918,7 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
     } else {
       if (staged) {
         CKS(tc_staged_plan(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1,
-                           par->precision == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32, (size_t)2 << 30, b.sg));
+                           par->precision == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32, (size_t)2 << 30, b.sg, true));
         nkc = std::min(nkc, b.sg.kc);
       }
       b.xbar = (double *)A.take<char>(sR * (size_t)nq * nkc * per);
@@ -1056,7 +1062,6 @@ extern "C" epw_status epw_phonon_selfenergy(const epw_model *mc, int nk, const d
   if (m->nw > 8 || nm > 9)
     return fail(EPW_ERR_UNSUPPORTED, "the phonon-side sums have no kernel for nw=%d, 3nat=%d (at most 8 and 9)",
                 m->nw, nm);
-  if (tcp && !m->same_ep) return fail(EPW_ERR_UNSUPPORTED, "the tensor-core forms need Re == Rp");
   const int wprec = tcp ? EPW_FP32 : par->precision;
   const bool sk = nk > 0 && !is_device_ptr(k), sq = nq > 0 && !is_device_ptr(q);
   const bool swk = wk && nk > 0 && !is_device_ptr(wk);
@@ -1210,7 +1215,6 @@ extern "C" epw_status epw_selfenergy(const epw_model *mc, int nk, const double *
     return fail(EPW_ERR_UNSUPPORTED, "the self-energy has no kernel for nw=%d, 3nat=%d (at most 8 and 9)", m->nw,
                 m->nm);
   const bool tcp = par->precision == EPW_BF16X3 || par->precision == EPW_TF32X3;
-  if (tcp && !m->same_ep) return fail(EPW_ERR_UNSUPPORTED, "the tensor-core forms need Re == Rp");
   cudaStream_t st = (cudaStream_t)stream;
   const int nw = m->nw;
   const size_t nout = (size_t)nk * nw * nomega;

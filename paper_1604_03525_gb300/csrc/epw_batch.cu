@@ -33,9 +33,9 @@
 namespace {
 
 // ----------------------------------------------------------------- autotuner
-// A job's path: the fused tensor-core kernel, the wide-shape fused form (no
-// tile knob), the staged tensor-core form, or the SIMT per-pair kernel (no tile
-// knob).
+// A job's path: the fused tensor-core kernel, the wide-shape form (one fused
+// kernel or two per chunk of k), the staged tensor-core form, or the SIMT
+// per-pair kernel (no tile knob).
 enum Path { PATH_SIMT = 0, PATH_FUSED = 1, PATH_STAGED = 2, PATH_WIDE = 3 };
 
 int job_path(const epw_model *m, int prec) {
@@ -68,7 +68,7 @@ std::mutex g_mu;
 std::map<std::string, EpwTune> g_cache;
 bool g_loaded = false;
 
-// File format, one entry per line: <key>|<a_block_bytes>|<staged_ct_bytes>
+// File format, one entry per line: <key>|<a_block_bytes>|<staged_ct_bytes>[|<wide_split>]
 void load_cache_file_locked() {
   if (g_loaded) return;
   g_loaded = true;
@@ -86,6 +86,8 @@ void load_cache_file_locked() {
     EpwTune t;
     t.a_block_bytes = strtoull(b1 + 1, nullptr, 10);
     t.staged_ct_bytes = strtoull(b2 + 1, nullptr, 10);
+    char *b3 = strchr(b2 + 1, '|');
+    t.wide_split = b3 ? atoi(b3 + 1) : 0;
     g_cache[line] = t;
   }
   fclose(f);
@@ -96,7 +98,7 @@ void append_cache_file_locked(const std::string &key, const EpwTune &t) {
   if (!path || !*path) return;
   FILE *f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s|%zu|%zu\n", key.c_str(), t.a_block_bytes, t.staged_ct_bytes);
+  fprintf(f, "%s|%zu|%zu|%d\n", key.c_str(), t.a_block_bytes, t.staged_ct_bytes, t.wide_split);
   fclose(f);
 }
 
@@ -104,9 +106,11 @@ std::vector<EpwTune> candidates(int path) {
   const EpwTune d = epwi_default_tune();
   std::vector<EpwTune> c;
   if (path == PATH_FUSED) {
-    for (size_t mib : {16, 32, 48, 96}) c.push_back(EpwTune{mib << 20, d.staged_ct_bytes});
+    for (size_t mib : {16, 32, 48, 96}) c.push_back(EpwTune{mib << 20, d.staged_ct_bytes, 0});
   } else if (path == PATH_STAGED) {
-    for (size_t gib : {1, 2, 4}) c.push_back(EpwTune{d.a_block_bytes, gib << 30});
+    for (size_t gib : {1, 2, 4}) c.push_back(EpwTune{d.a_block_bytes, gib << 30, 0});
+  } else if (path == PATH_WIDE) {
+    for (int split : {0, 1}) c.push_back(EpwTune{d.a_block_bytes, d.staged_ct_bytes, split});
   } else {
     c.push_back(d);
   }
@@ -309,7 +313,7 @@ epw_status create_impl(int njobs, const epw_linewidth_job *jobs, epw_batch *b) {
         (J.wq && J.nq > 0 && !epwi_is_device_ptr(J.wq)) || (J.nk > 0 && !epwi_is_device_ptr(J.imsigma)))
       return epwi_fail(EPW_ERR_INVALID_ARG, "job %d: batch buffers must be device pointers", j);
     if (J.nk > 0 && J.nq > 0 && job_path(J.model, J.params.precision) < 0)
-      return epwi_fail(EPW_ERR_UNSUPPORTED, "job %d: no tensor-core form for nw=%d, 3nat=%d (or Re != Rp)", j,
+      return epwi_fail(EPW_ERR_UNSUPPORTED, "job %d: no tensor-core form for nw=%d, 3nat=%d", j,
                        J.model->nw, J.model->nm);
     if (J.nk > 0 && J.nq > 0 && (J.model->nw > 18 || J.model->nm > 18))
       return epwi_fail(EPW_ERR_UNSUPPORTED, "job %d: no per-pair kernel for nw=%d, 3nat=%d", j, J.model->nw,

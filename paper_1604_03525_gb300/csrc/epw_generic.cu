@@ -519,8 +519,11 @@ __global__ void __launch_bounds__(128) k_pair(PairArgs a) {
           double c = keep ? cot[n] * EPW_PI * wqi : 0.0;
           R W = (R)(c * ((double)(nb + f) * dp + (double)(nb + R(1) - f) * dm));
           double g2 = (double)cabs2(G[v][m][n]);
-          sT += c * g2 * ((dn + dfT) * dp + (dn - dfT) * dm);
-          sE += c * g2 * dfE * (dp - dm);
+          // (dn + dfT) d+ + (dn - dfT) d- = dn (d+ + d-) + dfT (d+ - d-), the difference
+          // without cancellation for soft modes
+          const double dd = (double)gauss_diff_r<R>(x, w, inv_sigma, gnorm);
+          sT += c * g2 * (dn * ((double)dp + (double)dm) + dfT * dd);
+          sE += c * g2 * dfE * dd;
           G[v][m][n] = (R(2) * W) * G[v][m][n];
         }
       }

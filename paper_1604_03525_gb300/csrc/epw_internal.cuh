@@ -259,6 +259,17 @@ __device__ __forceinline__ R gauss_r(R x, R inv_sigma, R norm) {
   return norm * exp(-y * y);
 }
 
+// delta(x + w) - delta(x - w) for the Gaussian above.  With a = x/sigma, b = w/sigma the
+// two exponents differ by 4ab, so the difference is -2 norm exp(-(a^2 + b^2)) sinh(2ab),
+// which keeps its relative accuracy for w << sigma (no subtraction of close values); for
+// |2ab| > 1 the plain difference is well conditioned and is taken instead.
+template <typename R>
+__device__ __forceinline__ R gauss_diff_r(R x, R w, R inv_sigma, R norm) {
+  const R a = x * inv_sigma, b = w * inv_sigma, y = R(2) * a * b;
+  if (fabs(y) > R(1)) return gauss_r<R>(x + w, inv_sigma, norm) - gauss_r<R>(x - w, inv_sigma, norm);
+  return R(-2) * norm * exp(-(a * a + b * b)) * sinh(y);
+}
+
 // Occupations in working precision (FP64 forms in FP64, FP32 forms with 1/kT).
 template <typename R>
 __device__ __forceinline__ R occ_bose(R w, double T);

@@ -312,6 +312,21 @@ __device__ __forceinline__ void modes_linewidth_packed(const TcArgs &a, uint32_t
 // the packed counterpart of the generic MODE 2 loop in epilogue_pair: per mode
 // W_nu,mn = c_nk pi w_q [(n+f) d+ + (n+1-f) d-], Z_nu = U (2 W_nu o y_nu) with
 // y_nu = U^dagger G_nu, and Xbar_a = sum_nu conj(E[a][nu]) Z_nu, written as the
+// ep - en for ep = 2^(-(x + w)^2 s2), en = 2^(-(x - w)^2 s2) (the Gaussians of the
+// forward sums in base 2).  The exponents differ by 4 x w s2, so
+//   ep - en = -2 * 2^(-(x^2 + w^2) s2) * sinh(2 ln2 x w s2),
+// with sinh(y) from its Taylor series through y^9/9! for |y| <= 1 (truncation below
+// 3e-8 relative): no subtraction of close values when w << sigma.  For |y| > 1 the
+// two values differ by a factor e^2 or more and the plain difference is taken.
+__device__ __forceinline__ float gauss_diff2(float x, float w, float s2, float ep, float en) {
+  const float y = 1.3862943611198906f * x * w * s2;  // 2 ln2 x w s2
+  const float y2 = y * y;
+  const float sh =
+      y * fmaf(y2, fmaf(y2, fmaf(y2, fmaf(y2, 1.0f / 362880.0f, 1.0f / 5040.0f), 1.0f / 120.0f), 1.0f / 6.0f), 1.0f);
+  const float small = -2.0f * ex2_approx(-fmaf(x, x, w * w) * s2) * sh;
+  return fabsf(y) <= 1.0f ? small : ep - en;
+}
+
 // tf32-split rows (k, a, j, n); the dL/dT and dL/dE_F terms go to sT and sE.
 // Two n columns per packed FP32 instruction, as in modes_linewidth_packed.
 template <int NW, int NM>
@@ -420,7 +435,7 @@ __device__ __forceinline__ void modes_adjoint_packed(const TcArgs &a, uint32_t t
         }
       }
       const float2 cp = bc2(kf * (nbnu + fm[m])), cm = bc2(kf * (nbnu + 1.0f - fm[m]));
-      const float2 dpT = bc2(dn + dfT[m]), dmT = bc2(dn - dfT[m]), dE = bc2(dfE[m]);
+      const float2 dn2 = bc2(dn), dT2 = bc2(dfT[m]), dE = bc2(dfE[m]);
       const float ems = em[m] * sc;
       const float2 op = bc2(ws - ems), om = bc2(-ws - ems);
       float2 ybr[NP], ybi[NP];
@@ -433,8 +448,11 @@ __device__ __forceinline__ void modes_adjoint_packed(const TcArgs &a, uint32_t t
         const float2 en = make_float2(ex2_approx(-tm.x), ex2_approx(-tm.y));
         const float2 wv = fmul2(cw2x[p], ffma2(cm, en, fmul2(cp, ep)));
         const float2 kg = fmul2(kcw[p], g2);
-        sT2 = ffma2(kg, ffma2(dmT, en, fmul2(dpT, ep)), sT2);
-        sE2 = ffma2(fmul2(kg, dE), fadd2(ep, make_float2(-en.x, -en.y)), sE2);
+        // (dn + dfT) ep + (dn - dfT) en = dn (ep + en) + dfT (ep - en); ep - en in the sinh form
+        const float2 dd = make_float2(gauss_diff2(eks[p].x - ems, ws, 1.0f, ep.x, en.x),
+                                      gauss_diff2(eks[p].y - ems, ws, 1.0f, ep.y, en.y));
+        sT2 = ffma2(kg, ffma2(dT2, dd, fmul2(dn2, fadd2(ep, en))), sT2);
+        sE2 = ffma2(fmul2(kg, dE), dd, sE2);
         ybr[p] = fmul2(wv, yr[p]);
         ybi[p] = fmul2(wv, yi[p]);
       }
@@ -670,8 +688,9 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
           const float xp = xd + wnu, xm = xd - wnu;
           const float ep = ex2_approx(-xp * xp * s2), en = ex2_approx(-xm * xm * s2);
           const float wv = 2.0f * cw[n] * (cp * ep + cm * en);
-          sT = fmaf(kf * cw[n] * g2, (dn + dfT) * ep + (dn - dfT) * en, sT);
-          sE = fmaf(kf * cw[n] * g2, dfE * (ep - en), sE);
+          const float dd = gauss_diff2(xd, wnu, s2, ep, en);  // ep - en without cancellation
+          sT = fmaf(kf * cw[n] * g2, fmaf(dn, ep + en, dfT * dd), sT);
+          sE = fmaf(kf * cw[n] * g2, dfE * dd, sE);
           const cx<float> yb = mkc(wv * y.x, wv * y.y);
 #pragma unroll
           for (int j = 0; j < NW; j++) cfma(Z[j][n], V[j][m], yb);
@@ -937,28 +956,37 @@ __device__ __forceinline__ void split_store<float>(double v, float *hi, float *l
   lo[i] = tf32_round((float)(v - (double)h));
 }
 
-// A[q][kk] (K-major hi/lo): kk = 2r + t, value cos / sin of 2 pi (q.R_r mod 1).
+// A[q][kk] (K-major hi/lo): kk = 2r + t, value cos / sin of 2 pi (q.R_r mod 1), R
+// reversed (far shells first).  With a second set R2 (the vertex's Rp when it
+// differs from Re), its phases follow at K offset kg0 (a multiple of 64), zero between.
 template <typename T>
 __global__ void k_build_a(int nq, int nR, int kpad, const double *__restrict__ q, const int *__restrict__ R, T *hi,
-                          T *lo) {
+                          T *lo, int nR2 = 0, const int *__restrict__ R2 = nullptr, int kg0 = 0) {
   size_t n = (size_t)nq * kpad;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
     int kk = (int)(idx % kpad);
     int iq = (int)(idx / kpad);
     double d = 0.0;
-    if (kk < 2 * nR) {
-      int r = nR - 1 - (kk >> 1);
+    const int *Rs = R;
+    int nRs = nR, kl = kk;
+    if (R2 && kk >= kg0) {
+      Rs = R2;
+      nRs = nR2;
+      kl = kk - kg0;
+    }
+    if (kl < 2 * nRs) {
+      int r = nRs - 1 - (kl >> 1);
       // argument q.R reduced to [-1/2, 1/2] in FP64; 2x = xh + xl with xh in FP32,
       // then sin/cos(pi xh) in FP32 and the first-order correction in pi xl
       // (|xl| <= 2^-25): about 1 FP32 ulp, below the 2^-22 of the two-term split.
-      double x = q[3 * iq] * R[3 * r] + q[3 * iq + 1] * R[3 * r + 1] + q[3 * iq + 2] * R[3 * r + 2];
+      double x = q[3 * iq] * Rs[3 * r] + q[3 * iq + 1] * Rs[3 * r + 1] + q[3 * iq + 2] * Rs[3 * r + 2];
       x -= rint(x);
       const double x2 = 2.0 * x;
       const float xh = (float)x2;
       const float xl = (float)(x2 - (double)xh) * 3.14159265358979f;
       float s, c;
       sincospif(xh, &s, &c);
-      d = (kk & 1) ? (double)fmaf(xl, c, s) : (double)fmaf(-xl, s, c);
+      d = (kl & 1) ? (double)fmaf(xl, c, s) : (double)fmaf(-xl, s, c);
     }
     split_store<T>(d, hi, lo, idx);
   }
@@ -1024,20 +1052,32 @@ __device__ __forceinline__ void split_store_f<float>(float v, float *hi, float *
 // K entries along K (coalesced).  Rows k >= nk, columns c >= nc and K >= 2 nR are 0.
 template <typename T>
 __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad, int planar,
-                          const cx<float> *__restrict__ BH, const cx<float> *__restrict__ Bg, T *hi, T *lo) {
+                          const cx<float> *__restrict__ BH, const cx<float> *__restrict__ Bg, T *hi, T *lo, int nRp,
+                          int kg0) {
   __shared__ cx<float> tile[32][33];  // [R index from the K tile][c - c0]
   const int nw2 = nw * nw;
   const int nc = nw2 * (nm + 1);
   const int c0 = blockIdx.y * 32;
-  const int kk0 = blockIdx.x * 64, rr0 = kk0 >> 1;
+  const int kk0 = blockIdx.x * 64;
+  // K parts: one R set shared by H and the vertex (kg0 = 0), or H over Re in [0, 2 nRe)
+  // and the vertex over Rp from kg0 (a multiple of 64, so a K tile lies in one part)
+  const bool partG = kg0 > 0 && kk0 >= kg0;
+  const int kb = partG ? kg0 : 0;
+  const int rr0 = (kk0 - kb) >> 1;
+  const int nRH = nR, nRG = kg0 > 0 ? nRp : nR;
+  const int nRt = partG ? nRG : nRH;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   for (int k = blockIdx.z; k < nk_pad; k += gridDim.z) {
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
       const int rr = rr0 + j, c = c0 + threadIdx.x;
       cx<float> b = mkc(0.0f, 0.0f);
-      if (k < nk && rr < nR && c < nc) {
-        const int r = nR - 1 - rr;
-        b = c < nw2 ? BH[((size_t)k * nR + r) * nw2 + c] : Bg[((size_t)k * nR + r) * nm * nw2 + (c - nw2)];
+      if (k < nk && rr < nRt && c < nc) {
+        const int r = nRt - 1 - rr;
+        if (c < nw2) {
+          if (!partG) b = BH[((size_t)k * nRH + r) * nw2 + c];
+        } else if (kg0 == 0 || partG) {
+          b = Bg[((size_t)k * nRG + r) * nm * nw2 + (c - nw2)];
+        }
       }
       tile[j][threadIdx.x] = b;
     }
@@ -1049,8 +1089,8 @@ __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, i
       const int c = planar ? 2 * (col >> 2) + (col & 1) : col >> 1;
       const int sr = planar ? (col >> 1) & 1 : col & 1;
       float v = 0.0f;
-      if (kk < 2 * nR) {
-        const cx<float> b = tile[(kk >> 1) - rr0][c - c0];
+      if (kk - kb < 2 * nRt) {
+        const cx<float> b = tile[((kk - kb) >> 1) - rr0][c - c0];
         const int t = kk & 1;
         v = sr == 0 ? (t == 0 ? b.x : -b.y) : (t == 0 ? b.y : b.x);
       }
@@ -1060,11 +1100,13 @@ __global__ void k_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, i
   }
 }
 
+// nRp, kg0: the vertex's R set and its K offset when it differs from Re (else nRp = nR, kg0 = 0)
 template <typename T>
 void launch_build_b(int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad, int planar, const cx<float> *BH,
-                    const cx<float> *Bg, T *hi, T *lo, cudaStream_t st) {
+                    const cx<float> *Bg, T *hi, T *lo, cudaStream_t st, int nRp = 0, int kg0 = 0) {
   const dim3 grid((kpad + 63) / 64, (cpk + 63) / 64, std::min(nk_pad, 65535));
-  k_build_b<T><<<grid, dim3(32, 8), 0, st>>>(nk, nk_pad, nR, nw, nm, cpk, kpad, planar, BH, Bg, hi, lo);
+  k_build_b<T><<<grid, dim3(32, 8), 0, st>>>(nk, nk_pad, nR, nw, nm, cpk, kpad, planar, BH, Bg, hi, lo,
+                                             nRp > 0 ? nRp : nR, kg0);
   epw_count_launch();
 }
 
@@ -1098,8 +1140,13 @@ inline int grid_for(size_t n, int bs) {
 // A operand (q phases, split): from the FP64 phases when they exist, else computed here.
 template <typename T>
 void build_a(int nq, int nR, int kpad, const double *q, const int *R, const cx<double> *P64, T *hi, T *lo,
-             cudaStream_t st) {
-  if (P64) {
+             cudaStream_t st, int nR2 = 0, const int *R2 = nullptr, int kg0 = 0) {
+  if (R2 && kg0 > 0) {
+    // two R sets (Re, then Rp at kg0): computed from q
+    const size_t n = (size_t)nq * kpad;
+    k_build_a<T><<<grid_for(n, 256), 256, 0, st>>>(nq, nR, kpad, q, R, hi, lo, nR2, R2, kg0);
+    epw_count_launch();
+  } else if (P64) {
     dim3 grid((nq + 31) / 32, (nR + 31) / 32);
     k_build_a_from<T><<<grid, dim3(32, 8), 0, st>>>(nq, nR, kpad, P64, hi, lo);
     epw_count_launch();
@@ -1362,6 +1409,17 @@ cudaError_t launch_tc_shape(int nw, int nm, const CUtensorMap &ah, const CUtenso
 
 }  // namespace
 
+// K extent of the contraction: 2 nRe, or, when Rp differs from Re, the Re part padded
+// to a multiple of 64 (kg0) followed by 2 nRp; rounded up to the K step kal.
+static int k_layout(const epw_model *m, int kal, int &kg0) {
+  if (m->same_ep) {
+    kg0 = 0;
+    return (2 * m->nRe + kal - 1) / kal * kal;
+  }
+  kg0 = (2 * m->nRe + 63) / 64 * 64;
+  return (kg0 + 2 * m->nRp + kal - 1) / kal * kal;
+}
+
 // Operand builders, tensor maps and FP32 tables for the other tensor-core kernels.
 void tc_build_b_raw(int op, int nk, int nk_pad, int nR, int nw, int nm, int cpk, int kpad, const cx<float> *BH,
                     const cx<float> *Bg, void *hi, void *lo, cudaStream_t st) {
@@ -1407,21 +1465,22 @@ void tc_build_b(const epw_model *m, int nk, const cx<float> *Bg32, const cx<floa
                 cudaStream_t st) {
   if (b.op == TC_OP_BF16)
     launch_build_b<__nv_bfloat16>(nk, b.nk_pad, m->nRe, m->nw, m->nm, b.cpk, b.kpad, b.planar, BH32, Bg32,
-                                  (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo, st);
+                                  (__nv_bfloat16 *)b.Bhi, (__nv_bfloat16 *)b.Blo, st, m->nRp, b.kg0);
   else
     launch_build_b<float>(nk, b.nk_pad, m->nRe, m->nw, m->nm, b.cpk, b.kpad, b.planar, BH32, Bg32, (float *)b.Bhi,
-                          (float *)b.Blo, st);
+                          (float *)b.Blo, st, m->nRp, b.kg0);
 }
 
 void tc_build_a(const epw_model *m, int nq, const double *q, TcBuffers &b, cudaStream_t st) {
   if (b.op == TC_OP_BF16)
-    build_a<__nv_bfloat16>(nq, m->nRe, b.kpad, q, m->Re, b.Pq64, (__nv_bfloat16 *)b.Ahi, (__nv_bfloat16 *)b.Alo, st);
+    build_a<__nv_bfloat16>(nq, m->nRe, b.kpad, q, m->Re, b.Pq64, (__nv_bfloat16 *)b.Ahi, (__nv_bfloat16 *)b.Alo, st,
+                           m->nRp, m->Rp, b.kg0);
   else
-    build_a<float>(nq, m->nRe, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st);
+    build_a<float>(nq, m->nRe, b.kpad, q, m->Re, b.Pq64, (float *)b.Ahi, (float *)b.Alo, st, m->nRp, m->Rp, b.kg0);
 }
 
 bool tc_qside(const epw_model *m, int nq, const double *q, TcBuffers &b, cx<double> *D, cudaStream_t st) {
-  if (!b.ok || !m->same_eph || m->nm != 3 || m->rmax > QS_RMAX || nq <= 0) return false;
+  if (!b.ok || !m->same_ep || !m->same_eph || m->nm != 3 || m->rmax > QS_RMAX || nq <= 0) return false;
   const int grid = (nq + QS_THREADS - 1) / QS_THREADS;
   const size_t sh = (size_t)3 * (2 * m->rmax + 1) * QS_THREADS * sizeof(float4);  // <= 52 KB
   static bool attr = false;
@@ -1445,17 +1504,17 @@ bool tc_qside(const epw_model *m, int nq, const double *q, TcBuffers &b, cx<doub
 
 bool tc_supported(const epw_model *m) {
   int cpk, kpt, planar;
-  return m->same_ep && shape_info(m->nw, m->nm, cpk, kpt, planar);
+  return shape_info(m->nw, m->nm, cpk, kpt, planar);
 }
 
 epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffers &b) {
   b = TcBuffers{};
   b.op = op;
-  b.ok = m->same_ep && shape_info(m->nw, m->nm, b.cpk, b.kpt, b.planar);
+  b.ok = shape_info(m->nw, m->nm, b.cpk, b.kpt, b.planar);
   if (!b.ok) return EPW_OK;
   const int esz = op == TC_OP_BF16 ? 2 : 4;
   const int kal = op == TC_OP_BF16 ? 16 : 8;  // K per MMA
-  b.kpad = (2 * m->nRe + kal - 1) / kal * kal;
+  b.kpad = k_layout(m, kal, b.kg0);
   b.nk_pad = (nk + b.kpt - 1) / b.kpt * b.kpt;
   b.nqt = (nq + BM - 1) / BM;
   b.Ahi = A.take<char>((size_t)nq * b.kpad * esz);
@@ -2016,17 +2075,17 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
 // the tensor cores per chunk of k with its result written to HBM,
 //   Ct[kl cpk + col][q] = sum_kk A[q][kk] B[kl][col][kk],
 // and the per-pair kernel (eigensolve, rotation, deltas) reads it from there.
-bool tc_staged_supported(const epw_model *m) { return m->same_ep && !tc_supported(m) && m->nw <= 18 && m->nm <= 18; }
+bool tc_staged_supported(const epw_model *m) { return !tc_supported(m) && m->nw <= 18 && m->nm <= 18; }
 
 epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t ct_budget, TcStaged &s,
                           bool any_shape) {
   s = TcStaged{};
   s.op = op;
-  s.ok = any_shape ? (m->same_ep && m->nw <= 18 && m->nm <= 18) : tc_staged_supported(m);
+  s.ok = any_shape ? (m->nw <= 18 && m->nm <= 18) : tc_staged_supported(m);
   if (!s.ok) return EPW_OK;
   const int esz = op == TC_OP_BF16 ? 2 : 4;
   const int kal = op == TC_OP_BF16 ? 16 : 8;  // K per MMA
-  s.kpad = (2 * m->nRe + kal - 1) / kal * kal;
+  s.kpad = k_layout(m, kal, s.kg0);
   s.cpk = 2 * m->nw * m->nw * (m->nm + 1);
   s.mtiles = (std::max(nq, 1) + 127) / 128;
   s.ldc = s.mtiles * 128;
@@ -2048,9 +2107,10 @@ epw_status tc_staged_plan(Arena &A, const epw_model *m, int nk, int nq, int op, 
 epw_status tc_staged_phases(const epw_model *m, int nq, const double *q, TcStaged &s, cudaStream_t st) {
   if (!s.ok) return EPW_ERR_UNSUPPORTED;
   if (s.op == TC_OP_BF16)
-    build_a<__nv_bfloat16>(nq, m->nRe, s.kpad, q, m->Re, s.Pq64, (__nv_bfloat16 *)s.Ahi, (__nv_bfloat16 *)s.Alo, st);
+    build_a<__nv_bfloat16>(nq, m->nRe, s.kpad, q, m->Re, s.Pq64, (__nv_bfloat16 *)s.Ahi, (__nv_bfloat16 *)s.Alo, st,
+                           m->nRp, m->Rp, s.kg0);
   else
-    build_a<float>(nq, m->nRe, s.kpad, q, m->Re, s.Pq64, (float *)s.Ahi, (float *)s.Alo, st);
+    build_a<float>(nq, m->nRe, s.kpad, q, m->Re, s.Pq64, (float *)s.Ahi, (float *)s.Alo, st, m->nRp, m->Rp, s.kg0);
   return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
 }
 
@@ -2058,12 +2118,13 @@ epw_status tc_staged_contract(const epw_model *m, int k0, int kc, int nq, const 
                               const cx<float> *BH32, TcStaged &s, cudaStream_t st) {
   if (!s.ok || kc > s.kc) return EPW_ERR_UNSUPPORTED;
   const int nR = m->nRe, nw2 = m->nw * m->nw;
-  const cx<float> *bh = BH32 + (size_t)k0 * nR * nw2, *bg = Bg32 + (size_t)k0 * nR * m->nm * nw2;
+  const cx<float> *bh = BH32 + (size_t)k0 * nR * nw2, *bg = Bg32 + (size_t)k0 * m->nRp * m->nm * nw2;
   if (s.op == TC_OP_BF16)
     launch_build_b<__nv_bfloat16>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, 0, bh, bg, (__nv_bfloat16 *)s.Bhi,
-                                  (__nv_bfloat16 *)s.Blo, st);
+                                  (__nv_bfloat16 *)s.Blo, st, m->nRp, s.kg0);
   else
-    launch_build_b<float>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, 0, bh, bg, (float *)s.Bhi, (float *)s.Blo, st);
+    launch_build_b<float>(kc, kc, nR, m->nw, m->nm, s.cpk, s.kpad, 0, bh, bg, (float *)s.Bhi, (float *)s.Blo, st,
+                          m->nRp, s.kg0);
   const int rows = kc * s.cpk;
   CUtensorMap ah, al, bh_m, bl_m;
   if (!make_map(&ah, s.Ahi, s.op, s.kpad, nq, 128) || !make_map(&al, s.Alo, s.op, s.kpad, nq, 128) ||

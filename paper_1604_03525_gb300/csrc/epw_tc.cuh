@@ -17,6 +17,7 @@ struct TcBuffers {
   float *ekF;        // band energies at k [nk][nw]
   double *partial;   // [nk][4*nqt][nw]
   int op, kpad, cpk, nk_pad, nqt, kpt;
+  int kg0;           // K offset of the vertex's Rp phases when Rp differs from Re (0: one shared set)
   int planar;        // B columns in re/im pairs (see k_build_b)
   bool ok;           // shape has a tensor-core kernel
   bool prebuilt_a, prebuilt_b;  // A / B already built for the next tc_linewidth/tc_interp call
@@ -28,8 +29,9 @@ struct TcBuffers {
   const cx<double> *Pq64;    // FP64 q phases of the Re set [nR][nq] when already formed (else null)
 };
 
-// True when the model's shape has a tensor-core kernel (Re == Rp sets and a
-// compiled (nw, 3nat) pair).
+// True when the model's shape has a tensor-core kernel (a compiled (nw, 3nat)
+// pair).  When Rp differs from Re the contraction runs over K = [Re phases | Rp
+// phases]: H(k+q) columns are zero on the Rp part, vertex columns on the Re part.
 bool tc_supported(const epw_model *m);
 // Lay out (or measure, with a null arena base) the buffers of the tensor-core path.
 epw_status tc_plan(Arena &A, const epw_model *m, int nk, int nq, int op, TcBuffers &b);
@@ -70,14 +72,16 @@ bool tc_make_map_rb(CUtensorMap *map, const void *base, int op, uint64_t inner, 
 void tc_tables(int nq, int nm, int nk, int nw, const double *omegaT, double T, const double *wq, const double *epsk,
                float *nbT, float *omF, float *wqF, float *ekF, cudaStream_t st);
 
-// Wide-shape fused form (epw_tcw.cu) for shapes whose per-k columns exceed the
-// fused kernel's slot: per chunk of k, kernel E contracts H(k+q) on the tensor
-// cores and diagonalises it per pair (eigenvalues and the eigenvectors some
-// band at k can reach within the Gaussian cutoff go to HBM), then kernel G
-// contracts (g_a(k,q) U_k) and evaluates only the (m, n) terms whose Gaussians
-// do not underflow.
+// Wide-shape form (epw_tcw.cu) for shapes whose per-k columns exceed the fused
+// kernel's slot: H(k+q) is contracted on the tensor cores and diagonalised per
+// pair (eigenvalues and the eigenvectors some band at k can reach within the
+// Gaussian cutoff are kept), then (g_a(k,q) U_k) is contracted and only the
+// (m, n) terms whose Gaussians do not underflow are evaluated: by default in one
+// kernel (the eigensolve beside the vertex MMAs, eigen-data through an L2 ring),
+// or as two kernels per chunk of k (E, then G; eigen-data through HBM).
 struct TcwBuffers {
-  void *Ahi, *Alo;     // q phases [nq][kpad]
+  void *Ahi, *Alo;     // q phases of the Re set [nq][kpad]
+  void *AGhi, *AGlo;   // q phases of the Rp set [nq][kpadG] (the Re buffers when the sets agree)
   void *BEhi, *BElo;   // H(k+q) operand of one chunk [kc_pad][cpk][kpad]
   void *BGhi, *BGlo;   // vertex operand of one chunk [nchunk][bng][kpad]
   float *epsq;         // [kc][nw][ldq] eigenvalues of H(k+q)
@@ -85,12 +89,14 @@ struct TcwBuffers {
   float *nbT, *omF, *wqF, *ekF, *thr;
   double *partial;     // [nk][4 nqt][nw]
   float2 *UkF;         // polar models: FP32 U_k [nk][nw][nw]
-  int op, kpad, kc, ldq, nqt, cpk, kpt, entp, cn, bng;
+  int op, kpad, kpadG, kc, ldq, nqt, cpk, kpt, entp, cn, bng;
   bool ok;
+  bool fused;          // one kernel (E and G overlapped, eigen-data through a ring in L2); else two per chunk
 };
 bool tcw_supported(const epw_model *m);
-// bytes: budget of the per-chunk eigen buffers (0: default)
-epw_status tcw_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t bytes, TcwBuffers &b);
+// bytes: budget of the per-chunk buffers (0: default); split: the two-kernel form
+epw_status tcw_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t bytes, TcwBuffers &b,
+                    bool split = false);
 // Im Sigma [nk][nw] into `out` (device) from the preparation outputs (P64: FP64 q phases of
 // the Re set [nR][nq] or null; Cpol [nm][nq] and Uk for polar models, else null).
 epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, const double *wq,
@@ -125,8 +131,8 @@ epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const doubl
                                  const cx<float> *Bg32, const cx<float> *BH32, const double *cot, TcBuffers &b,
                                  TcBwdBuffers &w, cx<float> *gwbar, double *scal, cudaStream_t st);
 
-// Staged tensor-core form for shapes the fused kernel cannot hold (Re == Rp,
-// nw <= 18, 3nat <= 18): per chunk of k, a tcgen05 GEMM writes
+// Staged tensor-core form for shapes the fused kernel cannot hold (nw <= 18,
+// 3nat <= 18; K = [Re phases | zero pad | Rp phases] when Re != Rp): per chunk of k, a tcgen05 GEMM writes
 // Ct[kl*cpk + 2c + s][q] (c over [H(k+q)_ij | (g_a(k,q) U_k)_jn], s = re/im),
 // or Ct[q][kl*cpk + 2c + s] for the warp-per-pair kernel, which the per-pair
 // kernel reads.
@@ -135,6 +141,7 @@ struct TcStaged {
   void *Bhi, *Blo;  // k-side operand of one chunk [kc][cpk][kpad]
   float *Ct;        // [ntiles*144 rows][ldc], or q-major [ldc][ldn] when qmajor
   int op, kpad, cpk, kc, mtiles, ldc;
+  int kg0;          // K offset of the vertex's Rp phases when Rp differs from Re (0: one shared set)
   bool ok;
   bool qmajor;      // layout read by the warp-per-pair kernel (nw > 8 or 3nat > 9)
   size_t ldn;

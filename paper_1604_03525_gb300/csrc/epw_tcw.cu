@@ -116,6 +116,7 @@ constexpr int w_smem() {
 
 struct TcwArgs {
   int nq, nqt, ngrp, kpad, nkb, qblock;
+  int kpadG, nkbG;        // fused kernel: K extent of the vertex chunks (Rp phases) when it differs
   int k0, kc;             // chunk: global k = k0 + kl, kl < kc
   int ldq;                // q stride of the per-pair buffers (nqt * 128)
   const float *epsk;      // [nk][nw]
@@ -148,9 +149,24 @@ __device__ __forceinline__ void w_coords(const TcwArgs &a, int item, int &grp, i
 // The one relevance test both kernels evaluate (same FP32 operands, same result).
 __device__ __forceinline__ bool reachable(float ek, float em, float thr) { return fabsf(ek - em) <= thr; }
 
+// Where the eigen-data of one pair lives: eigenvalue m at eps[m ld + idx], component i
+// of eigenvector m at U[(m nw + i) ld + idx].
+struct EigView {
+  float *eps;
+  float2 *U;
+  size_t ld;
+  int idx;
+};
+
 // ------------------------------------------------------------ epilogue E
-template <int NW>
-__device__ __forceinline__ void eig_pair(const TcwArgs &a, uint32_t tcol, int q, int kl, bool valid) {
+// H(k+q) from tensor memory, its FP32 eigensolve, the eigenvalues and the
+// eigenvectors that some band n at k can reach into v (kg: global k index).
+// FUSED: release the H(k+q) region (arrive on hempty) once H is in registers, and
+// wait on eempty (phase epar) before writing v; false when that wait gave up.
+template <int NW, bool FUSED = false>
+__device__ __forceinline__ bool eig_pair(const TcwArgs &a, uint32_t tcol, int q, int kg, const EigView &v,
+                                         bool valid, uint32_t hempty = 0, uint32_t eempty = 0, uint32_t epar = 0,
+                                         volatile int *abort_flag = nullptr) {
   constexpr int H2 = 2 * NW * NW;
   constexpr int LD = (H2 + 31) / 32 * 32;
   Herm<NW> H;
@@ -171,18 +187,29 @@ __device__ __forceinline__ void eig_pair(const TcwArgs &a, uint32_t tcol, int q,
         H.a[i][j] = mkc(0.5f * (hb[o] + hb[o2]), i == j ? 0.0f : 0.5f * (hb[o + 1] - hb[o2 + 1]));
       }
   }
+  if constexpr (FUSED) {
+    // H is in registers: the tensor-memory region may take the next item's H(k+q)
+    tc_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(hempty);
+  }
   HhQR<NW> S;
   hh_tridiag<NW>(H, S);
   const bool conv = tri_qr<NW>(S);
   if (!conv && valid) atomicOr(a.dstatus, EPW_DEV_NOT_CONVERGED);
-  const int kg = valid ? a.k0 + kl : 0;
+  kg = valid ? kg : 0;
   const float thr = valid ? __ldg(a.thr + q) : -1.0f;
   float ek[NW];
 #pragma unroll
   for (int n = 0; n < NW; n++) ek[n] = __ldg(a.epsk + (size_t)kg * NW + n);
+  if constexpr (FUSED) {
+    // the eigen-data slot must be free (its previous item consumed) before it is written
+    const bool ok = wait_bar(eempty, epar, abort_flag, a.dstatus);
+    if (!__all_sync(0xffffffffu, ok)) return false;
+  }
   if (valid) {
 #pragma unroll
-    for (int m = 0; m < NW; m++) a.epsq[((size_t)kl * NW + m) * a.ldq + q] = S.d[m];
+    for (int m = 0; m < NW; m++) v.eps[(size_t)m * v.ld + v.idx] = S.d[m];
   }
   // one loop body over m (instruction cache); unreachable bands are skipped by the warp
 #pragma unroll 1
@@ -196,11 +223,12 @@ __device__ __forceinline__ void eig_pair(const TcwArgs &a, uint32_t tcol, int q,
     cx<float> u[NW];
     hh_vector<NW>(S, m, u);
     if (rel) {
-      float2 *dst = a.Uq + ((size_t)kl * NW + m) * NW * a.ldq + q;
+      float2 *dst = v.U + (size_t)m * NW * v.ld + v.idx;
 #pragma unroll
-      for (int i = 0; i < NW; i++) dst[(size_t)i * a.ldq] = make_float2(u[i].x, u[i].y);
+      for (int i = 0; i < NW; i++) dst[(size_t)i * v.ld] = make_float2(u[i].x, u[i].y);
     }
   }
+  return true;
 }
 
 // ------------------------------------------------------------ epilogue G
@@ -208,18 +236,19 @@ __device__ __forceinline__ void eig_pair(const TcwArgs &a, uint32_t tcol, int q,
 // columns (a, j) of (g_a(k,q) U_k)_{jn}: only the bands m with a reachable
 // delta are evaluated (the warp runs the union over its lanes).
 template <int NW, int NM>
-__device__ __forceinline__ float g_entry(const TcwArgs &a, uint32_t tcol, int q, int kl, int n, bool valid) {
+__device__ __forceinline__ float g_entry(const TcwArgs &a, uint32_t tcol, int q, int kg, int n, const EigView &v,
+                                         bool valid) {
   constexpr int ENT = 2 * NM * NW;
   constexpr int LD = (ENT + 31) / 32 * 32;
   const int qq = valid ? q : 0;
-  const int kg = valid ? a.k0 + kl : 0;
+  kg = valid ? kg : 0;
   const float thr = valid ? __ldg(a.thr + q) : -1.0f;
   const float ek = __ldg(a.epsk + (size_t)kg * NW + n);
   // bands m at k+q with a Gaussian above the cutoff, as a bit mask
   uint32_t relm = 0;
 #pragma unroll
   for (int m = 0; m < NW; m++) {
-    const float em = valid ? a.epsq[((size_t)kl * NW + m) * a.ldq + q] : 0.0f;
+    const float em = valid ? v.eps[(size_t)m * v.ld + v.idx] : 0.0f;
     if (valid && reachable(ek, em, thr)) relm |= 1u << m;
   }
   if (!__any_sync(0xffffffffu, relm != 0)) return 0.0f;
@@ -239,12 +268,12 @@ __device__ __forceinline__ float g_entry(const TcwArgs &a, uint32_t tcol, int q,
     cx<float> u[NW];
     float em = 0.0f;
     if (rel) {
-      em = a.epsq[((size_t)kl * NW + m) * a.ldq + q];
-      const float2 *src = a.Uq + ((size_t)kl * NW + m) * NW * a.ldq + q;
+      em = v.eps[(size_t)m * v.ld + v.idx];
+      const float2 *src = v.U + (size_t)m * NW * v.ld + v.idx;
 #pragma unroll
       for (int i = 0; i < NW; i++) {
-        const float2 v = src[(size_t)i * a.ldq];
-        u[i] = mkc(v.x, v.y);
+        const float2 w = src[(size_t)i * v.ld];
+        u[i] = mkc(w.x, w.y);
       }
     } else {
 #pragma unroll
@@ -458,13 +487,18 @@ __global__ void __launch_bounds__(nthreads<KIND>(), 1)
       const uint32_t tcol = tmem + ((uint32_t)(quad * 32) << 16) + ts * 256 + u * UCOLS;
       if constexpr (KIND == 0) {
         const int kl = grp * S::KPT + u;
-        eig_pair<NW>(a, tcol, q, kl, q < a.nq && kl < a.kc);
+        const bool valid = q < a.nq && kl < a.kc;
+        const EigView v{a.epsq + (size_t)(valid ? kl : 0) * NW * a.ldq, a.Uq + (size_t)(valid ? kl : 0) * NW * NW * a.ldq,
+                        (size_t)a.ldq, q};
+        eig_pair<NW>(a, tcol, q, a.k0 + kl, v, valid);
       } else {
         const int e = grp * S::CN + u;
         const int kl = e / NW, n = e % NW;
         const bool kval = kl < a.kc;
         const bool valid = q < a.nq && kval;
-        float v = g_entry<NW, NM>(a, tcol, q, kl, n, valid);
+        const EigView ev{a.epsq + (size_t)(kval ? kl : 0) * NW * a.ldq,
+                         a.Uq + (size_t)(kval ? kl : 0) * NW * NW * a.ldq, (size_t)a.ldq, q};
+        float v = g_entry<NW, NM>(a, tcol, q, a.k0 + kl, n, ev, valid);
         v *= valid ? __ldg(a.wq + q) : 0.0f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -474,6 +508,430 @@ __global__ void __launch_bounds__(nthreads<KIND>(), 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[ts]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ------------------------------------------------------------ fused kernel
+// E and G in one persistent kernel, so that the per-pair eigensolve (CUDA cores)
+// runs beside the vertex contraction (tensor cores) and the eigen-data stays in
+// L2.  Per (k, q tile) item j: the H(k+q) block (N = cpk) into a single tensor-
+// memory region, then the vertex chunks (N = bng, two stages).  The MMA order is
+// H(0), then for s = 1, 2, ...: H(s), chunks of item s - 1, so that the
+// eigensolve of an item overlaps the vertex MMAs of the one before.
+//   warp 0      TMA producer (four 64-byte-swizzled stages)
+//   warp 1      tensor memory and MMA issuer
+//   warps 2..5  eigensolve of the item's H(k+q), one per lane quadrant; the
+//               eigenvalues and reachable eigenvectors go to a per-CTA ring of
+//               two slots in global memory (L2-resident), signalled per quadrant
+//   warps 6..9  linewidth terms of the vertex chunks, one per lane quadrant
+constexpr int F_WARPS = 10;
+constexpr int F_RB = 64;
+
+// Operand stages (four, three when the per-q tables of 3nat = 9 modes need the room),
+// then per vertex warp its lanes' per-q tables: mode factors E [nm*nm][32] (float2),
+// frequencies and Bose factors [2 nm][32].
+template <int NM>
+constexpr int f_stages() {
+  return NM <= 6 ? 4 : 3;
+}
+template <int NW, int NM>
+constexpr int f_stage_bytes() {
+  return (2 * BM + 2 * WShape<NW, NM>::BNG) * F_RB;
+}
+template <int NM>
+constexpr int f_tab_bytes() {
+  return 32 * (8 * NM * NM + 4 * 2 * NM);  // per vertex warp
+}
+template <int NW, int NM>
+constexpr int f_smem() {
+  return f_stages<NM>() * f_stage_bytes<NW, NM>() + 4 * f_tab_bytes<NM>() + 1024;
+}
+
+// Linewidth terms of the entries (k, n0) and (k, n0 + 1) of one vertex chunk for the
+// warp's 32 pairs: the bands m reachable for either entry (bit m of rel0, rel1) are
+// visited once, their eigenvector loaded once for both entries.  em, ek: eigenvalues
+// at k+q and band energies at k (registers), tabE / tabW: the lanes' per-q tables.
+template <int NW, int NM>
+__device__ __forceinline__ void g_chunk(const TcwArgs &a, uint32_t tcol, int n0, int qq, int kg, const EigView &v,
+                                        const float (&em)[NW], const float (&ek)[NW], uint32_t rel0, uint32_t rel1,
+                                        const float2 *tabE, const float *tabW, float &acc0, float &acc1) {
+  constexpr int ENT = 2 * NM * NW;
+  constexpr int LD = (ENT + 31) / 32 * 32;
+  constexpr int ENTP = WShape<NW, NM>::ENTP;
+  const int lane = threadIdx.x & 31;
+  const float ek0 = pick<NW>(ek, n0), ek1 = pick<NW>(ek, n0 + 1 < NW ? n0 + 1 : n0);
+  acc0 = acc1 = 0.0f;
+#pragma unroll 1
+  for (int m = 0; m < NW; m++) {
+    const bool r0 = (rel0 >> m) & 1u, r1 = (rel1 >> m) & 1u;
+    if (!__any_sync(0xffffffffu, r0 || r1)) continue;
+    cx<float> u[NW];
+    {
+      const float2 *src = v.U + (size_t)m * NW * v.ld + v.idx;
+#pragma unroll
+      for (int i = 0; i < NW; i++) {
+        const float2 w = (r0 || r1) ? src[(size_t)i * v.ld] : make_float2(0.0f, 0.0f);
+        u[i] = mkc(w.x, w.y);
+      }
+    }
+    const float emm = pick<NW>(em, m);
+    const float fm = fermi_fast(emm - a.EF, a.invkT);
+    const float ems = emm * a.sc;
+#pragma unroll 1
+    for (int e = 0; e < 2; e++) {
+      const bool r = e == 0 ? r0 : r1;
+      if (!__any_sync(0xffffffffu, r)) continue;
+      // t_a = u_m^dagger (g_a U_k)_{:, n}: the entry's columns stream from tensor memory
+      cx<float> t[NM];
+#pragma unroll
+      for (int al = 0; al < NM; al++) t[al] = mkc(0.0f, 0.0f);
+#pragma unroll
+      for (int c0 = 0; c0 < LD; c0 += 32) {
+        float xc[32];
+        tmem_ld32(tcol + e * ENTP + c0, xc);
+#pragma unroll
+        for (int cc = 0; cc < 32; cc += 2) {
+          const int col = c0 + cc;
+          if (col < ENT) {
+            const int al = col / (2 * NW), j = (col >> 1) % NW;
+            const float br = xc[cc], bi = xc[cc + 1];
+            t[al] = mkc(fmaf(u[j].x, br, fmaf(u[j].y, bi, t[al].x)), fmaf(u[j].x, bi, fmaf(-u[j].y, br, t[al].y)));
+          }
+        }
+      }
+      if (!r) continue;
+      const int n = n0 + e;
+      cx<float> tp = mkc(0.0f, 0.0f);
+      if (a.Cpol) {
+        const float2 *Uk = a.UkF + (size_t)kg * NW * NW;
+#pragma unroll
+        for (int j = 0; j < NW; j++) {
+          const float2 w = __ldg(Uk + j * NW + n);
+          tp = mkc(fmaf(u[j].x, w.x, fmaf(u[j].y, w.y, tp.x)), fmaf(u[j].x, w.y, fmaf(-u[j].y, w.x, tp.y)));
+        }
+      }
+      const float eks = (e == 0 ? ek0 : ek1) * a.sc;
+      float acc = 0.0f;
+#pragma unroll
+      for (int nu = 0; nu < NM; nu++) {
+        cx<float> g = mkc(0.0f, 0.0f);
+#pragma unroll
+        for (int al = 0; al < NM; al++) {
+          const float2 ee = tabE[(al * NM + nu) * 32 + lane];
+          g = mkc(fmaf(ee.x, t[al].x, fmaf(-ee.y, t[al].y, g.x)), fmaf(ee.x, t[al].y, fmaf(ee.y, t[al].x, g.y)));
+        }
+        if (a.Cpol) {
+          const float2 c = __ldg(a.Cpol + (size_t)nu * a.nq + qq);
+          g = mkc(g.x - fmaf(c.x, tp.y, c.y * tp.x), g.y + fmaf(c.x, tp.x, -c.y * tp.y));
+        }
+        const float om = tabW[nu * 32 + lane], nb = tabW[(NM + nu) * 32 + lane];
+        const bool keep = (om >= a.omega_min) && (om > 0.0f);
+        const float ws = om * a.sc;
+        const float xp = eks - ems + ws, xm = eks - ems - ws;
+        const float cp = keep ? nb + fm : 0.0f, cm = keep ? nb + 1.0f - fm : 0.0f;
+        const float d = cp * ex2_approx(-xp * xp) + cm * ex2_approx(-xm * xm);
+        acc = fmaf(fmaf(g.x, g.x, g.y * g.y), d, acc);
+      }
+      if (e == 0)
+        acc0 += acc;
+      else
+        acc1 += acc;
+    }
+  }
+}
+
+template <int OP, int NW, int NM>
+__global__ void __launch_bounds__(32 * F_WARPS, 1)
+    k_tcwf(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+           const __grid_constant__ CUtensorMap mEhi, const __grid_constant__ CUtensorMap mElo,
+           const __grid_constant__ CUtensorMap mAGhi, const __grid_constant__ CUtensorMap mAGlo,
+           const __grid_constant__ CUtensorMap mGhi, const __grid_constant__ CUtensorMap mGlo, TcwArgs a) {
+  using O = WOp<OP>;
+  using S = WShape<NW, NM>;
+  constexpr int F_STAGES = f_stages<NM>();
+  constexpr int BK = F_RB / O::ESZ;
+  constexpr int CPK = S::CPK, BNG = S::BNG, CN = S::CN;
+  static_assert(CN == 2, "vertex chunks of two entries");
+  constexpr int NCH = (NW + CN - 1) / CN;  // vertex chunks per k
+  constexpr int A_BYTES = BM * F_RB;
+  constexpr int STAGE = f_stage_bytes<NW, NM>();
+  constexpr uint32_t ID_H = w_idesc<OP, CPK>(), ID_G = w_idesc<OP, BNG>();
+  constexpr uint32_t GCOL0 = CPK;  // tensor-memory columns: H [0, cpk), vertex stages cpk + s bng
+  static_assert(CPK + 2 * BNG <= 512, "tensor memory");
+  __shared__ __align__(8) uint64_t bar_full[F_STAGES], bar_empty[F_STAGES], bar_hfull, bar_hempty, bar_gfull[2],
+      bar_gempty[2], bar_efull[2][4], bar_eempty[2][4], bar_final;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t smem0 = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int *abort_flag = &abort_sh;
+  const int nitems = a.ngrp * a.nqt;
+  const int nmy = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < F_STAGES; s++) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_hfull), 1);
+    mbar_init(smem_u32(&bar_hempty), 4);
+    for (int s = 0; s < 2; s++) {
+      mbar_init(smem_u32(&bar_gfull[s]), 1);
+      mbar_init(smem_u32(&bar_gempty[s]), 4);
+      for (int qd = 0; qd < 4; qd++) {
+        mbar_init(smem_u32(&bar_efull[s][qd]), 1);
+        mbar_init(smem_u32(&bar_eempty[s][qd]), 1);
+      }
+    }
+    mbar_init(smem_u32(&bar_final), 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    int issued[F_STAGES];
+#pragma unroll
+    for (int s = 0; s < F_STAGES; s++) issued[s] = 0;
+    uint32_t it = 0;
+    bool ok = true;
+    // one group: the A rows of q tile qt (ah, al) and brows B rows from row0, nkb K blocks
+    auto load_group = [&](int qt, const CUtensorMap *ah, const CUtensorMap *al, const CUtensorMap *bh,
+                          const CUtensorMap *bl, int row0, uint32_t brows, int nkb) {
+      for (int kb = 0; kb < nkb && ok; kb++, it++) {
+        const int s = it % F_STAGES;
+        const uint32_t par = ((it / F_STAGES) & 1u) ^ 1u;
+        if (lane == 0) {
+          ok = wait_bar(smem_u32(&bar_empty[s]), par, abort_flag, a.dstatus);
+          if (ok) {
+            const uint32_t base = smem0 + s * STAGE;
+            const uint32_t fb = smem_u32(&bar_full[s]);
+            mbar_expect_tx(fb, 2 * A_BYTES + 2 * brows * F_RB);
+            tma_load_2d(base, ah, kb * BK, qt * BM, fb);
+            tma_load_2d(base + A_BYTES, al, kb * BK, qt * BM, fb);
+            tma_load_2d(base + 2 * A_BYTES, bh, kb * BK, row0, fb);
+            tma_load_2d(base + 2 * A_BYTES + BNG * F_RB, bl, kb * BK, row0, fb);
+            issued[s] = (int)(it / F_STAGES) + 1;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+      }
+    };
+    for (int st = 0; st <= nmy && ok; st++) {
+      if (st < nmy) {
+        int kl, qt;
+        w_coords(a, blockIdx.x + st * gridDim.x, kl, qt);
+        load_group(qt, &mAhi, &mAlo, &mEhi, &mElo, kl * CPK, CPK, a.nkb);
+      }
+      if (st >= 1) {
+        int kl, qt;
+        w_coords(a, blockIdx.x + (st - 1) * gridDim.x, kl, qt);
+        for (int c = 0; c < NCH && ok; c++)
+          load_group(qt, &mAGhi, &mAGlo, &mGhi, &mGlo, (kl * NCH + c) * BNG, BNG, a.nkbG);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int s = 0; s < F_STAGES; s++)
+        if (issued[s] > 0) drain_bar(smem_u32(&bar_full[s]), (uint32_t)((issued[s] - 1) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA
+    uint32_t it = 0;
+    int hcount = 0, gcount = 0;
+    bool ok = true;
+    auto mma_group = [&](uint32_t dcol, uint32_t idesc, int nkb, int kpad) {
+      for (int kb = 0; kb < nkb && ok; kb++, it++) {
+        const int s = it % F_STAGES;
+        const uint32_t par = (it / F_STAGES) & 1u;
+        if (lane == 0) {
+          ok = wait_bar(smem_u32(&bar_full[s]), par, abort_flag, a.dstatus);
+          if (ok) {
+            tc_fence_after();
+            const uint32_t base = smem0 + s * STAGE;
+            const uint64_t dAh = sdesc_sw<F_RB>(base), dAl = sdesc_sw<F_RB>(base + A_BYTES);
+            const uint64_t dBh = sdesc_sw<F_RB>(base + 2 * A_BYTES);
+            const uint64_t dBl = sdesc_sw<F_RB>(base + 2 * A_BYTES + BNG * F_RB);
+            const int ksteps = min(BK, kpad - kb * BK) / O::KSTEP;
+            for (int ks = 0; ks < ksteps; ks++) {
+              const uint64_t off = (uint64_t)((ks * 32) >> 4);
+              const uint32_t acc = (kb == 0 && ks == 0) ? 0u : 1u;
+              umma_id<O::F16>(dcol, dAl + off, dBh + off, idesc, acc);
+              umma_id<O::F16>(dcol, dAh + off, dBl + off, idesc, 1u);
+              umma_id<O::F16>(dcol, dAh + off, dBh + off, idesc, 1u);
+            }
+            umma_commit(smem_u32(&bar_empty[s]));
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+      }
+    };
+    for (int st = 0; st <= nmy && ok; st++) {
+      if (st < nmy) {
+        if (lane == 0) ok = wait_bar(smem_u32(&bar_hempty), (uint32_t)((hcount & 1) ^ 1), abort_flag, a.dstatus);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        tc_fence_after();
+        mma_group(tmem, ID_H, a.nkb, a.kpad);
+        if (!ok) break;
+        if (lane == 0) umma_commit(smem_u32(&bar_hfull));
+        __syncwarp();
+        hcount++;
+      }
+      if (st >= 1) {
+        for (int c = 0; c < NCH && ok; c++, gcount++) {
+          const int gs = gcount & 1;
+          if (lane == 0)
+            ok = wait_bar(smem_u32(&bar_gempty[gs]), (uint32_t)(((gcount >> 1) & 1) ^ 1), abort_flag, a.dstatus);
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) break;
+          tc_fence_after();
+          mma_group(tmem + GCOL0 + gs * BNG, ID_G, a.nkbG, a.kpadG);
+          if (!ok) break;
+          if (lane == 0) umma_commit(smem_u32(&bar_gfull[gs]));
+          __syncwarp();
+        }
+      }
+    }
+    if (lane == 0) {
+      umma_commit(smem_u32(&bar_final));
+      drain_bar(smem_u32(&bar_final), 0);
+    }
+    __syncwarp();
+  } else if (warp < 6) {
+    // --------------------------------------------------------- eigensolve
+    const int quad = warp & 3;
+    const int idx = quad * 32 + lane;
+    for (int j = 0; j < nmy; j++) {
+      int kl, qt;
+      w_coords(a, blockIdx.x + j * gridDim.x, kl, qt);
+      const int q = qt * BM + idx;
+      const bool valid = q < a.nq && kl < a.kc;
+      bool ok = wait_bar(smem_u32(&bar_hfull), (uint32_t)(j & 1), abort_flag, a.dstatus);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      const int slot = j & 1;
+      const size_t so = ((size_t)blockIdx.x * 2 + slot);
+      const EigView v{a.epsq + so * NW * BM, a.Uq + so * NW * NW * BM, (size_t)BM, idx};
+      ok = eig_pair<NW, true>(a, tmem + ((uint32_t)(quad * 32) << 16), q, a.k0 + kl, v, valid, smem_u32(&bar_hempty),
+                              smem_u32(&bar_eempty[slot][quad]), (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag);
+      if (!ok) break;
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_efull[slot][quad]));
+    }
+  } else {
+    // ------------------------------------------------------- vertex terms
+    const int quad = warp & 3;
+    const int idx = quad * 32 + lane;
+    // this warp's per-q tables in shared memory (after the operand stages)
+    uint8_t *tab = smem_raw + (smem0 - smem_u32(smem_raw)) + F_STAGES * STAGE + (warp - 6) * f_tab_bytes<NM>();
+    const float2 *tabE = reinterpret_cast<const float2 *>(tab);
+    const float *tabW = reinterpret_cast<const float *>(tab + 32 * 8 * NM * NM);
+    const uint32_t tabE_s = smem_u32(tab), tabW_s = tabE_s + 32 * 8 * NM * NM;
+    int gcount = 0;
+    bool ok = true;
+    for (int j = 0; j < nmy && ok; j++) {
+      int kl, qt;
+      w_coords(a, blockIdx.x + j * gridDim.x, kl, qt);
+      const int q = qt * BM + idx;
+      const bool kval = kl < a.kc;
+      const bool valid = q < a.nq && kval;
+      const int qq = valid ? q : 0;
+      const int kg = kval ? a.k0 + kl : 0;
+      // per-q tables of the item's rows: E [nm*nm] complex, w [nm], n [nm]
+      __syncwarp();
+#pragma unroll 1
+      for (int e = 0; e < NM * NM; e++) cp_async8(tabE_s + 8u * (e * 32 + lane), a.ET + (size_t)e * a.nq + qq);
+#pragma unroll 1
+      for (int nu = 0; nu < NM; nu++) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tabW_s + 4u * (nu * 32 + lane)),
+                     "l"(__cvta_generic_to_global(a.omegaT + (size_t)nu * a.nq + qq))
+                     : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tabW_s + 4u * ((NM + nu) * 32 + lane)),
+                     "l"(__cvta_generic_to_global(a.nbT + (size_t)nu * a.nq + qq))
+                     : "memory");
+      }
+      const float wqv = valid ? __ldg(a.wq + q) : 0.0f;
+      const float thr = valid ? __ldg(a.thr + q) : -1.0f;
+      float ek[NW];
+#pragma unroll
+      for (int n = 0; n < NW; n++) ek[n] = __ldg(a.epsk + (size_t)kg * NW + n);
+      const int slot = j & 1;
+      const size_t so = ((size_t)blockIdx.x * 2 + slot);
+      const EigView v{a.epsq + so * NW * BM, a.Uq + so * NW * NW * BM, (size_t)BM, idx};
+      ok = wait_bar(smem_u32(&bar_efull[slot][quad]), (uint32_t)((j >> 1) & 1), abort_flag, a.dstatus);
+      if (!__all_sync(0xffffffffu, ok)) {
+        ok = false;
+        cp_async_wait_all();
+        break;
+      }
+      // eigenvalues at k+q and the reachable (m, n) as 8-bit masks per n
+      float em[NW];
+#pragma unroll
+      for (int m = 0; m < NW; m++) em[m] = valid ? v.eps[(size_t)m * v.ld + v.idx] : 0.0f;
+      uint32_t rel[NW];
+#pragma unroll
+      for (int n = 0; n < NW; n++) {
+        rel[n] = 0;
+#pragma unroll
+        for (int m = 0; m < NW; m++)
+          if (valid && reachable(ek[n], em[m], thr)) rel[n] |= 1u << m;
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      for (int c = 0; c < NCH; c++, gcount++) {
+        const int gs = gcount & 1;
+        ok = wait_bar(smem_u32(&bar_gfull[gs]), (uint32_t)((gcount >> 1) & 1), abort_flag, a.dstatus);
+        if (!__all_sync(0xffffffffu, ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tcol = tmem + ((uint32_t)(quad * 32) << 16) + GCOL0 + gs * BNG;
+        const int n0 = c * CN;
+        uint32_t r0 = 0, r1 = 0;  // rel[n0], rel[n0 + 1] by masks (keeps rel in registers)
+#pragma unroll
+        for (int n = 0; n < NW; n++) {
+          r0 |= rel[n] & (0u - (uint32_t)(n == n0));
+          r1 |= rel[n] & (0u - (uint32_t)(n == n0 + 1));
+        }
+        float acc0, acc1;
+        g_chunk<NW, NM>(a, tcol, n0, qq, kg, v, em, ek, r0, r1, tabE, tabW, acc0, acc1);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_gempty[gs]));
+        float v0 = acc0 * wqv, v1 = acc1 * wqv;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          v0 += __shfl_down_sync(0xffffffffu, v0, o);
+          v1 += __shfl_down_sync(0xffffffffu, v1, o);
+        }
+        if (lane == 0 && kval) {
+          double *dst = a.partial + ((size_t)(a.k0 + kl) * (4 * a.nqt) + qt * 4 + quad) * NW;
+          dst[n0] = (double)v0 * (double)a.gnorm;
+          if (n0 + 1 < NW) dst[n0 + 1] = (double)v1 * (double)a.gnorm;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_eempty[slot][quad]));
     }
   }
   tc_fence_before();
@@ -500,13 +958,14 @@ __device__ __forceinline__ void wsplit<float>(float v, float *hi, float *lo, siz
   lo[i] = tf32_rn(v - h);
 }
 
-// B rows of kernel G: row = c bng + i entp + 2 (a nw + j) + s for entry e = c cn + i
-// = (kl, n) = (e / nw, e % nw); K index kk = 2 rr + t, R index r = nR - 1 - rr
+// B rows of the vertex contraction: row = c bng + i entp + 2 (a nw + j) + s for entry
+// e = c cn + i = (kl, n) = (e / epk, e % epk) (epk = nw: entries of consecutive k packed;
+// epk = cn ceil(nw / cn): each k starts a chunk, entries n >= nw are zero); K index kk = 2 rr + t, R index r = nR - 1 - rr
 // (far shells first, as the A operand); value from b = Bg[kl][r][a][j][n]:
 //   (s,t) = (0,0): Re b, (0,1): -Im b, (1,0): Im b, (1,1): Re b.
 // Rows past 2 nm nw in an entry, entries with kl >= kc and K >= 2 nR are 0.
 template <typename T>
-__global__ void k_build_bg(int kc, int nchunk, int nR, int nw, int nm, int cn, int entp, int bng, int kpad,
+__global__ void k_build_bg(int kc, int nchunk, int nR, int nw, int nm, int cn, int entp, int bng, int kpad, int epk,
                            const cx<float> *__restrict__ Bg, T *hi, T *lo) {
   const size_t n = (size_t)nchunk * bng * kpad;
   const int nw2 = nw * nw, ent = 2 * nm * nw;
@@ -516,9 +975,9 @@ __global__ void k_build_bg(int kc, int nchunk, int nR, int nw, int nm, int cn, i
     const int c = row / bng, rc = row % bng;
     const int i = rc / entp, re = rc % entp;
     const int e = c * cn + i;
-    const int kl = e / nw, nb = e % nw;
+    const int kl = e / epk, nb = e % epk;
     float v = 0.0f;
-    if (re < ent && kl < kc && kk < 2 * nR) {
+    if (re < ent && nb < nw && kl < kc && kk < 2 * nR) {
       const int al = re / (2 * nw), j = (re >> 1) % nw, s = re & 1;
       const int r = nR - 1 - (kk >> 1), t = kk & 1;
       const cx<float> b = Bg[((size_t)kl * nR + r) * nm * nw2 + al * nw2 + j * nw + nb];
@@ -564,6 +1023,22 @@ cudaError_t launch_tcw(const CUtensorMap &ah, const CUtensorMap &al, const CUten
   return cudaGetLastError();
 }
 
+template <int OP, int NW, int NM>
+cudaError_t launch_tcwf(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &eh, const CUtensorMap &el,
+                        const CUtensorMap &agh, const CUtensorMap &agl, const CUtensorMap &gh, const CUtensorMap &gl,
+                        const TcwArgs &a, int grid, cudaStream_t st) {
+  constexpr int SMEM = f_smem<NW, NM>();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tcwf<OP, NW, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_tcwf<OP, NW, NM><<<grid, 32 * F_WARPS, SMEM, st>>>(ah, al, eh, el, agh, agl, gh, gl, a);
+  epw_count_launch();
+  return cudaGetLastError();
+}
+
 // compiled (nw, 3nat) pairs
 #define EPW_TCW_SHAPES(X) X(8, 6) X(5, 9)
 
@@ -574,6 +1049,17 @@ cudaError_t launch_tcw_shape(int nw, int nm, const CUtensorMap &ah, const CUtens
   if (nw == W && nm == M) return launch_tcw<OP, W, M, KIND>(ah, al, bh, bl, a, st);
   EPW_TCW_SHAPES(EPW_TCW_CASE)
 #undef EPW_TCW_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <int OP>
+cudaError_t launch_tcwf_shape(int nw, int nm, const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &eh,
+                              const CUtensorMap &el, const CUtensorMap &agh, const CUtensorMap &agl,
+                              const CUtensorMap &gh, const CUtensorMap &gl, const TcwArgs &a, int grid, cudaStream_t st) {
+#define EPW_TCWF_CASE(W, M) \
+  if (nw == W && nm == M) return launch_tcwf<OP, W, M>(ah, al, eh, el, agh, agl, gh, gl, a, grid, st);
+  EPW_TCW_SHAPES(EPW_TCWF_CASE)
+#undef EPW_TCWF_CASE
   return cudaErrorInvalidValue;
 }
 
@@ -592,41 +1078,63 @@ bool tcw_shape(int nw, int nm, int &cpk, int &kpt, int &entp, int &cn, int &bng)
   return false;
 }
 
-constexpr size_t TCW_EIG_BYTES = (size_t)6 << 30;  // per-chunk eigenvalue + eigenvector buffers
+constexpr size_t TCW_EIG_BYTES = (size_t)6 << 30;  // split kernels: per-chunk eigenvalue + eigenvector buffers
+constexpr size_t TCWF_OPERAND_BYTES = (size_t)4 << 30;  // fused kernel: operands of one chunk of k
+constexpr int TCWF_MAX_CTAS = 256;  // eigen-data ring slots are laid out for up to this many CTAs
 
 }  // namespace
 
 bool tcw_supported(const epw_model *m) {
   int cpk, kpt, entp, cn, bng;
-  return m->same_ep && tcw_shape(m->nw, m->nm, cpk, kpt, entp, cn, bng);
+  return tcw_shape(m->nw, m->nm, cpk, kpt, entp, cn, bng);
 }
 
-epw_status tcw_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t bytes, TcwBuffers &b) {
+epw_status tcw_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t bytes, TcwBuffers &b, bool split) {
   b = TcwBuffers{};
   b.op = op;
-  b.ok = m->same_ep && tcw_shape(m->nw, m->nm, b.cpk, b.kpt, b.entp, b.cn, b.bng);
+  b.ok = tcw_shape(m->nw, m->nm, b.cpk, b.kpt, b.entp, b.cn, b.bng);
   if (!b.ok) return EPW_OK;
+  b.fused = !split;
   nk = std::max(nk, 1);
   nq = std::max(nq, 1);
   const int nw = m->nw, nm = m->nm;
   const int esz = op == TC_OP_BF16 ? 2 : 4;
   const int kal = op == TC_OP_BF16 ? 16 : 8;
+  // K extents: H(k+q) over the Re phases, the vertex over the Rp phases (a second A
+  // operand when the sets differ)
   b.kpad = (2 * m->nRe + kal - 1) / kal * kal;
+  b.kpadG = (2 * m->nRp + kal - 1) / kal * kal;
   b.nqt = (nq + BM - 1) / BM;
   b.ldq = b.nqt * BM;
-  const size_t per_k = (size_t)b.ldq * nw * (4 + 8 * (size_t)nw);
-  const size_t budget = bytes ? bytes : TCW_EIG_BYTES;
-  b.kc = (int)std::min<size_t>((size_t)nk, std::max<size_t>(1, budget / per_k));
-  const int kc_pad = (b.kc + b.kpt - 1) / b.kpt * b.kpt;
-  const int nchunk = (b.kc * nw + b.cn - 1) / b.cn;
   b.Ahi = A.take<char>((size_t)nq * b.kpad * esz);
   b.Alo = A.take<char>((size_t)nq * b.kpad * esz);
-  b.BEhi = A.take<char>((size_t)kc_pad * b.cpk * b.kpad * esz);
-  b.BElo = A.take<char>((size_t)kc_pad * b.cpk * b.kpad * esz);
-  b.BGhi = A.take<char>((size_t)nchunk * b.bng * b.kpad * esz);
-  b.BGlo = A.take<char>((size_t)nchunk * b.bng * b.kpad * esz);
-  b.epsq = A.take<float>((size_t)b.kc * nw * b.ldq);
-  b.Uq = A.take<float2>((size_t)b.kc * nw * nw * b.ldq);
+  b.AGhi = m->same_ep ? b.Ahi : A.take<char>((size_t)nq * b.kpadG * esz);
+  b.AGlo = m->same_ep ? b.Alo : A.take<char>((size_t)nq * b.kpadG * esz);
+  if (b.fused) {
+    // one k per item: its H(k+q) rows, then its vertex chunks (each k starts a chunk)
+    const int nch = (nw + b.cn - 1) / b.cn;
+    const size_t per_k = ((size_t)b.cpk * b.kpad + (size_t)nch * b.bng * b.kpadG) * esz * 2;
+    b.kc = (int)std::min<size_t>((size_t)nk, std::max<size_t>(1, (bytes ? bytes : TCWF_OPERAND_BYTES) / per_k));
+    b.BEhi = A.take<char>((size_t)b.kc * b.cpk * b.kpad * esz);
+    b.BElo = A.take<char>((size_t)b.kc * b.cpk * b.kpad * esz);
+    b.BGhi = A.take<char>((size_t)b.kc * nch * b.bng * b.kpadG * esz);
+    b.BGlo = A.take<char>((size_t)b.kc * nch * b.bng * b.kpadG * esz);
+    // eigen-data ring: [cta][slot][nw][128] eigenvalues, [cta][slot][nw][nw][128] eigenvectors
+    b.epsq = A.take<float>((size_t)TCWF_MAX_CTAS * 2 * nw * BM);
+    b.Uq = A.take<float2>((size_t)TCWF_MAX_CTAS * 2 * nw * nw * BM);
+  } else {
+    const size_t per_k = (size_t)b.ldq * nw * (4 + 8 * (size_t)nw);
+    const size_t budget = bytes ? bytes : TCW_EIG_BYTES;
+    b.kc = (int)std::min<size_t>((size_t)nk, std::max<size_t>(1, budget / per_k));
+    const int kc_pad = (b.kc + b.kpt - 1) / b.kpt * b.kpt;
+    const int nchunk = (b.kc * nw + b.cn - 1) / b.cn;
+    b.BEhi = A.take<char>((size_t)kc_pad * b.cpk * b.kpad * esz);
+    b.BElo = A.take<char>((size_t)kc_pad * b.cpk * b.kpad * esz);
+    b.BGhi = A.take<char>((size_t)nchunk * b.bng * b.kpadG * esz);
+    b.BGlo = A.take<char>((size_t)nchunk * b.bng * b.kpadG * esz);
+    b.epsq = A.take<float>((size_t)b.kc * nw * b.ldq);
+    b.Uq = A.take<float2>((size_t)b.kc * nw * nw * b.ldq);
+  }
   b.nbT = A.take<float>((size_t)nq * nm);
   b.omF = A.take<float>((size_t)nq * nm);
   b.wqF = A.take<float>((size_t)nq);
@@ -642,9 +1150,10 @@ epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, co
                          const cx<float> *Bg32, const cx<float> *BH32, const cx<double> *P64,
                          const cx<double> *Uk, const float2 *Cpol, TcwBuffers &b, double *out, cudaStream_t st) {
   if (!b.ok) return EPW_ERR_UNSUPPORTED;
-  const int nw = m->nw, nm = m->nm, nR = m->nRe, op = b.op;
+  const int nw = m->nw, nm = m->nm, nR = m->nRe, nRp = m->nRp, op = b.op;
   const int esz = op == TC_OP_BF16 ? 2 : 4;
   tc_build_a_raw(op, nq, nR, b.kpad, q, m->Re, P64, b.Ahi, b.Alo, st);
+  if (!m->same_ep) tc_build_a_raw(op, nq, nRp, b.kpadG, q, m->Rp, nullptr, b.AGhi, b.AGlo, st);
   tc_tables(nq, nm, nk, nw, omegaT, par->T_K, wq, epsk, b.nbT, b.omF, b.wqF, b.ekF, st);
   const float cut = (float)(CUT_SIGMAS * par->sigma_eV);
   k_tcw_thr<<<grid_n(nq, 256), 256, 0, st>>>(nq, nm, b.omF, (float)par->omega_min_eV, cut, b.thr);
@@ -655,7 +1164,8 @@ epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, co
   a.nq = nq;
   a.nqt = b.nqt;
   a.kpad = b.kpad;
-  const int nkb_e = (b.kpad * esz + 127) / 128, nkb_g = (b.kpad * esz + 63) / 64;
+  a.kpadG = b.kpadG;
+  const int nkb_e = (b.kpad * esz + 127) / 128, nkb_g = (b.kpadG * esz + 63) / 64;
   a.ldq = b.ldq;
   a.epsk = b.ekF;
   a.thr = b.thr;
@@ -680,17 +1190,67 @@ epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, co
     qb = std::max(qb, 152);
     a.qblock = std::max(1, std::min(qb, b.nqt));
   }
+  if (b.fused) {
+    const int nch = (nw + b.cn - 1) / b.cn;
+    CUtensorMap ah, al, eh, el, agh, agl, gh, gl;
+    if (!tc_make_map_rb(&ah, b.Ahi, op, b.kpad, nq, BM, F_RB) || !tc_make_map_rb(&al, b.Alo, op, b.kpad, nq, BM, F_RB) ||
+        !tc_make_map_rb(&agh, b.AGhi, op, b.kpadG, nq, BM, F_RB) ||
+        !tc_make_map_rb(&agl, b.AGlo, op, b.kpadG, nq, BM, F_RB) ||
+        !tc_make_map_rb(&eh, b.BEhi, op, b.kpad, (uint64_t)b.kc * b.cpk, (uint32_t)b.cpk, F_RB) ||
+        !tc_make_map_rb(&el, b.BElo, op, b.kpad, (uint64_t)b.kc * b.cpk, (uint32_t)b.cpk, F_RB) ||
+        !tc_make_map_rb(&gh, b.BGhi, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, (uint32_t)b.bng, F_RB) ||
+        !tc_make_map_rb(&gl, b.BGlo, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, (uint32_t)b.bng, F_RB))
+      return EPW_ERR_CUDA;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sms = std::min(sms, TCWF_MAX_CTAS);
+    a.nkb = (b.kpad * esz + F_RB - 1) / F_RB;
+    a.nkbG = (b.kpadG * esz + F_RB - 1) / F_RB;
+    const size_t nw2 = (size_t)nw * nw;
+    epw_model *mm = const_cast<epw_model *>(m);
+    for (int k0 = 0; k0 < nk; k0 += b.kc) {
+      const int kc = std::min(b.kc, nk - k0);
+      tc_build_b_raw(op, kc, kc, nR, nw, 0, b.cpk, b.kpad, BH32 + (size_t)k0 * nR * nw2, nullptr, b.BEhi, b.BElo, st);
+      {
+        const int nchunk = kc * nch;
+        const size_t n = (size_t)nchunk * b.bng * b.kpadG;
+        const cx<float> *bg = Bg32 + (size_t)k0 * nRp * nm * nw2;
+        if (op == TC_OP_BF16)
+          k_build_bg<__nv_bfloat16><<<grid_n(n, 256), 256, 0, st>>>(kc, nchunk, nRp, nw, nm, b.cn, b.entp, b.bng,
+                                                                    b.kpadG, nch * b.cn, bg, (__nv_bfloat16 *)b.BGhi,
+                                                                    (__nv_bfloat16 *)b.BGlo);
+        else
+          k_build_bg<float><<<grid_n(n, 256), 256, 0, st>>>(kc, nchunk, nRp, nw, nm, b.cn, b.entp, b.bng, b.kpadG,
+                                                            nch * b.cn, bg, (float *)b.BGhi, (float *)b.BGlo);
+        epw_count_launch();
+      }
+      a.k0 = k0;
+      a.kc = kc;
+      a.ngrp = kc;
+      const int grid = (int)std::min<long>((long)kc * b.nqt, (long)sms);
+      epw_timing_begin_tag(mm, st, 0);
+      const cudaError_t e = op == TC_OP_BF16
+                                ? launch_tcwf_shape<TC_OP_BF16>(nw, nm, ah, al, eh, el, agh, agl, gh, gl, a, grid, st)
+                                : launch_tcwf_shape<TC_OP_TF32>(nw, nm, ah, al, eh, el, agh, agl, gh, gl, a, grid, st);
+      epw_timing_end(mm, st);
+      if (e != cudaSuccess) return EPW_ERR_CUDA;
+    }
+    launch_finalize(nk, 4 * b.nqt, nw, b.partial, out, st);
+    return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
+  }
   CUtensorMap ah, al, eh, el, gh, gl;
   CUtensorMap ah64, al64;
   if (!tc_make_map(&ah, b.Ahi, op, b.kpad, nq, BM) || !tc_make_map(&al, b.Alo, op, b.kpad, nq, BM) ||
-      !tc_make_map_rb(&ah64, b.Ahi, op, b.kpad, nq, BM, 64) || !tc_make_map_rb(&al64, b.Alo, op, b.kpad, nq, BM, 64))
+      !tc_make_map_rb(&ah64, b.AGhi, op, b.kpadG, nq, BM, 64) ||
+      !tc_make_map_rb(&al64, b.AGlo, op, b.kpadG, nq, BM, 64))
     return EPW_ERR_CUDA;
   const int kc_pad = (b.kc + b.kpt - 1) / b.kpt * b.kpt;
   const int nchunk_max = (b.kc * nw + b.cn - 1) / b.cn;
   if (!tc_make_map(&eh, b.BEhi, op, b.kpad, (uint64_t)kc_pad * b.cpk, 256) ||
       !tc_make_map(&el, b.BElo, op, b.kpad, (uint64_t)kc_pad * b.cpk, 256) ||
-      !tc_make_map_rb(&gh, b.BGhi, op, b.kpad, (uint64_t)nchunk_max * b.bng, (uint32_t)b.bng, 64) ||
-      !tc_make_map_rb(&gl, b.BGlo, op, b.kpad, (uint64_t)nchunk_max * b.bng, (uint32_t)b.bng, 64))
+      !tc_make_map_rb(&gh, b.BGhi, op, b.kpadG, (uint64_t)nchunk_max * b.bng, (uint32_t)b.bng, 64) ||
+      !tc_make_map_rb(&gl, b.BGlo, op, b.kpadG, (uint64_t)nchunk_max * b.bng, (uint32_t)b.bng, 64))
     return EPW_ERR_CUDA;
   const size_t nw2 = (size_t)nw * nw;
   epw_model *mm = const_cast<epw_model *>(m);
@@ -700,14 +1260,15 @@ epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, co
     const int nchunk = (kc * nw + b.cn - 1) / b.cn;
     tc_build_b_raw(op, kc, kcp, nR, nw, 0, b.cpk, b.kpad, BH32 + (size_t)k0 * nR * nw2, nullptr, b.BEhi, b.BElo, st);
     {
-      const size_t n = (size_t)nchunk * b.bng * b.kpad;
-      const cx<float> *bg = Bg32 + (size_t)k0 * nR * nm * nw2;
+      const size_t n = (size_t)nchunk * b.bng * b.kpadG;
+      const cx<float> *bg = Bg32 + (size_t)k0 * nRp * nm * nw2;
       if (op == TC_OP_BF16)
-        k_build_bg<__nv_bfloat16><<<grid_n(n, 256), 256, 0, st>>>(kc, nchunk, nR, nw, nm, b.cn, b.entp, b.bng, b.kpad,
-                                                                  bg, (__nv_bfloat16 *)b.BGhi, (__nv_bfloat16 *)b.BGlo);
+        k_build_bg<__nv_bfloat16><<<grid_n(n, 256), 256, 0, st>>>(kc, nchunk, nRp, nw, nm, b.cn, b.entp, b.bng,
+                                                                  b.kpadG, nw, bg, (__nv_bfloat16 *)b.BGhi,
+                                                                  (__nv_bfloat16 *)b.BGlo);
       else
-        k_build_bg<float><<<grid_n(n, 256), 256, 0, st>>>(kc, nchunk, nR, nw, nm, b.cn, b.entp, b.bng, b.kpad, bg,
-                                                          (float *)b.BGhi, (float *)b.BGlo);
+        k_build_bg<float><<<grid_n(n, 256), 256, 0, st>>>(kc, nchunk, nRp, nw, nm, b.cn, b.entp, b.bng, b.kpadG, nw,
+                                                          bg, (float *)b.BGhi, (float *)b.BGlo);
       epw_count_launch();
     }
     a.k0 = k0;
@@ -715,6 +1276,7 @@ epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, co
     cudaError_t e;
     a.ngrp = kcp / b.kpt;
     a.nkb = nkb_e;
+    a.kpad = b.kpad;
     epw_timing_begin_tag(mm, st, 1);
     e = op == TC_OP_BF16 ? launch_tcw_shape<TC_OP_BF16, 0>(nw, nm, ah, al, eh, el, a, st)
                          : launch_tcw_shape<TC_OP_TF32, 0>(nw, nm, ah, al, eh, el, a, st);
@@ -722,6 +1284,7 @@ epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, co
     if (e != cudaSuccess) return EPW_ERR_CUDA;
     a.ngrp = nchunk;
     a.nkb = nkb_g;
+    a.kpad = b.kpadG;
     epw_timing_begin_tag(mm, st, 0);
     e = op == TC_OP_BF16 ? launch_tcw_shape<TC_OP_BF16, 1>(nw, nm, ah64, al64, gh, gl, a, st)
                          : launch_tcw_shape<TC_OP_TF32, 1>(nw, nm, ah64, al64, gh, gl, a, st);

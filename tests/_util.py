@@ -56,3 +56,30 @@ def rel_err(a, b, floor=0.0):
     a = np.asarray(a)
     b = np.asarray(b)
     return np.max(np.abs(a - b) / np.maximum(np.abs(b), floor))
+
+
+def fermi_level_term_scale(oracle_lib, wm, k, q, wq, T, EF, sigma, cot, omega_min=1e-5):
+    """sum over (k, q, nu, m, n) of |c_nk pi w_q |g|^2 df/dE_F (d+ - d-)|: the magnitude of the
+    terms whose signed sum is dL/dE_F.  Those terms change sign with e_nk - e_mk+q, and their
+    sum can be orders of magnitude below this scale; an error of relative size r per term
+    then bounds the error of dL/dE_F by about r times this scale, not r times |dL/dE_F|.
+    Values from the oracle's interpolation and its Gaussian difference."""
+    ek, ekq, om, g = oracle_lib.interp(wm, k, q, omega_min)
+    nq = len(q)
+    wq = np.full(nq, 1.0 / nq) if wq is None else np.asarray(wq)
+    kT = 8.617333262e-5 * T
+    x = (ekq - EF) / kT                                   # [nk, nq, m]
+    t = np.exp(-np.abs(x))
+    dfdE = t / (1.0 + t) ** 2 / kT
+    gd = np.vectorize(oracle_lib.gauss_diff)
+    total = 0.0
+    for iq in range(nq):
+        for nu in range(om.shape[1]):
+            w = om[iq, nu]
+            if w < omega_min:
+                continue
+            xd = ek[:, None, :] - ekq[:, iq, :, None]      # [nk, m, n]
+            dd = gd(xd, w, sigma)
+            g2 = np.abs(g[:, iq, nu]) ** 2                  # [nk, m, n]
+            total += float(np.sum(np.abs(cot[:, None, :] * np.pi * wq[iq] * g2 * dfdE[:, iq, :, None] * dd)))
+    return total

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from tests._util import fermi_level_term_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -86,11 +87,15 @@ def test_tensor_core_adjoint_matches_oracle(nw, nR, oracle_lib):
     rdg, rdT, rdE = oracle_lib.linewidth_grad(wm, k, q, None, 300.0, 0.1, 0.05, cot=cot)
     assert np.abs(dg - rdg).max() <= 2e-4 * np.abs(rdg).max()
     assert abs(dT - rdT) <= 2e-4 * abs(rdT)
-    # dL/dE_F weights each pair by f(1-f) (d+ - d-): the two Gaussians cancel to
-    # O(w/sigma), so an FP32-level error dx ~ 1e-6 eV in e_k - e_k+q becomes a
-    # relative error ~ dx / w_q, up to a few 1e-3 for soft modes and more for
-    # the q closest to Gamma.
-    assert abs(dE - rdE) <= 3e-2 * abs(rdE)
+    # dL/dE_F weights each pair by df/dE_F (d+ - d-); the kernels form d+ - d- as
+    # -2 e^-(x^2 + w^2)/sigma^2 sinh(2xw/sigma^2), so each term keeps the forward's relative
+    # error (no cancellation for soft modes).  The terms change sign with e_nk - e_mk+q and
+    # their sum cancels (here by up to ~1300x against the sum of their magnitudes), so the
+    # bound is on the error against that magnitude.
+    scale = fermi_level_term_scale(oracle_lib, wm, k, q, None, 300.0, 0.1, 0.05, cot)
+    print("fused TF32x3 adjoint nw", nw, "dT", abs(dT - rdT) / abs(rdT), "dE_F", abs(dE - rdE) / abs(rdE),
+          "against the term magnitude", abs(dE - rdE) / scale, "cancellation", scale / abs(rdE))
+    assert abs(dE - rdE) <= 1e-4 * scale
 
 
 def test_tensor_core_adjoint_chunks_at_benchmark_q():
@@ -110,4 +115,5 @@ def test_tensor_core_adjoint_chunks_at_benchmark_q():
     ga, gb = a[0].cpu().numpy(), b[0].cpu().numpy()
     assert np.abs(ga - gb).max() <= 1e-3 * np.abs(gb).max()
     assert abs(a[1] - b[1]) <= 1e-3 * abs(b[1])
-    assert abs(a[2] - b[2]) <= 3e-2 * abs(b[2])  # see the E_F note above
+    print("benchmark q: TF32x3 vs FP32 adjoint dT", abs(a[1] - b[1]) / abs(b[1]), "dE_F", abs(a[2] - b[2]) / abs(b[2]))
+    assert abs(a[2] - b[2]) <= 1e-3 * abs(b[2])  # see the E_F note above

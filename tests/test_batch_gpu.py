@@ -117,7 +117,3 @@ def test_batch_rejects_host_buffers_and_unsupported_shapes(epw):
     m = epw.Model(W.make_model("sc", 1, 1, [1.0], None, None, rng, box=1))
     with pytest.raises(ValueError):
         epw.Batch([dict(model=m, k=np.zeros((2, 3)), q=np.zeros((4, 3)), T=300.0, EF=0.0, sigma=0.05)])
-    big = epw.Model(W.make_model("hex", 5, 3, [1.0, 1.1, 1.2], 20, 40, rng))  # Re != Rp: no tensor-core form
-    with pytest.raises(epw.EPWError) as e:
-        epw.Batch([_job(big, rng.random((2, 3)), rng.random((8, 3)), epw.TF32X3)])
-    assert e.value.status == 6

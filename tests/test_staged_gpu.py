@@ -89,17 +89,11 @@ def test_staged_backward_matches_oracle(epw, oracle_lib):
     rdg, rdT, rdE = oracle_lib.linewidth_grad(wm, k, q, None, 300.0, 0.1, 0.05, cot=cot)
     assert np.abs(dg - rdg).max() <= 2e-4 * np.abs(rdg).max()
     assert abs(dT - rdT) <= 2e-4 * abs(rdT)
-    assert abs(dE - rdE) <= 3e-2 * abs(rdE)  # f(1-f)(d+ - d-) cancellation, as for the fused form
+    print("staged TF32x3 adjoint dT", abs(dT - rdT) / abs(rdT), "dE_F", abs(dE - rdE) / abs(rdE))
+    assert abs(dE - rdE) <= 1e-3 * abs(rdE)  # d+ - d- in the sinh form, as for the fused form
 
 
 def test_shapes_without_a_tensor_core_form_report(epw):
-    # Re != Rp: the k-first contraction needs one R set
-    wm = W.make_model("hex", 5, 3, [1.0, 1.1, 1.2], 20, 40, np.random.default_rng(530))
-    m = epw.Model(wm)
-    for prec in (epw.BF16X3, epw.TF32X3):
-        with pytest.raises(epw.EPWError) as e:
-            m.linewidth(np.zeros((2, 3)), np.zeros((4, 3)), T=300.0, EF=0.0, sigma=0.05, precision=prec)
-        assert e.value.status == 6
     # nw above the widest per-pair kernel (18) is refused when the model is loaded
     wm = W.make_model("sc", 20, 1, [1.0], None, None, np.random.default_rng(531), box=1)
     with pytest.raises(epw.EPWError) as e:

@@ -482,7 +482,8 @@ class BatchSpec:
     lattice: str
     nw: int
     nat: int
-    nR: int      # shell target of the common Re = Rp (= phonon) set
+    nRe: int     # shell target of the electronic (and phonon) R set
+    nRp: int     # shell target of the vertex's phonon-displacement R set, drawn independently
     nk: int
     nq_grid: int  # q on an N^3 grid
     seed: int
@@ -490,11 +491,11 @@ class BatchSpec:
 
 def batch_specs(n: int = 64, seed: int = SEED_BASE + 3, nR_range=(27, 400), nk_range=(50, 5000),
                 nq_range=(16, 48), cap_bytes: float = 64e9, max_nw: int = 18, max_modes: int = 18):
-    """Seeded draw of uneven systems: nw from BATCH_NW, nat 1..6, one shell target
-    for Re and Rp uniform in nR_range, nk log-uniform in nk_range, q grids N^3 with
-    N uniform in nq_range.  Redrawn (next seed) until the vertices g(Re,Rp) of all
-    systems take at most cap_bytes as complex64.  max_nw / max_modes keep only
-    systems within given per-pair limits (each drawn system is kept or dropped
+    """Seeded draw of uneven systems: nw from BATCH_NW, nat 1..6, shell targets for Re
+    and for Rp each uniform in nR_range (independently), nk log-uniform in nk_range, q
+    grids N^3 with N uniform in nq_range.  Redrawn (next seed) until the vertices
+    g(Re,Rp) of all systems take at most cap_bytes as complex64.  max_nw / max_modes keep
+    only systems within given per-pair limits (each drawn system is kept or dropped
     whole, so the others keep their sizes)."""
     lats = ("sc", "fcc", "diamond", "hex")
     s = seed
@@ -505,11 +506,12 @@ def batch_specs(n: int = 64, seed: int = SEED_BASE + 3, nR_range=(27, 400), nk_r
             lat = lats[rng.integers(len(lats))]
             nw = int(BATCH_NW[rng.integers(len(BATCH_NW))])
             nat = int(rng.integers(1, 7))
-            nR = int(rng.integers(nR_range[0], nR_range[1] + 1))
+            nRe = int(rng.integers(nR_range[0], nR_range[1] + 1))
+            nRp = int(rng.integers(nR_range[0], nR_range[1] + 1))
             nk = int(round(math.exp(rng.uniform(math.log(nk_range[0]), math.log(nk_range[1])))))
             N = int(rng.integers(nq_range[0], nq_range[1] + 1))
-            out.append(BatchSpec(lat, nw, nat, nR, nk, N, int(rng.integers(1 << 30))))
-        gbytes = sum(8.0 * b.nR * b.nR * 3 * b.nat * b.nw * b.nw for b in out)
+            out.append(BatchSpec(lat, nw, nat, nRe, nRp, nk, N, int(rng.integers(1 << 30))))
+        gbytes = sum(8.0 * b.nRe * b.nRp * 3 * b.nat * b.nw * b.nw for b in out)
         if gbytes <= cap_bytes:
             return [b for b in out if b.nw <= max_nw and 3 * b.nat <= max_modes]
         s += 1
@@ -518,7 +520,8 @@ def batch_specs(n: int = 64, seed: int = SEED_BASE + 3, nR_range=(27, 400), nk_r
 def batch_system(spec: BatchSpec):
     """(model, k [nk,3], q [N^3,3]) of one drawn system; masses 1 + 0.1 i; E_F = 0."""
     rng = np.random.default_rng(spec.seed)
-    m = make_model(spec.lattice, spec.nw, spec.nat, [1.0 + 0.1 * i for i in range(spec.nat)], spec.nR, spec.nR, rng)
+    m = make_model(spec.lattice, spec.nw, spec.nat, [1.0 + 0.1 * i for i in range(spec.nat)], spec.nRe, spec.nRp,
+                   rng)
     k = random_points(rng, spec.nk)
     q = uniform_grid(spec.nq_grid)
     return m, k, q
