@@ -50,7 +50,7 @@ DESCR = {
     "hex_nw5": "hexagonal nw=5 nat=3 (9 modes), ~300 Re=Rp, 20^3 k x 40^3 q, sigma=15 meV, T=50 K",
 }
 CPU_SAMPLE = {"diamond_nw8": (32, 8192), "fcc_nw4": (1000, 2560), "hex_nw5": (64, 16384)}
-WIDE_PROFILE = os.path.join(ROOT, "profiles", "k_tcw_diamond_nw8.md")
+WIDE_PROFILE = os.path.join(ROOT, "profiles", "k_tcwf_diamond_nw8.md")
 WIDE_SOURCE = os.path.join(ROOT, "paper_1604_03525_gb300", "csrc", "epw_tcw.cu")
 TC_PROFILE = os.path.join(ROOT, "profiles", "k_tc_linewidth_fcc_nw4.md")
 TC_SOURCE = os.path.join(ROOT, "paper_1604_03525_gb300", "csrc", "epw_tc.cu")
@@ -228,13 +228,14 @@ def run_reference(args):
 
 
 def run_batch(args):
-    """Uneven systems (the 64-system draw at reduced sizes) through one captured CUDA graph.
+    """Uneven systems (the seeded 64-system draw at its stated sizes) through one captured CUDA graph.
 
-    The draw is the configuration's (nw, nat, lattice, R-shell target, k count, q grid per
-    system) with nR <= 150, nk <= 1000, q grids 16^3..32^3 and nw <= 12 (the host builds every
-    model in NumPy); systems outside the limits are dropped whole.  All jobs run
-    split-BF16 (the fused kernel where the shape has one, else the wide or staged tensor-core
-    form).  A step is one graph replay; the L2 is flushed between steps.
+    Each system draws nw from {1, 2, 4, 5, 8, 12, 18}, nat 1..6, Re and Rp shell targets
+    27..400 each, nk 50..5000 (log-uniform) and a q grid N^3 with N in 16..48; the draw is
+    redrawn until the vertices take at most 64 GB as complex64.  All jobs run split-BF16 (the
+    fused kernel where the shape has one, else the wide or staged tensor-core form); jobs
+    whose k-side buffers would pass 8 GiB run their k list in passes.  A step is one graph
+    replay; the L2 is flushed between steps.
     """
     import torch
     import paper_1604_03525_gb300 as epw
@@ -244,8 +245,13 @@ def run_batch(args):
         return
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    specs = W.models.batch_specs(64, nR_range=(27, 150), nk_range=(50, 1000), nq_range=(16, 32), max_nw=12)
+    specs = W.models.batch_specs(64)
     jobs, pairs, tfl = [], 0, 0.0
+    t0 = time.perf_counter()
+
+    def note(msg):
+        print(f"[batch {time.perf_counter() - t0:8.1f} s] {msg}", file=sys.stderr, flush=True)
+
     for sp in specs:
         wm, k, q = W.models.batch_system(sp)
         m = epw.Model(wm)
@@ -254,9 +260,17 @@ def run_batch(args):
         pairs += len(k) * len(q)
         h, g, _ = flops_per_pair(wm)
         tfl += (h + g) * len(k) * len(q)
+        del wm
+    t_models = time.perf_counter() - t0
+    note(f"{len(jobs)} models built and loaded, {pairs:.3e} pairs per replay")
+    tc = time.perf_counter()
     b = epw.Batch(jobs)  # autotunes, captures the graph and runs every job once
+    t_create = time.perf_counter() - tc
+    note(f"batch created (autotune, eager pass, candidate graphs): {t_create:.1f} s")
     for _ in range(args.warmup):
         b.run()
+        torch.cuda.synchronize()
+        note("warm-up replay done")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -272,14 +286,19 @@ def run_batch(args):
     ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
     peaks, peak_src = measured_peaks()
     ach = tfl / (ms / 1e3) / 1e12
+    info = b.info()
     print(json.dumps({
         "metric": METRIC, "value": pairs / (ms / 1e3), "unit": "pairs/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3+f32+f64", "data": "synthetic",
-        "config": {"workload": f"uneven batch: {len(jobs)} systems of the 64-system draw (nw in "
+        "config": {"workload": f"uneven batch: the {len(jobs)}-system draw (nw in "
                                f"{sorted({sp.nw for sp in specs})}, nat in {sorted({sp.nat for sp in specs})}, "
-                               "nR 27..150, nk 50..1000, q 16^3..32^3), one CUDA graph replay per step",
+                               "Re and Rp shell targets 27..400, nk 50..5000, q 16^3..48^3), one CUDA graph "
+                               "replay per step",
                    "pairs_per_step": pairs, "precision": "bf16x3",
+                   "systems": [[sp.lattice, sp.nw, sp.nat, sp.nRe, sp.nRp, sp.nk, sp.nq_grid] for sp in specs],
+                   "graph": {"branches": info[0], "workspace_bytes": info[1], "nodes": info[2]},
+                   "host_model_build_s": t_models, "batch_create_s": t_create,
                    "l2": "flushed between timed steps (256 MB write)"},
         "clocks": clk.summary(), "gpu_launches": int(launches),
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
@@ -294,10 +313,14 @@ def run_batch(args):
 class Runner:
     """One workload on this rank's k shard, device buffers, L2 flushed between timed steps."""
 
-    def __init__(self, epw, torch, name, rank, world, dev):
+    def __init__(self, epw, torch, name, rank, world, dev, nk=0):
+        import dataclasses
+
         import workloads as W
         self.epw, self.torch, self.name, self.dev = epw, torch, name, dev
         self.wl = W.make_workload(name)
+        if nk > 0:  # the first nk of the k list (small profiling cases)
+            self.wl = dataclasses.replace(self.wl, k=self.wl.k[:nk])
         from paper_1604_03525_gb300.shard import shard_bounds
         self.lo, self.hi = shard_bounds(len(self.wl.k), rank, world)
         self.m = epw.Model(self.wl.model)
@@ -368,6 +391,15 @@ def roofline(wl_model, prec_name, r, pairs, peaks, peak_src, fused):
                "peak_source": src, "kernel": "k_tc_linewidth (fused: contraction, eigensolve, rotation, deltas)",
                "work": f"{h + g} algorithmic contraction flops/pair x {pairs} pairs per step",
                "kernel_ms": g_ms, "kernel_launches": g_n}
+    elif e_n == 0:
+        ach = (h + g) * pairs / (g_ms / 1e3) / 1e12
+        out = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+               "peak_source": src,
+               "kernel": "k_tcwf (wide shapes, one persistent kernel: H(k+q) contraction and per-pair "
+                         "eigensolve beside the vertex contraction, rotation and deltas of the reachable terms)",
+               "work": f"{h + g} algorithmic contraction flops/pair ({h} H(k+q), {g} vertex) x {pairs} pairs "
+                       "per step",
+               "kernel_ms": g_ms, "kernel_launches": g_n}
     else:
         tot = e_ms + g_ms
         ach = (h + g) * pairs / (tot / 1e3) / 1e12
@@ -400,6 +432,8 @@ def main():
     ap.add_argument("--extras", type=int, default=1, help="also time the other configurations and the adjoint")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nk", type=int, default=0,
+                    help="time only the first NK of the k list (a small case for ncu captures; not a bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -425,7 +459,7 @@ def main():
     precs = {"tf32x3": epw.TF32X3, "bf16x3": epw.BF16X3, "fp32": epw.FP32, "fp64": epw.FP64}
     name = AUTO_PRECISION[args.workload] if args.precision == "auto" else args.precision
     prec = precs[name]
-    R = Runner(epw, torch, args.workload, rank, world, dev)
+    R = Runner(epw, torch, args.workload, rank, world, dev, args.nk)
     with ClockSampler(local) as clk:
         r = R.timed(args.steps, args.warmup, prec, barrier)
     t_local = float(np.sum(r["step_ms"]))
@@ -456,7 +490,7 @@ def main():
         if fused:
             roof["traffic"], roof["traffic_source"] = profiled(TC_PROFILE, TC_SOURCE, "traffic", name)
         else:
-            tpp, src = profiled(WIDE_PROFILE, WIDE_SOURCE, "traffic_per_pair_G", name)
+            tpp, src = profiled(WIDE_PROFILE, WIDE_SOURCE, "traffic_per_pair", name)
             nlaunch = max(r["kern"][1], 1)
             roof["traffic"] = None if tpp is None else tpp * R.pairs / nlaunch
             roof["traffic_source"] = src + ("" if tpp is None else
@@ -475,7 +509,8 @@ def main():
         "scaling": "strong", "vs_baseline": None,
         "dtype": {"tf32x3": "tf32x3+f32+f64", "bf16x3": "bf16x3+f32+f64", "fp32": "f32+f64", "fp64": "f64"}[name],
         "data": "synthetic",
-        "config": {"workload": DESCR[args.workload], "pairs_per_step": R.pairs_total,
+        "config": {"workload": DESCR[args.workload] + (f" (first {args.nk} k only)" if args.nk else ""),
+                   "pairs_per_step": R.pairs_total,
                    "k_shard": "contiguous k slice per rank (strong scaling)", "precision": name,
                    "l2": "flushed between timed steps (256 MB write)"},
         "clocks": clk.summary(), "gpu_launches": int(r["launches"] // max(args.steps, 1) * args.steps),

@@ -171,7 +171,10 @@ epw_status epw_interp_g(const epw_model *model, int nk, const double *k, int nq,
  * contraction; only terms whose Gaussians do not underflow in FP32 are
  * evaluated, which leaves the sums unchanged); the environment variable
  * EPW_WIDE_FORM=split selects its two-kernel variant instead of the fused one;
- * other shapes take the staged form. */
+ * other shapes take the staged form.  When the buffers that grow with nk (bands
+ * and vertex at k, operands, partial sums) would exceed EPW_K_SIDE_BYTES
+ * (environment; 8 GiB by default), the k list runs in equal passes, each with
+ * the whole q list (results do not depend on the pass count). */
 epw_status epw_linewidth(const epw_model *model, int nk, const double *k, int nq, const double *q,
                          const double *wq, const epw_params *params, double *imsigma, void *stream);
 
@@ -274,9 +277,13 @@ typedef struct {
 typedef struct epw_batch epw_batch;
 
 /* Plans the jobs and allocates one device workspace for all of them (owned by
- * the batch), picks each job's tile parameters with the autotuner, and
+ * the batch; four regions, each as large as the largest job of the jobs that
+ * share it and run one after another), picks each job's tile parameters with
+ * the autotuner, and
  * captures the whole batch as one CUDA graph whose jobs run on parallel
  * branches (the branch count is chosen by timing the candidate graphs).
+ * Jobs whose buffers would grow past EPW_K_SIDE_BYTES (environment; 8 GiB by
+ * default) with their k count run their k list in passes, as epw_linewidth does.
  * Autotuning runs timed trials of a job shape the first time the process
  * sees it (kept per process; with the environment variable EPW_TUNE_CACHE
  * naming a file, also read from and appended to it).  Creating a batch runs

@@ -551,18 +551,24 @@ extern "C" epw_status epw_sync(const epw_model *m, void *stream) {
 // ------------------------------------------------------------- linewidth
 // Contraction buffer of the staged tensor-core form (per chunk of k).
 static const size_t STAGED_CT_BYTES = (size_t)4 << 30;
+// Buffers that grow with the k count stay within this (the larger uneven-batch systems need
+// up to ~19 MB per k for g(k,Rp) U_k alone); EPW_K_SIDE_BYTES overrides it.
+static const size_t K_SIDE_BYTES = (size_t)8 << 30;
 
 // EPW_WIDE_FORM=split selects the two-kernel wide-shape form (default: the fused kernel).
 EpwTune epwi_default_tune() {
   const char *w = getenv("EPW_WIDE_FORM");
-  return EpwTune{0, STAGED_CT_BYTES, (w && strcmp(w, "split") == 0) ? 1 : 0};
+  const char *kb = getenv("EPW_K_SIDE_BYTES");
+  const size_t kside = (kb && *kb) ? (size_t)strtoull(kb, nullptr, 10) : K_SIDE_BYTES;
+  return EpwTune{0, STAGED_CT_BYTES, (w && strcmp(w, "split") == 0) ? 1 : 0, kside};
 }
 
-epw_status epwi_plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,
-                               bool sout, const EpwTune &tune, LwPlan &L) {
+// The buffers of one pass over nk k-points (k and output staging excluded).
+static epw_status plan_linewidth_pass(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sq, bool swq,
+                                      const EpwTune &tune, LwPlan &L) {
   const bool tc = prec == EPW_BF16X3 || prec == EPW_TF32X3;
   const int op = prec == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32;
-  plan_prep(A, m, nk, nq, tc ? EPW_FP32 : prec, sk, sq, swq, true, L.p);
+  plan_prep(A, m, nk, nq, tc ? EPW_FP32 : prec, false, sq, swq, true, L.p);
   L.sg = TcStaged{};
   L.tc = TcBuffers{};
   L.w = TcwBuffers{};
@@ -578,6 +584,31 @@ epw_status epwi_plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int
     int nqb = (nq + 127) / 128;
     L.partial = A.take<double>((size_t)nk * nqb * m->nw);
   }
+  return EPW_OK;
+}
+
+// k per pass: the k list runs in equal passes when the buffers that grow with nk (k-side
+// bands and vertex g(k,Rp) U_k, partial sums, operands and contraction chunks) would exceed
+// tune.k_side_bytes.  The growth per k is measured from the plans of one and two k.
+static int k_per_pass(const epw_model *m, int nk, int nq, int prec, const EpwTune &tune) {
+  if (tune.k_side_bytes == 0 || nk <= 1) return nk;
+  Arena a1{nullptr, 0, 0}, a2{nullptr, 0, 0};
+  LwPlan t;
+  if (plan_linewidth_pass(a1, m, 1, nq, prec, false, false, tune, t) != EPW_OK ||
+      plan_linewidth_pass(a2, m, 2, nq, prec, false, false, tune, t) != EPW_OK)
+    return nk;
+  const size_t per_k = a2.off > a1.off ? a2.off - a1.off : 1;
+  if (per_k * (size_t)nk <= tune.k_side_bytes) return nk;
+  const size_t npass = (per_k * (size_t)nk + tune.k_side_bytes - 1) / tune.k_side_bytes;
+  return (int)(((size_t)nk + npass - 1) / npass);
+}
+
+epw_status epwi_plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,
+                               bool sout, const EpwTune &tune, LwPlan &L) {
+  L.kchunk = k_per_pass(m, nk, nq, prec, tune);
+  double *kd = sk ? A.take<double>(3 * (size_t)nk) : nullptr;  // the whole k list, staged from the host
+  CKS(plan_linewidth_pass(A, m, L.kchunk, nq, prec, sq, swq, tune, L));
+  L.p.kd = kd;
   L.out_d = sout ? A.take<double>((size_t)nk * m->nw) : nullptr;
   return EPW_OK;
 }
@@ -645,8 +676,22 @@ extern "C" epw_status epw_linewidth(const epw_model *mc, int nk, const double *k
   return EPW_OK;
 }
 
+static epw_status linewidth_pass(epw_model *m, int nk, const double *kd, int nq, const double *qd, const double *wqd,
+                                 const epw_params *par, LwPlan &L, double *out, cudaStream_t st);
+
 epw_status epwi_linewidth_exec(epw_model *m, int nk, const double *kd, int nq, const double *qd, const double *wqd,
                                const epw_params *par, LwPlan &L, double *out, cudaStream_t st) {
+  const int kc = L.kchunk > 0 ? std::min(L.kchunk, nk) : nk;
+  for (int k0 = 0; k0 < nk; k0 += kc)
+    CKS(linewidth_pass(m, std::min(kc, nk - k0), kd + 3 * (size_t)k0, nq, qd, wqd, par, L,
+                       out + (size_t)k0 * m->nw, st));
+  return EPW_OK;
+}
+
+// One pass over nk <= L.kchunk k-points (q side recomputed per pass: it costs a small
+// fraction of the pass's pairs).
+static epw_status linewidth_pass(epw_model *m, int nk, const double *kd, int nq, const double *qd, const double *wqd,
+                                 const epw_params *par, LwPlan &L, double *out, cudaStream_t st) {
   const int prec = par->precision;
   Prep &p = L.p;
   const bool tcp = prec == EPW_BF16X3 || prec == EPW_TF32X3;

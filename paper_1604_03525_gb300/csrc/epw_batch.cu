@@ -1,5 +1,6 @@
 // Batched linewidth over many systems of uneven size (Eq. (linewidthel) per
-// system): one device workspace for all jobs, tile parameters from a timing
+// system): one device workspace (jobs that run one after another on a branch
+// share a region of it), tile parameters from a timing
 // autotuner, and the whole batch captured as one CUDA graph whose jobs run
 // on parallel branches.  Replaying the graph costs one launch on the host
 // however many kernels the jobs hold.
@@ -83,7 +84,7 @@ void load_cache_file_locked() {
     char *b2 = strchr(b1 + 1, '|');
     if (!b2) continue;
     *b1 = 0;
-    EpwTune t;
+    EpwTune t = epwi_default_tune();
     t.a_block_bytes = strtoull(b1 + 1, nullptr, 10);
     t.staged_ct_bytes = strtoull(b2 + 1, nullptr, 10);
     char *b3 = strchr(b2 + 1, '|');
@@ -106,12 +107,12 @@ std::vector<EpwTune> candidates(int path) {
   const EpwTune d = epwi_default_tune();
   std::vector<EpwTune> c;
   if (path == PATH_FUSED) {
-    for (size_t mib : {16, 32, 48, 96}) c.push_back(EpwTune{mib << 20, d.staged_ct_bytes, 0});
+    for (size_t mib : {16, 32, 48, 96}) c.push_back(EpwTune{mib << 20, d.staged_ct_bytes, 0, d.k_side_bytes});
   } else if (path == PATH_STAGED) {
-    for (size_t gib : {1, 2, 4}) c.push_back(EpwTune{d.a_block_bytes, gib << 30, 0});
-  } else if (path == PATH_WIDE) {
-    for (int split : {0, 1}) c.push_back(EpwTune{d.a_block_bytes, d.staged_ct_bytes, split});
+    for (size_t gib : {1, 2, 4}) c.push_back(EpwTune{d.a_block_bytes, gib << 30, 0, d.k_side_bytes});
   } else {
+    // wide shapes: the form single calls take (fused unless EPW_WIDE_FORM=split), so that
+    // batch and single-call results agree bit for bit
     c.push_back(d);
   }
   return c;
@@ -217,6 +218,7 @@ struct epw_batch {
   cudaGraphExec_t exec = nullptr;
   int nbranch = 1;
   size_t nodes = 0;
+  std::vector<int> region;  // workspace region of each job (its branch in the 4-branch graph)
 };
 
 namespace {
@@ -335,24 +337,30 @@ epw_status create_impl(int njobs, const epw_linewidth_job *jobs, epw_batch *b) {
     BCKS(tune_job(J, job_path(J.model, J.params.precision), b->streams[0], &b->tunes[j]));
     b->cost[j] = job_cost(J);
   }
-  // one workspace: each job's buffers at its own offset
-  std::vector<size_t> off(nj, 0);
-  size_t total = 0;
+  // one workspace in MAX_BRANCHES regions: the jobs of a region always run one after
+  // another on one stream (every candidate graph maps regions onto branches), so they
+  // share the region, which is as large as its largest job
+  b->region = assign(b, MAX_BRANCHES);
+  std::vector<size_t> rsize(MAX_BRANCHES, 0), roff(MAX_BRANCHES, 0);
   for (int j = 0; j < nj; j++) {
     const epw_linewidth_job &J = b->jobs[j];
     if (J.nk == 0 || J.nq == 0) continue;
     Arena A{nullptr, 0, 0};
     BCKS(epwi_plan_linewidth(A, J.model, J.nk, J.nq, J.params.precision, false, false, false, false, b->tunes[j],
                              b->plans[j]));
-    off[j] = total;
-    total += (A.off + 255) & ~size_t(255);
+    rsize[b->region[j]] = std::max(rsize[b->region[j]], (A.off + 255) & ~size_t(255));
+  }
+  size_t total = 0;
+  for (int r = 0; r < MAX_BRANCHES; r++) {
+    roff[r] = total;
+    total += rsize[r];
   }
   if (total) BCK(cudaMalloc((void **)&b->ws, total));
   b->ws_bytes = total;
   for (int j = 0; j < nj; j++) {
     const epw_linewidth_job &J = b->jobs[j];
     if (J.nk == 0 || J.nq == 0) continue;
-    Arena A{b->ws + off[j], total - off[j], 0};
+    Arena A{b->ws + roff[b->region[j]], rsize[b->region[j]], 0};
     BCKS(epwi_plan_linewidth(A, J.model, J.nk, J.nq, J.params.precision, false, false, false, false, b->tunes[j],
                              b->plans[j]));
   }
@@ -370,7 +378,8 @@ epw_status create_impl(int njobs, const epw_linewidth_job *jobs, epw_batch *b) {
   epw_status s = EPW_OK;
   for (int nb : {1, 2, 4}) {
     if (nb > 1 && nb > busy) break;
-    const std::vector<int> br = assign(b, nb);
+    std::vector<int> br(nj);
+    for (int j = 0; j < nj; j++) br[j] = b->region[j] * nb / MAX_BRANCHES;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t x = nullptr;
     s = capture(b, br, nb, &g, &x);

@@ -16,6 +16,7 @@ struct EpwTune {
   size_t a_block_bytes;    // fused kernel: q-block of the A operand kept in L2 across the k groups
   size_t staged_ct_bytes;  // staged form: contraction buffer per chunk of k
   int wide_split;          // wide-shape form: 1 = two kernels per chunk of k, 0 = one fused kernel
+  size_t k_side_bytes;     // buffers that grow with nk stay within this: larger k lists run in k chunks
 };
 EpwTune epwi_default_tune();
 
@@ -46,6 +47,7 @@ struct LwPlan {
   TcBuffers tc;
   TcStaged sg;
   TcwBuffers w;  // wide-shape fused form
+  int kchunk;    // k per pass (the buffers are laid out for this many); the k list runs in passes
 };
 
 // Lays out (or, with a null arena base, measures) the buffers of one job.

@@ -3,7 +3,7 @@
 // kernel's 128-column slot (diamond nw = 8 with 6 modes, hexagonal nw = 5 with 9).
 //
 // The per-pair work of Eq. (linewidthel) splits into two tcgen05 kernels per
-// chunk of k-points, both over the same A operand of q phases P_q(R) (real GEMM,
+// chunk of k-points, both over A operands of q phases P_q(R) (real GEMM,
 // K = 2 nR with re/im interleaved, split into two bf16 or tf32 terms, three
 // MMAs per K step, FP32 accumulation in tensor memory):
 //
@@ -12,7 +12,9 @@
 //     implicit QR, epw_eigqr.cuh), writes the eigenvalues e_m,k+q and, for the
 //     bands m that some band n at k can reach within the Gaussian cutoff
 //     (|e_nk - e_m,k+q| <= max_nu w_q,nu + X sigma), the eigenvectors u_m.
-//  G  C[q][((k, n), a, j)] = sum_R P_q(R) (g_a(k,R) U_k)_jn = (g_a(k,q) U_k)_jn,
+//  G  C[q][((k, n), a, j)] = sum_Rp P_q(Rp) (g_a(k,Rp) U_k)_jn = (g_a(k,q) U_k)_jn
+//     (over its own A operand of phases P_q(Rp) when the phonon-displacement set Rp
+//     differs from Re),
 //     the columns of one band n of k contiguous; the epilogue forms, for the
 //     reachable (m, n) only, t_a = u_m^dagger (g_a U_k)_{:,n},
 //     g_mn,nu = sum_a E_q[a][nu] t_a (+ i C_nu(q) u_m^dagger U_k e_n for the
@@ -52,8 +54,7 @@ constexpr int w_stages() {
   return KIND == 0 ? 2 : 4;
 }
 constexpr int EPI_WARP0 = 2;
-// Epilogue warps: kernel E one per TMEM lane quadrant (six warps in all, so that
-// each thread may hold 255 registers for the eigensolve); kernel G two per quadrant.
+// Epilogue warps: two per TMEM lane quadrant in both kernels (eight warps).
 template <int KIND>
 constexpr int epi_warps() {
   return KIND == 0 ? 8 : 8;

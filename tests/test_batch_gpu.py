@@ -39,7 +39,7 @@ def test_uneven_batch_reproduces_single_calls(epw, oracle_lib):
     rng = np.random.default_rng(700)
     m_fcc = epw.Model(W.make_model("fcc", 4, 1, [1.0], 60, 60, rng))       # fused tensor-core kernel
     hexm = W.make_model("hex", 5, 3, [1.0, 1.1, 1.2], 30, 30, rng)
-    m_hex = epw.Model(hexm)                                                 # staged form
+    m_hex = epw.Model(hexm)                                                 # wide-shape form
     scm = W.make_model("sc", 2, 1, [1.0], None, None, rng, box=1)
     m_sc = epw.Model(scm)                                                   # SIMT forms
     jobs = [
