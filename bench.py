@@ -297,10 +297,10 @@ def run_batch(args):
                                "replay per step",
                    "pairs_per_step": pairs, "precision": "bf16x3",
                    "systems": [[sp.lattice, sp.nw, sp.nat, sp.nRe, sp.nRp, sp.nk, sp.nq_grid] for sp in specs],
-                   "graph": {"branches": info[0], "workspace_bytes": info[1], "nodes": info[2]},
+                   "graph": {"branches": info[0], "workspace_bytes": info[1], "kernel_nodes": info[2]},
                    "host_model_build_s": t_models, "batch_create_s": t_create,
                    "l2": "flushed between timed steps (256 MB write)"},
-        "clocks": clk.summary(), "gpu_launches": int(launches),
+        "clocks": clk.summary(), "gpu_launches": int(launches + info[2] * args.steps),
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": ach / peaks["bf16_tflops"], "traffic": None,
                      "peak_source": f"{peak_src} bf16_tflops (burst)",

@@ -169,8 +169,9 @@ epw_status epw_interp_g(const epw_model *model, int nk, const double *k, int nq,
  * 2 nw^2 (3nat + 1) fit 128 take one fused kernel; (nw, 3nat) = (8, 6) and
  * (5, 9) take the wide-shape form (H(k+q) eigensolve beside the vertex
  * contraction; only terms whose Gaussians do not underflow in FP32 are
- * evaluated, which leaves the sums unchanged); the environment variable
- * EPW_WIDE_FORM=split selects its two-kernel variant instead of the fused one;
+ * evaluated, which leaves the sums unchanged), whose fused kernel runs on CTA
+ * pairs (2-SM MMAs over 256 q rows; the environment variable EPW_WIDE_FORM=single
+ * selects the single-CTA kernel, EPW_WIDE_FORM=split a two-kernel variant);
  * other shapes take the staged form.  When the buffers that grow with nk (bands
  * and vertex at k, operands, partial sums) would exceed EPW_K_SIDE_BYTES
  * (environment; 8 GiB by default), the k list runs in equal passes, each with
@@ -281,7 +282,8 @@ typedef struct epw_batch epw_batch;
  * share it and run one after another), picks each job's tile parameters with
  * the autotuner, and
  * captures the whole batch as one CUDA graph whose jobs run on parallel
- * branches (the branch count is chosen by timing the candidate graphs).
+ * branches (the branch count is chosen by timing the candidate graphs; a batch
+ * whose first pass takes over 5 s takes four branches without timing).
  * Jobs whose buffers would grow past EPW_K_SIDE_BYTES (environment; 8 GiB by
  * default) with their k count run their k list in passes, as epw_linewidth does.
  * Autotuning runs timed trials of a job shape the first time the process
@@ -295,7 +297,8 @@ epw_status epw_batch_create(int njobs, const epw_linewidth_job *jobs, epw_batch 
 /* Replays the batch's graph on `stream` (asynchronous); epw_sync on a job's
  * model reports device-side failures. */
 epw_status epw_batch_run(epw_batch *batch, void *stream);
-/* Graph branches, workspace bytes and number of graph nodes (any may be NULL). */
+/* Graph branches, workspace bytes and the number of kernel nodes of the graph (the
+ * kernels one replay launches); any output may be NULL. */
 epw_status epw_batch_info(const epw_batch *batch, int *branches, size_t *workspace_bytes, size_t *graph_nodes);
 /* Waits for the batch's work and releases its graph, streams and workspace. */
 void epw_batch_free(epw_batch *batch);

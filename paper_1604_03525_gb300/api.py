@@ -355,7 +355,7 @@ class Batch:
         return self.outputs
 
     def info(self):
-        """(graph branches, workspace bytes, graph nodes)."""
+        """(graph branches, workspace bytes, kernel nodes of the graph: the kernels one replay launches)."""
         b, w, n = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_size_t()
         _check(_lib.load().epw_batch_info(self._h, ctypes.byref(b), ctypes.byref(w), ctypes.byref(n)))
         return b.value, w.value, n.value

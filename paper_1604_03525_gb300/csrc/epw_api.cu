@@ -555,12 +555,17 @@ static const size_t STAGED_CT_BYTES = (size_t)4 << 30;
 // up to ~19 MB per k for g(k,Rp) U_k alone); EPW_K_SIDE_BYTES overrides it.
 static const size_t K_SIDE_BYTES = (size_t)8 << 30;
 
-// EPW_WIDE_FORM=split selects the two-kernel wide-shape form (default: the fused kernel).
+// EPW_WIDE_FORM selects the wide-shape form: unset or "pair", the fused kernel on CTA pairs;
+// "single", the fused kernel on single CTAs; "split", the two-kernel form.
 EpwTune epwi_default_tune() {
   const char *w = getenv("EPW_WIDE_FORM");
   const char *kb = getenv("EPW_K_SIDE_BYTES");
   const size_t kside = (kb && *kb) ? (size_t)strtoull(kb, nullptr, 10) : K_SIDE_BYTES;
-  return EpwTune{0, STAGED_CT_BYTES, (w && strcmp(w, "split") == 0) ? 1 : 0, kside};
+  const int form = !w ? TCW_FORM_PAIR
+                 : strcmp(w, "split") == 0 ? TCW_FORM_SPLIT
+                 : strcmp(w, "single") == 0 ? TCW_FORM_SINGLE
+                                            : TCW_FORM_PAIR;
+  return EpwTune{0, STAGED_CT_BYTES, form, kside};
 }
 
 // The buffers of one pass over nk k-points (k and output staging excluded).
@@ -577,7 +582,7 @@ static epw_status plan_linewidth_pass(Arena &A, const epw_model *m, int nk, int 
     L.tc.a_block_bytes = tune.a_block_bytes;
     L.partial = nullptr;
   } else if (tc && tcw_supported(m)) {
-    CKS(tcw_plan(A, m, nk, nq, op, 0, L.w, tune.wide_split != 0));
+    CKS(tcw_plan(A, m, nk, nq, op, 0, L.w, tune.wide_form));
     L.partial = nullptr;
   } else {
     if (tc) CKS(tc_staged_plan(A, m, nk, nq, op, tune.staged_ct_bytes ? tune.staged_ct_bytes : STAGED_CT_BYTES, L.sg));
@@ -952,6 +957,7 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
     TcBuffers tc;
     TcBwdBuffers tw;
     TcStaged sg;
+    TcBwdBuffers sw;  // staged shapes: the q contraction of Xbar on the tensor cores
   } b;
   b.sg = TcStaged{};
   auto plan = [&](Arena &A) -> epw_status {
@@ -965,6 +971,7 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
         CKS(tc_staged_plan(A, m, nk > 0 ? nk : 1, nq > 0 ? nq : 1,
                            par->precision == EPW_BF16X3 ? TC_OP_BF16 : TC_OP_TF32, (size_t)2 << 30, b.sg, true));
         nkc = std::min(nkc, b.sg.kc);
+        CKS(tc_sbwd_plan(A, m, nq > 0 ? nq : 1, nkc, b.sw));
       }
       b.xbar = (double *)A.take<char>(sR * (size_t)nq * nkc * per);
       b.Bbar = (double *)A.take<char>(sR * (size_t)m->nRp * nkc * per);
@@ -1011,7 +1018,10 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
   } else if (nk > 0 && nq > 0) {
     CKS(run_prep(m, nk, kd, nq, qd, prec, par->omega_min_eV, true, p, nullptr, st));
     b.sg.Pq64 = m->same_eph ? p.PqTph : nullptr;
-    if (staged) CKS(tc_staged_phases(m, nq, qd, b.sg, st));
+    if (staged) {
+      CKS(tc_staged_phases(m, nq, qd, b.sg, st));
+      CKS(tc_sbwd_phases(m, nq, qd, b.sw, st));
+    }
     for (int k0 = 0; k0 < nk; k0 += nkc) {
       const int kc = std::min(nkc, nk - k0);
       if (staged) {
@@ -1067,8 +1077,13 @@ extern "C" epw_status epw_linewidth_backward(const epw_model *mc, int nk, const 
         launch_cgemm<double>(m->nRe, ncol2, kc, p.PkRM + (size_t)k0 * m->nRe, m->nRe, true, true,
                              (const cx<double> *)b.G1bar, ncol2, (cx<double> *)b.gwbar, ncol2, true, st);
       } else {
-        launch_cgemm<float>(m->nRp, ncol, nq, (const cx<float> *)p.PqTp, nq, false, true, (const cx<float> *)b.xbar,
-                            ncol, (cx<float> *)b.Bbar, ncol, false, st);
+        if (staged) {
+          epw_status s = tc_sbwd_contract(m, kc, nq, (const cx<float> *)b.xbar, b.sw, (cx<float> *)b.Bbar, st);
+          if (s != EPW_OK) return fail(s, "tensor-core adjoint contraction failed");
+        } else {
+          launch_cgemm<float>(m->nRp, ncol, nq, (const cx<float> *)p.PqTp, nq, false, true,
+                              (const cx<float> *)b.xbar, ncol, (cx<float> *)b.Bbar, ncol, false, st);
+        }
         launch_bg_adjoint_rotate_k0<float>(kc, k0, m->nRp, m->nm, m->nw, (const cx<float> *)b.Bbar, p.Uk,
                                            (cx<float> *)b.G1bar, st);
         launch_cgemm<float>(m->nRe, ncol2, kc, p.Pk32 + (size_t)k0 * m->nRe, m->nRe, true, true,

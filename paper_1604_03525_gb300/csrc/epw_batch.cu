@@ -69,7 +69,7 @@ std::mutex g_mu;
 std::map<std::string, EpwTune> g_cache;
 bool g_loaded = false;
 
-// File format, one entry per line: <key>|<a_block_bytes>|<staged_ct_bytes>[|<wide_split>]
+// File format, one entry per line: <key>|<a_block_bytes>|<staged_ct_bytes>[|<wide_form>]
 void load_cache_file_locked() {
   if (g_loaded) return;
   g_loaded = true;
@@ -88,7 +88,7 @@ void load_cache_file_locked() {
     t.a_block_bytes = strtoull(b1 + 1, nullptr, 10);
     t.staged_ct_bytes = strtoull(b2 + 1, nullptr, 10);
     char *b3 = strchr(b2 + 1, '|');
-    t.wide_split = b3 ? atoi(b3 + 1) : 0;
+    t.wide_form = b3 ? atoi(b3 + 1) : 0;
     g_cache[line] = t;
   }
   fclose(f);
@@ -99,7 +99,7 @@ void append_cache_file_locked(const std::string &key, const EpwTune &t) {
   if (!path || !*path) return;
   FILE *f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s|%zu|%zu|%d\n", key.c_str(), t.a_block_bytes, t.staged_ct_bytes, t.wide_split);
+  fprintf(f, "%s|%zu|%zu|%d\n", key.c_str(), t.a_block_bytes, t.staged_ct_bytes, t.wide_form);
   fclose(f);
 }
 
@@ -111,7 +111,7 @@ std::vector<EpwTune> candidates(int path) {
   } else if (path == PATH_STAGED) {
     for (size_t gib : {1, 2, 4}) c.push_back(EpwTune{d.a_block_bytes, gib << 30, 0, d.k_side_bytes});
   } else {
-    // wide shapes: the form single calls take (fused unless EPW_WIDE_FORM=split), so that
+    // wide shapes: the form single calls take (EPW_WIDE_FORM, default the paired fused kernel), so that
     // batch and single-call results agree bit for bit
     c.push_back(d);
   }
@@ -153,8 +153,9 @@ epw_status tune_job(const epw_linewidth_job &j, int path, cudaStream_t st, EpwTu
     return EPW_OK;
   }
   // enough k for the tiles to repeat: the fused kernel's k groups fill the
-  // SMs a few times over; the staged form runs a few chunks
-  const int nk_t = std::min(j.nk, path == PATH_FUSED ? 608 : 64);
+  // SMs a few times over; the staged form runs a few chunks (16 k: its heaviest
+  // shapes take seconds per trial over a 48^3 q grid)
+  const int nk_t = std::min(j.nk, path == PATH_FUSED ? 608 : 16);
   size_t need = 0;
   for (const EpwTune &t : cand) {
     Arena A{nullptr, 0, 0};
@@ -224,6 +225,7 @@ struct epw_batch {
 namespace {
 
 constexpr int MAX_BRANCHES = 4;
+constexpr int LONG_BATCH_MS = 5000;  // eager pass above which the branch count is not timed
 
 // Enqueues every job on its branch stream (branch[i] < nb), forked from and
 // joined back into streams[0].
@@ -365,19 +367,27 @@ epw_status create_impl(int njobs, const epw_linewidth_job *jobs, epw_batch *b) {
                              b->plans[j]));
   }
   // one eager pass (validates every job and sets kernel attributes outside capture)
-  std::vector<int> one(nj, 0);
-  BCKS(enqueue_all(b, one, 1));
-  BCK(cudaStreamSynchronize(b->streams[0]));
-  // candidate graphs: 1, 2 and 4 branches; keep the fastest
-  int busy = 0;
-  for (int j = 0; j < nj; j++) busy += (b->jobs[j].nk > 0) ? 1 : 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
+  std::vector<int> one(nj, 0);
+  BCK(cudaEventRecord(e0, b->streams[0]));
+  BCKS(enqueue_all(b, one, 1));
+  BCK(cudaEventRecord(e1, b->streams[0]));
+  BCK(cudaStreamSynchronize(b->streams[0]));
+  float eager_ms = 0.0f;
+  BCK(cudaEventElapsedTime(&eager_ms, e0, e1));
+  // candidate graphs: 1, 2 and 4 branches, the fastest kept; a batch whose eager pass
+  // takes seconds gains nothing measurable from the choice and takes the 4-branch graph
+  // without timing replays
+  const bool long_batch = eager_ms > (float)LONG_BATCH_MS;
+  int busy = 0;
+  for (int j = 0; j < nj; j++) busy += (b->jobs[j].nk > 0) ? 1 : 0;
   float best = 0.0f;
   epw_status s = EPW_OK;
   for (int nb : {1, 2, 4}) {
     if (nb > 1 && nb > busy) break;
+    if (long_batch && nb != (busy >= 4 ? 4 : busy >= 2 ? 2 : 1)) continue;
     std::vector<int> br(nj);
     for (int j = 0; j < nj; j++) br[j] = b->region[j] * nb / MAX_BRANCHES;
     cudaGraph_t g = nullptr;
@@ -385,11 +395,14 @@ epw_status create_impl(int njobs, const epw_linewidth_job *jobs, epw_batch *b) {
     s = capture(b, br, nb, &g, &x);
     if (s != EPW_OK) break;
     float ms = 0.0f;
-    cudaEventRecord(e0, b->streams[0]);
-    cudaError_t e = cudaGraphLaunch(x, b->streams[0]);
-    cudaEventRecord(e1, b->streams[0]);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaError_t e = cudaSuccess;
+    if (!long_batch) {
+      cudaEventRecord(e0, b->streams[0]);
+      e = cudaGraphLaunch(x, b->streams[0]);
+      cudaEventRecord(e1, b->streams[0]);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
     if (e != cudaSuccess) {
       cudaGraphExecDestroy(x);
       cudaGraphDestroy(g);
@@ -413,7 +426,19 @@ epw_status create_impl(int njobs, const epw_linewidth_job *jobs, epw_batch *b) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != EPW_OK) return s;
-  if (b->graph) BCK(cudaGraphGetNodes(b->graph, nullptr, &b->nodes));
+  if (b->graph) {
+    // kernel nodes: the kernels one replay launches
+    size_t n = 0;
+    BCK(cudaGraphGetNodes(b->graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) BCK(cudaGraphGetNodes(b->graph, nodes.data(), &n));
+    b->nodes = 0;
+    for (size_t i = 0; i < n; i++) {
+      cudaGraphNodeType t;
+      BCK(cudaGraphNodeGetType(nodes[i], &t));
+      if (t == cudaGraphNodeTypeKernel) b->nodes++;
+    }
+  }
   return EPW_OK;
 }
 

@@ -15,7 +15,7 @@ epw_status epwi_check_params(const epw_params *p);
 struct EpwTune {
   size_t a_block_bytes;    // fused kernel: q-block of the A operand kept in L2 across the k groups
   size_t staged_ct_bytes;  // staged form: contraction buffer per chunk of k
-  int wide_split;          // wide-shape form: 1 = two kernels per chunk of k, 0 = one fused kernel
+  int wide_form;           // wide-shape form: TCW_FORM_PAIR (fused, CTA pairs), _SPLIT (two kernels), _SINGLE
   size_t k_side_bytes;     // buffers that grow with nk stay within this: larger k lists run in k chunks
 };
 EpwTune epwi_default_tune();

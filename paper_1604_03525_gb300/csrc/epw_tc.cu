@@ -1948,6 +1948,114 @@ epw_status tc_bwd_plan(Arena &A, const epw_model *m, int nk, int nq, TcBuffers &
   return EPW_OK;
 }
 
+// ------------------------------------------------------ staged adjoint
+// The q contraction of the staged adjoint, Bbar[Rp][kl nc + c] = sum_q conj(P_q(Rp)) Xbar[q][kl][c],
+// as the same split-TF32 GEMM on the tensor cores: Xbar (FP32 complex, q-major, written by the
+// per-pair adjoint kernel) is transposed into K-major rows split into two tf32 terms, K index
+// 2q + (re, im), against the conj-phase operand of the Rp set.
+
+// xhi/xlo[m][2q + t] (t = re, im) from xbar[q][m], m < nrow: 32 x 32 tiles through shared memory
+__global__ void k_xbar_split(int nq, int nrow, int ld, const float2 *__restrict__ xbar, float *hi, float *lo) {
+  __shared__ float2 tile[32][33];
+  const int tq = (nq + 31) / 32, tm = (nrow + 31) / 32;
+  for (int t = blockIdx.x; t < tq * tm; t += gridDim.x) {
+    const int q0 = (t / tm) * 32, m0 = (t % tm) * 32;
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      const int q = q0 + i, mm = m0 + threadIdx.x;
+      tile[i][threadIdx.x] = (q < nq && mm < nrow) ? xbar[(size_t)q * nrow + mm] : make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      const int mm = m0 + i, q = q0 + threadIdx.x;
+      if (mm < nrow && q < nq) {
+        const float2 v = tile[threadIdx.x][i];
+        const float h0 = tf32_rn(v.x), h1 = tf32_rn(v.y);
+        const size_t o = (size_t)mm * ld + 2 * (size_t)q;
+        *reinterpret_cast<float2 *>(hi + o) = make_float2(h0, h1);
+        *reinterpret_cast<float2 *>(lo + o) = make_float2(tf32_rn(v.x - h0), tf32_rn(v.y - h1));
+      }
+    }
+  }
+}
+
+epw_status tc_sbwd_plan(Arena &A, const epw_model *m, int nq, int kc, TcBwdBuffers &w) {
+  w = TcBwdBuffers{};
+  const int nc = m->nm * m->nw * m->nw;
+  w.nc = nc;
+  w.ld = (2 * nq + 31) / 32 * 32;
+  w.kc = kc;
+  w.mtiles = (kc * nc + 127) / 128;
+  w.ntiles = (2 * m->nRp + G_NT - 1) / G_NT;
+  w.kblocks = (2 * nq + 31) / 32;
+  const int tiles = w.mtiles * w.ntiles;
+  const int splits = std::max(1, std::min(w.kblocks, (2 * 152 + tiles - 1) / tiles));
+  w.kb_per_split = (w.kblocks + splits - 1) / splits;
+  w.splits = (w.kblocks + w.kb_per_split - 1) / w.kb_per_split;
+  w.ldc = w.mtiles * 128;
+  w.npad = w.ntiles * G_NT;
+  w.phi = A.take<float>((size_t)2 * m->nRp * w.ld);
+  w.plo = A.take<float>((size_t)2 * m->nRp * w.ld);
+  w.xhi = A.take<float>((size_t)kc * nc * w.ld);
+  w.xlo = A.take<float>((size_t)kc * nc * w.ld);
+  w.Ct = A.take<float>((size_t)w.splits * w.npad * w.ldc);
+  return EPW_OK;
+}
+
+epw_status tc_sbwd_phases(const epw_model *m, int nq, const double *q, TcBwdBuffers &w, cudaStream_t st) {
+  const size_t n = (size_t)nq * 2 * m->nRp;
+  k_build_pconj<<<grid_for(n, 256), 256, 0, st>>>(nq, m->nRp, w.ld, q, m->Rp, w.phi, w.plo);
+  epw_count_launch();
+  return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
+}
+
+epw_status tc_sbwd_contract(const epw_model *m, int kc, int nq, const cx<float> *xbar, TcBwdBuffers &w,
+                            cx<float> *Bbar, cudaStream_t st) {
+  if (kc > w.kc) return EPW_ERR_UNSUPPORTED;
+  const int nc = w.nc, M = kc * nc;
+  {
+    const int tiles = ((nq + 31) / 32) * ((M + 31) / 32);
+    k_xbar_split<<<std::min(tiles, 152 * 16), dim3(32, 8), 0, st>>>(nq, M, w.ld, (const float2 *)xbar, w.xhi, w.xlo);
+    epw_count_launch();
+  }
+  CUtensorMap xh, xl, ph, pl;
+  if (!make_map_f32(&xh, w.xhi, 2 * (uint64_t)nq, w.ld, (uint64_t)M, 128) ||
+      !make_map_f32(&xl, w.xlo, 2 * (uint64_t)nq, w.ld, (uint64_t)M, 128) ||
+      !make_map_f32(&ph, w.phi, 2 * (uint64_t)nq, w.ld, 2 * (uint64_t)m->nRp, G_NT) ||
+      !make_map_f32(&pl, w.plo, 2 * (uint64_t)nq, w.ld, 2 * (uint64_t)m->nRp, G_NT))
+    return EPW_ERR_CUDA;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_tc_gemm_nt<TC_OP_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM) !=
+        cudaSuccess)
+      return EPW_ERR_CUDA;
+    attr = true;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  GemmArgs g;
+  g.mtiles = (M + 127) / 128;
+  g.ntiles = w.ntiles;
+  g.kblocks = w.kblocks;
+  g.kb_per_split = w.kb_per_split;
+  g.splits = w.splits;
+  g.ldc = w.ldc;
+  g.npad = w.npad;
+  g.Ct = w.Ct;
+  g.qmajor = 0;
+  g.ldn = 0;
+  g.dstatus = m->dstatus;
+  const int items = g.mtiles * g.ntiles * g.splits;
+  k_tc_gemm_nt<TC_OP_TF32><<<std::min(items, sms), G_THREADS, G_SMEM, st>>>(xh, xl, ph, pl, g);
+  epw_count_launch();
+  if (cudaGetLastError() != cudaSuccess) return EPW_ERR_CUDA;
+  const size_t nred = (size_t)m->nRp * kc * nc;
+  k_xbar_reduce<<<grid_for(nred, 256), 256, 0, st>>>(m->nRp, kc, nc, g.splits, g.npad, g.ldc, w.Ct, Bbar);
+  epw_count_launch();
+  return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
+}
+
 epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const double *q, const double *wq,
                                  const epw_params *par, const double *epsk, const cx<double> *Uk,
                                  const cx<float> *Pk32, const double *omegaT, const cx<float> *ET32,

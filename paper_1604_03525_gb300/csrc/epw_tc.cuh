@@ -92,11 +92,15 @@ struct TcwBuffers {
   int op, kpad, kpadG, kc, ldq, nqt, cpk, kpt, entp, cn, bng;
   bool ok;
   bool fused;          // one kernel (E and G overlapped, eigen-data through a ring in L2); else two per chunk
+  bool pair;           // the fused kernel on CTA pairs (cta_group::2 MMAs over 256 q rows)
 };
+// forms of the wide path: the fused kernel on CTA pairs (default), the two-kernel form, the
+// fused kernel on single CTAs
+enum { TCW_FORM_PAIR = 0, TCW_FORM_SPLIT = 1, TCW_FORM_SINGLE = 2 };
 bool tcw_supported(const epw_model *m);
-// bytes: budget of the per-chunk buffers (0: default); split: the two-kernel form
+// bytes: budget of the per-chunk buffers (0: default); form: TCW_FORM_*
 epw_status tcw_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t bytes, TcwBuffers &b,
-                    bool split = false);
+                    int form = TCW_FORM_PAIR);
 // Im Sigma [nk][nw] into `out` (device) from the preparation outputs (P64: FP64 q phases of
 // the Re set [nR][nq] or null; Cpol [nm][nq] and Uk for polar models, else null).
 epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, const double *wq,
@@ -123,6 +127,12 @@ struct TcBwdBuffers {
 
 // Lay out the adjoint's buffers (forward operands at TF32 included).
 epw_status tc_bwd_plan(Arena &A, const epw_model *m, int nk, int nq, TcBuffers &b, TcBwdBuffers &w);
+// Staged adjoint's q contraction on the tensor cores (TF32 split), chunks of up to kc k:
+// Bbar[Rp][kl][c] = sum_q conj(P_q(Rp)) xbar[q][kl][c] (xbar FP32 complex [nq][kc][nc]).
+epw_status tc_sbwd_plan(Arena &A, const epw_model *m, int nq, int kc, TcBwdBuffers &w);
+epw_status tc_sbwd_phases(const epw_model *m, int nq, const double *q, TcBwdBuffers &w, cudaStream_t st);
+epw_status tc_sbwd_contract(const epw_model *m, int kc, int nq, const cx<float> *xbar, TcBwdBuffers &w,
+                            cx<float> *Bbar, cudaStream_t st);
 // Accumulates dL/dgw into gwbar [nRe][nRp][nm][nw][nw] and (dL/dT, dL/dE_F) into scal[0..1],
 // for L = sum c_nk Im Sigma_nk with c = cot [nk][nw] (device).
 epw_status tc_linewidth_backward(const epw_model *m, int nk, int nq, const double *q, const double *wq,

@@ -90,6 +90,12 @@ constexpr uint32_t w_idesc() {
   return (1u << 4) | (WOp<OP>::FMT << 7) | (WOp<OP>::FMT << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(BM >> 4) << 24);
 }
+// the same for a CTA pair's MMA (M = 256: 128 rows in each CTA)
+template <int OP, int N>
+constexpr uint32_t w_idesc_pair() {
+  return (1u << 4) | (WOp<OP>::FMT << 7) | (WOp<OP>::FMT << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)((2 * BM) >> 4) << 24);
+}
 
 template <int NW, int NM>
 struct WShape {
@@ -136,15 +142,18 @@ struct TcwArgs {
 };
 
 // Tile -> (column group, q tile): q-blocks of `qblock` tiles, group-major inside a block.
-__device__ __forceinline__ void w_coords(const TcwArgs &a, int item, int &grp, int &qt) {
-  const int per = a.qblock * a.ngrp;
-  const int nb = (a.nqt + a.qblock - 1) / a.qblock;
+__device__ __forceinline__ void w_coords_n(int nqt, int qblock, int ngrp, int item, int &grp, int &qt) {
+  const int per = qblock * ngrp;
+  const int nb = (nqt + qblock - 1) / qblock;
   int b = item / per;
   if (b > nb - 1) b = nb - 1;
   const int r = item - b * per;
-  const int qbs = min(a.qblock, a.nqt - b * a.qblock);
+  const int qbs = min(qblock, nqt - b * qblock);
   grp = r / qbs;
-  qt = b * a.qblock + r % qbs;
+  qt = b * qblock + r % qbs;
+}
+__device__ __forceinline__ void w_coords(const TcwArgs &a, int item, int &grp, int &qt) {
+  w_coords_n(a.nqt, a.qblock, a.ngrp, item, grp, qt);
 }
 
 // The one relevance test both kernels evaluate (same FP32 operands, same result).
@@ -167,7 +176,7 @@ struct EigView {
 template <int NW, bool FUSED = false>
 __device__ __forceinline__ bool eig_pair(const TcwArgs &a, uint32_t tcol, int q, int kg, const EigView &v,
                                          bool valid, uint32_t hempty = 0, uint32_t eempty = 0, uint32_t epar = 0,
-                                         volatile int *abort_flag = nullptr) {
+                                         volatile int *abort_flag = nullptr, bool hempty_cluster = false) {
   constexpr int H2 = 2 * NW * NW;
   constexpr int LD = (H2 + 31) / 32 * 32;
   Herm<NW> H;
@@ -192,7 +201,12 @@ __device__ __forceinline__ bool eig_pair(const TcwArgs &a, uint32_t tcol, int q,
     // H is in registers: the tensor-memory region may take the next item's H(k+q)
     tc_fence_before();
     __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(hempty);
+    if ((threadIdx.x & 31) == 0) {
+      if (hempty_cluster)
+        mbar_arrive_cluster(hempty);
+      else
+        mbar_arrive(hempty);
+    }
   }
   HhQR<NW> S;
   hh_tridiag<NW>(H, S);
@@ -535,24 +549,38 @@ __global__ void __launch_bounds__(nthreads<KIND>(), 1)
 constexpr int F_WARPS = 10;
 constexpr int F_RB = 64;
 
-// Operand stages (four, three when the per-q tables of 3nat = 9 modes need the room),
-// then per vertex warp its lanes' per-q tables: mode factors E [nm*nm][32] (float2),
-// frequencies and Bose factors [2 nm][32].
-template <int NM>
+// Operand stages, then per vertex warp its lanes' per-q tables: mode factors E [nm*nm][32]
+// (float2), frequencies and Bose factors [2 nm][32].  A stage holds the A rows (hi, lo) and
+// the B rows (hi, lo) of one K block: all B rows for a single CTA, half of them for a CTA
+// pair (each CTA holds half of the MMA's N columns), so a pair's stages are smaller and
+// more of them fit (single CTA: four, three with the tables of 3nat = 9 modes; pair: six, four).
+template <int NM, bool PAIR>
 constexpr int f_stages() {
-  return NM <= 6 ? 4 : 3;
+  return PAIR ? (NM <= 6 ? 6 : 4) : (NM <= 6 ? 4 : 3);
 }
-template <int NW, int NM>
+template <int NW, int NM, bool PAIR>
 constexpr int f_stage_bytes() {
-  return (2 * BM + 2 * WShape<NW, NM>::BNG) * F_RB;
+  return (2 * BM + (PAIR ? 1 : 2) * WShape<NW, NM>::BNG) * F_RB;
 }
 template <int NM>
 constexpr int f_tab_bytes() {
   return 32 * (8 * NM * NM + 4 * 2 * NM);  // per vertex warp
 }
-template <int NW, int NM>
+template <int NW, int NM, bool PAIR>
 constexpr int f_smem() {
-  return f_stages<NM>() * f_stage_bytes<NW, NM>() + 4 * f_tab_bytes<NM>() + 1024;
+  return f_stages<NM, PAIR>() * f_stage_bytes<NW, NM, PAIR>() + 4 * f_tab_bytes<NM>() + 1024;
+}
+// Item -> (k, q tile): one q tile per item for a single CTA; a pair takes two neighbouring
+// q tiles per item, rank r the tile 2 u + r (the second may lie past nq: its rows are invalid).
+template <bool PAIR>
+__device__ __forceinline__ void f_coords(const TcwArgs &a, int item, uint32_t rank, int &kl, int &qt) {
+  if constexpr (PAIR) {
+    int u;
+    w_coords_n((a.nqt + 1) / 2, a.qblock > 1 ? a.qblock / 2 : 1, a.ngrp, item, kl, u);
+    qt = 2 * u + (int)rank;
+  } else {
+    w_coords(a, item, kl, qt);
+  }
 }
 
 // Linewidth terms of the entries (k, n0) and (k, n0 + 1) of one vertex chunk for the
@@ -648,7 +676,7 @@ __device__ __forceinline__ void g_chunk(const TcwArgs &a, uint32_t tcol, int n0,
   }
 }
 
-template <int OP, int NW, int NM>
+template <int OP, int NW, int NM, bool PAIR>
 __global__ void __launch_bounds__(32 * F_WARPS, 1)
     k_tcwf(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
            const __grid_constant__ CUtensorMap mEhi, const __grid_constant__ CUtensorMap mElo,
@@ -656,14 +684,17 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
            const __grid_constant__ CUtensorMap mGhi, const __grid_constant__ CUtensorMap mGlo, TcwArgs a) {
   using O = WOp<OP>;
   using S = WShape<NW, NM>;
-  constexpr int F_STAGES = f_stages<NM>();
+  constexpr int F_STAGES = f_stages<NM, PAIR>();
   constexpr int BK = F_RB / O::ESZ;
   constexpr int CPK = S::CPK, BNG = S::BNG, CN = S::CN;
   static_assert(CN == 2, "vertex chunks of two entries");
   constexpr int NCH = (NW + CN - 1) / CN;  // vertex chunks per k
   constexpr int A_BYTES = BM * F_RB;
-  constexpr int STAGE = f_stage_bytes<NW, NM>();
-  constexpr uint32_t ID_H = w_idesc<OP, CPK>(), ID_G = w_idesc<OP, BNG>();
+  constexpr int STAGE = f_stage_bytes<NW, NM, PAIR>();
+  constexpr int BROWS = PAIR ? BNG / 2 : BNG;  // B rows of a stage held by this CTA
+  constexpr uint32_t ID_H = PAIR ? w_idesc_pair<OP, CPK>() : w_idesc<OP, CPK>();
+  constexpr uint32_t ID_G = PAIR ? w_idesc_pair<OP, BNG>() : w_idesc<OP, BNG>();
+  static_assert(!PAIR || (CPK % 32 == 0 && BNG % 32 == 0), "a pair's MMA splits N in halves of 16-column multiples");
   constexpr uint32_t GCOL0 = CPK;  // tensor-memory columns: H [0, cpk), vertex stages cpk + s bng
   static_assert(CPK + 2 * BNG <= 512, "tensor memory");
   __shared__ __align__(8) uint64_t bar_full[F_STAGES], bar_empty[F_STAGES], bar_hfull, bar_hempty, bar_gfull[2],
@@ -674,8 +705,14 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
   const uint32_t smem0 = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int *abort_flag = &abort_sh;
-  const int nitems = a.ngrp * a.nqt;
-  const int nmy = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // a pair (cluster of two CTAs) shares each item: the leader (rank 0) issues the MMAs for
+  // both, the epilogue warps of both arrive on the leader's tensor-memory barriers
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const bool leader = rank == 0;
+  const int cid = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int ncl = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int nitems = a.ngrp * (PAIR ? (a.nqt + 1) / 2 : a.nqt);
+  const int nmy = nitems > cid ? (nitems - 1 - cid) / ncl + 1 : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < F_STAGES; s++) {
@@ -683,10 +720,10 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
     mbar_init(smem_u32(&bar_hfull), 1);
-    mbar_init(smem_u32(&bar_hempty), 4);
+    mbar_init(smem_u32(&bar_hempty), PAIR ? 8 : 4);
     for (int s = 0; s < 2; s++) {
       mbar_init(smem_u32(&bar_gfull[s]), 1);
-      mbar_init(smem_u32(&bar_gempty[s]), 4);
+      mbar_init(smem_u32(&bar_gempty[s]), PAIR ? 8 : 4);
       for (int qd = 0; qd < 4; qd++) {
         mbar_init(smem_u32(&bar_efull[s][qd]), 1);
         mbar_init(smem_u32(&bar_eempty[s][qd]), 1);
@@ -697,13 +734,23 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc_pair(smem_u32(&tmem_base_sh), TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // both CTAs' barriers and tensor memory exist
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
+  // the leader's barriers that the pair's loads and epilogue warps signal
+  const uint32_t full_c0 = PAIR ? cluster_addr(smem_u32(&bar_full[0]), 0) : smem_u32(&bar_full[0]);
+  const uint32_t hempty_c = PAIR ? cluster_addr(smem_u32(&bar_hempty), 0) : smem_u32(&bar_hempty);
+  const uint32_t gempty_c0 = PAIR ? cluster_addr(smem_u32(&bar_gempty[0]), 0) : smem_u32(&bar_gempty[0]);
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -722,12 +769,24 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
           ok = wait_bar(smem_u32(&bar_empty[s]), par, abort_flag, a.dstatus);
           if (ok) {
             const uint32_t base = smem0 + s * STAGE;
-            const uint32_t fb = smem_u32(&bar_full[s]);
-            mbar_expect_tx(fb, 2 * A_BYTES + 2 * brows * F_RB);
-            tma_load_2d(base, ah, kb * BK, qt * BM, fb);
-            tma_load_2d(base + A_BYTES, al, kb * BK, qt * BM, fb);
-            tma_load_2d(base + 2 * A_BYTES, bh, kb * BK, row0, fb);
-            tma_load_2d(base + 2 * A_BYTES + BNG * F_RB, bl, kb * BK, row0, fb);
+            if constexpr (PAIR) {
+              // this CTA's A tile and its half of the B rows; the leader's barrier counts
+              // the bytes of both CTAs
+              const uint32_t fb = full_c0 + 8u * (uint32_t)s;
+              if (leader) mbar_expect_tx(smem_u32(&bar_full[s]), 2 * (2 * A_BYTES + brows * F_RB));
+              const int hrow = row0 + (int)rank * (int)(brows / 2);
+              tma_load_2d_pair(base, ah, kb * BK, qt * BM, fb);
+              tma_load_2d_pair(base + A_BYTES, al, kb * BK, qt * BM, fb);
+              tma_load_2d_pair(base + 2 * A_BYTES, bh, kb * BK, hrow, fb);
+              tma_load_2d_pair(base + 2 * A_BYTES + BROWS * F_RB, bl, kb * BK, hrow, fb);
+            } else {
+              const uint32_t fb = smem_u32(&bar_full[s]);
+              mbar_expect_tx(fb, 2 * A_BYTES + 2 * brows * F_RB);
+              tma_load_2d(base, ah, kb * BK, qt * BM, fb);
+              tma_load_2d(base + A_BYTES, al, kb * BK, qt * BM, fb);
+              tma_load_2d(base + 2 * A_BYTES, bh, kb * BK, row0, fb);
+              tma_load_2d(base + 2 * A_BYTES + BNG * F_RB, bl, kb * BK, row0, fb);
+            }
             issued[s] = (int)(it / F_STAGES) + 1;
           }
         }
@@ -737,17 +796,17 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
     for (int st = 0; st <= nmy && ok; st++) {
       if (st < nmy) {
         int kl, qt;
-        w_coords(a, blockIdx.x + st * gridDim.x, kl, qt);
+        f_coords<PAIR>(a, cid + st * ncl, rank, kl, qt);
         load_group(qt, &mAhi, &mAlo, &mEhi, &mElo, kl * CPK, CPK, a.nkb);
       }
       if (st >= 1) {
         int kl, qt;
-        w_coords(a, blockIdx.x + (st - 1) * gridDim.x, kl, qt);
+        f_coords<PAIR>(a, cid + (st - 1) * ncl, rank, kl, qt);
         for (int c = 0; c < NCH && ok; c++)
           load_group(qt, &mAGhi, &mAGlo, &mGhi, &mGlo, (kl * NCH + c) * BNG, BNG, a.nkbG);
       }
     }
-    if (lane == 0) {
+    if (lane == 0 && leader) {  // (a pair's loads complete on the leader's barriers)
 #pragma unroll
       for (int s = 0; s < F_STAGES; s++)
         if (issued[s] > 0) drain_bar(smem_u32(&bar_full[s]), (uint32_t)((issued[s] - 1) & 1));
@@ -769,22 +828,38 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
             const uint32_t base = smem0 + s * STAGE;
             const uint64_t dAh = sdesc_sw<F_RB>(base), dAl = sdesc_sw<F_RB>(base + A_BYTES);
             const uint64_t dBh = sdesc_sw<F_RB>(base + 2 * A_BYTES);
-            const uint64_t dBl = sdesc_sw<F_RB>(base + 2 * A_BYTES + BNG * F_RB);
+            const uint64_t dBl = sdesc_sw<F_RB>(base + 2 * A_BYTES + BROWS * F_RB);
             const int ksteps = min(BK, kpad - kb * BK) / O::KSTEP;
             for (int ks = 0; ks < ksteps; ks++) {
               const uint64_t off = (uint64_t)((ks * 32) >> 4);
               const uint32_t acc = (kb == 0 && ks == 0) ? 0u : 1u;
-              umma_id<O::F16>(dcol, dAl + off, dBh + off, idesc, acc);
-              umma_id<O::F16>(dcol, dAh + off, dBl + off, idesc, 1u);
-              umma_id<O::F16>(dcol, dAh + off, dBh + off, idesc, 1u);
+              if constexpr (PAIR) {
+                umma_pair<O::F16>(dcol, dAl + off, dBh + off, idesc, acc);
+                umma_pair<O::F16>(dcol, dAh + off, dBl + off, idesc, 1u);
+                umma_pair<O::F16>(dcol, dAh + off, dBh + off, idesc, 1u);
+              } else {
+                umma_id<O::F16>(dcol, dAl + off, dBh + off, idesc, acc);
+                umma_id<O::F16>(dcol, dAh + off, dBl + off, idesc, 1u);
+                umma_id<O::F16>(dcol, dAh + off, dBh + off, idesc, 1u);
+              }
             }
-            umma_commit(smem_u32(&bar_empty[s]));
+            if constexpr (PAIR)
+              umma_commit_pair(smem_u32(&bar_empty[s]));
+            else
+              umma_commit(smem_u32(&bar_empty[s]));
           }
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
       }
     };
-    for (int st = 0; st <= nmy && ok; st++) {
+    auto commit = [&](uint32_t bar) {
+      if constexpr (PAIR)
+        umma_commit_pair(bar);
+      else
+        umma_commit(bar);
+    };
+    // a pair's second CTA issues no MMAs: the leader's land in both CTAs' tensor memory
+    for (int st = 0; st <= nmy && ok && leader; st++) {
       if (st < nmy) {
         if (lane == 0) ok = wait_bar(smem_u32(&bar_hempty), (uint32_t)((hcount & 1) ^ 1), abort_flag, a.dstatus);
         ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -792,7 +867,7 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
         tc_fence_after();
         mma_group(tmem, ID_H, a.nkb, a.kpad);
         if (!ok) break;
-        if (lane == 0) umma_commit(smem_u32(&bar_hfull));
+        if (lane == 0) commit(smem_u32(&bar_hfull));
         __syncwarp();
         hcount++;
       }
@@ -806,14 +881,14 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
           tc_fence_after();
           mma_group(tmem + GCOL0 + gs * BNG, ID_G, a.nkbG, a.kpadG);
           if (!ok) break;
-          if (lane == 0) umma_commit(smem_u32(&bar_gfull[gs]));
+          if (lane == 0) commit(smem_u32(&bar_gfull[gs]));
           __syncwarp();
         }
       }
     }
-    if (lane == 0) {
-      umma_commit(smem_u32(&bar_final));
-      drain_bar(smem_u32(&bar_final), 0);
+    if (lane == 0 && leader) {
+      commit(smem_u32(&bar_final));
+      drain_bar(smem_u32(&bar_final), 0);  // every MMA (into both CTAs' tensor memory) is complete
     }
     __syncwarp();
   } else if (warp < 6) {
@@ -822,7 +897,7 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
     const int idx = quad * 32 + lane;
     for (int j = 0; j < nmy; j++) {
       int kl, qt;
-      w_coords(a, blockIdx.x + j * gridDim.x, kl, qt);
+      f_coords<PAIR>(a, cid + j * ncl, rank, kl, qt);
       const int q = qt * BM + idx;
       const bool valid = q < a.nq && kl < a.kc;
       bool ok = wait_bar(smem_u32(&bar_hfull), (uint32_t)(j & 1), abort_flag, a.dstatus);
@@ -831,8 +906,8 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
       const int slot = j & 1;
       const size_t so = ((size_t)blockIdx.x * 2 + slot);
       const EigView v{a.epsq + so * NW * BM, a.Uq + so * NW * NW * BM, (size_t)BM, idx};
-      ok = eig_pair<NW, true>(a, tmem + ((uint32_t)(quad * 32) << 16), q, a.k0 + kl, v, valid, smem_u32(&bar_hempty),
-                              smem_u32(&bar_eempty[slot][quad]), (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag);
+      ok = eig_pair<NW, true>(a, tmem + ((uint32_t)(quad * 32) << 16), q, a.k0 + kl, v, valid, hempty_c,
+                              smem_u32(&bar_eempty[slot][quad]), (uint32_t)(((j >> 1) & 1) ^ 1), abort_flag, PAIR);
       if (!ok) break;
       __threadfence_block();
       __syncwarp();
@@ -851,9 +926,9 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
     bool ok = true;
     for (int j = 0; j < nmy && ok; j++) {
       int kl, qt;
-      w_coords(a, blockIdx.x + j * gridDim.x, kl, qt);
+      f_coords<PAIR>(a, cid + j * ncl, rank, kl, qt);
       const int q = qt * BM + idx;
-      const bool kval = kl < a.kc;
+      const bool kval = kl < a.kc && qt < a.nqt;
       const bool valid = q < a.nq && kval;
       const int qq = valid ? q : 0;
       const int kg = kval ? a.k0 + kl : 0;
@@ -918,7 +993,12 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
         g_chunk<NW, NM>(a, tcol, n0, qq, kg, v, em, ek, r0, r1, tabE, tabW, acc0, acc1);
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bar_gempty[gs]));
+        if (lane == 0) {
+          if constexpr (PAIR)
+            mbar_arrive_cluster(gempty_c0 + 8u * (uint32_t)gs);
+          else
+            mbar_arrive(smem_u32(&bar_gempty[gs]));
+        }
         float v0 = acc0 * wqv, v1 = acc1 * wqv;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -937,10 +1017,15 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // neither CTA frees tensor memory the pair still uses
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    if constexpr (PAIR)
+      tmem_dealloc_pair(tmem, TMEM_COLS);
+    else
+      tmem_dealloc(tmem, TMEM_COLS);
   }
+  if constexpr (PAIR) cluster_sync();
 }
 
 // ------------------------------------------------------- operand builder G
@@ -1024,19 +1109,38 @@ cudaError_t launch_tcw(const CUtensorMap &ah, const CUtensorMap &al, const CUten
   return cudaGetLastError();
 }
 
-template <int OP, int NW, int NM>
+template <int OP, int NW, int NM, bool PAIR>
 cudaError_t launch_tcwf(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &eh, const CUtensorMap &el,
                         const CUtensorMap &agh, const CUtensorMap &agl, const CUtensorMap &gh, const CUtensorMap &gl,
                         const TcwArgs &a, int grid, cudaStream_t st) {
-  constexpr int SMEM = f_smem<NW, NM>();
+  constexpr int SMEM = f_smem<NW, NM, PAIR>();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tcwf<OP, NW, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_tcwf<OP, NW, NM, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_tcwf<OP, NW, NM><<<grid, 32 * F_WARPS, SMEM, st>>>(ah, al, eh, el, agh, agl, gh, gl, a);
-  epw_count_launch();
+  if constexpr (PAIR) {
+    // clusters of two CTAs (grid even)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(32 * F_WARPS, 1, 1);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tcwf<OP, NW, NM, true>, ah, al, eh, el, agh, agl, gh, gl, a);
+    epw_count_launch();
+    if (e != cudaSuccess) return e;
+  } else {
+    k_tcwf<OP, NW, NM, false><<<grid, 32 * F_WARPS, SMEM, st>>>(ah, al, eh, el, agh, agl, gh, gl, a);
+    epw_count_launch();
+  }
   return cudaGetLastError();
 }
 
@@ -1053,12 +1157,12 @@ cudaError_t launch_tcw_shape(int nw, int nm, const CUtensorMap &ah, const CUtens
   return cudaErrorInvalidValue;
 }
 
-template <int OP>
+template <int OP, bool PAIR>
 cudaError_t launch_tcwf_shape(int nw, int nm, const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &eh,
                               const CUtensorMap &el, const CUtensorMap &agh, const CUtensorMap &agl,
                               const CUtensorMap &gh, const CUtensorMap &gl, const TcwArgs &a, int grid, cudaStream_t st) {
 #define EPW_TCWF_CASE(W, M) \
-  if (nw == W && nm == M) return launch_tcwf<OP, W, M>(ah, al, eh, el, agh, agl, gh, gl, a, grid, st);
+  if (nw == W && nm == M) return launch_tcwf<OP, W, M, PAIR>(ah, al, eh, el, agh, agl, gh, gl, a, grid, st);
   EPW_TCW_SHAPES(EPW_TCWF_CASE)
 #undef EPW_TCWF_CASE
   return cudaErrorInvalidValue;
@@ -1090,12 +1194,13 @@ bool tcw_supported(const epw_model *m) {
   return tcw_shape(m->nw, m->nm, cpk, kpt, entp, cn, bng);
 }
 
-epw_status tcw_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t bytes, TcwBuffers &b, bool split) {
+epw_status tcw_plan(Arena &A, const epw_model *m, int nk, int nq, int op, size_t bytes, TcwBuffers &b, int form) {
   b = TcwBuffers{};
   b.op = op;
   b.ok = tcw_shape(m->nw, m->nm, b.cpk, b.kpt, b.entp, b.cn, b.bng);
   if (!b.ok) return EPW_OK;
-  b.fused = !split;
+  b.fused = form != TCW_FORM_SPLIT;
+  b.pair = form == TCW_FORM_PAIR;
   nk = std::max(nk, 1);
   nq = std::max(nq, 1);
   const int nw = m->nw, nm = m->nm;
@@ -1194,13 +1299,16 @@ epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, co
   if (b.fused) {
     const int nch = (nw + b.cn - 1) / b.cn;
     CUtensorMap ah, al, eh, el, agh, agl, gh, gl;
+    // a CTA pair loads half of the B rows in each CTA
+    const uint32_t ebox = b.pair ? (uint32_t)b.cpk / 2 : (uint32_t)b.cpk;
+    const uint32_t gbox = b.pair ? (uint32_t)b.bng / 2 : (uint32_t)b.bng;
     if (!tc_make_map_rb(&ah, b.Ahi, op, b.kpad, nq, BM, F_RB) || !tc_make_map_rb(&al, b.Alo, op, b.kpad, nq, BM, F_RB) ||
         !tc_make_map_rb(&agh, b.AGhi, op, b.kpadG, nq, BM, F_RB) ||
         !tc_make_map_rb(&agl, b.AGlo, op, b.kpadG, nq, BM, F_RB) ||
-        !tc_make_map_rb(&eh, b.BEhi, op, b.kpad, (uint64_t)b.kc * b.cpk, (uint32_t)b.cpk, F_RB) ||
-        !tc_make_map_rb(&el, b.BElo, op, b.kpad, (uint64_t)b.kc * b.cpk, (uint32_t)b.cpk, F_RB) ||
-        !tc_make_map_rb(&gh, b.BGhi, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, (uint32_t)b.bng, F_RB) ||
-        !tc_make_map_rb(&gl, b.BGlo, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, (uint32_t)b.bng, F_RB))
+        !tc_make_map_rb(&eh, b.BEhi, op, b.kpad, (uint64_t)b.kc * b.cpk, ebox, F_RB) ||
+        !tc_make_map_rb(&el, b.BElo, op, b.kpad, (uint64_t)b.kc * b.cpk, ebox, F_RB) ||
+        !tc_make_map_rb(&gh, b.BGhi, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, gbox, F_RB) ||
+        !tc_make_map_rb(&gl, b.BGlo, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, gbox, F_RB))
       return EPW_ERR_CUDA;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -1229,11 +1337,18 @@ epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, co
       a.k0 = k0;
       a.kc = kc;
       a.ngrp = kc;
-      const int grid = (int)std::min<long>((long)kc * b.nqt, (long)sms);
       epw_timing_begin_tag(mm, st, 0);
-      const cudaError_t e = op == TC_OP_BF16
-                                ? launch_tcwf_shape<TC_OP_BF16>(nw, nm, ah, al, eh, el, agh, agl, gh, gl, a, grid, st)
-                                : launch_tcwf_shape<TC_OP_TF32>(nw, nm, ah, al, eh, el, agh, agl, gh, gl, a, grid, st);
+      cudaError_t e;
+      if (b.pair) {
+        // clusters of two CTAs, each cluster two q tiles of one k per item
+        const int grid = 2 * (int)std::min<long>((long)kc * ((b.nqt + 1) / 2), (long)(sms / 2));
+        e = op == TC_OP_BF16 ? launch_tcwf_shape<TC_OP_BF16, true>(nw, nm, ah, al, eh, el, agh, agl, gh, gl, a, grid, st)
+                             : launch_tcwf_shape<TC_OP_TF32, true>(nw, nm, ah, al, eh, el, agh, agl, gh, gl, a, grid, st);
+      } else {
+        const int grid = (int)std::min<long>((long)kc * b.nqt, (long)sms);
+        e = op == TC_OP_BF16 ? launch_tcwf_shape<TC_OP_BF16, false>(nw, nm, ah, al, eh, el, agh, agl, gh, gl, a, grid, st)
+                             : launch_tcwf_shape<TC_OP_TF32, false>(nw, nm, ah, al, eh, el, agh, agl, gh, gl, a, grid, st);
+      }
       epw_timing_end(mm, st);
       if (e != cudaSuccess) return EPW_ERR_CUDA;
     }

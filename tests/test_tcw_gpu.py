@@ -1,11 +1,11 @@
 """Wide-shape fused tensor-core form against the FP64 oracle.
 
 Shapes whose per-k columns exceed the fused kernel's 128-column slot and have a
-compiled wide form ((nw, 3nat) = (8, 6) and (5, 9)) run two tcgen05 kernels per
-chunk of k: E contracts H(k+q) and diagonalises it per pair (writing the
-eigenvalues and the eigenvectors that some band at k can reach within the
-Gaussian cutoff), G contracts (g_a(k,q) U_k) and evaluates only those (m, n)
-terms.  The skipped Gaussians are ones that flush to zero in FP32, so the sums
+compiled wide form ((nw, 3nat) = (8, 6) and (5, 9)) contract H(k+q) and
+diagonalise it per pair (keeping the eigenvalues and the eigenvectors that some
+band at k can reach within the Gaussian cutoff), then contract (g_a(k,q) U_k)
+and evaluate only those (m, n) terms: in one persistent kernel on CTA pairs (the
+default), on single CTAs, or as two kernels per chunk of k.  The skipped Gaussians are ones that flush to zero in FP32, so the sums
 are the dense ones; these tests pin the results to the oracle on edge cases
 (every term reachable, almost none, none, zero temperature, a polar vertex,
 ragged k and q) and, at the two configurations' full q lists, on sampled k
@@ -140,24 +140,31 @@ def test_wide_workload_full_size_sampled_k(epw, name, prec):
     assert err < 1e-4
 
 
+@pytest.mark.parametrize("nk,nq", [(9, 700), (5, 300)])
 @pytest.mark.parametrize("lat,nw,nat,masses", SHAPES)
-def test_wide_fused_and_split_kernels_agree(epw, lat, nw, nat, masses):
-    """The fused kernel (eigensolve beside the vertex MMAs, eigen-data through an L2 ring) and
-    the two-kernel form (EPW_WIDE_FORM=split) run the same arithmetic: agreement to FP32 rounding
-    on a ragged problem (9 k over several fused work items, 700 q)."""
-    rng = np.random.default_rng(1230 + nw)
+def test_wide_forms_agree(epw, lat, nw, nat, masses, nk, nq):
+    """The fused kernel on CTA pairs (default: 2-SM MMAs over 256 q rows, each CTA holding half
+    of the B columns), the fused kernel on single CTAs (EPW_WIDE_FORM=single) and the two-kernel
+    form (EPW_WIDE_FORM=split) run the same arithmetic: agreement to FP32 rounding on ragged
+    problems (several fused work items; 300 q is three q tiles, so the last pair has one tile
+    past the list)."""
+    rng = np.random.default_rng(1230 + nw + nq)
     wm = W.make_model(lat, nw, nat, list(masses), 30, 30, rng)
-    k = rng.random((9, 3))
-    q = rng.random((700, 3))
+    k = rng.random((nk, 3))
+    q = rng.random((nq, 3))
     m = epw.Model(wm)
     kw = dict(T=300.0, EF=0.1, sigma=0.03, precision=epw.BF16X3)
-    fused = m.linewidth(k, q, **kw)
-    os.environ["EPW_WIDE_FORM"] = "split"
-    try:
-        split = m.linewidth(k, q, **kw)
-    finally:
-        del os.environ["EPW_WIDE_FORM"]
+    pair = m.linewidth(k, q, **kw)
+    out = {}
+    for form in ("single", "split"):
+        os.environ["EPW_WIDE_FORM"] = form
+        try:
+            out[form] = m.linewidth(k, q, **kw)
+        finally:
+            del os.environ["EPW_WIDE_FORM"]
     m.sync()
-    err = _rel(fused, split)
-    print(lat, nw, "fused vs split max rel diff", err)
-    assert err < 1e-6
+    for form, o in out.items():
+        err = _rel(pair, o)
+        print(lat, nw, nk, nq, "pair vs", form, "max rel diff", err)
+        assert err < 1e-6
+    assert np.all(pair >= 0)
