@@ -166,7 +166,8 @@ epw_status epw_interp_g(const epw_model *model, int nk, const double *k, int nq,
  * q list with weights wq (NULL: 1/nq each).  Sums of the positive terms are
  * deterministic (fixed order, compensated in FP64).
  * Split precisions run on the tensor cores: models whose per-k columns
- * 2 nw^2 (3nat + 1) fit 128 take one fused kernel; (nw, 3nat) = (8, 6) and
+ * 2 nw^2 (3nat + 1) fit 128 take one fused kernel (on CTA pairs, 2-SM MMAs over
+ * 256 q rows; EPW_NARROW_FORM=single selects single CTAs); (nw, 3nat) = (8, 6) and
  * (5, 9) take the wide-shape form (H(k+q) eigensolve beside the vertex
  * contraction; only terms whose Gaussians do not underflow in FP32 are
  * evaluated, which leaves the sums unchanged), whose fused kernel runs on CTA

@@ -48,6 +48,14 @@ constexpr int A_BYTES = BM * ROWB;    // 16 KiB
 constexpr int B_BYTES = BN * ROWB;    // 32 KiB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+// A CTA pair (cluster of two CTAs, cta_group::2 MMAs with M = 256 over two neighbouring q
+// tiles) holds half of the B rows per CTA, so its stages are smaller and three fit.
+template <bool PAIR>
+constexpr int tc_stages() { return PAIR ? 3 : STAGES; }
+template <bool PAIR>
+constexpr int tc_stage_bytes() { return 2 * A_BYTES + 2 * (PAIR ? B_BYTES / 2 : B_BYTES); }
+template <bool PAIR>
+constexpr int tc_smem_bytes() { return tc_stages<PAIR>() * tc_stage_bytes<PAIR>() + 1024; }
 constexpr int EPI_WARP0 = 2;
 constexpr int ITEMS_PER_TILE = 8;     // (lane quadrant, k slot) items per tile
 // Epilogue warps per form, a multiple of 4 (one group per TMEM lane quadrant; a
@@ -75,6 +83,9 @@ struct OpT<TC_OP_BF16> {
   // kind::f16 instruction descriptor: D=F32, A=B=BF16, K-major, N=256, M=128
   static constexpr uint32_t IDESC =
       (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static constexpr uint32_t IDESC_PAIR =  // M = 256 (128 rows in each CTA of the pair)
+      (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+  static constexpr bool F16 = true;
 };
 template <>
 struct OpT<TC_OP_TF32> {
@@ -85,6 +96,9 @@ struct OpT<TC_OP_TF32> {
   // kind::tf32 instruction descriptor: D=F32, A=B=TF32, K-major, N=256, M=128
   static constexpr uint32_t IDESC =
       (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static constexpr uint32_t IDESC_PAIR =
+      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24);
+  static constexpr bool F16 = false;
 };
 
 template <int OP>
@@ -167,15 +181,30 @@ constexpr int tab_bytes() {
 }
 
 // Tile -> (k group, q tile) in q-blocks of `qblock` tiles, k-group-major inside a block.
-__device__ __forceinline__ void item_coords(const TcArgs &a, int item, int &kg, int &qt) {
-  const int per = a.qblock * a.nkg;
-  const int nb = (a.nqt + a.qblock - 1) / a.qblock;
+__device__ __forceinline__ void item_coords_n(int nqt, int qblock, int nkg, int item, int &kg, int &qt) {
+  const int per = qblock * nkg;
+  const int nb = (nqt + qblock - 1) / qblock;
   int b = item / per;
   if (b > nb - 1) b = nb - 1;
   const int r = item - b * per;
-  const int qbs = min(a.qblock, a.nqt - b * a.qblock);
+  const int qbs = min(qblock, nqt - b * qblock);
   kg = r / qbs;
-  qt = b * a.qblock + r % qbs;
+  qt = b * qblock + r % qbs;
+}
+__device__ __forceinline__ void item_coords(const TcArgs &a, int item, int &kg, int &qt) {
+  item_coords_n(a.nqt, a.qblock, a.nkg, item, kg, qt);
+}
+// A CTA pair takes two neighbouring q tiles per item, rank r the tile 2 u + r (the second may
+// lie past nq: its rows are invalid and its partial sums are not written).
+template <bool PAIR>
+__device__ __forceinline__ void item_coords_p(const TcArgs &a, int item, uint32_t rank, int &kg, int &qt) {
+  if constexpr (PAIR) {
+    int u;
+    item_coords_n((a.nqt + 1) / 2, a.qblock > 1 ? a.qblock / 2 : 1, a.nkg, item, kg, u);
+    qt = 2 * u + (int)rank;
+  } else {
+    item_coords(a, item, kg, qt);
+  }
 }
 
 // Real column of the re (s = 0) or im (s = 1) part of complex column c of one
@@ -770,79 +799,109 @@ __device__ __forceinline__ void epilogue_pair(const TcArgs &a, uint32_t tcol, in
   }
 }
 
-template <int OP, int NW, int NM, int MODE>
+template <int OP, int NW, int NM, int MODE, bool PAIR>
 __global__ void __launch_bounds__(nthreads<MODE>(), 1)
     k_tc_linewidth(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                    const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcArgs a) {
   using S = Shape<NW, NM>;
   using O = OpT<OP>;
-  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_tfull[2], bar_tempty[2], bar_final;
+  static_assert(!PAIR || MODE == 0, "CTA pairs serve the linewidth form");
+  constexpr int NSTAGE = tc_stages<PAIR>();
+  constexpr int STAGE = tc_stage_bytes<PAIR>();
+  constexpr int BROWS = PAIR ? BN / 2 : BN;  // B rows of a stage held by this CTA
+  __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_tfull[2], bar_tempty[2], bar_final;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t smem0 = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int *abort_flag = &abort_sh;
-  const int nitems = a.nkg * a.nqt;
+  // a pair (cluster of two CTAs) shares each item: the leader (rank 0) issues the MMAs for
+  // both, the epilogue warps of both release tensor memory on the leader's barriers
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const bool leader = rank == 0;
+  const int cid = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int ncl = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int nitems = a.nkg * (PAIR ? (a.nqt + 1) / 2 : a.nqt);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; s++) {
+    for (int s = 0; s < NSTAGE; s++) {
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
     for (int s = 0; s < 2; s++) {
       mbar_init(smem_u32(&bar_tfull[s]), 1);
-      mbar_init(smem_u32(&bar_tempty[s]), ITEMS_PER_TILE);
+      mbar_init(smem_u32(&bar_tempty[s]), PAIR ? 2 * ITEMS_PER_TILE : ITEMS_PER_TILE);
     }
     mbar_init(smem_u32(&bar_final), 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc_pair(smem_u32(&tmem_base_sh), TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // both CTAs' barriers and tensor memory exist
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
+  const uint32_t full_c0 = PAIR ? cluster_addr(smem_u32(&bar_full[0]), 0) : smem_u32(&bar_full[0]);
+  const uint32_t tempty_c0 = PAIR ? cluster_addr(smem_u32(&bar_tempty[0]), 0) : smem_u32(&bar_tempty[0]);
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     // The whole warp walks the schedule; lane 0 waits and issues the copies.
-    int issued0 = 0, issued1 = 0;
+    int issued[NSTAGE];
+#pragma unroll
+    for (int s = 0; s < NSTAGE; s++) issued[s] = 0;
     uint32_t it = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    for (int item = cid; item < nitems && ok; item += ncl) {
       int kg, qt;
-      item_coords(a, item, kg, qt);
+      item_coords_p<PAIR>(a, item, rank, kg, qt);
       for (int kb = 0; kb < a.nkb; kb++, it++) {
-        const int s = it % STAGES;
-        const uint32_t par = ((it / STAGES) & 1u) ^ 1u;
+        const int s = it % NSTAGE;
+        const uint32_t par = ((it / NSTAGE) & 1u) ^ 1u;
         if (lane == 0) {
           ok = wait_bar(smem_u32(&bar_empty[s]), par, abort_flag, a.dstatus);
           if (ok) {
-            const uint32_t base = smem0 + s * STAGE_BYTES;
-            const uint32_t fb = smem_u32(&bar_full[s]);
-            mbar_expect_tx(fb, STAGE_BYTES);
-            tma_load_2d(base, &mAhi, kb * O::BK, qt * BM, fb);
-            tma_load_2d(base + A_BYTES, &mAlo, kb * O::BK, qt * BM, fb);
-            tma_load_2d(base + 2 * A_BYTES, &mBhi, kb * O::BK, kg * (S::KPT * S::CPK), fb);
-            tma_load_2d(base + 2 * A_BYTES + B_BYTES, &mBlo, kb * O::BK, kg * (S::KPT * S::CPK), fb);
-            if (s == 0)
-              issued0 = (int)(it / STAGES) + 1;
-            else
-              issued1 = (int)(it / STAGES) + 1;
+            const uint32_t base = smem0 + s * STAGE;
+            const int brow = kg * (S::KPT * S::CPK) + (int)rank * BROWS;
+            if constexpr (PAIR) {
+              // this CTA's A tile and half of the B rows; the leader's barrier counts both CTAs'
+              const uint32_t fb = full_c0 + 8u * (uint32_t)s;
+              if (leader) mbar_expect_tx(smem_u32(&bar_full[s]), 2 * STAGE);
+              tma_load_2d_pair(base, &mAhi, kb * O::BK, qt * BM, fb);
+              tma_load_2d_pair(base + A_BYTES, &mAlo, kb * O::BK, qt * BM, fb);
+              tma_load_2d_pair(base + 2 * A_BYTES, &mBhi, kb * O::BK, brow, fb);
+              tma_load_2d_pair(base + 2 * A_BYTES + BROWS * ROWB, &mBlo, kb * O::BK, brow, fb);
+            } else {
+              const uint32_t fb = smem_u32(&bar_full[s]);
+              mbar_expect_tx(fb, STAGE);
+              tma_load_2d(base, &mAhi, kb * O::BK, qt * BM, fb);
+              tma_load_2d(base + A_BYTES, &mAlo, kb * O::BK, qt * BM, fb);
+              tma_load_2d(base + 2 * A_BYTES, &mBhi, kb * O::BK, brow, fb);
+              tma_load_2d(base + 2 * A_BYTES + B_BYTES, &mBlo, kb * O::BK, brow, fb);
+            }
+            issued[s] = (int)(it / NSTAGE) + 1;
           }
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
       }
     }
-    // drain: every issued copy must land before the CTA exits
-    if (lane == 0) {
-      if (issued0 > 0) drain_bar(smem_u32(&bar_full[0]), (uint32_t)((issued0 - 1) & 1));
-      if (issued1 > 0) drain_bar(smem_u32(&bar_full[1]), (uint32_t)((issued1 - 1) & 1));
+    // drain: every issued copy must land before the CTA exits (a pair's loads complete on
+    // the leader's barriers)
+    if (lane == 0 && leader) {
+#pragma unroll
+      for (int s = 0; s < NSTAGE; s++)
+        if (issued[s] > 0) drain_bar(smem_u32(&bar_full[s]), (uint32_t)((issued[s] - 1) & 1));
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -851,7 +910,14 @@ __global__ void __launch_bounds__(nthreads<MODE>(), 1)
     uint32_t it = 0;
     int titer = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, titer++) {
+    auto commit = [&](uint32_t bar) {
+      if constexpr (PAIR)
+        umma_commit_pair(bar);
+      else
+        umma_commit(bar);
+    };
+    // a pair's second CTA issues no MMAs: the leader's land in both CTAs' tensor memory
+    for (int item = cid; item < nitems && ok && leader; item += ncl, titer++) {
       const int ts = titer & 1;
       const uint32_t tpar = ((titer >> 1) & 1) ^ 1;
       if (lane == 0) ok = wait_bar(smem_u32(&bar_tempty[ts]), tpar, abort_flag, a.dstatus);
@@ -860,36 +926,42 @@ __global__ void __launch_bounds__(nthreads<MODE>(), 1)
       tc_fence_after();
       const uint32_t dcol = tmem + ts * BN;
       for (int kb = 0; kb < a.nkb; kb++, it++) {
-        const int s = it % STAGES;
-        const uint32_t par = (it / STAGES) & 1u;
+        const int s = it % NSTAGE;
+        const uint32_t par = (it / NSTAGE) & 1u;
         if (lane == 0) {
           ok = wait_bar(smem_u32(&bar_full[s]), par, abort_flag, a.dstatus);
           if (ok) {
             tc_fence_after();
-            const uint32_t base = smem0 + s * STAGE_BYTES;
+            const uint32_t base = smem0 + s * STAGE;
             const uint64_t dAh = sdesc_sw128(base), dAl = sdesc_sw128(base + A_BYTES);
-            const uint64_t dBh = sdesc_sw128(base + 2 * A_BYTES), dBl = sdesc_sw128(base + 2 * A_BYTES + B_BYTES);
+            const uint64_t dBh = sdesc_sw128(base + 2 * A_BYTES), dBl = sdesc_sw128(base + 2 * A_BYTES + BROWS * ROWB);
             const int ksteps = min(O::BK, a.kpad - kb * O::BK) / O::KSTEP;
             for (int ks = 0; ks < ksteps; ks++) {
               const uint64_t off = (uint64_t)((ks * 32) >> 4);  // 32 bytes of K per MMA
               const uint32_t acc = (kb == 0 && ks == 0) ? 0u : 1u;
-              umma<OP>(dcol, dAl + off, dBh + off, acc);
-              umma<OP>(dcol, dAh + off, dBl + off, 1u);
-              umma<OP>(dcol, dAh + off, dBh + off, 1u);
+              if constexpr (PAIR) {
+                umma_pair<O::F16>(dcol, dAl + off, dBh + off, O::IDESC_PAIR, acc);
+                umma_pair<O::F16>(dcol, dAh + off, dBl + off, O::IDESC_PAIR, 1u);
+                umma_pair<O::F16>(dcol, dAh + off, dBh + off, O::IDESC_PAIR, 1u);
+              } else {
+                umma<OP>(dcol, dAl + off, dBh + off, acc);
+                umma<OP>(dcol, dAh + off, dBl + off, 1u);
+                umma<OP>(dcol, dAh + off, dBh + off, 1u);
+              }
             }
-            umma_commit(smem_u32(&bar_empty[s]));
+            commit(smem_u32(&bar_empty[s]));
           }
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
       }
       if (!ok) break;
-      if (lane == 0) umma_commit(smem_u32(&bar_tfull[ts]));
+      if (lane == 0) commit(smem_u32(&bar_tfull[ts]));
       __syncwarp();
     }
-    // drain: all issued MMAs complete before tensor memory is released
-    if (lane == 0) {
-      umma_commit(smem_u32(&bar_final));
+    // drain: all issued MMAs (into both CTAs' tensor memory) complete before it is released
+    if (lane == 0 && leader) {
+      commit(smem_u32(&bar_final));
       drain_bar(smem_u32(&bar_final), 0);
     }
     __syncwarp();
@@ -902,10 +974,10 @@ __global__ void __launch_bounds__(nthreads<MODE>(), 1)
     constexpr int NG = epi_warps<MODE>() / 4;
     const int quad = warp & 3;
     const int widx = (warp - EPI_WARP0) >> 2;
-    float *tab = reinterpret_cast<float *>(smem_raw + (smem0 - smem_u32(smem_raw)) + STAGES * STAGE_BYTES);
+    float *tab = reinterpret_cast<float *>(smem_raw + (smem0 - smem_u32(smem_raw)) + NSTAGE * STAGE);
     for (int it = widx;; it += NG) {
       const int titer = it >> 1, slot = it & 1;
-      const int item = blockIdx.x + titer * gridDim.x;
+      const int item = cid + titer * ncl;
       if (item >= nitems) break;
       const int ts = titer & 1;
       const uint32_t tpar = (titer >> 1) & 1;
@@ -913,25 +985,37 @@ __global__ void __launch_bounds__(nthreads<MODE>(), 1)
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       int kg, qt;
-      item_coords(a, item, kg, qt);
+      item_coords_p<PAIR>(a, item, rank, kg, qt);
       const int q = qt * BM + quad * 32 + lane;
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + ts * BN + slot * 128;
+      if (qt < a.nqt) {  // (a pair's second tile may lie past the q list)
 #pragma unroll 1
-      for (int j = 0; j < S::KPS; j++) {
-        const int k = kg * S::KPT + slot * S::KPS + j;
-        epilogue_pair<NW, NM, MODE>(a, tbase + j * S::CPK, q, k, q < a.nq && k < a.nk, quad, qt, tab);
+        for (int j = 0; j < S::KPS; j++) {
+          const int k = kg * S::KPT + slot * S::KPS + j;
+          epilogue_pair<NW, NM, MODE>(a, tbase + j * S::CPK, q, k, q < a.nq && k < a.nk, quad, qt, tab);
+        }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[ts]));
+      if (lane == 0) {
+        if constexpr (PAIR)
+          mbar_arrive_cluster(tempty_c0 + 8u * (uint32_t)ts);
+        else
+          mbar_arrive(smem_u32(&bar_tempty[ts]));
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // neither CTA frees tensor memory the pair still uses
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    if constexpr (PAIR)
+      tmem_dealloc_pair(tmem, TMEM_COLS);
+    else
+      tmem_dealloc(tmem, TMEM_COLS);
   }
+  if constexpr (PAIR) cluster_sync();
 }
 
 // ------------------------------------------------------- operand builders
@@ -1377,33 +1461,52 @@ bool shape_info(int nw, int nm, int &cpk, int &kpt, int &planar) {
   return false;
 }
 
-template <int OP, int NW, int NM, int MODE>
+template <int OP, int NW, int NM, int MODE, bool PAIR = false>
 cudaError_t launch_tc(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh, const CUtensorMap &bl,
                       const TcArgs &a, cudaStream_t st) {
+  constexpr int SMEM = tc_smem_bytes<PAIR>() + tab_bytes<NW, NM, MODE>();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_linewidth<OP, NW, NM, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES + tab_bytes<NW, NM, MODE>());
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tc_linewidth<OP, NW, NM, MODE, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int items = a.nkg * a.nqt;
-  int grid = items < sms ? items : sms;
-  k_tc_linewidth<OP, NW, NM, MODE><<<grid, nthreads<MODE>(), SMEM_BYTES + tab_bytes<NW, NM, MODE>(), st>>>(ah, al, bh,
-                                                                                                   bl, a);
+  if constexpr (PAIR) {
+    // clusters of two CTAs, each cluster two q tiles of one k group per item
+    const int items = a.nkg * ((a.nqt + 1) / 2);
+    const int grid = 2 * (items < sms / 2 ? items : sms / 2);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(nthreads<MODE>(), 1, 1);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_linewidth<OP, NW, NM, MODE, true>, ah, al, bh, bl, a);
+    if (e != cudaSuccess) return e;
+  } else {
+    int items = a.nkg * a.nqt;
+    int grid = items < sms ? items : sms;
+    k_tc_linewidth<OP, NW, NM, MODE, false><<<grid, nthreads<MODE>(), SMEM, st>>>(ah, al, bh, bl, a);
+  }
   return cudaGetLastError();
 }
 
-template <int OP, int MODE>
+template <int OP, int MODE, bool PAIR = false>
 cudaError_t launch_tc_shape(int nw, int nm, const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &bh,
                             const CUtensorMap &bl, const TcArgs &a, cudaStream_t st) {
-  if (nw == 4 && nm == 3) return launch_tc<OP, 4, 3, MODE>(ah, al, bh, bl, a, st);
-  if (nw == 1 && nm == 3) return launch_tc<OP, 1, 3, MODE>(ah, al, bh, bl, a, st);
-  if (nw == 2 && nm == 3) return launch_tc<OP, 2, 3, MODE>(ah, al, bh, bl, a, st);
+  if (nw == 4 && nm == 3) return launch_tc<OP, 4, 3, MODE, PAIR>(ah, al, bh, bl, a, st);
+  if (nw == 1 && nm == 3) return launch_tc<OP, 1, 3, MODE, PAIR>(ah, al, bh, bl, a, st);
+  if (nw == 2 && nm == 3) return launch_tc<OP, 2, 3, MODE, PAIR>(ah, al, bh, bl, a, st);
   return cudaErrorInvalidValue;
 }
 
@@ -1548,11 +1651,15 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
     epw_count_launch();
     if (b.Cpol) launch_cast_c64_to_c32((size_t)nk * m->nw * m->nw, b.Uk64, (cx<float> *)b.UkF, st);
   }
+  // the linewidth form runs on CTA pairs unless EPW_NARROW_FORM=single (each CTA of a pair
+  // loads half of the B rows)
+  const char *nf = getenv("EPW_NARROW_FORM");
+  const bool pair = mode == 0 && !(nf && strcmp(nf, "single") == 0);
   CUtensorMap ah, al, bh, bl;
   std::memset(&ah, 0, sizeof(ah));
   if (!make_map(&ah, b.Ahi, op, b.kpad, nq, BM) || !make_map(&al, b.Alo, op, b.kpad, nq, BM) ||
-      !make_map(&bh, b.Bhi, op, b.kpad, (uint64_t)b.nk_pad * b.cpk, BN) ||
-      !make_map(&bl, b.Blo, op, b.kpad, (uint64_t)b.nk_pad * b.cpk, BN))
+      !make_map(&bh, b.Bhi, op, b.kpad, (uint64_t)b.nk_pad * b.cpk, pair ? BN / 2 : BN) ||
+      !make_map(&bl, b.Blo, op, b.kpad, (uint64_t)b.nk_pad * b.cpk, pair ? BN / 2 : BN))
     return EPW_ERR_CUDA;
   TcArgs a;
   a.nk = nk;
@@ -1588,8 +1695,12 @@ static epw_status tc_run(int mode, const epw_model *m, int nk, int nq, const dou
   cudaError_t e;
   if (mode == 0) {
     epw_timing_begin(const_cast<epw_model *>(m), st);
-    e = op == TC_OP_BF16 ? launch_tc_shape<TC_OP_BF16, 0>(m->nw, m->nm, ah, al, bh, bl, a, st)
-                         : launch_tc_shape<TC_OP_TF32, 0>(m->nw, m->nm, ah, al, bh, bl, a, st);
+    if (pair)
+      e = op == TC_OP_BF16 ? launch_tc_shape<TC_OP_BF16, 0, true>(m->nw, m->nm, ah, al, bh, bl, a, st)
+                           : launch_tc_shape<TC_OP_TF32, 0, true>(m->nw, m->nm, ah, al, bh, bl, a, st);
+    else
+      e = op == TC_OP_BF16 ? launch_tc_shape<TC_OP_BF16, 0>(m->nw, m->nm, ah, al, bh, bl, a, st)
+                           : launch_tc_shape<TC_OP_TF32, 0>(m->nw, m->nm, ah, al, bh, bl, a, st);
     epw_timing_end(const_cast<epw_model *>(m), st);
   } else {
     e = op == TC_OP_BF16 ? launch_tc_shape<TC_OP_BF16, 1>(m->nw, m->nm, ah, al, bh, bl, a, st)

@@ -250,3 +250,34 @@ def test_tc_phonons_wide_r_set(epw, oracle_lib, prec):
     print(prec, "wide R set: w^2 max abs err", w2err, "eps_k+q max abs err", np.abs(ekq - rkq).max())
     assert w2err < 1e-14
     assert np.abs(ekq - rkq).max() < (2e-4 if prec == "bf16x3" else 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("lattice,nw,nR,nk,nq", [("fcc", 4, 60, 37, 700), ("fcc", 4, 60, 5, 300),
+                                                 ("fcc", 2, 40, 9, 129), ("sc", 1, 27, 3, 1000)])
+def test_tc_pair_and_single_forms_agree(epw, lattice, nw, nR, nk, nq, prec):
+    """The fused kernel's linewidth on CTA pairs (default: 2-SM MMAs over 256 q rows, each CTA
+    holding half of the B rows) and on single CTAs (EPW_NARROW_FORM=single) run the same
+    arithmetic: identical sums, including ragged q lists whose last pair has a tile past the
+    list (300 q: three tiles; 129 q: two, the second with one row)."""
+    import os
+    rng = np.random.default_rng(1700 + nw + nq)
+    if lattice == "sc":
+        wm = W.make_model("sc", nw, 1, [1.0], None, None, rng, box=1)
+    else:
+        wm = W.make_model(lattice, nw, 1, [1.0], nR, nR, rng)
+    k = rng.random((nk, 3))
+    q = rng.random((nq, 3))
+    m = epw.Model(wm)
+    kw = dict(T=300.0, EF=0.1, sigma=0.05, precision=epw.PRECISIONS[prec])
+    pair = m.linewidth(k, q, **kw)
+    os.environ["EPW_NARROW_FORM"] = "single"
+    try:
+        single = m.linewidth(k, q, **kw)
+    finally:
+        del os.environ["EPW_NARROW_FORM"]
+    m.sync()
+    err = _rel(pair, single)
+    print(lattice, nw, nk, nq, prec, "pair vs single max rel diff", err)
+    assert err < 1e-6
+    assert np.all(pair >= 0)
