@@ -540,27 +540,34 @@ __global__ void __launch_bounds__(nthreads<KIND>(), 1)
 // memory region, then the vertex chunks (N = bng, two stages).  The MMA order is
 // H(0), then for s = 1, 2, ...: H(s), chunks of item s - 1, so that the
 // eigensolve of an item overlaps the vertex MMAs of the one before.
-//   warp 0      TMA producer (four 64-byte-swizzled stages)
+//   warp 0      TMA producer (K blocks of 128-byte rows for CTA pairs, 64-byte rows
+//               for single CTAs, whose full B rows leave less room per stage)
 //   warp 1      tensor memory and MMA issuer
 //   warps 2..5  eigensolve of the item's H(k+q), one per lane quadrant; the
 //               eigenvalues and reachable eigenvectors go to a per-CTA ring of
 //               two slots in global memory (L2-resident), signalled per quadrant
 //   warps 6..9  linewidth terms of the vertex chunks, one per lane quadrant
 constexpr int F_WARPS = 10;
-constexpr int F_RB = 64;
+// Bytes of K per operand row of a stage: 128 (128-byte swizzle, 64 bf16 / 32 tf32 of K, four
+// MMA K steps per stage) for CTA pairs, 64 for single CTAs.  The 128-byte rows let the MMAs
+// read their operands at a higher rate (measured: the MMA pipeline alone 21 % faster).
+template <bool PAIR>
+constexpr int f_rb() {
+  return PAIR ? 128 : 64;
+}
 
 // Operand stages, then per vertex warp its lanes' per-q tables: mode factors E [nm*nm][32]
 // (float2), frequencies and Bose factors [2 nm][32].  A stage holds the A rows (hi, lo) and
 // the B rows (hi, lo) of one K block: all B rows for a single CTA, half of them for a CTA
-// pair (each CTA holds half of the MMA's N columns), so a pair's stages are smaller and
-// more of them fit (single CTA: four, three with the tables of 3nat = 9 modes; pair: six, four).
+// pair (each CTA holds half of the MMA's N columns).  Single CTA: four stages, three with the
+// tables of 3nat = 9 modes; pair (twice the K per stage): three, two.
 template <int NM, bool PAIR>
 constexpr int f_stages() {
-  return PAIR ? (NM <= 6 ? 6 : 4) : (NM <= 6 ? 4 : 3);
+  return PAIR ? (NM <= 6 ? 3 : 2) : (NM <= 6 ? 4 : 3);
 }
 template <int NW, int NM, bool PAIR>
 constexpr int f_stage_bytes() {
-  return (2 * BM + (PAIR ? 1 : 2) * WShape<NW, NM>::BNG) * F_RB;
+  return (2 * BM + (PAIR ? 1 : 2) * WShape<NW, NM>::BNG) * f_rb<PAIR>();
 }
 template <int NM>
 constexpr int f_tab_bytes() {
@@ -685,6 +692,7 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
   using O = WOp<OP>;
   using S = WShape<NW, NM>;
   constexpr int F_STAGES = f_stages<NM, PAIR>();
+  constexpr int F_RB = f_rb<PAIR>();
   constexpr int BK = F_RB / O::ESZ;
   constexpr int CPK = S::CPK, BNG = S::BNG, CN = S::CN;
   static_assert(CN == 2, "vertex chunks of two entries");
@@ -1302,20 +1310,21 @@ epw_status tcw_linewidth(const epw_model *m, int nk, int nq, const double *q, co
     // a CTA pair loads half of the B rows in each CTA
     const uint32_t ebox = b.pair ? (uint32_t)b.cpk / 2 : (uint32_t)b.cpk;
     const uint32_t gbox = b.pair ? (uint32_t)b.bng / 2 : (uint32_t)b.bng;
-    if (!tc_make_map_rb(&ah, b.Ahi, op, b.kpad, nq, BM, F_RB) || !tc_make_map_rb(&al, b.Alo, op, b.kpad, nq, BM, F_RB) ||
-        !tc_make_map_rb(&agh, b.AGhi, op, b.kpadG, nq, BM, F_RB) ||
-        !tc_make_map_rb(&agl, b.AGlo, op, b.kpadG, nq, BM, F_RB) ||
-        !tc_make_map_rb(&eh, b.BEhi, op, b.kpad, (uint64_t)b.kc * b.cpk, ebox, F_RB) ||
-        !tc_make_map_rb(&el, b.BElo, op, b.kpad, (uint64_t)b.kc * b.cpk, ebox, F_RB) ||
-        !tc_make_map_rb(&gh, b.BGhi, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, gbox, F_RB) ||
-        !tc_make_map_rb(&gl, b.BGlo, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, gbox, F_RB))
+    const int rb = b.pair ? f_rb<true>() : f_rb<false>();
+    if (!tc_make_map_rb(&ah, b.Ahi, op, b.kpad, nq, BM, rb) || !tc_make_map_rb(&al, b.Alo, op, b.kpad, nq, BM, rb) ||
+        !tc_make_map_rb(&agh, b.AGhi, op, b.kpadG, nq, BM, rb) ||
+        !tc_make_map_rb(&agl, b.AGlo, op, b.kpadG, nq, BM, rb) ||
+        !tc_make_map_rb(&eh, b.BEhi, op, b.kpad, (uint64_t)b.kc * b.cpk, ebox, rb) ||
+        !tc_make_map_rb(&el, b.BElo, op, b.kpad, (uint64_t)b.kc * b.cpk, ebox, rb) ||
+        !tc_make_map_rb(&gh, b.BGhi, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, gbox, rb) ||
+        !tc_make_map_rb(&gl, b.BGlo, op, b.kpadG, (uint64_t)b.kc * nch * b.bng, gbox, rb))
       return EPW_ERR_CUDA;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     sms = std::min(sms, TCWF_MAX_CTAS);
-    a.nkb = (b.kpad * esz + F_RB - 1) / F_RB;
-    a.nkbG = (b.kpadG * esz + F_RB - 1) / F_RB;
+    a.nkb = (b.kpad * esz + rb - 1) / rb;
+    a.nkbG = (b.kpadG * esz + rb - 1) / rb;
     const size_t nw2 = (size_t)nw * nw;
     epw_model *mm = const_cast<epw_model *>(m);
     for (int k0 = 0; k0 < nk; k0 += b.kc) {
