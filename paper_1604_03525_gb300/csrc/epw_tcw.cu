@@ -226,18 +226,26 @@ __device__ __forceinline__ bool eig_pair(const TcwArgs &a, uint32_t tcol, int q,
 #pragma unroll
     for (int m = 0; m < NW; m++) v.eps[(size_t)m * v.ld + v.idx] = S.d[m];
   }
-  // one loop body over m (instruction cache); unreachable bands are skipped by the warp
-#pragma unroll 1
+  // the bands m that some band n at k can reach, one bit per m
+  uint32_t need = 0;
+#pragma unroll
   for (int m = 0; m < NW; m++) {
-    const float dm = pick<NW>(S.d, m);
     bool rel = false;
 #pragma unroll
-    for (int n = 0; n < NW; n++) rel = rel || reachable(ek[n], dm, thr);
-    rel = rel && valid;
-    if (!__any_sync(0xffffffffu, rel)) continue;
+    for (int n = 0; n < NW; n++) rel = rel || reachable(ek[n], S.d[m], thr);
+    if (rel && valid) need |= 1u << m;
+  }
+  // each lane forms its own reachable eigenvectors, lowest m first: the warp runs as many
+  // rounds as its busiest lane needs (not the union of the lanes' bands); one loop body
+  // for the instruction cache, m a per-lane index (hh_vector picks by weights)
+#pragma unroll 1
+  while (__any_sync(0xffffffffu, need != 0)) {
+    const bool act = need != 0;
+    const int m = act ? __ffs(need) - 1 : 0;
+    need &= need - 1;
     cx<float> u[NW];
     hh_vector<NW>(S, m, u);
-    if (rel) {
+    if (act) {
       float2 *dst = v.U + (size_t)m * NW * v.ld + v.idx;
 #pragma unroll
       for (int i = 0; i < NW; i++) dst[(size_t)i * v.ld] = make_float2(u[i].x, u[i].y);
@@ -591,9 +599,12 @@ __device__ __forceinline__ void f_coords(const TcwArgs &a, int item, uint32_t ra
 }
 
 // Linewidth terms of the entries (k, n0) and (k, n0 + 1) of one vertex chunk for the
-// warp's 32 pairs: the bands m reachable for either entry (bit m of rel0, rel1) are
-// visited once, their eigenvector loaded once for both entries.  em, ek: eigenvalues
-// at k+q and band energies at k (registers), tabE / tabW: the lanes' per-q tables.
+// warp's 32 pairs (bit m of rel0, rel1: band m reachable for that entry).  Per entry
+// (warp-uniform: the entry's tensor-memory columns are one address for the warp) each
+// lane walks its own reachable bands, lowest m first, so the warp runs as many rounds
+// as its busiest lane needs; each term adds to the entry's sum in ascending m.  em, ek:
+// eigenvalues at k+q and band energies at k (registers), tabE / tabW: the lanes' per-q
+// tables.
 template <int NW, int NM>
 __device__ __forceinline__ void g_chunk(const TcwArgs &a, uint32_t tcol, int n0, int qq, int kg, const EigView &v,
                                         const float (&em)[NW], const float (&ek)[NW], uint32_t rel0, uint32_t rel1,
@@ -602,28 +613,27 @@ __device__ __forceinline__ void g_chunk(const TcwArgs &a, uint32_t tcol, int n0,
   constexpr int LD = (ENT + 31) / 32 * 32;
   constexpr int ENTP = WShape<NW, NM>::ENTP;
   const int lane = threadIdx.x & 31;
-  const float ek0 = pick<NW>(ek, n0), ek1 = pick<NW>(ek, n0 + 1 < NW ? n0 + 1 : n0);
   acc0 = acc1 = 0.0f;
 #pragma unroll 1
-  for (int m = 0; m < NW; m++) {
-    const bool r0 = (rel0 >> m) & 1u, r1 = (rel1 >> m) & 1u;
-    if (!__any_sync(0xffffffffu, r0 || r1)) continue;
-    cx<float> u[NW];
-    {
-      const float2 *src = v.U + (size_t)m * NW * v.ld + v.idx;
-#pragma unroll
-      for (int i = 0; i < NW; i++) {
-        const float2 w = (r0 || r1) ? src[(size_t)i * v.ld] : make_float2(0.0f, 0.0f);
-        u[i] = mkc(w.x, w.y);
-      }
-    }
-    const float emm = pick<NW>(em, m);
-    const float fm = fermi_fast(emm - a.EF, a.invkT);
-    const float ems = emm * a.sc;
+  for (int e = 0; e < 2; e++) {
+    uint32_t need = e == 0 ? rel0 : rel1;
+    const int n = n0 + e;
+    const float eks = pick<NW>(ek, n < NW ? n : n0) * a.sc;
+    float acc = 0.0f;
 #pragma unroll 1
-    for (int e = 0; e < 2; e++) {
-      const bool r = e == 0 ? r0 : r1;
-      if (!__any_sync(0xffffffffu, r)) continue;
+    while (__any_sync(0xffffffffu, need != 0)) {
+      const bool act = need != 0;
+      const int m = act ? __ffs(need) - 1 : 0;
+      need &= need - 1;
+      cx<float> u[NW];
+      {
+        const float2 *src = v.U + (size_t)m * NW * v.ld + v.idx;
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+          const float2 w = act ? src[(size_t)i * v.ld] : make_float2(0.0f, 0.0f);
+          u[i] = mkc(w.x, w.y);
+        }
+      }
       // t_a = u_m^dagger (g_a U_k)_{:, n}: the entry's columns stream from tensor memory
       cx<float> t[NM];
 #pragma unroll
@@ -642,8 +652,10 @@ __device__ __forceinline__ void g_chunk(const TcwArgs &a, uint32_t tcol, int n0,
           }
         }
       }
-      if (!r) continue;
-      const int n = n0 + e;
+      if (!act) continue;
+      const float emm = pick<NW>(em, m);
+      const float fm = fermi_fast(emm - a.EF, a.invkT);
+      const float ems = emm * a.sc;
       cx<float> tp = mkc(0.0f, 0.0f);
       if (a.Cpol) {
         const float2 *Uk = a.UkF + (size_t)kg * NW * NW;
@@ -653,8 +665,7 @@ __device__ __forceinline__ void g_chunk(const TcwArgs &a, uint32_t tcol, int n0,
           tp = mkc(fmaf(u[j].x, w.x, fmaf(u[j].y, w.y, tp.x)), fmaf(u[j].x, w.y, fmaf(-u[j].y, w.x, tp.y)));
         }
       }
-      const float eks = (e == 0 ? ek0 : ek1) * a.sc;
-      float acc = 0.0f;
+      float accm = 0.0f;
 #pragma unroll
       for (int nu = 0; nu < NM; nu++) {
         cx<float> g = mkc(0.0f, 0.0f);
@@ -673,13 +684,14 @@ __device__ __forceinline__ void g_chunk(const TcwArgs &a, uint32_t tcol, int n0,
         const float xp = eks - ems + ws, xm = eks - ems - ws;
         const float cp = keep ? nb + fm : 0.0f, cm = keep ? nb + 1.0f - fm : 0.0f;
         const float d = cp * ex2_approx(-xp * xp) + cm * ex2_approx(-xm * xm);
-        acc = fmaf(fmaf(g.x, g.x, g.y * g.y), d, acc);
+        accm = fmaf(fmaf(g.x, g.x, g.y * g.y), d, accm);
       }
-      if (e == 0)
-        acc0 += acc;
-      else
-        acc1 += acc;
+      acc += accm;
     }
+    if (e == 0)
+      acc0 = acc;
+    else
+      acc1 = acc;
   }
 }
 
