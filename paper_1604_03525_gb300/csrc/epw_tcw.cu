@@ -714,7 +714,11 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
   constexpr int BROWS = PAIR ? BNG / 2 : BNG;  // B rows of a stage held by this CTA
   constexpr uint32_t ID_H = PAIR ? w_idesc_pair<OP, CPK>() : w_idesc<OP, CPK>();
   constexpr uint32_t ID_G = PAIR ? w_idesc_pair<OP, BNG>() : w_idesc<OP, BNG>();
-  static_assert(!PAIR || (CPK % 32 == 0 && BNG % 32 == 0), "a pair's MMA splits N in halves of 16-column multiples");
+  // odd nw: the last chunk holds one entry, so its MMAs take N = ENTP (no all-zero entry)
+  constexpr bool ODD = NW % CN != 0;
+  constexpr uint32_t ID_G1 = PAIR ? w_idesc_pair<OP, S::ENTP>() : w_idesc<OP, S::ENTP>();
+  static_assert(!PAIR || (CPK % 32 == 0 && BNG % 32 == 0 && S::ENTP % 32 == 0),
+                "a pair's MMA splits N in halves of 16-column multiples");
   constexpr uint32_t GCOL0 = CPK;  // tensor-memory columns: H [0, cpk), vertex stages cpk + s bng
   static_assert(CPK + 2 * BNG <= 512, "tensor memory");
   __shared__ __align__(8) uint64_t bar_full[F_STAGES], bar_empty[F_STAGES], bar_hfull, bar_hempty, bar_gfull[2],
@@ -779,9 +783,10 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
     for (int s = 0; s < F_STAGES; s++) issued[s] = 0;
     uint32_t it = 0;
     bool ok = true;
-    // one group: the A rows of q tile qt (ah, al) and brows B rows from row0, nkb K blocks
+    // one group: the A rows of q tile qt (ah, al) and the B boxes (brows rows for the pair,
+    // hi and lo) from row0, nkb K blocks; rank r of a pair loads its box from row0 + r hoff
     auto load_group = [&](int qt, const CUtensorMap *ah, const CUtensorMap *al, const CUtensorMap *bh,
-                          const CUtensorMap *bl, int row0, uint32_t brows, int nkb) {
+                          const CUtensorMap *bl, int row0, uint32_t brows, int hoff, int nkb) {
       for (int kb = 0; kb < nkb && ok; kb++, it++) {
         const int s = it % F_STAGES;
         const uint32_t par = ((it / F_STAGES) & 1u) ^ 1u;
@@ -794,7 +799,7 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
               // the bytes of both CTAs
               const uint32_t fb = full_c0 + 8u * (uint32_t)s;
               if (leader) mbar_expect_tx(smem_u32(&bar_full[s]), 2 * (2 * A_BYTES + brows * F_RB));
-              const int hrow = row0 + (int)rank * (int)(brows / 2);
+              const int hrow = row0 + (int)rank * hoff;
               tma_load_2d_pair(base, ah, kb * BK, qt * BM, fb);
               tma_load_2d_pair(base + A_BYTES, al, kb * BK, qt * BM, fb);
               tma_load_2d_pair(base + 2 * A_BYTES, bh, kb * BK, hrow, fb);
@@ -817,13 +822,14 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
       if (st < nmy) {
         int kl, qt;
         f_coords<PAIR>(a, cid + st * ncl, rank, kl, qt);
-        load_group(qt, &mAhi, &mAlo, &mEhi, &mElo, kl * CPK, CPK, a.nkb);
+        load_group(qt, &mAhi, &mAlo, &mEhi, &mElo, kl * CPK, CPK, CPK / 2, a.nkb);
       }
       if (st >= 1) {
         int kl, qt;
         f_coords<PAIR>(a, cid + (st - 1) * ncl, rank, kl, qt);
         for (int c = 0; c < NCH && ok; c++)
-          load_group(qt, &mAGhi, &mAGlo, &mGhi, &mGlo, (kl * NCH + c) * BNG, BNG, a.nkbG);
+          load_group(qt, &mAGhi, &mAGlo, &mGhi, &mGlo, (kl * NCH + c) * BNG, BNG,
+                     (ODD && c == NCH - 1 ? S::ENTP : BNG) / 2, a.nkbG);
       }
     }
     if (lane == 0 && leader) {  // (a pair's loads complete on the leader's barriers)
@@ -899,7 +905,7 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
           ok = __shfl_sync(0xffffffffu, ok, 0);
           if (!ok) break;
           tc_fence_after();
-          mma_group(tmem + GCOL0 + gs * BNG, ID_G, a.nkbG, a.kpadG);
+          mma_group(tmem + GCOL0 + gs * BNG, ODD && c == NCH - 1 ? ID_G1 : ID_G, a.nkbG, a.kpadG);
           if (!ok) break;
           if (lane == 0) commit(smem_u32(&bar_gfull[gs]));
           __syncwarp();
