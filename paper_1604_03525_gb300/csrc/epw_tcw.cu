@@ -564,26 +564,36 @@ constexpr int f_rb() {
   return PAIR ? 128 : 64;
 }
 
-// Operand stages, then per vertex warp its lanes' per-q tables: mode factors E [nm*nm][32]
-// (float2), frequencies and Bose factors [2 nm][32].  A stage holds the A rows (hi, lo) and
-// the B rows (hi, lo) of one K block: all B rows for a single CTA, half of them for a CTA
-// pair (each CTA holds half of the MMA's N columns).  Single CTA: four stages, three with the
-// tables of 3nat = 9 modes; pair (twice the K per stage): three, two.
+// Operand stages, then per vertex warp its lanes' per-q tables: frequencies and Bose factors
+// [2 nm][32], and the first F_EROWS rows a of the mode factors E [a][nu][32] (float2); the
+// other rows are read from global memory (L1).  A stage holds the A rows (hi, lo) and the B
+// rows (hi, lo) of one K block: all B rows for a single CTA, half of them for a CTA pair (each
+// CTA holds half of the MMA's N columns).  Single CTA: four stages (three for 3nat = 9
+// modes); pair (twice the K per stage): three.  The operand pipeline wants the third stage more
+// than the tables want shared memory (measured, hexagonal nw = 5 with 9 modes: two stages and
+// every table in shared memory 112 ms, three stages and E through L1 102 ms).
 template <int NM, bool PAIR>
 constexpr int f_stages() {
-  return PAIR ? (NM <= 6 ? 3 : 2) : (NM <= 6 ? 4 : 3);
+  return PAIR ? 3 : (NM <= 6 ? 4 : 3);
 }
 template <int NW, int NM, bool PAIR>
 constexpr int f_stage_bytes() {
   return (2 * BM + (PAIR ? 1 : 2) * WShape<NW, NM>::BNG) * f_rb<PAIR>();
 }
-template <int NM>
+constexpr int F_SMEM_MAX = 232448 - 512;  // dynamic shared memory per CTA, less the static barriers
+template <int NW, int NM, bool PAIR>
+constexpr int f_erows() {
+  constexpr int per_warp = (F_SMEM_MAX - 1024 - f_stages<NM, PAIR>() * f_stage_bytes<NW, NM, PAIR>()) / 4;
+  constexpr int rows = (per_warp - 32 * 4 * 2 * NM) / (32 * 8 * NM);
+  return rows < NM ? rows : NM;
+}
+template <int NW, int NM, bool PAIR>
 constexpr int f_tab_bytes() {
-  return 32 * (8 * NM * NM + 4 * 2 * NM);  // per vertex warp
+  return 32 * (4 * 2 * NM + 8 * NM * f_erows<NW, NM, PAIR>());  // per vertex warp
 }
 template <int NW, int NM, bool PAIR>
 constexpr int f_smem() {
-  return f_stages<NM, PAIR>() * f_stage_bytes<NW, NM, PAIR>() + 4 * f_tab_bytes<NM>() + 1024;
+  return f_stages<NM, PAIR>() * f_stage_bytes<NW, NM, PAIR>() + 4 * f_tab_bytes<NW, NM, PAIR>() + 1024;
 }
 // Item -> (k, q tile): one q tile per item for a single CTA; a pair takes two neighbouring
 // q tiles per item, rank r the tile 2 u + r (the second may lie past nq: its rows are invalid).
@@ -604,8 +614,8 @@ __device__ __forceinline__ void f_coords(const TcwArgs &a, int item, uint32_t ra
 // lane walks its own reachable bands, lowest m first, so the warp runs as many rounds
 // as its busiest lane needs; each term adds to the entry's sum in ascending m.  em, ek:
 // eigenvalues at k+q and band energies at k (registers), tabE / tabW: the lanes' per-q
-// tables.
-template <int NW, int NM>
+// tables (rows a < EROWS of E; the others from global memory).
+template <int NW, int NM, int EROWS>
 __device__ __forceinline__ void g_chunk(const TcwArgs &a, uint32_t tcol, int n0, int qq, int kg, const EigView &v,
                                         const float (&em)[NW], const float (&ek)[NW], uint32_t rel0, uint32_t rel1,
                                         const float2 *tabE, const float *tabW, float &acc0, float &acc1) {
@@ -671,7 +681,7 @@ __device__ __forceinline__ void g_chunk(const TcwArgs &a, uint32_t tcol, int n0,
         cx<float> g = mkc(0.0f, 0.0f);
 #pragma unroll
         for (int al = 0; al < NM; al++) {
-          const float2 ee = tabE[(al * NM + nu) * 32 + lane];
+          const float2 ee = al < EROWS ? tabE[(al * NM + nu) * 32 + lane] : __ldg(a.ET + (size_t)(al * NM + nu) * a.nq + qq);
           g = mkc(fmaf(ee.x, t[al].x, fmaf(-ee.y, t[al].y, g.x)), fmaf(ee.x, t[al].y, fmaf(ee.y, t[al].x, g.y)));
         }
         if (a.Cpol) {
@@ -721,6 +731,7 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
                 "a pair's MMA splits N in halves of 16-column multiples");
   constexpr uint32_t GCOL0 = CPK;  // tensor-memory columns: H [0, cpk), vertex stages cpk + s bng
   static_assert(CPK + 2 * BNG <= 512, "tensor memory");
+  static_assert(f_smem<NW, NM, PAIR>() <= F_SMEM_MAX && f_erows<NW, NM, PAIR>() >= 0, "shared memory");
   __shared__ __align__(8) uint64_t bar_full[F_STAGES], bar_empty[F_STAGES], bar_hfull, bar_hempty, bar_gfull[2],
       bar_gempty[2], bar_efull[2][4], bar_eempty[2][4], bar_final;
   __shared__ uint32_t tmem_base_sh;
@@ -944,10 +955,11 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
     const int quad = warp & 3;
     const int idx = quad * 32 + lane;
     // this warp's per-q tables in shared memory (after the operand stages)
-    uint8_t *tab = smem_raw + (smem0 - smem_u32(smem_raw)) + F_STAGES * STAGE + (warp - 6) * f_tab_bytes<NM>();
+    constexpr int EROWS = f_erows<NW, NM, PAIR>();
+    uint8_t *tab = smem_raw + (smem0 - smem_u32(smem_raw)) + F_STAGES * STAGE + (warp - 6) * f_tab_bytes<NW, NM, PAIR>();
     const float2 *tabE = reinterpret_cast<const float2 *>(tab);
-    const float *tabW = reinterpret_cast<const float *>(tab + 32 * 8 * NM * NM);
-    const uint32_t tabE_s = smem_u32(tab), tabW_s = tabE_s + 32 * 8 * NM * NM;
+    const float *tabW = reinterpret_cast<const float *>(tab + 32 * 8 * NM * EROWS);
+    const uint32_t tabE_s = smem_u32(tab), tabW_s = tabE_s + 32 * 8 * NM * EROWS;
     int gcount = 0;
     bool ok = true;
     for (int j = 0; j < nmy && ok; j++) {
@@ -958,10 +970,10 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
       const bool valid = q < a.nq && kval;
       const int qq = valid ? q : 0;
       const int kg = kval ? a.k0 + kl : 0;
-      // per-q tables of the item's rows: E [nm*nm] complex, w [nm], n [nm]
+      // per-q tables of the item's rows: E [EROWS][nm] complex, w [nm], n [nm]
       __syncwarp();
 #pragma unroll 1
-      for (int e = 0; e < NM * NM; e++) cp_async8(tabE_s + 8u * (e * 32 + lane), a.ET + (size_t)e * a.nq + qq);
+      for (int e = 0; e < EROWS * NM; e++) cp_async8(tabE_s + 8u * (e * 32 + lane), a.ET + (size_t)e * a.nq + qq);
 #pragma unroll 1
       for (int nu = 0; nu < NM; nu++) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tabW_s + 4u * (nu * 32 + lane)),
@@ -1016,7 +1028,7 @@ __global__ void __launch_bounds__(32 * F_WARPS, 1)
           r1 |= rel[n] & (0u - (uint32_t)(n == n0 + 1));
         }
         float acc0, acc1;
-        g_chunk<NW, NM>(a, tcol, n0, qq, kg, v, em, ek, r0, r1, tabE, tabW, acc0, acc1);
+        g_chunk<NW, NM, EROWS>(a, tcol, n0, qq, kg, v, em, ek, r0, r1, tabE, tabW, acc0, acc1);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
