@@ -173,10 +173,14 @@ epw_status epw_interp_g(const epw_model *model, int nk, const double *k, int nq,
  * evaluated, which leaves the sums unchanged), whose fused kernel runs on CTA
  * pairs (2-SM MMAs over 256 q rows; the environment variable EPW_WIDE_FORM=single
  * selects the single-CTA kernel, EPW_WIDE_FORM=split a two-kernel variant);
- * other shapes take the staged form.  When the buffers that grow with nk (bands
- * and vertex at k, operands, partial sums) would exceed EPW_K_SIDE_BYTES
- * (environment; 8 GiB by default), the k list runs in equal passes, each with
- * the whole q list (results do not depend on the pass count). */
+ * other shapes take the staged form (the contraction per chunk of k on the
+ * tensor cores, then one warp per pair; for nw > 8 or 3nat > 9 that warp
+ * evaluates only the terms within the same cutoff, EPW_STAGED_PAIR=dense every
+ * term).  When the buffers that grow with nk (bands and vertex at k, operands,
+ * partial sums; a staged contraction chunk counts once, at its capped size)
+ * would exceed EPW_K_SIDE_BYTES (environment; 8 GiB by default), the k list
+ * runs in equal passes, each with the whole q list (results do not depend on
+ * the pass count). */
 epw_status epw_linewidth(const epw_model *model, int nk, const double *k, int nq, const double *q,
                          const double *wq, const epw_params *params, double *imsigma, void *stream);
 

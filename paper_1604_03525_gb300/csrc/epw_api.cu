@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -594,18 +595,34 @@ static epw_status plan_linewidth_pass(Arena &A, const epw_model *m, int nk, int 
 
 // k per pass: the k list runs in equal passes when the buffers that grow with nk (k-side
 // bands and vertex g(k,Rp) U_k, partial sums, operands and contraction chunks) would exceed
-// tune.k_side_bytes.  The growth per k is measured from the plans of one and two k.
+// tune.k_side_bytes: the longest pass whose plan exceeds the plan of one k by at most that
+// budget (a binary search over the plans; a staged contraction chunk is capped by its own
+// budget, so it stops growing at one chunk and each pass repeats the q-side preparation only
+// when the k-side buffers really do not fit).
 static int k_per_pass(const epw_model *m, int nk, int nq, int prec, const EpwTune &tune) {
   if (tune.k_side_bytes == 0 || nk <= 1) return nk;
-  Arena a1{nullptr, 0, 0}, a2{nullptr, 0, 0};
-  LwPlan t;
-  if (plan_linewidth_pass(a1, m, 1, nq, prec, false, false, tune, t) != EPW_OK ||
-      plan_linewidth_pass(a2, m, 2, nq, prec, false, false, tune, t) != EPW_OK)
-    return nk;
-  const size_t per_k = a2.off > a1.off ? a2.off - a1.off : 1;
-  if (per_k * (size_t)nk <= tune.k_side_bytes) return nk;
-  const size_t npass = (per_k * (size_t)nk + tune.k_side_bytes - 1) / tune.k_side_bytes;
-  return (int)(((size_t)nk + npass - 1) / npass);
+  auto bytes = [&](int nkp) -> size_t {
+    Arena a{nullptr, 0, 0};
+    LwPlan t;
+    return plan_linewidth_pass(a, m, nkp, nq, prec, false, false, tune, t) == EPW_OK ? a.off : SIZE_MAX;
+  };
+  const size_t b1 = bytes(1);
+  if (b1 == SIZE_MAX) return nk;
+  auto fits = [&](int nkp) {
+    const size_t b = bytes(nkp);
+    return b != SIZE_MAX && b - b1 <= tune.k_side_bytes;
+  };
+  if (fits(nk)) return nk;
+  int lo = 1, hi = nk;  // fits(lo), not fits(hi)
+  while (hi - lo > 1) {
+    const int mid = lo + (hi - lo) / 2;
+    if (fits(mid))
+      lo = mid;
+    else
+      hi = mid;
+  }
+  const int npass = (nk + lo - 1) / lo;
+  return (nk + npass - 1) / npass;
 }
 
 epw_status epwi_plan_linewidth(Arena &A, const epw_model *m, int nk, int nq, int prec, bool sk, bool sq, bool swq,

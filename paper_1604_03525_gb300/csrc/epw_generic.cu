@@ -1173,7 +1173,13 @@ epw_status launch_pair_staged(const PairArgs &a, int mode, cudaStream_t st) {
   int nkl = (mode == 2) ? a.nkc : a.nk;
   if (nkl <= 0 || a.nq <= 0) return EPW_OK;
   if (!a.Cq) return EPW_ERR_UNSUPPORTED;
-  if (a.nw > 8 || a.nm > 9) return launch_pair_wide<float>(a, mode, st);
+  if (a.nw > 8 || a.nm > 9) {
+    // linewidth: only the terms within the Gaussian cutoff (EPW_STAGED_PAIR=dense: every term,
+    // cyclic Jacobi per warp)
+    const char *f = getenv("EPW_STAGED_PAIR");
+    if (mode == 0 && !(f && !strcmp(f, "dense"))) return launch_pair_sparse(a, st);
+    return launch_pair_wide<float>(a, mode, st);
+  }
   dim3 grid((a.nq + 127) / 128, nkl);
   if (mode == 0)
     k_pair<float, 8, 9, 0, true><<<grid, 128, 0, st>>>(a);

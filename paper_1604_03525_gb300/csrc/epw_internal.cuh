@@ -445,6 +445,9 @@ void launch_se_finalize(int nkc, int k0, int nw, int nqw, int nom, const double2
 // contraction in the q-major layout Cq[q*ldc + kl*cpk + 2c + s], FP32 only)
 template <typename R>
 epw_status launch_pair_wide(const PairArgs &a, int mode, cudaStream_t st);
+// linewidth (mode 0) of the staged FP32 form for nw <= 18, 3nat <= 18: one warp per pair,
+// Householder + implicit QR eigensolve, only the terms within the Gaussian cutoff
+epw_status launch_pair_sparse(const PairArgs &a, cudaStream_t st);
 void launch_finalize(int nk, int nqb, int nw, const double *partial, double *out, cudaStream_t st);
 // m->gw = wRe wRp g (g on the device)
 void launch_set_vertex(const epw_model *m, const void *g, int is_c64, cudaStream_t st);
