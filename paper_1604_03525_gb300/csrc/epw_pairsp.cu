@@ -427,6 +427,8 @@ epw_status launch_pair_sparse(const PairArgs &a, cudaStream_t st) {
     epw_count_launch();
     return cudaGetLastError() == cudaSuccess ? EPW_OK : EPW_ERR_CUDA;
   };
+  // register arrays (QR rows, eigenvectors) sized for the smallest width that holds nw
   if (a.nw <= 8) return go(k_pair_sparse<8>, SP_WARPS * sizeof(SpWarp<8>));
+  if (a.nw <= 12) return go(k_pair_sparse<12>, SP_WARPS * sizeof(SpWarp<12>));
   return go(k_pair_sparse<18>, SP_WARPS * sizeof(SpWarp<18>));
 }
