@@ -149,6 +149,22 @@ void epw_free_model(epw_model *model);
  * graph capture). */
 epw_status epw_reserve(epw_model *model, int nk, int nq, int precision);
 
+/* Planning without a model or a device: the device workspace (bytes) that
+ * epw_linewidth, or epw_reserve, takes for a model of this shape -- nw Wannier
+ * functions, nat atoms, nRe / nRp / nRph lattice vectors of H, g and the force
+ * constants, same_ep / same_eph nonzero when the Re and Rp (Re and Rph) sets are
+ * identical, polar nonzero with a long-range vertex -- on nk k-points and nq
+ * q-points (k, q and weights as host arrays) in the given precision, and the k
+ * per pass (nk when the k list runs in one pass; see EPW_K_SIDE_BYTES under
+ * epw_linewidth).  The figures follow the same plan the library lays out at
+ * run time, with the environment as it is at the call.  Either output may be
+ * NULL.  Errors: EPW_ERR_INVALID_ARG for sizes outside the limits of
+ * epw_load_wannier, unequal sizes of sets declared identical, or an unknown
+ * precision; EPW_ERR_UNSUPPORTED where epw_linewidth has no form for the shape
+ * in that precision.  Reads no device state and launches nothing. */
+epw_status epw_plan_linewidth(int nw, int nat, int nRe, int nRp, int nRph, int same_ep, int same_eph, int polar,
+                              int nk, int nq, int precision, size_t *ws_bytes, int *k_per_pass);
+
 /* Interpolated quantities on the product k x q (the unreduced path):
  *   eps_k  [nk][nw]          band energies at k (FP64)
  *   eps_kq [nk][nq][nw]      band energies at k+q

@@ -26,6 +26,7 @@ SIGNATURES = {
     "epw_free_model": (None, [P]),
     "epw_set_vertex": (I, [P, P, I, P]),
     "epw_reserve": (I, [P, I, I, I]),
+    "epw_plan_linewidth": (I, [I, I, I, I, I, I, I, I, I, I, I, P, P]),
     "epw_interp_g": (I, [P, I, P, I, P, I, D, P, P, P, P, P]),
     "epw_linewidth": (I, [P, I, P, I, P, P, P, P, P]),
     "epw_linewidth_backward": (I, [P, I, P, I, P, P, P, P, P, P, P, P]),

@@ -290,6 +290,19 @@ def launch_count() -> int:
     return int(_lib.load().epw_launch_count())
 
 
+def plan_linewidth(nw: int, nat: int, nRe: int, nRp: int, nRph: int, nk: int, nq: int, precision: int = BF16X3,
+                   same_ep: bool = False, same_eph: bool = False, polar: bool = False):
+    """(workspace bytes, k per pass) that Model.linewidth takes for a model of this shape on nk x nq
+    points with host inputs (epw_plan_linewidth): no model, no device work."""
+    lib = _lib.load()
+    ws = ctypes.c_size_t(0)
+    kp = ctypes.c_int(0)
+    _check(lib.epw_plan_linewidth(int(nw), int(nat), int(nRe), int(nRp), int(nRph), int(bool(same_ep)),
+                                  int(bool(same_eph)), int(bool(polar)), int(nk), int(nq), int(precision),
+                                  ctypes.byref(ws), ctypes.byref(kp)))
+    return int(ws.value), int(kp.value)
+
+
 def eliashberg(omega, lam, grid, sigma_ph: float, wq=None):
     """alpha^2 F on `grid` (Eq. isotropiceliash) from w_qnu and lambda_qnu [nq, 3nat] (epw_eliashberg)."""
     lib = _lib.load()

@@ -649,6 +649,42 @@ extern "C" epw_status epw_reserve(epw_model *m, int nk, int nq, int precision) {
   return ensure_ws(m, A.off);
 }
 
+// Planning by shape alone: the same plan as epw_reserve on a host-side model that holds the
+// shape and no device state (the planners only compute offsets).
+extern "C" epw_status epw_plan_linewidth(int nw, int nat, int nRe, int nRp, int nRph, int same_ep, int same_eph,
+                                         int polar, int nk, int nq, int precision, size_t *ws_bytes,
+                                         int *k_per_pass) {
+  g_err[0] = 0;
+  if (nw < 1 || nw > EPW_MAX_NW) return fail(EPW_ERR_INVALID_ARG, "nw=%d outside [1,%d]", nw, EPW_MAX_NW);
+  if (nat < 1 || 3 * nat > EPW_MAX_MODES) return fail(EPW_ERR_INVALID_ARG, "3*nat=%d outside [3,%d]", 3 * nat, EPW_MAX_MODES);
+  if (nRe < 1 || nRp < 1 || nRph < 1) return fail(EPW_ERR_INVALID_ARG, "empty R set");
+  if ((same_ep && nRe != nRp) || (same_eph && nRe != nRph))
+    return fail(EPW_ERR_INVALID_ARG, "identical R sets need equal sizes");
+  if (nk < 1 || nq < 1) return fail(EPW_ERR_INVALID_ARG, "nk and nq must be positive");
+  if ((size_t)nk * (size_t)nq > (size_t)1 << 44) return fail(EPW_ERR_INVALID_ARG, "nk*nq too large");
+  if (precision < EPW_FP64 || precision > EPW_TF32X3) return fail(EPW_ERR_INVALID_ARG, "unknown precision");
+  epw_model m{};
+  m.device = -1;
+  m.nw = nw;
+  m.nat = nat;
+  m.nm = 3 * nat;
+  m.nRe = nRe;
+  m.nRp = nRp;
+  m.nRph = nRph;
+  m.same_ep = same_ep ? 1 : 0;
+  m.same_eph = same_eph ? 1 : 0;
+  m.polar = polar ? 1 : 0;
+  Arena A{nullptr, 0, 0};
+  LwPlan L;
+  CKS(plan_linewidth(A, &m, nk, nq, precision, true, true, true, true, L));
+  const bool tcp = precision == EPW_BF16X3 || precision == EPW_TF32X3;
+  if (tcp && !L.tc.ok && !L.sg.ok && !L.w.ok)
+    return fail(EPW_ERR_UNSUPPORTED, "no tensor-core form for nw=%d, 3nat=%d", nw, 3 * nat);
+  if (ws_bytes) *ws_bytes = A.off;
+  if (k_per_pass) *k_per_pass = L.kchunk;
+  return EPW_OK;
+}
+
 extern "C" epw_status epw_linewidth(const epw_model *mc, int nk, const double *k, int nq, const double *q,
                                     const double *wq, const epw_params *par, double *imsigma, void *stream) {
   g_err[0] = 0;
